@@ -1,0 +1,290 @@
+"""Benchmark of the GB300 VEGAS+ iteration loop.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Workload: plain VEGAS+ on the d = 8 unit cube.  The integrand is a sum of 5
+isotropic Gaussians (sigma 0.05) on the main diagonal, normalised to an
+integral of exactly 1.  The run uses 50 intervals per axis, 9 strata per axis
+(9^8 = 43,046,721 hypercubes, about 2 evaluations each), beta = 0.75 and
+alpha = 0.5, with 1e8 evaluations per iteration and Philox seed 0.  A step is
+one whole iteration (allocation, fill, map refinement, combination) over 1e8
+evaluations.
+The headline line times the FP32-evaluation form (compensated FP32 cube sums,
+FP64 across cubes).  Plain FP64 VEGAS+ on the same workload is timed beside
+it, together with the time each takes to reach a relative error of 1e-4.
+
+Timing: W warm-up iterations, then K timed iterations in one integrate call.
+The call sits between a barrier and a device synchronisation on both sides.
+Per-iteration device time comes from CUDA events that the library records on
+its stream.  The per-cube arrays (0.5 GB) are larger than L2.  --gpus N > 1
+runs N independent replicas, one process per GPU under torchrun.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "evals/s and time to 1e-4 rel. error, chosen form vs plain VEGAS+, 1 GB300"
+D, NBINS, NSTRAT, ALPHA, BETA, NEVAL, NITN, SEED, K_PEAKS, SIGMA = 8, 50, 9, 0.5, 0.75, 100_000_000, 15, 0, 5, 0.05
+WORKLOAD = ("plain VEGAS+ d=8, ridge of 5 Gaussians (s=0.05) on the diagonal, Ng=50, 9^8 cubes, "
+            "1e8 evals/iteration, beta=0.75, alpha=0.5, Philox seed 0")
+# MEASURED_PEAKS-independent nominal SM facts of GB300 (152 SMs, 128 FP32 lanes per SM, 2070 MHz max)
+FP32_LANES_PER_SM = 128
+
+
+def fp32_ops_per_eval(d=D, K=K_PEAKS):
+    """FP32 FMA-pipe operations the method needs per evaluation of the d-dimensional
+    ridge in the FP32 form (counted from the algorithm):
+      point + map, per axis: c+u, *g, z-i, fma(dz,dx,e), J*=jk        -> 5 d
+      integrand, per peak:   per axis x-mu, fma(dx,dx,r2); r2*c; acc+= -> K (2 d + 2)
+      A*acc, v = J f, v*v, *1/n_h                                      -> 4"""
+    return 5 * d + K * (2 * d + 2) + 4
+
+
+def sample_clocks(stop, out):
+    cmd = ["nvidia-smi", "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+           "--format=csv,noheader,nounits", "-i", str(int(os.environ.get("LOCAL_RANK", 0))), "-lms", "100"]
+    try:
+        p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except OSError:
+        return
+    def reader():
+        for line in p.stdout:
+            out.append(line.strip())
+    th = threading.Thread(target=reader, daemon=True)
+    th.start()
+    stop.wait()
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        p.kill()
+    th.join(timeout=2)
+
+
+def summarize_clocks(lines):
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ln in lines:
+        f = [x.strip() for x in ln.split(",")]
+        if len(f) < 7:
+            continue
+        try:
+            sm.append(float(f[0]))
+            mx.append(float(f[1]))
+        except ValueError:
+            continue
+        for name, v in zip(names, f[3:7]):
+            if v.lower().startswith("active"):
+                reasons.add(name)
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(gpus):
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if gpus > 0 else "gloo"
+        dist.init_process_group(backend)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device="cuda"):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2408_09229_gb300 import vegas as V
+    from paper_2408_09229_gb300 import workloads as W
+
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    params = W.ridge8_params()
+
+    def timed_run(precision):
+        v = V.Vegas(D, NBINS, NSTRAT, ALPHA, BETA, precision=precision, stream=stream)
+        v.integrate(W.GAUSS_SUM, params, NEVAL, args.warmup, seed=SEED + rank)
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = v.integrate(W.GAUSS_SUM, params, NEVAL, args.steps, seed=SEED + rank)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        outer_ms = e0.elapsed_time(e1)
+        it_ms, fill_ms = v.timings()
+        return v, r, outer_ms, it_ms, fill_ms
+
+    stop = threading.Event()
+    clock_lines = []
+    th = threading.Thread(target=sample_clocks, args=(stop, clock_lines), daemon=True)
+    th.start()
+    time.sleep(0.3)
+    v32, r32, outer32, it32, fill32 = timed_run(V.FP32)
+    v64, r64, outer64, it64, fill64 = timed_run(V.FP64)
+    stop.set()
+    th.join(timeout=10)
+    clocks = summarize_clocks(clock_lines)
+
+    # end to end through the public call: host params in, host results out, per step
+    v_e2e = V.Vegas(D, NBINS, NSTRAT, ALPHA, BETA, precision=V.FP32, stream=stream)
+    v_e2e.integrate(W.GAUSS_SUM, params, NEVAL, args.warmup, seed=SEED + rank)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v_e2e.integrate(W.GAUSS_SUM, params, NEVAL, 1, seed=SEED + rank)
+    t_e2e = max_over_ranks(time.perf_counter() - t0, world)
+
+    # time to a relative error of 1e-4 from a fresh map, both forms
+    def time_to_rtol(precision):
+        v = V.Vegas(D, NBINS, NSTRAT, ALPHA, BETA, precision=precision, rtol=1e-4, stream=stream)
+        v.integrate(W.GAUSS_SUM, params, NEVAL, 1, seed=99)  # sizes the buffers outside the clock
+        v.reset_map()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = v.integrate(W.GAUSS_SUM, params, NEVAL, 60, seed=SEED + 1000 + rank)
+        dt = time.perf_counter() - t0
+        return {"seconds": dt, "iterations": r["nitn_run"], "evals": r["neval_total"], "estimate": r["estimate"],
+                "sigma": r["sigma"], "rel_err_reached": r["sigma"] / abs(r["estimate"]),
+                "within_3_sigma_of_exact": abs(r["estimate"] - 1.0) <= 3 * r["sigma"]}
+
+    ttr32 = time_to_rtol(V.FP32)
+    ttr64 = time_to_rtol(V.FP64)
+
+    t_dev32 = max_over_ranks(float(np.sum(it32)) / 1e3, world)
+    t_dev64 = max_over_ranks(float(np.sum(it64)) / 1e3, world)
+    fill_mean32 = float(np.mean(fill32)) / 1e3
+    evals = NEVAL * args.steps * world
+    value = evals / t_dev32
+    rates = V.probe_pipes()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    ops = fp32_ops_per_eval()
+    achieved = ops * NEVAL / fill_mean32 / 1e12
+    peak = FP32_LANES_PER_SM * sms * 2070e6 / 1e12
+    launches_per_it = 12
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_dev32 / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": "FP32 evaluation, compensated cube sums, FP64 across cubes",
+                   "neval_per_step": NEVAL, "ncubes": NSTRAT ** D, "l2": "per-cube arrays 0.5 GB > L2; no flush",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "plain_fp64": {"value": evals / t_dev64, "unit": "evals/s", "ms_per_step": t_dev64 / args.steps * 1e3,
+                       "estimate": r64["estimate"], "sigma": r64["sigma"]},
+        "result_fp32": {"estimate": r32["estimate"], "sigma": r32["sigma"], "chi2_dof": r32["chi2_dof"]},
+        "time_to_rtol": {"rtol": 1e-4, "fp32_form": ttr32, "plain_fp64": ttr64},
+        "e2e": {"value": NEVAL * args.steps * world / t_e2e, "unit": "evals/s",
+                "h2d_bytes_per_step": 8 * len(params), "d2h_bytes_per_step": 8 * 4 + 2 * 8 + 4},
+        "roofline": {"bound": "alu", "kernel": "fill_kernel<GAUSS_SUM, float, 8>", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "ops_per_eval": ops, "fill_ms": fill_mean32 * 1e3,
+                     "peak_basis": "FP32 FMA pipe: 128 lanes x %d SMs x 2070 MHz (max SM clock)" % sms,
+                     "probe_ops_per_sm_clk": {"ffma": rates[0], "dfma": rates[1], "mufu_ex2": rates[2],
+                                              "imad_hi": rates[3]}},
+        "clocks": clocks,
+        "gpu_launches": launches_per_it * args.steps,
+        "timing_check": {"outer_event_ms": outer32, "sum_iteration_ms": float(np.sum(it32))},
+    }
+    if rank == 0:
+        try:
+            line["cpu_baseline"] = cpu_baseline()
+        except Exception as e:  # the oracle build needs gcc; report instead of failing the bench
+            line["cpu_baseline"] = {"error": str(e)[:200]}
+        print(json.dumps(line))
+
+
+def cpu_baseline(neval=10_000_000, nitn=2):
+    """the CPU oracle as it stands, single-threaded, on a bounded sample of the workload"""
+    import oracle
+    from paper_2408_09229_gb300 import workloads as W
+    cfg = oracle.Config(D, NBINS, oracle.default_nstrat(neval, D), ALPHA, BETA)
+    t0 = time.perf_counter()
+    oracle.integrate(cfg, W.GAUSS_SUM, W.ridge8_params(), neval, nitn, seed=SEED)
+    dt = time.perf_counter() - t0
+    return {"value": neval * nitn / dt, "unit": "evals/s", "cores": 1, "kind": "oracle",
+            "sample": f"{nitn} iterations x {neval:.0e} evals of the same integrand, d, Ng, alpha, beta; "
+                      f"{int(cfg.nstrat[0])}^8 cubes (auto strata for that size); {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the CPU oracle, as it stands, one bounded-sample iteration per step"""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2408_09229_gb300 import workloads as W
+    neval = 1_000_000
+    cfg = oracle.Config(D, NBINS, oracle.default_nstrat(neval, D), ALPHA, BETA)
+    params = W.ridge8_params()
+    oracle.integrate(cfg, W.GAUSS_SUM, params, neval, max(args.warmup, 1), seed=SEED)
+    t0 = time.perf_counter()
+    r = oracle.integrate(cfg, W.GAUSS_SUM, params, neval, args.steps, seed=SEED)
+    dt = time.perf_counter() - t0
+    value = neval * args.steps / dt
+    sample = (f"each step one oracle iteration of {neval:.0e} evals of the same integrand, d, Ng, alpha, beta "
+              f"({int(cfg.nstrat[0])}^8 cubes); single-threaded")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": "CPU oracle (plain FP64 VEGAS+)", "neval_per_step": neval},
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "result": {"estimate": r["estimate"], "sigma": r["sigma"]},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=NITN)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    rank, world = dist_setup(args.gpus if args.impl == "ours" else 0)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        import __graft_entry__
+        __graft_entry__.build()
+        run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

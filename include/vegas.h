@@ -1,0 +1,251 @@
+/*
+ * vegas.h -- C ABI of the GB300 (sm_103a) VEGAS+ iteration loop.
+ *
+ * The library computes the VEGAS+ method as described in cuVegas (Tolotti,
+ * Jnini, Vella, Passerone, arXiv 2408.09229):
+ *   Sec. 2.1.1  adaptive importance sampling.  Separable map with N_g
+ *               intervals per axis; Eqs. (2)-(4): J(y) = N_g dx_{i(y)} and
+ *               I_MC = (1/N_ev) sum J f.
+ *   Sec. 2.1.2  adaptive stratified sampling.  Eqs. (5)-(7): I = sum dI_h and
+ *               sigma^2 = sum sigma_h^2 / n_h, with n_h proportional to sigma_h
+ *               damped by beta, and sum n_h = N_eval.
+ *   Sec. 2.1.3  inverse-variance combination of iterations, Eqs. (8)-(9).
+ *   Algorithm 1 iteration loop; Algorithm 2 vegasFill.
+ *
+ * Two levels of entry points:
+ *   1. A handle (vegas_create / vegas_integrate / vegas_destroy, plus setters,
+ *      state and timing queries).  It owns its device buffers and runs whole
+ *      integrations.
+ *   2. Step entry points (vegas_allocate, vegas_fill, vegas_refine,
+ *      vegas_combine).  Each runs one row of the iteration on caller-owned
+ *      device buffers.  They are stateless: the caller passes plain device
+ *      pointers and sizes, plus a caller-owned device scratch area whose size
+ *      the matching *_scratch_bytes query returns.
+ *
+ * Conventions for all entry points:
+ *   - The domain is the unit cube [0,1]^d.
+ *   - Device pointers are "d_*" and must point to memory of the current CUDA
+ *     device.  Host pointers have no prefix.
+ *   - "stream" is a cudaStream_t passed as void*.  NULL means the legacy
+ *     default stream.
+ *   - Step entry points are asynchronous on the stream.  They return after
+ *     queuing their kernels and report launch errors only.  Errors found on
+ *     the device (a non-finite integrand value) go to the caller's device flag.
+ *   - Every entry point returns VEGAS_OK (0) or a negative status from the
+ *     list below.  No C++ exception crosses the ABI.
+ *   - Arrays are row-major.  The map edges are [d][N_g+1] and the map weights
+ *     are [d][N_g].  Hypercube h has coordinates c_k = (h / prod_{l<k} s_l)
+ *     mod s_k, so axis 0 varies fastest.
+ * Limits: 1 <= d <= 32, 2 <= N_g <= 4096, N_h = prod s_k < 2^31,
+ * 2 N_h <= N_eval < 2^31 evaluations per iteration.
+ */
+#ifndef VEGAS_GB300_H
+#define VEGAS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define VEGAS_API __attribute__((visibility("default")))
+#else
+#define VEGAS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define VEGAS_OK 0
+#define VEGAS_EINVAL (-1)     /* an argument is out of range                   */
+#define VEGAS_ENOMEM (-2)     /* a device or host allocation failed            */
+#define VEGAS_ECUDA (-3)      /* a CUDA runtime call or kernel launch failed   */
+#define VEGAS_ENONFINITE (-4) /* the integrand returned NaN or +-inf           */
+#define VEGAS_ETIMEOUT (-5)   /* a bounded device wait ran out                 */
+#define VEGAS_ESTATE (-6)     /* a state blob does not match this handle       */
+#define VEGAS_ENOSPACE (-7)   /* the caller's scratch or array is too small    */
+
+/* ---- integrand families (compiled in; the layout of params per family) --- */
+enum vegas_integrand {
+  VEGAS_GAUSS_SUM = 0,         /* A sum_k exp(-|x-mu_k|^2/(2 s^2)); params [A, s, K, mu(K*d)]     */
+  VEGAS_PRODUCT_PEAK = 1,      /* prod_i 1/(c_i^-2 + (x_i-w_i)^2); params [c(d), w(d)]            */
+  VEGAS_OSCILLATORY = 2,       /* cos(2 pi u + sum_i a_i x_i); params [u, a(d)]                   */
+  VEGAS_SIN_EXP = 3,           /* Table 3 (1): sin x_1 + exp x_2 (d = 2); no params              */
+  VEGAS_LINEAR = 4,            /* Table 3 (2): sum x_i                                          */
+  VEGAS_COSINE = 5,            /* Table 3 (3): prod cos x_i                                     */
+  VEGAS_EXPONENTIAL = 6,       /* Table 3 (4): exp(sum x_i^2)                                   */
+  VEGAS_ROOS_ARNOLD = 7,       /* Table 3 (5): prod |4 x_i - 2|                                 */
+  VEGAS_MOROKOFF_CAFLISCH = 8, /* Table 3 (6): (1+1/d)^d prod x_i^(1/d)                         */
+  VEGAS_MAP_DENSITY = 9,       /* density of a fixed separable map; params = its edges [d][G+1] */
+  VEGAS_N_INTEGRANDS = 10
+};
+/* Table 3 (7) Gaussian and (8) Ridge are VEGAS_GAUSS_SUM instances. */
+
+/* ---- precision of the per-evaluation arithmetic -------------------------- */
+enum vegas_precision {
+  VEGAS_FP64 = 0, /* points, map, integrand, cube and map-weight sums in FP64          */
+  VEGAS_FP32 = 1  /* points, map and integrand in FP32; compensated FP32 sums per
+                     cube, FP64 across cubes, map refinement and combination in FP64 */
+};
+
+/* ======================================================================== */
+/* Level 1: handle                                                          */
+/* ======================================================================== */
+typedef struct vegas_s *vegas_handle;
+
+typedef struct {
+  double estimate;      /* Eq. (8): inverse-variance weighted mean of the used iterations   */
+  double sigma;         /* Eq. (9)                                                          */
+  double chi2_dof;      /* sum_t (I_t - I)^2 / sigma_t^2 / (n_used - 1); 0 for one iteration */
+  int64_t neval_total;  /* evaluations made by this call                                    */
+  int32_t nitn_run;     /* iterations run (fewer than asked when the rtol target was met)   */
+  int32_t n_used;       /* iterations in the weighted mean (those with index >= skip)       */
+  double *it_est;       /* caller-owned host array of it_cap entries, or NULL: I_t          */
+  double *it_sigma;     /* caller-owned host array of it_cap entries, or NULL: sigma_t      */
+  int32_t it_cap;
+} vegas_result;
+
+/* Create a handle for dimension dim, N_g = nbins intervals per axis, nstrat
+ * strata per axis (nstrat <= 0: chosen at each integrate call as the largest s
+ * with s^d <= neval/2), map damping alpha >= 0 (Sec. 2.1.1) and stratification
+ * damping beta in [0, 1] (Sec. 2.1.2).  The handle binds to the current CUDA
+ * device.  It allocates the map buffers there and uploads the uniform map.  The
+ * per-cube buffers and scratch are sized on the first integrate call.
+ * Errors: EINVAL for an out-of-range argument or NULL out, ENOMEM, ECUDA. */
+VEGAS_API int vegas_create(int dim, int nbins, int nstrat, double alpha, double beta, vegas_handle *out);
+
+/* Release the handle and its device buffers (synchronises its stream).
+ * NULL is accepted. */
+VEGAS_API int vegas_destroy(vegas_handle h);
+
+/* Per-axis strata s_k (dim entries, each >= 1).  This overrides the nstrat
+ * given to vegas_create.  Errors: EINVAL. */
+VEGAS_API int vegas_set_nstrat_axes(vegas_handle h, const int32_t *nstrat, int dim);
+/* Iterations with index < skip are left out of the weighted mean (default 0). */
+VEGAS_API int vegas_set_skip(vegas_handle h, int skip);
+/* VEGAS_FP64 (default) or VEGAS_FP32. */
+VEGAS_API int vegas_set_precision(vegas_handle h, int precision);
+/* Run on this cudaStream_t.  NULL restores the handle's own stream. */
+VEGAS_API int vegas_set_stream(vegas_handle h, void *stream);
+/* Stop an integrate call early once sigma/|estimate| <= rtol (0 disables the
+ * check, which is the default).  The check reads the result to the host after
+ * every iteration. */
+VEGAS_API int vegas_set_rtol(vegas_handle h, double rtol);
+/* Back to the uniform map and uniform allocation; iteration counter to 0. */
+VEGAS_API int vegas_reset_map(vegas_handle h);
+
+/* Run nitn iterations of Algorithm 1 on integrand family `integrand` with the
+ * host array params[nparams] (layout in enum vegas_integrand).  Each iteration
+ * makes neval evaluations.  The map and the stratification carry over from
+ * earlier calls on the same handle.  The stratification is reset to uniform
+ * when the number of hypercubes changes.  Evaluation j of iteration t (the
+ * handle's iteration counter) draws its point from Philox4x32-10 with key
+ * seed and counter (j, t, block), so results do not depend on the launch
+ * shape.  The call synchronises the stream and fills *out.
+ * Errors: EINVAL (bad integrand id, parameter count, neval < 2 N_h or
+ * neval >= 2^31), ENOMEM, ECUDA, ENONFINITE (the result is still filled in). */
+VEGAS_API int vegas_integrate(vegas_handle h, int integrand, const double *params, int64_t nparams, int64_t neval,
+                    int nitn, uint64_t seed, vegas_result *out);
+
+/* Device time of each iteration (iter_ms) and of its fill kernel (fill_ms) in
+ * the last integrate call, from CUDA events on the handle's stream.  At most
+ * cap entries are written; *n gets the number of iterations run. */
+VEGAS_API int vegas_get_timings(vegas_handle h, float *iter_ms, float *fill_ms, int cap, int *n);
+
+/* Checkpoint: the map edges, the stratification weights of the last
+ * iteration, the strata and the iteration counter, in a self-describing blob.
+ * vegas_get_state with buf == NULL stores the size in *bytes. */
+VEGAS_API int vegas_get_state(vegas_handle h, void *buf, size_t *bytes);
+/* Restore a blob made by vegas_get_state on a handle with the same dim and
+ * nbins.  Errors: ESTATE for a mismatch. */
+VEGAS_API int vegas_set_state(vegas_handle h, const void *buf, size_t bytes);
+
+/* Copy the current map edges [dim][nbins+1] to a host array. */
+VEGAS_API int vegas_get_edges(vegas_handle h, double *edges, size_t count);
+
+/* A static string for a status code. */
+VEGAS_API const char *vegas_strerror(int status);
+
+/* ======================================================================== */
+/* Level 2: step entry points (one row of Algorithm 1 each)                  */
+/* ======================================================================== */
+
+/* Geometry shared by the step entry points.  Host struct, host pointer. */
+typedef struct {
+  int32_t dim;           /* d                                    */
+  int32_t nbins;         /* N_g                                  */
+  const int32_t *nstrat; /* host array of d strata s_k           */
+} vegas_geometry;
+
+/* -- updateEvalsPerCube + mapEvalsToCubes (Algorithm 1; Sec. 2.1.2, Eq. (7)) --
+ * From the per-cube weights d_ell[ncubes] (float, ell_h = (beta/2) log2 of the
+ * cube's sample variance of J f, -inf for zero variance, as written by
+ * vegas_fill), write d_offsets[ncubes+1] (int64): off_0 = 0, off_N = neval,
+ * and n_h = off_{h+1} - off_h = 2 + a share of neval - 2 N_h proportional to
+ * q_h = rint(2^24 2^(ell_h - max ell)).  The shares use cumulative rounding,
+ * off_h = 2h + floor(R Q_h / Q), so sum n_h = neval exactly and every decision
+ * is integer.  uniform != 0 (first iteration, beta = 0) ignores d_ell, which may
+ * be NULL; so does the case where every ell is -inf.  d_scratch holds
+ * vegas_allocate_scratch_bytes(ncubes) bytes.
+ * Errors: EINVAL (neval < 2 ncubes, neval >= 2^31, ncubes >= 2^31), ENOSPACE. */
+VEGAS_API size_t vegas_allocate_scratch_bytes(int64_t ncubes);
+VEGAS_API int vegas_allocate(const float *d_ell, int64_t ncubes, int64_t neval, int uniform, int64_t *d_offsets,
+                   void *d_scratch, size_t scratch_bytes, void *stream);
+
+/* -- vegasFill (Algorithm 2; Eqs. (3)-(6)) ----------------------------------
+ * Evaluate the integrand at the neval points of iteration `iteration`.
+ * Evaluation j lies in the cube h with off_h <= j < off_{h+1}.  Its point comes
+ * from Philox4x32-10 (key seed, counter (j, iteration, problem_id<<16 | block))
+ * and goes through the map d_edges[d][N_g+1] (FP64).  The outputs are:
+ *   d_ell[ncubes]     per-cube allocation weight for vegas_allocate (beta used);
+ *   d_bins[d*N_g]     map weights sum over the cube's evaluations of (J f)^2 / n_h
+ *                     (FP64, overwritten);
+ *   d_result[2]       (I_t, sigma_t^2) of this iteration, Eqs. (5)-(6), FP64;
+ *   d_cube_mean, d_cube_m2 [ncubes]  per-cube mean and centred second moment
+ *                     of J f (FP64), or NULL to skip them;
+ *   d_flags           device int; bit 0 is set when an integrand value was not
+ *                     finite (never cleared by the library).
+ * d_params[nparams] is a device copy of the integrand parameters.
+ * precision is VEGAS_FP64 or VEGAS_FP32.
+ * d_scratch holds vegas_fill_scratch_bytes(geometry, neval) bytes.
+ * Errors: EINVAL, ENOSPACE, ECUDA. */
+VEGAS_API size_t vegas_fill_scratch_bytes(const vegas_geometry *g, int64_t neval);
+VEGAS_API int vegas_fill(const vegas_geometry *g, int precision, int integrand, const double *d_params, int64_t nparams,
+               int64_t neval, uint64_t seed, int32_t iteration, uint32_t problem_id, double beta,
+               const double *d_edges, const int64_t *d_offsets, float *d_ell, double *d_bins, double *d_result,
+               double *d_cube_mean, double *d_cube_m2, int *d_flags, void *d_scratch, size_t scratch_bytes,
+               void *stream);
+
+/* -- adjustWeights + updateMap (Algorithm 1; Sec. 2.1.1) ---------------------
+ * Per axis: smooth the map weights d_bins[d][N_g] with neighbours (weights
+ * (7,1)/8 at the ends, (1,6,1)/8 inside), normalise to r_i, damp to
+ * m_i = ((1 - r_i)/ln(1/r_i))^alpha, and place the N_g - 1 inner edges so that
+ * each new interval holds 1/N_g of sum m.  The weight is uniform inside each
+ * old interval.  Writes d_edges_out[d][N_g+1].  An axis whose weights are all
+ * zero or not finite, or alpha == 0, keeps its edges.  d_edges_in and
+ * d_edges_out must not overlap.  Errors: EINVAL, ECUDA. */
+VEGAS_API int vegas_refine(int32_t dim, int32_t nbins, double alpha, const double *d_bins, const double *d_edges_in,
+                 double *d_edges_out, void *stream);
+
+/* -- combineIterationsResults (Algorithm 1; Sec. 2.1.3, Eqs. (8)-(9)) -------
+ * From d_it_est[n] and d_it_sigma[n] (device), combine the iterations
+ * t >= skip.  Writes d_out[4] = {estimate, sigma, chi2/dof, n_used}.
+ * Iterations with sigma_t = 0 give their mean exactly with sigma 0.
+ * Errors: EINVAL, ECUDA. */
+VEGAS_API int vegas_combine(const double *d_it_est, const double *d_it_sigma, int32_t n, int32_t skip, double *d_out,
+                  void *stream);
+
+/* ======================================================================== */
+/* Measurement support                                                      */
+/* ======================================================================== */
+/* Measure issue rates of the arithmetic pipes on the current device with
+ * dependent-chain microkernels (FP32 FMA, FP64 FMA, MUFU ex2, integer
+ * multiply-high).  rates[4] receives operations per SM per clock, measured
+ * with the device clock counter.  Used to state the roofline of the fill
+ * kernel.  Errors: ECUDA. */
+VEGAS_API int vegas_probe_pipes(double rates[4]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VEGAS_GB300_H */

@@ -57,6 +57,9 @@ def lib():
         L.orc_fill_range.argtypes = [ctypes.POINTER(_Config), i32, P, i64, i64, i32, ctypes.c_uint64,
                                      P, P, i64, i64, P, P, P, P]
         L.orc_fill_range.restype = i32
+        L.orc_cube_stats.argtypes = [ctypes.POINTER(_Config), i32, P, i64, i32, ctypes.c_uint64, P, i64, i64, i64,
+                                     P, P]
+        L.orc_cube_stats.restype = i32
         L.orc_finish_cubes.argtypes = [ctypes.POINTER(_Config), P, P, P, P, P, P]
         L.orc_iteration.argtypes = [ctypes.POINTER(_Config), i32, P, i64, i64, i32, ctypes.c_uint64,
                                     P, P, P, P, P, P, P, P, P, P]
@@ -170,6 +173,18 @@ def fill_range(cfg, iid, params, neval, t, seed, edges, offsets, j_begin, j_end)
     if rc not in (0, -2):
         raise ValueError(f"orc_fill_range failed: {rc}")
     return cnt, mean, m2, bins.reshape(cfg.dim, cfg.nbins)
+
+
+def cube_stats(cfg, iid, params, t, seed, edges, h, off_h, n_h):
+    """mean and M2 of J f over the evaluations of one cube (Algorithm 2 on one cube)"""
+    p = np.ascontiguousarray(params, dtype=np.float64) if len(params) else np.zeros(1)
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    mean, m2 = np.zeros(1), np.zeros(1)
+    rc = lib().orc_cube_stats(ctypes.byref(cfg._c), iid, _ptr(p), len(params), t, seed, _ptr(e), int(h), int(off_h),
+                              int(n_h), _ptr(mean), _ptr(m2))
+    if rc not in (0, -2):
+        raise ValueError(f"orc_cube_stats failed: {rc}")
+    return float(mean[0]), float(m2[0])
 
 
 def finish_cubes(cfg, offsets, mean, m2):

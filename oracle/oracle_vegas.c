@@ -496,6 +496,69 @@ int orc_fill_range(const orc_config *cfg, int integrand, const double *params, i
   return status;
 }
 
+int orc_cube_stats(const orc_config *cfg, int integrand, const double *params, int64_t nparams, int t,
+                   uint64_t seed, const double *edges, int64_t h, int64_t off_h, int64_t n_h, double *mean,
+                   double *m2) {
+  /* the same sample loop as orc_fill_range, on a two-cube offset table
+   * that places cube h at its true evaluation indices */
+  orc_config one = *cfg;
+  const int64_t NH = orc_ncubes(cfg);
+  if (h < 0 || h >= NH || n_h < 2) return -1;
+  int64_t offs[2] = {off_h, off_h + n_h};
+  const int d = cfg->dim, G = cfg->nbins;
+  double *gz = (double *)malloc(sizeof(double) * d);
+  float *gz32 = (float *)malloc(sizeof(float) * d);
+  double *u = (double *)malloc(sizeof(double) * d);
+  float *u32 = (float *)malloc(sizeof(float) * d);
+  double *x = (double *)malloc(sizeof(double) * d);
+  double *buf = (double *)malloc(sizeof(double) * (size_t)n_h);
+  int *c = (int *)malloc(sizeof(int) * d);
+  int64_t rest = h;
+  for (int k = 0; k < d; ++k) {
+    gz[k] = (double)G / (double)cfg->nstrat[k];
+    gz32[k] = fdiv((float)G, (float)cfg->nstrat[k]);
+    c[k] = (int)(rest % cfg->nstrat[k]);
+    rest /= cfg->nstrat[k];
+  }
+  int status = 0;
+  for (int64_t j = offs[0]; j < offs[1]; ++j) {
+    double J = 1.0;
+    if (one.points_f32) point_coordinates_f32(&one, seed, t, j, u32);
+    else point_coordinates_f64(&one, seed, t, j, u);
+    for (int k = 0; k < d; ++k) {
+      const double *e = edges + (size_t)k * (G + 1);
+      double dz;
+      int i;
+      if (one.points_f32) {
+        float zf = fmul(fadd((float)c[k], u32[k]), gz32[k]);
+        i = (int)floorf(zf);
+        if (i > G - 1) i = G - 1;
+        dz = (double)fsub(zf, (float)i);
+      } else {
+        double z = ((double)c[k] + u[k]) * gz[k];
+        i = (int)floor(z);
+        if (i > G - 1) i = G - 1;
+        dz = z - (double)i;
+      }
+      double width = e[i + 1] - e[i];
+      x[k] = fma(dz, width, e[i]);
+      J *= (double)G * width;
+    }
+    double f;
+    orc_integrand(integrand, d, params, nparams, x, &f);
+    if (!isfinite(f)) status = -2;
+    buf[j - offs[0]] = J * f;
+  }
+  double s = 0.0;
+  for (int64_t r = 0; r < n_h; ++r) s += buf[r];
+  double mu = s / (double)n_h, q = 0.0;
+  for (int64_t r = 0; r < n_h; ++r) q += (buf[r] - mu) * (buf[r] - mu);
+  *mean = mu;
+  *m2 = q;
+  free(gz); free(gz32); free(u); free(u32); free(x); free(buf); free(c);
+  return status;
+}
+
 void orc_finish_cubes(const orc_config *cfg, const int64_t *offsets, const double *mean, const double *m2,
                       float *ell, double *it_est, double *it_var) {
   /* Eqs. (5)-(6): I = sum_h V_h mean_h, sigma^2 = sum_h V_h^2 var_h / n_h, with

@@ -104,6 +104,13 @@ int orc_fill_range(const orc_config *cfg, int integrand, const double *params, i
                    int64_t neval, int t, uint64_t seed, const double *edges, const int64_t *offsets,
                    int64_t j_begin, int64_t j_end, int64_t *cnt, double *mean, double *m2, double *bins);
 
+/* Algorithm 2 restricted to the evaluations of one cube h, whose evaluations
+ * are [off_h, off_h + n_h): mean and centred second moment of J f (two-pass),
+ * for spot checks of a full-size run one cube at a time. */
+int orc_cube_stats(const orc_config *cfg, int integrand, const double *params, int64_t nparams, int t,
+                   uint64_t seed, const double *edges, int64_t h, int64_t off_h, int64_t n_h, double *mean,
+                   double *m2);
+
 /* Eqs. (5)-(6) with V_h = 1/N_h (reading R12): iteration estimate and variance
  * from complete per-cube statistics, plus ell_h for the next allocation. */
 void orc_finish_cubes(const orc_config *cfg, const int64_t *offsets, const double *mean, const double *m2,

@@ -1,0 +1,212 @@
+// vegas_alloc.cu -- updateEvalsPerCube + mapEvalsToCubes of Algorithm 1
+// (Sec. 2.1.2 of cuVegas: n_h proportional to sigma_h damped by beta, with
+// sum n_h = N_eval, Eq. (7)).
+//
+// n_h = 2 + a share of R = neval - 2 N_h proportional to the quantised weight
+// q_h = rint(2^24 2^(ell_h - max ell)), with ell_h = (beta/2) log2 var_h from
+// the fill.  Cumulative rounding gives the shares:
+//   off_h = 2h + floor(R Q_h / Q),  Q_h = sum_{h'<h} q_h',  Q = Q_{N_h},
+// so sum n_h = neval exactly and n_h >= 2.  Integer arithmetic makes every
+// decision, so the counts are a function of the ell_h bits alone.  The
+// offsets of the scan are the thread-to-cube mapping; the fill reads them
+// and never materialises a per-evaluation array.
+//
+// Passes: (0) max ell, (1) per-block sums of q, (2) scan of the block sums in
+// one CTA, (3) per-block scan and offsets.  The uniform allocation (first
+// iteration, beta = 0, every variance zero) needs pass 3 only.
+#include <algorithm>
+
+#include "vegas_device.cuh"
+#include "vegas_internal.h"
+
+namespace vg {
+namespace {
+
+constexpr int kBlockCubes = kAllocThreads * kAllocItems;
+
+struct AllocScratch {
+  size_t key, bsum, total;
+  int64_t nblocks;
+};
+
+AllocScratch alloc_layout(int64_t ncubes) {
+  AllocScratch L{};
+  L.nblocks = (ncubes + kBlockCubes - 1) / kBlockCubes;
+  L.key = 0;
+  L.bsum = 256;
+  L.total = L.bsum + sizeof(uint64_t) * (size_t)(L.nblocks + 1) + 256;
+  return L;
+}
+
+__global__ void key_init_kernel(int* key) { *key = float_key(-__int_as_float(0x7f800000)); }
+
+__global__ void max_kernel(const float* __restrict__ ell, int64_t n, int* key) {
+  float m = -__int_as_float(0x7f800000);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, ell[i]);
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(key, float_key(m));
+}
+
+__device__ __forceinline__ bool is_uniform(const int* key, int uniform) {
+  return uniform || *key == float_key(-__int_as_float(0x7f800000));
+}
+
+__device__ __forceinline__ uint64_t weight_of(const float* __restrict__ ell, int64_t h, bool uni, float emax) {
+  return uni ? 1ull : (uint64_t)quant_weight(ell[h], emax);
+}
+
+// pass 1: sum of q over each block of kBlockCubes cubes
+__global__ void __launch_bounds__(kAllocThreads) block_sum_kernel(const float* __restrict__ ell, int64_t n,
+                                                                  const int* key, int uniform, uint64_t* bsum) {
+  __shared__ uint64_t red[kAllocThreads / 32];
+  const bool uni = is_uniform(key, uniform);
+  const float emax = key_float(*key);
+  const int64_t base = (int64_t)blockIdx.x * kBlockCubes;
+  uint64_t s = 0;
+  for (int i = threadIdx.x; i < kBlockCubes; i += kAllocThreads) {
+    const int64_t h = base + i;
+    if (h < n) s += weight_of(ell, h, uni, emax);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t t = 0;
+    for (int w = 0; w < kAllocThreads / 32; ++w) t += red[w];
+    bsum[blockIdx.x] = t;
+  }
+}
+
+// pass 2: exclusive scan of the block sums, in place; bsum[nb] = Q
+__global__ void __launch_bounds__(1024) block_scan_kernel(uint64_t* bsum, int64_t nb) {
+  __shared__ uint64_t warp_tot[32];
+  __shared__ uint64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < nb; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const uint64_t v = i < nb ? bsum[i] : 0ull;
+    uint64_t x = v;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      uint64_t t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0ull;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      warp_tot[lane] = t;  // inclusive scan of warp totals
+    }
+    __syncthreads();
+    const uint64_t before = carry + (w > 0 ? warp_tot[w - 1] : 0ull) + (x - v);
+    if (i < nb) bsum[i] = before;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = before + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bsum[nb] = carry;
+}
+
+// floor(R * Qh / Q) exactly: a double estimate, corrected with 128-bit products
+__device__ __forceinline__ uint64_t share_floor(uint64_t R, uint64_t Qh, uint64_t Q, double r_over_q) {
+  uint64_t c = (uint64_t)((double)Qh * r_over_q);
+  const unsigned __int128 P = (unsigned __int128)R * Qh;
+  unsigned __int128 CQ = (unsigned __int128)c * Q;
+  for (int it = 0; it < 8 && CQ > P; ++it) {
+    --c;
+    CQ -= Q;
+  }
+  for (int it = 0; it < 8 && CQ + Q <= P; ++it) {
+    ++c;
+    CQ += Q;
+  }
+  return c;
+}
+
+// pass 3: block scan of q and the offsets off_h = 2h + floor(R Q_h / Q)
+__global__ void __launch_bounds__(kAllocThreads) offsets_kernel(const float* __restrict__ ell, int64_t n,
+                                                                int64_t neval, const int* key, int uniform,
+                                                                const uint64_t* __restrict__ bpre,
+                                                                int64_t* __restrict__ offsets) {
+  __shared__ uint64_t warp_tot[kAllocThreads / 32];
+  const bool uni = is_uniform(key, uniform);
+  const float emax = uni ? 0.0f : key_float(*key);
+  const int64_t nb = (n + kBlockCubes - 1) / kBlockCubes;
+  const uint64_t R = (uint64_t)(neval - 2 * n);
+  const uint64_t Q = uni ? (uint64_t)n : bpre[nb];
+  const double r_over_q = (double)R / (double)Q;
+  const int64_t base = (int64_t)blockIdx.x * kBlockCubes + (int64_t)threadIdx.x * kAllocItems;
+  uint32_t q[kAllocItems];
+  uint64_t tsum = 0;
+#pragma unroll
+  for (int i = 0; i < kAllocItems; ++i) {
+    const int64_t h = base + i;
+    q[i] = (h < n) ? (uni ? 1u : quant_weight(ell[h], emax)) : 0u;
+    tsum += q[i];
+  }
+  // exclusive scan of the thread sums across the block
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint64_t x = tsum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[w] = x;
+  __syncthreads();
+  uint64_t wbefore = 0;
+  for (int k = 0; k < w; ++k) wbefore += warp_tot[k];
+  uint64_t Qh = (uni ? (uint64_t)blockIdx.x * kBlockCubes : bpre[blockIdx.x]) + wbefore + (x - tsum);
+#pragma unroll
+  for (int i = 0; i < kAllocItems; ++i) {
+    const int64_t h = base + i;
+    if (h < n) offsets[h] = 2 * h + (int64_t)share_floor(R, Qh, Q, r_over_q);
+    Qh += q[i];
+  }
+  if (base <= n - 1 && n - 1 < base + kAllocItems) offsets[n] = neval;  // the thread of the last cube
+}
+
+}  // namespace
+}  // namespace vg
+
+using namespace vg;
+
+extern "C" size_t vegas_allocate_scratch_bytes(int64_t ncubes) {
+  if (ncubes < 1) return 0;
+  return alloc_layout(ncubes).total;
+}
+
+extern "C" int vegas_allocate(const float* d_ell, int64_t ncubes, int64_t neval, int uniform, int64_t* d_offsets,
+                              void* d_scratch, size_t scratch_bytes, void* stream) {
+  if (ncubes < 1 || ncubes >= (int64_t(1) << 31) || neval < 2 * ncubes || neval > kMaxEval) return VEGAS_EINVAL;
+  if (!d_offsets || !d_scratch || (!uniform && !d_ell)) return VEGAS_EINVAL;
+  const AllocScratch L = alloc_layout(ncubes);
+  if (scratch_bytes < L.total) return VEGAS_ENOSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char* sc = (unsigned char*)d_scratch;
+  int* key = (int*)(sc + L.key);
+  uint64_t* bsum = (uint64_t*)(sc + L.bsum);
+  key_init_kernel<<<1, 1, 0, s>>>(key);
+  VG_CHECK(cudaGetLastError());
+  if (!uniform) {
+    const int grid = (int)std::min<int64_t>((ncubes + 255) / 256, 4096);
+    max_kernel<<<grid, 256, 0, s>>>(d_ell, ncubes, key);
+    VG_CHECK(cudaGetLastError());
+    block_sum_kernel<<<(unsigned)L.nblocks, kAllocThreads, 0, s>>>(d_ell, ncubes, key, 0, bsum);
+    VG_CHECK(cudaGetLastError());
+    block_scan_kernel<<<1, 1024, 0, s>>>(bsum, L.nblocks);
+    VG_CHECK(cudaGetLastError());
+  }
+  offsets_kernel<<<(unsigned)L.nblocks, kAllocThreads, 0, s>>>(d_ell, ncubes, neval, key, uniform, bsum, d_offsets);
+  VG_CHECK(cudaGetLastError());
+  return VEGAS_OK;
+}

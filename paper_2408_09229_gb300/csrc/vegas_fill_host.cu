@@ -1,0 +1,326 @@
+// vegas_fill_host.cu -- vegas_fill: scratch layout, the tile-to-cube search,
+// the fix-up of cubes that cross tile edges, the fixed-order reductions of
+// the iteration sums and of the map weights, and the launch sequence
+// (Algorithm 1 "fill weights" with Algorithm 2 inside).
+#include <algorithm>
+#include <cmath>
+
+#include "vegas_device.cuh"
+#include "vegas_fill.cuh"
+#include "vegas_internal.h"
+
+namespace vg {
+
+int dmax_for(int d) { return d <= 4 ? 4 : d <= 8 ? 8 : d <= 16 ? 16 : 32; }
+
+// Number of derived parameters the fill stages, or -1 when the caller's
+// parameter count does not fit the family (layouts in vegas.h).
+int derived_param_count(int integrand, int d, const double* host_params, int64_t np) {
+  switch (integrand) {
+    case VEGAS_GAUSS_SUM:
+      if (np < 3 + d || (np - 3) % d != 0) return -1;
+      if (host_params && (int64_t)host_params[2] * d + 3 != np) return -1;
+      return (int)np;
+    case VEGAS_PRODUCT_PEAK: return np == 2 * d ? (int)np : -1;
+    case VEGAS_OSCILLATORY: return np == 1 + d ? (int)np : -1;
+    case VEGAS_SIN_EXP: return (d == 2 && np == 0) ? 0 : -1;
+    case VEGAS_LINEAR:
+    case VEGAS_COSINE:
+    case VEGAS_EXPONENTIAL:
+    case VEGAS_ROOS_ARNOLD: return np == 0 ? 0 : -1;
+    case VEGAS_MOROKOFF_CAFLISCH: return np == 0 ? 2 : -1;
+    case VEGAS_MAP_DENSITY: return (np % d == 0 && np / d >= 2) ? (int)np : -1;
+    default: return -1;
+  }
+}
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct ScratchLayout {
+  size_t tile_first, carries, cta_part, fix_part, hist_part, gtable, ellmax, total;
+  int ntiles, grid_max, nfix;
+};
+
+int num_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return n;
+}
+
+ScratchLayout scratch_layout(int d, int G, int64_t neval, int sms) {
+  ScratchLayout L{};
+  L.ntiles = (int)((neval + kTile - 1) / kTile);
+  L.grid_max = std::max(1, std::min(L.ntiles, 8 * std::max(sms, 1)));
+  L.nfix = (L.ntiles + 255) / 256;
+  size_t off = 0;
+  L.tile_first = off; off = align_up(off + sizeof(int32_t) * L.ntiles);
+  L.carries = off;    off = align_up(off + sizeof(Carry) * 2 * (size_t)L.ntiles);
+  L.cta_part = off;   off = align_up(off + sizeof(double) * 2 * (size_t)L.grid_max);
+  L.fix_part = off;   off = align_up(off + sizeof(double) * 2 * (size_t)L.nfix);
+  L.hist_part = off;  off = align_up(off + sizeof(double) * (size_t)L.grid_max * d * G);
+  L.gtable = off;     off = align_up(off + sizeof(TabEntry<double>) * (size_t)d * G);
+  L.ellmax = off;     off = align_up(off + 16);
+  L.total = off;
+  return L;
+}
+
+// Shared-memory regions of the fill kernel.  The map table and the histogram
+// go to shared memory when they fit the budget; otherwise the table is read
+// from global memory and the histogram is accumulated with global atomics.
+int smem_layout(FillArgs& a, size_t tsz, int np_derived) {
+  const int dG = a.d * a.G;
+  const size_t fixed = align_up(np_derived * tsz) + align_up(sizeof(int64_t) * (kMaxCubesPerTile + 1)) +
+                       align_up(tsz * kMaxCubesPerTile) + align_up(tsz * kTile) +
+                       align_up(sizeof(int) * kMaxCubesPerTile) + align_up(kMaxDim * tsz + 16 + 8 * 32);
+  const size_t budget = 160 * 1024;
+  const size_t table = align_up((size_t)dG * 4 * tsz), hist = align_up((size_t)dG * tsz);
+  a.hist_smem = fixed + hist <= budget;
+  a.table_smem = a.hist_smem && fixed + hist + table <= budget;
+  size_t off = 0;
+  a.sm_table = (int)off; off += a.table_smem ? table : 0;
+  a.sm_hist = (int)off;  off += a.hist_smem ? hist : 0;
+  a.sm_params = (int)off; off += align_up(np_derived * tsz);
+  a.sm_off = (int)off;   off += align_up(sizeof(int64_t) * (kMaxCubesPerTile + 1));
+  a.sm_invn = (int)off;  off += align_up(tsz * kMaxCubesPerTile);
+  a.sm_vals = (int)off;  off += align_up(tsz * kTile);
+  a.sm_long = (int)off;  off += align_up(sizeof(int) * kMaxCubesPerTile);
+  a.sm_misc = (int)off;  off += align_up(kMaxDim * tsz + 16 + 8 * 32);
+  a.sm_total = (int)off;
+  return off <= 227 * 1024 ? VEGAS_OK : VEGAS_EINVAL;
+}
+
+// first cube of every tile: largest h with offsets[h] <= tile * kTile
+__global__ void tile_first_kernel(const int64_t* __restrict__ offsets, int NH, int ntiles, int32_t* tile_first,
+                                  int* ellmax_key) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) *ellmax_key = float_key(-__int_as_float(0x7f800000));
+  if (t >= ntiles) return;
+  const int64_t j0 = (int64_t)t * kTile;
+  int lo = 0, hi = NH - 1;
+  while (lo < hi) {
+    const int mid = (int)(((int64_t)lo + hi + 1) >> 1);
+    if (offsets[mid] <= j0) lo = mid;
+    else hi = mid - 1;
+  }
+  tile_first[t] = lo;
+}
+
+template <typename T>
+__global__ void table_kernel(const double* __restrict__ edges, int d, int G, TabEntry<T>* tab) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= d * G) return;
+  const int k = b / G, i = b - k * G;
+  const double e0 = edges[k * (G + 1) + i], e1 = edges[k * (G + 1) + i + 1];
+  const double dx = __dsub_rn(e1, e0), jk = __dmul_rn((double)G, dx);
+  tab[b] = TabEntry<T>{(T)e0, (T)dx, (T)jk, T(0)};
+}
+
+// Merge, in tile order, the parts of every cube that crosses a tile edge.
+// Thread t owns the cube that starts in tile t and ends after it (slot
+// 2t+1); the later parts are the "starts before" slots 2u of tiles u > t.
+__global__ void fixup_kernel(const __grid_constant__ FillArgs a, double* fix_part) {
+  __shared__ double red[32];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  double ai = 0.0, av = 0.0;
+  float lmax = -__int_as_float(0x7f800000);
+  bool broken = false;
+  if (t < a.ntiles) {
+    const Carry r = a.carries[2 * t + 1];
+    if (r.h >= 0) {
+      const int h = r.h;
+      const int64_t n = a.offsets[h + 1] - a.offsets[h];
+      double cnt = r.cnt, mean = r.mean, m2 = r.m2;
+      for (int u = t + 1; cnt < (double)n && u < a.ntiles; ++u) {
+        const Carry q = a.carries[2 * u];
+        if (q.h != h) {
+          broken = true;
+          break;
+        }
+        const double nb = q.cnt, nt = cnt + nb, delta = q.mean - mean;
+        mean += delta * nb / nt;
+        m2 += q.m2 + delta * delta * cnt * nb / nt;
+        cnt = nt;
+      }
+      if (cnt != (double)n) broken = true;
+      ai = mean;
+      av = m2 / ((double)n * (double)(n - 1));
+      const float ell = __fmul_rn(a.half_beta, log2r(m2 / (double)(n - 1)));
+      a.ell[h] = ell;
+      lmax = ell;
+      if (a.cube_mean) {
+        a.cube_mean[h] = mean;
+        a.cube_m2[h] = m2;
+      }
+    }
+  }
+  const double si = block_sum(ai, red);
+  const double sv = block_sum(av, red);
+  if (threadIdx.x == 0) {
+    fix_part[2 * blockIdx.x] = si;
+    fix_part[2 * blockIdx.x + 1] = sv;
+  }
+  for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(a.ellmax_key, float_key(lmax));
+  if (broken) atomicOr(a.flags, 2);
+}
+
+// (I_t, sigma_t^2) = (sum mean_h / N_h, sum M2_h/(n_h(n_h-1)) / N_h^2), Eqs. (5)-(6)
+__global__ void results_kernel(const double* __restrict__ cta_part, int ncta, const double* __restrict__ fix_part,
+                               int nfix, int NH, double* result) {
+  __shared__ double red[32];
+  double si = 0.0, sv = 0.0;
+  for (int i = threadIdx.x; i < ncta; i += blockDim.x) {
+    si += cta_part[2 * i];
+    sv += cta_part[2 * i + 1];
+  }
+  for (int i = threadIdx.x; i < nfix; i += blockDim.x) {
+    si += fix_part[2 * i];
+    sv += fix_part[2 * i + 1];
+  }
+  si = block_sum(si, red);
+  sv = block_sum(sv, red);
+  if (threadIdx.x == 0) {
+    result[0] = si / (double)NH;
+    result[1] = sv / ((double)NH * (double)NH);
+  }
+}
+
+// map weights: sum the per-CTA histograms in CTA order
+__global__ void bins_kernel(const double* __restrict__ hist_part, int ncta, int dG, double* bins) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= dG) return;
+  double s = 0.0;
+  for (int c = 0; c < ncta; ++c) s += hist_part[(size_t)c * dG + b];
+  bins[b] = s;
+}
+
+// magic multiplier for n / s with n < 2^31 (Granlund & Montgomery, PLDI'94,
+// Thm 4.2): l = ceil(log2 s), m = ceil(2^(31+l) / s), n / s = (n m) >> (31+l)
+void magic_div(uint32_t s, uint32_t& m, uint32_t& shift) {
+  uint32_t l = 0;
+  while ((uint64_t(1) << l) < s) ++l;
+  m = (uint32_t)(((uint64_t(1) << (31 + l)) + s - 1) / s);
+  shift = 31 + l;
+}
+
+}  // namespace
+}  // namespace vg
+
+using namespace vg;
+
+extern "C" size_t vegas_fill_scratch_bytes(const vegas_geometry* g, int64_t neval) {
+  if (!g || g->dim < 1 || g->dim > kMaxDim || g->nbins < 2 || g->nbins > kMaxBins || neval < 1) return 0;
+  return scratch_layout(g->dim, g->nbins, neval, num_sms()).total;
+}
+
+namespace vg {
+int fill_impl(const vegas_geometry* g, int precision, int integrand, const double* d_params, int64_t nparams,
+              int64_t neval, uint64_t seed, int32_t iteration, uint32_t problem_id, double beta,
+              const double* d_edges, const int64_t* d_offsets, float* d_ell, double* d_bins, double* d_result,
+              double* d_cube_mean, double* d_cube_m2, int* d_flags, void* d_scratch, size_t scratch_bytes,
+              void* stream, cudaEvent_t ev_before, cudaEvent_t ev_after) {
+  if (!g || !g->nstrat || g->dim < 1 || g->dim > kMaxDim || g->nbins < 2 || g->nbins > kMaxBins)
+    return VEGAS_EINVAL;
+  if (precision != VEGAS_FP64 && precision != VEGAS_FP32) return VEGAS_EINVAL;
+  if (!d_edges || !d_offsets || !d_ell || !d_bins || !d_result || !d_flags || !d_scratch) return VEGAS_EINVAL;
+  if ((d_cube_mean == nullptr) != (d_cube_m2 == nullptr)) return VEGAS_EINVAL;
+  if (nparams > 0 && !d_params) return VEGAS_EINVAL;
+  if (!(beta >= 0.0 && beta <= 1.0) || iteration < 0 || problem_id > 0xFFFFu) return VEGAS_EINVAL;
+  const int d = g->dim, G = g->nbins;
+  int64_t NH = 1;
+  for (int k = 0; k < d; ++k) {
+    if (g->nstrat[k] < 1) return VEGAS_EINVAL;
+    if (precision == VEGAS_FP32 && g->nstrat[k] > 65536) return VEGAS_EINVAL;
+    NH *= g->nstrat[k];
+    if (NH >= (int64_t(1) << 31)) return VEGAS_EINVAL;
+  }
+  if (neval < 2 * NH || neval > kMaxEval) return VEGAS_EINVAL;
+  const int npd = derived_param_count(integrand, d, nullptr, nparams);
+  if (npd < 0 || npd > kMaxDerivedParams) return VEGAS_EINVAL;
+
+  const int sms = num_sms();
+  if (sms <= 0) return VEGAS_ECUDA;
+  const ScratchLayout L = scratch_layout(d, G, neval, sms);
+  if (scratch_bytes < L.total) return VEGAS_ENOSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char* sc = (unsigned char*)d_scratch;
+
+  FillArgs a{};
+  a.d = d;
+  a.G = G;
+  a.NH = (int)NH;
+  a.ntiles = L.ntiles;
+  a.neval = neval;
+  a.key0 = (uint32_t)seed;
+  a.key1 = (uint32_t)(seed >> 32);
+  a.iter = (uint32_t)iteration;
+  a.pid = problem_id;
+  a.half_beta = (float)beta * 0.5f;
+  a.np_derived = npd;
+  a.edges = d_edges;
+  a.offsets = d_offsets;
+  a.tile_first = (const int32_t*)(sc + L.tile_first);
+  a.params_raw = d_params;
+  a.np_raw = (int)nparams;
+  a.ell = d_ell;
+  a.cube_mean = d_cube_mean;
+  a.cube_m2 = d_cube_m2;
+  a.flags = d_flags;
+  a.ellmax_key = (int*)(sc + L.ellmax);
+  a.carries = (Carry*)(sc + L.carries);
+  a.cta_part = (double*)(sc + L.cta_part);
+  a.hist_part = (double*)(sc + L.hist_part);
+  a.gtable = sc + L.gtable;
+  for (int k = 0; k < d; ++k) {
+    a.nstrat[k] = (uint32_t)g->nstrat[k];
+    magic_div(a.nstrat[k], a.magic[k], a.shift[k]);
+  }
+  const size_t tsz = precision == VEGAS_FP64 ? sizeof(double) : sizeof(float);
+  if (smem_layout(a, tsz, npd) != VEGAS_OK) return VEGAS_EINVAL;
+
+  const int dmax = dmax_for(d);
+  const int per_sm = precision == VEGAS_FP64 ? fill_occupancy_f64(integrand, dmax, a.sm_total)
+                                             : fill_occupancy_f32(integrand, dmax, a.sm_total);
+  if (per_sm <= 0) return VEGAS_ECUDA;
+  const int grid = std::max(1, std::min(L.grid_max, per_sm * sms));
+
+  tile_first_kernel<<<(L.ntiles + 255) / 256, 256, 0, s>>>(d_offsets, a.NH, L.ntiles, (int32_t*)(sc + L.tile_first),
+                                                            a.ellmax_key);
+  VG_CHECK(cudaGetLastError());
+  if (!a.hist_smem) VG_CHECK(cudaMemsetAsync(a.hist_part, 0, sizeof(double) * (size_t)grid * d * G, s));
+  if (!a.table_smem) {
+    const int n = d * G;
+    if (precision == VEGAS_FP64) table_kernel<double><<<(n + 255) / 256, 256, 0, s>>>(d_edges, d, G, (TabEntry<double>*)a.gtable);
+    else table_kernel<float><<<(n + 255) / 256, 256, 0, s>>>(d_edges, d, G, (TabEntry<float>*)a.gtable);
+    VG_CHECK(cudaGetLastError());
+  }
+  if (ev_before) VG_CHECK(cudaEventRecord(ev_before, s));
+  const int rc = precision == VEGAS_FP64 ? launch_fill_f64(integrand, dmax, a, grid, s)
+                                         : launch_fill_f32(integrand, dmax, a, grid, s);
+  if (rc != VEGAS_OK) return rc;
+  if (ev_after) VG_CHECK(cudaEventRecord(ev_after, s));
+  double* fix_part = (double*)(sc + L.fix_part);
+  fixup_kernel<<<L.nfix, 256, 0, s>>>(a, fix_part);
+  VG_CHECK(cudaGetLastError());
+  results_kernel<<<1, 256, 0, s>>>(a.cta_part, grid, fix_part, L.nfix, a.NH, d_result);
+  VG_CHECK(cudaGetLastError());
+  bins_kernel<<<(d * G + 255) / 256, 256, 0, s>>>(a.hist_part, grid, d * G, d_bins);
+  VG_CHECK(cudaGetLastError());
+  return VEGAS_OK;
+}
+}  // namespace vg
+
+extern "C" int vegas_fill(const vegas_geometry* g, int precision, int integrand, const double* d_params,
+                          int64_t nparams, int64_t neval, uint64_t seed, int32_t iteration, uint32_t problem_id,
+                          double beta, const double* d_edges, const int64_t* d_offsets, float* d_ell,
+                          double* d_bins, double* d_result, double* d_cube_mean, double* d_cube_m2, int* d_flags,
+                          void* d_scratch, size_t scratch_bytes, void* stream) {
+  return fill_impl(g, precision, integrand, d_params, nparams, neval, seed, iteration, problem_id, beta, d_edges,
+                   d_offsets, d_ell, d_bins, d_result, d_cube_mean, d_cube_m2, d_flags, d_scratch, scratch_bytes,
+                   stream, nullptr, nullptr);
+}
+

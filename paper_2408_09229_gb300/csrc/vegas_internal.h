@@ -1,0 +1,85 @@
+// vegas_internal.h -- host-side declarations shared by the library's .cu files.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/vegas.h"
+
+namespace vg {
+
+constexpr int kMaxDim = 32;
+constexpr int kMaxBins = 4096;
+constexpr int kFillThreads = 256;
+constexpr int kSamplesPerThread = 4;
+constexpr int kTile = kFillThreads * kSamplesPerThread;  // evaluations per tile
+constexpr int kMaxCubesPerTile = kTile / 2 + 3;          // n_h >= 2 bounds the cubes a tile meets
+constexpr int kLongSegment = 32;                         // longer cube segments go to a warp
+constexpr int kMaxDerivedParams = 8192;
+constexpr int kAllocThreads = 256;
+constexpr int kAllocItems = 16;  // cubes per thread in the allocation scan
+constexpr int64_t kMaxEval = (int64_t(1) << 31) - 1;
+
+// Per-tile record of a cube that crosses a tile edge: the tile's part of its
+// evaluations as (count, mean, centred second moment).
+struct Carry {
+  int32_t h;    // cube, -1 when the slot is empty
+  int32_t cnt;  // evaluations of the cube inside the tile
+  double mean;
+  double m2;
+};
+
+// Everything the fill kernel needs; passed by value.
+struct FillArgs {
+  int d, G, NH, ntiles;
+  int64_t neval;
+  uint32_t key0, key1, iter, pid;
+  float half_beta;
+  int table_smem, hist_smem;  // 1: map table / map-weight histogram in shared memory
+  int np_derived;
+  const double* edges;     // [d][G+1] FP64
+  const int64_t* offsets;  // [NH+1]
+  const int32_t* tile_first;
+  const double* params_raw;  // caller params (device)
+  int np_raw;
+  float* ell;
+  double* cube_mean;
+  double* cube_m2;
+  int* flags;
+  int* ellmax_key;
+  Carry* carries;       // [2*ntiles]
+  double* cta_part;     // [grid][2]
+  double* hist_part;    // [grid][d*G]
+  void* gtable;         // global map table when it does not fit in shared memory
+  uint32_t nstrat[kMaxDim], magic[kMaxDim], shift[kMaxDim];
+  // shared-memory byte offsets of the regions
+  int sm_table, sm_hist, sm_params, sm_off, sm_invn, sm_vals, sm_long, sm_misc, sm_total;
+};
+
+// launchers (one per precision, defined in vegas_fill_f64.cu / vegas_fill_f32.cu)
+int launch_fill_f64(int integrand, int dmax, FillArgs& a, int grid, cudaStream_t s);
+int launch_fill_f32(int integrand, int dmax, FillArgs& a, int grid, cudaStream_t s);
+int fill_occupancy_f64(int integrand, int dmax, int smem);
+int fill_occupancy_f32(int integrand, int dmax, int smem);
+
+int fill_impl(const vegas_geometry* g, int precision, int integrand, const double* d_params, int64_t nparams,
+              int64_t neval, uint64_t seed, int32_t iteration, uint32_t problem_id, double beta,
+              const double* d_edges, const int64_t* d_offsets, float* d_ell, double* d_bins, double* d_result,
+              double* d_cube_mean, double* d_cube_m2, int* d_flags, void* d_scratch, size_t scratch_bytes,
+              void* stream, cudaEvent_t ev_before, cudaEvent_t ev_after);
+int launch_record_combine(const double* d_result, int t, double* d_est, double* d_sig, int skip, double* d_out,
+                          cudaStream_t s);
+
+int dmax_for(int d);
+int derived_param_count(int integrand, int d, const double* host_params_or_null, int64_t np);
+
+// status helpers
+inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? VEGAS_OK : VEGAS_ECUDA; }
+
+}  // namespace vg
+
+#define VG_CHECK(call)                                  \
+  do {                                                  \
+    cudaError_t _e = (call);                            \
+    if (_e != cudaSuccess) return VEGAS_ECUDA;          \
+  } while (0)

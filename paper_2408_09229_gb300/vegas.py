@@ -1,0 +1,251 @@
+"""GB300 (sm_103a) VEGAS+ iteration loop: thin Python binding of the C ABI.
+
+Every function here marshals arguments to the entry point of the same name
+in libvegas_gb300.so (declared in include/vegas.h).  The compute runs only in
+the library's CUDA kernels.  Importing this package fails loudly when the
+library is missing; there is no CPU fallback.  Build the library with
+``python -c "import __graft_entry__ as g; g.build()"`` or with
+``python paper_2408_09229_gb300/build_lib.py``.
+
+Device buffers for the step entry points are torch CUDA tensors.  torch is
+used only for device memory and streams; the pointers go to the library.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from .workloads import (GAUSS_SUM, PRODUCT_PEAK, OSCILLATORY, SIN_EXP, LINEAR, COSINE, EXPONENTIAL,  # noqa: F401
+                        ROOS_ARNOLD, MOROKOFF_CAFLISCH, MAP_DENSITY)
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvegas_gb300.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ESTATE, ENOSPACE = 0, -1, -2, -3, -4, -5, -6, -7
+FP64, FP32 = 0, 1
+
+
+class VegasError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        super().__init__(f"{where}: {strerror(status)} ({status})" if where else strerror(status))
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("estimate", ctypes.c_double), ("sigma", ctypes.c_double), ("chi2_dof", ctypes.c_double),
+                ("neval_total", ctypes.c_int64), ("nitn_run", ctypes.c_int32), ("n_used", ctypes.c_int32),
+                ("it_est", ctypes.POINTER(ctypes.c_double)), ("it_sigma", ctypes.POINTER(ctypes.c_double)),
+                ("it_cap", ctypes.c_int32)]
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("nbins", ctypes.c_int32), ("nstrat", ctypes.POINTER(ctypes.c_int32))]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it first (paper_2408_09229_gb300/build_lib.py); "
+                          "the VEGAS+ loop has no CPU fallback")
+    L = ctypes.CDLL(LIB_PATH)
+    P, i32, i64, f64, u64, u32 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double,
+                                  ctypes.c_uint64, ctypes.c_uint32)
+    sz = ctypes.c_size_t
+    sig = {
+        "vegas_create": ([i32, i32, i32, f64, f64, ctypes.POINTER(P)], i32),
+        "vegas_destroy": ([P], i32),
+        "vegas_set_nstrat_axes": ([P, P, i32], i32),
+        "vegas_set_skip": ([P, i32], i32),
+        "vegas_set_precision": ([P, i32], i32),
+        "vegas_set_stream": ([P, P], i32),
+        "vegas_set_rtol": ([P, f64], i32),
+        "vegas_reset_map": ([P], i32),
+        "vegas_integrate": ([P, i32, P, i64, i64, i32, u64, ctypes.POINTER(Result)], i32),
+        "vegas_get_timings": ([P, P, P, i32, ctypes.POINTER(i32)], i32),
+        "vegas_get_state": ([P, P, ctypes.POINTER(sz)], i32),
+        "vegas_set_state": ([P, P, sz], i32),
+        "vegas_get_edges": ([P, P, sz], i32),
+        "vegas_strerror": ([i32], ctypes.c_char_p),
+        "vegas_allocate_scratch_bytes": ([i64], sz),
+        "vegas_allocate": ([P, i64, i64, i32, P, P, sz, P], i32),
+        "vegas_fill_scratch_bytes": ([ctypes.POINTER(Geometry), i64], sz),
+        "vegas_fill": ([ctypes.POINTER(Geometry), i32, i32, P, i64, i64, u64, i32, u32, f64, P, P, P, P, P, P, P,
+                        P, P, sz, P], i32),
+        "vegas_refine": ([i32, i32, f64, P, P, P, P], i32),
+        "vegas_combine": ([P, P, i32, i32, P, P], i32),
+        "vegas_probe_pipes": ([P], i32),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    return L
+
+
+lib = _load()
+
+
+def strerror(status):
+    return lib.vegas_strerror(status).decode()
+
+
+def _check(status, where):
+    if status != OK:
+        raise VegasError(status, where)
+
+
+def _ptr(t):
+    """device pointer of a torch tensor (or None)"""
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+# ---------------------------------------------------------------------------
+# Level 1: handle
+# ---------------------------------------------------------------------------
+class Vegas:
+    """A VEGAS+ integrator on the current CUDA device (vegas_create ... vegas_destroy)."""
+
+    def __init__(self, dim, nbins=50, nstrat=0, alpha=0.5, beta=0.75, precision=FP64, skip=0, rtol=0.0,
+                 nstrat_axes=None, stream=None):
+        h = ctypes.c_void_p()
+        _check(lib.vegas_create(dim, nbins, nstrat, alpha, beta, ctypes.byref(h)), "vegas_create")
+        self._h = h
+        self.dim, self.nbins = dim, nbins
+        self.set_precision(precision)
+        self.set_skip(skip)
+        self.set_rtol(rtol)
+        if nstrat_axes is not None:
+            self.set_nstrat_axes(nstrat_axes)
+        if stream is not None:
+            self.set_stream(stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.vegas_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_precision(self, precision):
+        _check(lib.vegas_set_precision(self._h, precision), "vegas_set_precision")
+
+    def set_skip(self, skip):
+        _check(lib.vegas_set_skip(self._h, skip), "vegas_set_skip")
+
+    def set_rtol(self, rtol):
+        _check(lib.vegas_set_rtol(self._h, rtol), "vegas_set_rtol")
+
+    def set_stream(self, stream):
+        _check(lib.vegas_set_stream(self._h, _stream_ptr(stream)), "vegas_set_stream")
+
+    def set_nstrat_axes(self, nstrat):
+        a = np.ascontiguousarray(nstrat, dtype=np.int32)
+        _check(lib.vegas_set_nstrat_axes(self._h, a.ctypes.data_as(ctypes.c_void_p), a.size), "vegas_set_nstrat_axes")
+
+    def reset_map(self):
+        _check(lib.vegas_reset_map(self._h), "vegas_reset_map")
+
+    def integrate(self, integrand, params, neval, nitn, seed=0, check=True):
+        p = np.ascontiguousarray(params, dtype=np.float64) if len(params) else np.zeros(0)
+        it_est = np.zeros(nitn)
+        it_sig = np.zeros(nitn)
+        r = Result()
+        r.it_est = it_est.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        r.it_sigma = it_sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        r.it_cap = nitn
+        st = lib.vegas_integrate(self._h, integrand, p.ctypes.data_as(ctypes.c_void_p) if p.size else None, p.size,
+                                 int(neval), int(nitn), int(seed), ctypes.byref(r))
+        if check and st not in (OK, ENONFINITE):
+            raise VegasError(st, "vegas_integrate")
+        n = r.nitn_run
+        return {"estimate": r.estimate, "sigma": r.sigma, "chi2_dof": r.chi2_dof, "n_used": r.n_used,
+                "nitn_run": n, "neval_total": r.neval_total, "it_est": it_est[:n], "it_sig": it_sig[:n],
+                "status": st}
+
+    def timings(self, cap=4096):
+        it = np.zeros(cap, dtype=np.float32)
+        fl = np.zeros(cap, dtype=np.float32)
+        n = ctypes.c_int32()
+        _check(lib.vegas_get_timings(self._h, it.ctypes.data_as(ctypes.c_void_p), fl.ctypes.data_as(ctypes.c_void_p),
+                                     cap, ctypes.byref(n)), "vegas_get_timings")
+        m = min(n.value, cap)
+        return it[:m].copy(), fl[:m].copy()
+
+    def get_state(self):
+        size = ctypes.c_size_t()
+        _check(lib.vegas_get_state(self._h, None, ctypes.byref(size)), "vegas_get_state")
+        buf = ctypes.create_string_buffer(size.value)
+        _check(lib.vegas_get_state(self._h, buf, ctypes.byref(size)), "vegas_get_state")
+        return buf.raw[:size.value]
+
+    def set_state(self, blob):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(lib.vegas_set_state(self._h, buf, len(blob)), "vegas_set_state")
+
+    def edges(self):
+        e = np.zeros((self.dim, self.nbins + 1))
+        _check(lib.vegas_get_edges(self._h, e.ctypes.data_as(ctypes.c_void_p), e.size), "vegas_get_edges")
+        return e
+
+
+# ---------------------------------------------------------------------------
+# Level 2: step entry points on torch CUDA tensors
+# ---------------------------------------------------------------------------
+def _geometry(dim, nbins, nstrat):
+    ns = np.ascontiguousarray(nstrat if not isinstance(nstrat, int) else [nstrat] * dim, dtype=np.int32)
+    g = Geometry(dim, nbins, ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    g._keep = ns
+    return g
+
+
+def allocate_scratch_bytes(ncubes):
+    return lib.vegas_allocate_scratch_bytes(int(ncubes))
+
+
+def allocate(ell, ncubes, neval, uniform, offsets, scratch, stream=None):
+    """vegas_allocate: ell (float32 [ncubes] or None), offsets (int64 [ncubes+1]), scratch (uint8)."""
+    _check(lib.vegas_allocate(_ptr(ell), int(ncubes), int(neval), int(bool(uniform)), _ptr(offsets), _ptr(scratch),
+                              scratch.numel(), _stream_ptr(stream)), "vegas_allocate")
+
+
+def fill_scratch_bytes(dim, nbins, nstrat, neval):
+    g = _geometry(dim, nbins, nstrat)
+    return lib.vegas_fill_scratch_bytes(ctypes.byref(g), int(neval))
+
+
+def fill(dim, nbins, nstrat, precision, integrand, params, neval, seed, iteration, beta, edges, offsets, ell, bins,
+         result, flags, scratch, cube_mean=None, cube_m2=None, problem_id=0, stream=None):
+    """vegas_fill on torch CUDA tensors: params/edges/bins/result/cube_* float64, offsets int64,
+    ell float32, flags int32, scratch uint8."""
+    g = _geometry(dim, nbins, nstrat)
+    _check(lib.vegas_fill(ctypes.byref(g), precision, integrand, _ptr(params) if params is not None and
+                          params.numel() else None, 0 if params is None else params.numel(), int(neval), int(seed),
+                          int(iteration), int(problem_id), float(beta), _ptr(edges), _ptr(offsets), _ptr(ell),
+                          _ptr(bins), _ptr(result), _ptr(cube_mean), _ptr(cube_m2), _ptr(flags), _ptr(scratch),
+                          scratch.numel(), _stream_ptr(stream)), "vegas_fill")
+
+
+def refine(dim, nbins, alpha, bins, edges_in, edges_out, stream=None):
+    _check(lib.vegas_refine(dim, nbins, float(alpha), _ptr(bins), _ptr(edges_in), _ptr(edges_out),
+                            _stream_ptr(stream)), "vegas_refine")
+
+
+def combine(it_est, it_sig, skip, out, stream=None):
+    _check(lib.vegas_combine(_ptr(it_est), _ptr(it_sig), it_est.numel(), int(skip), _ptr(out), _stream_ptr(stream)),
+           "vegas_combine")
+
+
+def probe_pipes():
+    """(FP32 FMA, FP64 FMA, MUFU ex2, IMAD.HI) issue rates in operations per SM per clock"""
+    r = np.zeros(4)
+    _check(lib.vegas_probe_pipes(r.ctypes.data_as(ctypes.c_void_p)), "vegas_probe_pipes")
+    return r

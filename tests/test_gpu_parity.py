@@ -1,0 +1,372 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer work is compared bit for bit; floating point within the tolerances
+below, each derived in DESIGN.md ("Tolerances"):
+  FP64 path, same points and map as the oracle: cube means 1e-12 relative
+    (plus 1e-12 of the largest mean); I_t 1e-12; map weights 1e-12; sigma_t^2
+    1e-10 (the centred moments inherit the cancellation of near-equal
+    samples); refined edges 1e-13 absolute; allocation weights ell within
+    4 float ulps.
+  FP32 path against the oracle on the same FP32 points: I_t 2e-5 relative,
+    sigma_t^2 2e-3 relative, cube means 5e-4 relative of the largest mean.
+Inputs are seeded and synthetic; sizes span several tiles (1024 evaluations)
+and a ragged last tile, plus the full 1e8-evaluation, 43-million-cube
+configuration checked on sampled cubes.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from paper_2408_09229_gb300 import workloads as W  # noqa: E402
+
+TILE = 1024
+
+
+@pytest.fixture(scope="module")
+def V():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2408_09229_gb300 import vegas
+    assert torch.cuda.is_available()
+    return vegas
+
+
+def dev(a, dtype=None):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype).cuda()
+
+
+def gpu_fill(V, cfg, precision, iid, params, neval, t, seed, edges, offsets, beta=0.75, want_cubes=True):
+    nh = cfg.ncubes
+    sb = V.fill_scratch_bytes(cfg.dim, cfg.nbins, list(cfg.nstrat), neval)
+    scratch = torch.empty(sb, dtype=torch.uint8, device="cuda")
+    ell = torch.full((nh,), float("nan"), dtype=torch.float32, device="cuda")
+    bins = torch.zeros(cfg.dim * cfg.nbins, dtype=torch.float64, device="cuda")
+    result = torch.zeros(2, dtype=torch.float64, device="cuda")
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+    cm = torch.full((nh,), float("nan"), dtype=torch.float64, device="cuda") if want_cubes else None
+    c2 = torch.full((nh,), float("nan"), dtype=torch.float64, device="cuda") if want_cubes else None
+    p = dev(params, torch.float64) if len(params) else None
+    V.fill(cfg.dim, cfg.nbins, list(cfg.nstrat), precision, iid, p, neval, seed, t, beta,
+           dev(edges, torch.float64), dev(offsets, torch.int64), ell, bins, result, flags, scratch, cm, c2)
+    torch.cuda.synchronize()
+    out = {"ell": ell.cpu().numpy(), "bins": bins.cpu().numpy().reshape(cfg.dim, cfg.nbins),
+           "est": float(result[0]), "var": float(result[1]), "flags": int(flags[0])}
+    if want_cubes:
+        out["mean"] = cm.cpu().numpy()
+        out["m2"] = c2.cpu().numpy()
+    return out
+
+
+def gpu_allocate(V, ell, nh, neval, uniform):
+    scratch = torch.empty(V.allocate_scratch_bytes(nh), dtype=torch.uint8, device="cuda")
+    off = torch.full((nh + 1,), -1, dtype=torch.int64, device="cuda")
+    e = dev(ell, torch.float32) if ell is not None else None
+    V.allocate(e, nh, neval, uniform, off, scratch)
+    torch.cuda.synchronize()
+    return off.cpu().numpy()
+
+
+def random_edges(rng, d, G):
+    return np.stack([np.concatenate([[0.0], np.sort(rng.random(G - 1)), [1.0]]) for _ in range(d)])
+
+
+def ulp_diff_float32(a, b):
+    a = np.asarray(a, np.float32).view(np.int32).astype(np.int64)
+    b = np.asarray(b, np.float32).view(np.int32).astype(np.int64)
+    return np.abs(a - b)
+
+
+# ---------------------------------------------------------------------------
+# allocation (updateEvalsPerCube + mapEvalsToCubes): bit-exact
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("nh,extra", [(1, 0), (1, 12345), (7, 3), (4095, 9999), (4096, 1), (4097, 77777),
+                                      (38416, 100000 - 2 * 38416), (1_000_003, 3_000_001)])
+def test_allocate_bit_exact(V, orc, nh, extra):
+    rng = np.random.default_rng(nh)
+    neval = 2 * nh + extra
+    ell = rng.normal(-3, 6, nh).astype(np.float32)
+    ell[rng.random(nh) < 0.05] = -np.inf
+    want = orc.allocate(ell, nh, neval, 0.75)
+    got = gpu_allocate(V, ell, nh, neval, False)
+    assert np.array_equal(got, want)
+    want_u = orc.allocate(None, nh, neval, 0.75)
+    got_u = gpu_allocate(V, None, nh, neval, True)
+    assert np.array_equal(got_u, want_u)
+
+
+def test_allocate_all_zero_variance_is_uniform(V, orc):
+    ell = np.full(5000, -np.inf, dtype=np.float32)
+    assert np.array_equal(gpu_allocate(V, ell, 5000, 20000, False), orc.allocate(None, 5000, 20000, 0.75))
+
+
+def test_allocate_full_size(V, orc):
+    # 9^8 = 43,046,721 cubes and 1e8 evaluations: the d = 8 configuration
+    nh, neval = 9 ** 8, 100_000_000
+    rng = np.random.default_rng(8)
+    ell = (rng.standard_normal(nh, dtype=np.float32) * 4).astype(np.float32)
+    want = orc.allocate(ell, nh, neval, 0.75)
+    got = gpu_allocate(V, ell, nh, neval, False)
+    assert np.array_equal(got, want)
+
+
+def test_allocate_rejects_bad_sizes(V):
+    scratch = torch.empty(4096, dtype=torch.uint8, device="cuda")
+    off = torch.empty(11, dtype=torch.int64, device="cuda")
+    with pytest.raises(V.VegasError) as e:
+        V.allocate(None, 10, 19, True, off, scratch)
+    assert e.value.status == V.EINVAL
+    with pytest.raises(V.VegasError) as e:
+        V.allocate(None, 10, 40, True, off, torch.empty(1, dtype=torch.uint8, device="cuda"))
+    assert e.value.status == V.ENOSPACE
+
+
+# ---------------------------------------------------------------------------
+# fill (Algorithm 2): FP64 against the oracle on the same points and map
+# ---------------------------------------------------------------------------
+FILL_CASES = [
+    # name, d, G, nstrat, iid, params, neval
+    ("ridge d4 cfg1", 4, 50, 14, W.GAUSS_SUM, W.ridge4_params(), 100_000),
+    ("ridge d8 small", 8, 50, 3, W.GAUSS_SUM, W.ridge(8, 5, 0.05), 50_001),
+    ("product peak d5", 5, 30, [3, 2, 4, 1, 2], W.PRODUCT_PEAK, W.product_peak(5, 1), 20_000),
+    ("oscillatory d3", 3, 17, 5, W.OSCILLATORY, W.oscillatory(3, 2), 7_777),
+    ("sin-exp d2", 2, 64, 40, W.SIN_EXP, [], 4_000),
+    ("roos-arnold d10", 10, 20, 2, W.ROOS_ARNOLD, [], 12_345),
+    ("morokoff d8", 8, 10, 2, W.MOROKOFF_CAFLISCH, [], 3_000),
+    ("cosine d16", 16, 8, 1, W.COSINE, [], 5_000),
+    ("exponential d1", 1, 100, 300, W.EXPONENTIAL, [], 2_000),
+    ("linear d32", 32, 4, 1, W.LINEAR, [], 3_333),
+    ("one cube, many tiles", 3, 20, 1, W.GAUSS_SUM, W.ridge(3, 2, 0.1), 300_000),
+    ("two evaluations per cube", 4, 16, 7, W.GAUSS_SUM, W.ridge(4, 3, 0.1), 2 * 7 ** 4),
+    ("paper ridge N=1000", 4, 50, 6, W.GAUSS_SUM, W.paper_ridge(4, 1000), 8_192),
+]
+
+
+@pytest.mark.parametrize("name,d,G,ns,iid,params,neval", FILL_CASES, ids=[c[0] for c in FILL_CASES])
+def test_fill_fp64_matches_oracle(V, orc, name, d, G, ns, iid, params, neval):
+    cfg = orc.Config(d, G, ns, 0.5, 0.75)
+    rng = np.random.default_rng(len(name))
+    edges = random_edges(rng, d, G) if "one cube" not in name else cfg.uniform_edges()
+    ell = rng.normal(0, 5, cfg.ncubes).astype(np.float32)
+    off = orc.allocate(ell, cfg.ncubes, neval, 0.75)
+    t, seed = 3, 12345
+    g = gpu_fill(V, cfg, V.FP64, iid, params, neval, t, seed, edges, off)
+    r = orc.iteration(cfg, iid, params, neval, t, seed, edges, off)
+    assert g["flags"] == 0
+    big = np.abs(r["mean"]).max()
+    assert np.allclose(g["mean"], r["mean"], rtol=1e-12, atol=1e-12 * big)
+    assert np.allclose(g["m2"], r["m2"], rtol=1e-9, atol=1e-12 * max(np.abs(r["m2"]).max(), 1e-300))
+    assert g["est"] == pytest.approx(r["est"], rel=1e-12, abs=1e-300)
+    assert g["var"] == pytest.approx(r["var"], rel=1e-10, abs=1e-300)
+    assert np.allclose(g["bins"], r["bins"], rtol=1e-12, atol=1e-12 * r["bins"].max())
+    fin = np.isfinite(r["ell"])
+    assert np.array_equal(np.isfinite(g["ell"]), fin)
+    assert ulp_diff_float32(g["ell"][fin], r["ell"][fin]).max() <= 4
+
+
+def test_fill_map_density_unit_weights(V, orc):
+    # the map's own density: J f = 1 for every evaluation, on the GPU too
+    d, G = 3, 9
+    cfg = orc.Config(d, G, [2, 3, 2], 0.5, 0.75)
+    edges = random_edges(np.random.default_rng(1), d, G)
+    off = orc.allocate(None, cfg.ncubes, 5000, 0.75)
+    g = gpu_fill(V, cfg, V.FP64, W.MAP_DENSITY, edges.ravel(), 5000, 0, 9, edges, off)
+    assert g["est"] == pytest.approx(1.0, rel=1e-13)
+    assert g["var"] < 1e-26
+    assert np.allclose(g["mean"], 1.0, rtol=1e-13)
+
+
+def test_fill_nonfinite_flag(V, orc):
+    cfg = orc.Config(2, 8, 2, 0.5, 0.75)
+    params = W.gauss_sum(2, [[0.5, 0.5]], 0.1, math.inf)
+    off = orc.allocate(None, cfg.ncubes, 100, 0.75)
+    g = gpu_fill(V, cfg, V.FP64, W.GAUSS_SUM, params, 100, 0, 0, cfg.uniform_edges(), off)
+    assert g["flags"] & 1
+
+
+# ---------------------------------------------------------------------------
+# fill: FP32 evaluation path against the oracle on the same FP32 points
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name,d,G,ns,iid,params,neval", FILL_CASES[:4] + FILL_CASES[10:12],
+                         ids=[c[0] for c in FILL_CASES[:4] + FILL_CASES[10:12]])
+def test_fill_fp32_matches_oracle(V, orc, name, d, G, ns, iid, params, neval):
+    cfg = orc.Config(d, G, ns, 0.5, 0.75, points_f32=True)
+    rng = np.random.default_rng(len(name) + 1)
+    edges = random_edges(rng, d, G)
+    ell = rng.normal(0, 5, cfg.ncubes).astype(np.float32)
+    off = orc.allocate(ell, cfg.ncubes, neval, 0.75)
+    g = gpu_fill(V, cfg, V.FP32, iid, params, neval, 1, 77, edges, off)
+    r = orc.iteration(cfg, iid, params, neval, 1, 77, edges, off)
+    assert g["flags"] == 0
+    assert g["est"] == pytest.approx(r["est"], rel=2e-5)
+    assert g["var"] == pytest.approx(r["var"], rel=2e-3)
+    assert np.allclose(g["mean"], r["mean"], rtol=0, atol=5e-4 * np.abs(r["mean"]).max())
+    assert np.allclose(g["bins"], r["bins"], rtol=0, atol=1e-3 * r["bins"].max())
+
+
+# ---------------------------------------------------------------------------
+# map refinement and combination
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("d,G,alpha", [(1, 2, 0.5), (4, 50, 0.5), (8, 50, 1.5), (3, 1024, 0.5), (2, 4096, 1.0)])
+def test_refine_matches_oracle(V, orc, d, G, alpha):
+    rng = np.random.default_rng(G + d)
+    edges = random_edges(rng, d, G)
+    w = rng.exponential(1.0, (d, G)) * (rng.random((d, G)) < 0.8)
+    if d > 2:
+        w[1] = 0.0          # zero weights: axis unchanged
+        w[2, 3] = np.nan    # non-finite weight: axis unchanged
+    e_out = torch.zeros((d, G + 1), dtype=torch.float64, device="cuda")
+    V.refine(d, G, alpha, dev(w, torch.float64), dev(edges, torch.float64), e_out)
+    got = e_out.cpu().numpy()
+    for k in range(d):
+        want, _ = orc.refine_axis(w[k], edges[k], alpha)
+        assert np.allclose(got[k], want, rtol=0, atol=1e-13), k
+        assert np.all(np.diff(got[k]) > 0)
+
+
+def test_combine_matches_oracle(V, orc):
+    rng = np.random.default_rng(3)
+    for n, skip in [(1, 0), (5, 0), (10, 3), (4, 4)]:
+        I = rng.normal(1, 0.1, n)
+        S = rng.uniform(0.01, 0.2, n)
+        out = torch.zeros(4, dtype=torch.float64, device="cuda")
+        V.combine(dev(I, torch.float64), dev(S, torch.float64), skip, out)
+        got = out.cpu().numpy()
+        want = orc.combine(I, S, skip)
+        if want["n_used"] == 0:
+            assert got[3] == 0 and np.isnan(got[0])
+            continue
+        assert got[0] == pytest.approx(want["estimate"], rel=1e-14)
+        assert got[1] == pytest.approx(want["sigma"], rel=1e-14)
+        assert got[2] == pytest.approx(want["chi2_dof"], rel=1e-12, abs=1e-15)
+        assert got[3] == want["n_used"]
+
+
+# ---------------------------------------------------------------------------
+# whole iterations through the handle
+# ---------------------------------------------------------------------------
+def test_integrate_fp64_matches_oracle_ridge4(V, orc):
+    p = W.ridge4_params()
+    cfg = orc.Config(4, 50, orc.default_nstrat(100_000, 4), 0.5, 0.75)
+    want = orc.integrate(cfg, W.GAUSS_SUM, p, 100_000, 10, seed=0)
+    v = V.Vegas(4, 50, 0, 0.5, 0.75)
+    got = v.integrate(W.GAUSS_SUM, p, 100_000, 10, seed=0)
+    assert np.allclose(got["it_est"], want["it_est"], rtol=1e-10)
+    assert np.allclose(got["it_sig"], want["it_sig"], rtol=1e-8)
+    assert got["estimate"] == pytest.approx(want["estimate"], rel=1e-10)
+    assert abs(got["estimate"] - 1.0) < 4 * got["sigma"]
+    e_gpu = v.edges()
+    assert np.allclose(e_gpu, want["edges"], rtol=0, atol=1e-10)
+
+
+def test_state_injection_each_iteration(V, orc):
+    """every iteration from the oracle's own state: offsets bit-exact, sums to 1e-12"""
+    p = W.ridge4_params()
+    d, G, neval = 4, 50, 100_000
+    cfg = orc.Config(d, G, 14, 0.5, 0.75)
+    edges = cfg.uniform_edges()
+    off = orc.allocate(None, cfg.ncubes, neval, 0.75)
+    for t in range(5):
+        r = orc.iteration(cfg, W.GAUSS_SUM, p, neval, t, 0, edges, off)
+        g = gpu_fill(V, cfg, V.FP64, W.GAUSS_SUM, p, neval, t, 0, edges, off)
+        assert g["est"] == pytest.approx(r["est"], rel=1e-12)
+        assert g["var"] == pytest.approx(r["var"], rel=1e-10)
+        # allocation from the oracle's weights: bit-exact
+        assert np.array_equal(gpu_allocate(V, r["ell"], cfg.ncubes, neval, False), r["offsets_next"])
+        e_out = torch.zeros((d, G + 1), dtype=torch.float64, device="cuda")
+        V.refine(d, G, 0.5, dev(r["bins"], torch.float64), dev(edges, torch.float64), e_out)
+        assert np.allclose(e_out.cpu().numpy(), r["edges_next"], rtol=0, atol=1e-13)
+        edges, off = r["edges_next"], r["offsets_next"]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name,iid,d,params,neval,nitn", [
+    ("ridge d4", W.GAUSS_SUM, 4, W.ridge4_params(), 100_000, 10),
+    ("product peak d8", W.PRODUCT_PEAK, 8, W.product_peak8_params(), 1_000_000, 10),
+    ("oscillatory d6", W.OSCILLATORY, 6, W.oscillatory(6, 3), 200_000, 6),
+    ("roos-arnold d10", W.ROOS_ARNOLD, 10, [], 1_000_000, 8),
+    ("morokoff d8", W.MOROKOFF_CAFLISCH, 8, [], 1_000_000, 8),
+    ("paper ridge d4", W.GAUSS_SUM, 4, W.paper_ridge(4, 1000), 1_000_000, 6),
+])
+def test_integrate_closed_form(V, name, iid, d, params, neval, nitn, precision):
+    v = V.Vegas(d, 50, 0, 0.5, 0.75, precision=precision)
+    r = v.integrate(iid, params, neval, nitn, seed=1)
+    exact = W.exact(iid, d, params)
+    assert r["status"] == 0
+    assert abs(r["estimate"] - exact) < 4 * r["sigma"], (r["estimate"], r["sigma"], exact)
+
+
+def test_full_size_ridge8_sampled_cubes(V, orc):
+    """d = 8, 1e8 evaluations, 9^8 cubes: sampled cubes against the oracle one by one"""
+    d, G, neval = 8, 50, 100_000_000
+    p = W.ridge8_params()
+    cfg = orc.Config(d, G, 9, 0.5, 0.75)
+    nh = cfg.ncubes
+    rng = np.random.default_rng(5)
+    edges = random_edges(rng, d, G)
+    ell = (rng.standard_normal(nh, dtype=np.float32) * 3).astype(np.float32)
+    ell[:10] = 40.0  # a few very heavy cubes that cross many tiles
+    off = orc.allocate(ell, nh, neval, 0.75)
+    g = gpu_fill(V, cfg, V.FP64, W.GAUSS_SUM, p, neval, 2, 4, edges, off)
+    n = np.diff(off)
+    assert n.sum() == neval
+    starts = off[:-1]
+    crossing = np.nonzero((starts // TILE) != ((off[1:] - 1) // TILE))[0]
+    picks = np.concatenate([np.arange(10), rng.choice(nh, 24, replace=False), rng.choice(crossing, 16),
+                            [nh - 1, int(np.argmax(n))]])
+    for h in picks:
+        m, q = orc.cube_stats(cfg, W.GAUSS_SUM, p, 2, 4, edges, h, off[h], n[h])
+        assert g["mean"][h] == pytest.approx(m, rel=1e-12, abs=1e-300), h
+        assert g["m2"][h] == pytest.approx(q, rel=1e-9, abs=1e-280), h
+    # the iteration estimate is the mean of the cube means (Eq. (5))
+    assert g["est"] == pytest.approx(np.mean(g["mean"]), rel=1e-12)
+
+
+def test_checkpoint_resume(V):
+    p = W.ridge4_params()
+    a = V.Vegas(4, 50, 0, 0.5, 0.75)
+    full = a.integrate(W.GAUSS_SUM, p, 100_000, 6, seed=7)
+    b = V.Vegas(4, 50, 0, 0.5, 0.75)
+    first = b.integrate(W.GAUSS_SUM, p, 100_000, 3, seed=7)
+    blob = b.get_state()
+    c = V.Vegas(4, 50, 0, 0.5, 0.75)
+    c.set_state(blob)
+    rest = c.integrate(W.GAUSS_SUM, p, 100_000, 3, seed=7)
+    both = np.concatenate([first["it_est"], rest["it_est"]])
+    assert np.allclose(both, full["it_est"], rtol=1e-12)
+
+
+def test_rtol_stops_early(V):
+    v = V.Vegas(4, 50, 0, 0.5, 0.75, rtol=5e-3)
+    r = v.integrate(W.GAUSS_SUM, W.ridge4_params(), 100_000, 50, seed=2)
+    assert r["nitn_run"] < 50
+    assert r["sigma"] <= 5e-3 * abs(r["estimate"])
+
+
+def test_handle_errors(V):
+    with pytest.raises(V.VegasError):
+        V.Vegas(0, 50)
+    with pytest.raises(V.VegasError):
+        V.Vegas(4, 1)
+    with pytest.raises(V.VegasError):
+        V.Vegas(4, 50, beta=1.5)
+    v = V.Vegas(4, 50, 10)
+    with pytest.raises(V.VegasError) as e:
+        v.integrate(W.GAUSS_SUM, W.ridge4_params(), 1000, 1)  # 2 * 10^4 cubes > 1000 evaluations
+    assert e.value.status == V.EINVAL
+    with pytest.raises(V.VegasError):
+        v.integrate(W.PRODUCT_PEAK, [1.0, 2.0], 100000, 1)  # wrong parameter count
+    with pytest.raises(V.VegasError):
+        v.set_state(b"not a state blob at all, definitely not" * 4)
+    r = v.integrate(W.GAUSS_SUM, W.gauss_sum(4, [[0.5] * 4], 0.1, math.inf), 100_000, 1, check=False)
+    assert r["status"] == V.ENONFINITE
+
+
+def test_probe_pipes(V):
+    r = V.probe_pipes()
+    assert np.all(r > 0)
+    assert r[0] > 16  # FP32 FMA per SM per clock
