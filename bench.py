@@ -146,6 +146,14 @@ def run_ours(args, rank, world):
         it_ms, fill_ms = v.timings()
         return v, r, outer_ms, it_ms, fill_ms
 
+    if args.profile:
+        v, r, outer_ms, it_ms, fill_ms = timed_run(V.FP32)
+        if rank == 0:
+            print(json.dumps({"profile": True, "evals_per_s": NEVAL * args.steps / (float(np.sum(it_ms)) / 1e3),
+                              "fill_ms": [float(x) for x in fill_ms], "iteration_ms": [float(x) for x in it_ms],
+                              "estimate": r["estimate"], "sigma": r["sigma"]}))
+        return
+
     stop = threading.Event()
     clock_lines = []
     th = threading.Thread(target=sample_clocks, args=(stop, clock_lines), daemon=True)
@@ -271,6 +279,8 @@ def main():
     ap.add_argument("--steps", type=int, default=NITN)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--profile", action="store_true",
+                    help="profiling run: only the warm-up and timed FP32 iterations, a short JSON line")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -3,7 +3,9 @@
 Integer work is compared bit for bit; floating point within the tolerances
 below, each derived in DESIGN.md ("Tolerances"):
   FP64 path, same points and map as the oracle: cube means 1e-12 relative
-    (plus 1e-12 of the largest mean); I_t 1e-12; map weights 1e-12; sigma_t^2
+    (plus 1e-12 of the largest mean), widened to 2 (n_h - 1) 2^-53 for cubes
+    of n_h > 4500 evaluations, whose sequential sum in the oracle carries
+    that rounding bound; I_t 1e-12; map weights 1e-12; sigma_t^2
     1e-10 (the centred moments inherit the cancellation of near-equal
     samples); refined edges 1e-13 absolute; allocation weights ell within
     4 float ulps.
@@ -318,10 +320,14 @@ def test_full_size_ridge8_sampled_cubes(V, orc):
     crossing = np.nonzero((starts // TILE) != ((off[1:] - 1) // TILE))[0]
     picks = np.concatenate([np.arange(10), rng.choice(nh, 24, replace=False), rng.choice(crossing, 16),
                             [nh - 1, int(np.argmax(n))]])
+    u = 2.0 ** -53
     for h in picks:
         m, q = orc.cube_stats(cfg, W.GAUSS_SUM, p, 2, 4, edges, h, off[h], n[h])
-        assert g["mean"][h] == pytest.approx(m, rel=1e-12, abs=1e-300), h
-        assert g["m2"][h] == pytest.approx(q, rel=1e-9, abs=1e-280), h
+        # the oracle sums a cube's n_h non-negative terms in sequence (error <= (n_h - 1) u of the sum);
+        # the GPU merges tile parts pairwise: the two differ by at most twice that bound
+        rel = max(1e-12, 2 * (n[h] - 1) * u)
+        assert g["mean"][h] == pytest.approx(m, rel=rel, abs=1e-300), h
+        assert g["m2"][h] == pytest.approx(q, rel=max(1e-9, 4 * (n[h] - 1) * u), abs=1e-280), h
     # the iteration estimate is the mean of the cube means (Eq. (5))
     assert g["est"] == pytest.approx(np.mean(g["mean"]), rel=1e-12)
 
