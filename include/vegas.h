@@ -192,6 +192,33 @@ VEGAS_API size_t vegas_allocate_scratch_bytes(int64_t ncubes);
 VEGAS_API int vegas_allocate(const float *d_ell, int64_t ncubes, int64_t neval, int uniform, int64_t *d_offsets,
                    void *d_scratch, size_t scratch_bytes, void *stream);
 
+/* -- vegas_allocate_static: the allocation step without any allocation ----
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory.  Examples are code whose device memory is
+ * owned by another allocator (a framework's caching pool that has reserved the
+ * free memory, or a process held to a fixed budget), and latency-critical
+ * loops, where cudaMalloc or cudaFree would synchronise the device or fail.
+ * It computes exactly what vegas_allocate computes, with the same arguments
+ * except the scratch area.  Its scratch is a fixed array of about 0.5 MiB in
+ * device global memory, declared in the library.  Every GPU that loads the
+ * library holds that array until the process exits.
+ *   - Limit: ncubes <= VEGAS_ALLOCATE_STATIC_MAX_CUBES; larger sizes return
+ *     VEGAS_ENOSPACE before anything runs.
+ *   - Set-up: the first call on a device looks up the array's device address
+ *     with that device current.  Make that first call before any stream
+ *     capture on the device.
+ *   - Sharing: every call on a device shares the one array, which keeps the
+ *     contents of the last call.  Each call re-initialises what it reads, so
+ *     sequential calls are independent.  Calls that overlap on the GPU
+ *     (different streams, or host threads without ordering) race on the
+ *     array and give wrong offsets.
+ *   - Allocation: the entry point calls no cudaMalloc, cudaFree or other
+ *     allocating routine.
+ * Errors: EINVAL as vegas_allocate, ENOSPACE above the limit, ECUDA. */
+#define VEGAS_ALLOCATE_STATIC_MAX_CUBES (1LL << 28)
+VEGAS_API int vegas_allocate_static(const float *d_ell, int64_t ncubes, int64_t neval, int uniform,
+                                    int64_t *d_offsets, void *stream);
+
 /* -- vegasFill (Algorithm 2; Eqs. (3)-(6)) ----------------------------------
  * Evaluate the integrand at the neval points of iteration `iteration`.
  * Evaluation j lies in the cube h with off_h <= j < off_{h+1}.  Its point comes

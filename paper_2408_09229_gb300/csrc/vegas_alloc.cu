@@ -15,6 +15,7 @@
 // one CTA, (3) per-block scan and offsets.  The uniform allocation (first
 // iteration, beta = 0, every variance zero) needs pass 3 only.
 #include <algorithm>
+#include <mutex>
 
 #include "vegas_device.cuh"
 #include "vegas_internal.h"
@@ -195,6 +196,76 @@ extern "C" int vegas_allocate(const float* d_ell, int64_t ncubes, int64_t neval,
   unsigned char* sc = (unsigned char*)d_scratch;
   int* key = (int*)(sc + L.key);
   uint64_t* bsum = (uint64_t*)(sc + L.bsum);
+  key_init_kernel<<<1, 1, 0, s>>>(key);
+  VG_CHECK(cudaGetLastError());
+  if (!uniform) {
+    const int grid = (int)std::min<int64_t>((ncubes + 255) / 256, 4096);
+    max_kernel<<<grid, 256, 0, s>>>(d_ell, ncubes, key);
+    VG_CHECK(cudaGetLastError());
+    block_sum_kernel<<<(unsigned)L.nblocks, kAllocThreads, 0, s>>>(d_ell, ncubes, key, 0, bsum);
+    VG_CHECK(cudaGetLastError());
+    block_scan_kernel<<<1, 1024, 0, s>>>(bsum, L.nblocks);
+    VG_CHECK(cudaGetLastError());
+  }
+  offsets_kernel<<<(unsigned)L.nblocks, kAllocThreads, 0, s>>>(d_ell, ncubes, neval, key, uniform, bsum, d_offsets);
+  VG_CHECK(cudaGetLastError());
+  return VEGAS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// vegas_allocate_static: the same allocation with no caller scratch and no
+// allocation at all.  Its scratch (the per-block sums and the max key) is a
+// fixed array in device global memory, sized for VEGAS_ALLOCATE_STATIC_MAX_CUBES
+// cubes, that every GPU which loads this library holds until the process exits.
+// ---------------------------------------------------------------------------
+namespace vg {
+namespace {
+
+constexpr size_t kStaticScratchBytes =
+    256 + sizeof(uint64_t) * (size_t)((VEGAS_ALLOCATE_STATIC_MAX_CUBES + kBlockCubes - 1) / kBlockCubes + 1) + 256;
+
+__device__ __align__(256) unsigned char g_allocate_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+void* g_static_scratch[kMaxDevices] = {};
+
+// Device address of g_allocate_scratch on the current device.  In host code
+// the array's name is only a host-side stand-in, so the address comes from
+// cudaGetSymbolAddress, once per device, with that device current.
+int static_scratch(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return VEGAS_ECUDA;
+  if (dev < 0 || dev >= kMaxDevices) return VEGAS_EINVAL;
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (!g_static_scratch[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_allocate_scratch) != cudaSuccess || !p) return VEGAS_ECUDA;
+    g_static_scratch[dev] = p;
+  }
+  *out = g_static_scratch[dev];
+  return VEGAS_OK;
+}
+
+}  // namespace
+}  // namespace vg
+
+extern "C" int vegas_allocate_static(const float* d_ell, int64_t ncubes, int64_t neval, int uniform,
+                                     int64_t* d_offsets, void* stream) {
+  if (ncubes < 1 || neval < 2 * ncubes || neval > kMaxEval) return VEGAS_EINVAL;
+  if (ncubes > VEGAS_ALLOCATE_STATIC_MAX_CUBES) return VEGAS_ENOSPACE;
+  if (!d_offsets || (!uniform && !d_ell)) return VEGAS_EINVAL;
+  void* base = nullptr;
+  const int rc = static_scratch(&base);
+  if (rc != VEGAS_OK) return rc;
+  const AllocScratch L = alloc_layout(ncubes);
+  if (L.total > kStaticScratchBytes) return VEGAS_ENOSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char* sc = (unsigned char*)base;
+  int* key = (int*)(sc + L.key);
+  uint64_t* bsum = (uint64_t*)(sc + L.bsum);
+  // the key is re-initialised and every block sum rewritten on each call, so
+  // nothing left by an earlier call is read
   key_init_kernel<<<1, 1, 0, s>>>(key);
   VG_CHECK(cudaGetLastError());
   if (!uniform) {

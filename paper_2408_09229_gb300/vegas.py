@@ -67,6 +67,7 @@ def _load():
         "vegas_strerror": ([i32], ctypes.c_char_p),
         "vegas_allocate_scratch_bytes": ([i64], sz),
         "vegas_allocate": ([P, i64, i64, i32, P, P, sz, P], i32),
+        "vegas_allocate_static": ([P, i64, i64, i32, P, P], i32),
         "vegas_fill_scratch_bytes": ([ctypes.POINTER(Geometry), i64], sz),
         "vegas_fill": ([ctypes.POINTER(Geometry), i32, i32, P, i64, i64, u64, i32, u32, f64, P, P, P, P, P, P, P,
                         P, P, sz, P], i32),
@@ -215,6 +216,15 @@ def allocate(ell, ncubes, neval, uniform, offsets, scratch, stream=None):
     """vegas_allocate: ell (float32 [ncubes] or None), offsets (int64 [ncubes+1]), scratch (uint8)."""
     _check(lib.vegas_allocate(_ptr(ell), int(ncubes), int(neval), int(bool(uniform)), _ptr(offsets), _ptr(scratch),
                               scratch.numel(), _stream_ptr(stream)), "vegas_allocate")
+
+
+ALLOCATE_STATIC_MAX_CUBES = 1 << 28
+
+
+def allocate_static(ell, ncubes, neval, uniform, offsets, stream=None):
+    """vegas_allocate_static: as allocate(), with the library's fixed device scratch instead of a caller area."""
+    _check(lib.vegas_allocate_static(_ptr(ell), int(ncubes), int(neval), int(bool(uniform)), _ptr(offsets),
+                                     _stream_ptr(stream)), "vegas_allocate_static")
 
 
 def fill_scratch_bytes(dim, nbins, nstrat, neval):
