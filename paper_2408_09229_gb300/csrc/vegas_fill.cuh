@@ -5,9 +5,10 @@
 // evaluations).  Evaluations j in [0, neval) are cut into tiles of kTile
 // consecutive indices; a persistent grid walks the tiles round-robin.  A tile
 // meets at most kMaxCubesPerTile hypercubes because n_h >= 2.  It stages their
-// offsets in shared memory, and each thread takes kSamplesPerThread consecutive
-// evaluations.  A thread binary-searches the cube of its first evaluation and
-// steps forward from there; no evaluation-to-cube array is ever built.
+// offsets, relative to the tile start, in shared memory.  Each thread takes
+// kSamplesPerThread consecutive evaluations.  A thread binary-searches the
+// cube of its first evaluation and steps forward from there; no
+// evaluation-to-cube array is ever built.
 //
 // Accumulation without global atomics (the paper's atomicAdd of Sec. 3.3.3):
 //  * cube weights: every J f goes to a shared array.  The cubes that lie inside
@@ -15,9 +16,14 @@
 //    one thread, or from one warp for long runs.  A cube that crosses a tile
 //    edge leaves a Carry record, and a fix-up kernel merges the records
 //    (Chan's pairwise formula) in tile order.
-//  * map weights: a per-CTA histogram in shared memory (shared atomics),
-//    written once per CTA to a partial array that a second kernel sums in a
-//    fixed order.
+//  * map weights: a per-CTA histogram.  The FP64 form adds with shared FP64
+//    atomics.  Shared FP32 atomic adds become compare-and-swap loops, and the
+//    32 lanes of a warp share a stratum on the high axes, so they collide on
+//    a handful of bins.  The FP32 form therefore adds in two phases per tile:
+//    the tile's largest weight fixes a power-of-two scale, the weights go in
+//    as 32-bit fixed-point integers through native shared integer atomics,
+//    and every tile's totals are folded into float-float accumulators.
+//    The per-CTA histograms are summed in a fixed order by a second kernel.
 //  * iteration estimate / variance: per-thread sums, reduced per CTA, then
 //    summed over CTAs in a fixed order.
 #pragma once
@@ -79,37 +85,203 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return r;
 }
 
-// Turn the caller's parameters into the derived form used by vg::integrand.
-template <int ID, typename T>
+// Number of shared-memory elements of the derived parameters.  The Gaussian
+// centres are padded to rows of DMAX so that a row loads as vectors.
+__host__ __device__ inline int derived_smem_count(int integrand, int d, int dmax, int np) {
+  if (integrand == VEGAS_GAUSS_SUM) return 4 + ((np - 3) / d) * dmax;
+  if (integrand == VEGAS_PRODUCT_PEAK) return 2 * dmax;
+  if (integrand == VEGAS_OSCILLATORY) return 4 + dmax;
+  if (integrand == VEGAS_MOROKOFF_CAFLISCH) return 4;
+  if (integrand == VEGAS_MAP_DENSITY) return np;
+  return 0;
+}
+
+// Turn the caller's parameters into the derived form read by vg::integrand:
+//   GAUSS_SUM         [A, c, K, 0, mu rows of DMAX]  c = -1/(2 s^2) (FP64, exp),
+//                                                    c = -log2(e)/(2 s^2) (FP32, exp2)
+//   PRODUCT_PEAK      [c_i^-2 (DMAX), w (DMAX)]
+//   OSCILLATORY       [2 pi u, 0, 0, 0, a (DMAX)]
+//   MOROKOFF_CAFLISCH [(1+1/d)^d, 1/d, 0, 0]
+//   MAP_DENSITY       [edges (d*(G'+1))]
+template <int ID, typename T, int DMAX>
 __device__ void prep_params(const double* __restrict__ raw, int np, int d, T* out) {
-  for (int i = threadIdx.x; i < np; i += blockDim.x) {
-    double v = raw[i];
-    if constexpr (ID == VEGAS_GAUSS_SUM) {
-      if (i == 1) {
-        const double s2 = 2.0 * v * v;
-        v = sizeof(T) == 8 ? -1.0 / s2 : -1.4426950408889634 / s2;  // exp or exp2 exponent
-      } else if (i == 2) {
-        v = (double)((np - 3) / d);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if constexpr (ID == VEGAS_GAUSS_SUM) {
+    const int K = (np - 3) / d;
+    for (int i = tid; i < 4 + K * DMAX; i += nt) {
+      double v = 0.0;
+      if (i == 0) v = raw[0];
+      else if (i == 1) v = (sizeof(T) == 8 ? -1.0 : -1.4426950408889634) / (2.0 * raw[1] * raw[1]);
+      else if (i == 2) v = (double)K;
+      else if (i >= 4) {
+        const int k = (i - 4) / DMAX, j = (i - 4) - k * DMAX;
+        v = j < d ? raw[3 + k * d + j] : 0.0;
       }
-    } else if constexpr (ID == VEGAS_PRODUCT_PEAK) {
-      if (i < d) v = 1.0 / (v * v);
-    } else if constexpr (ID == VEGAS_OSCILLATORY) {
-      if (i == 0) v = 6.283185307179586 * v;
+      out[i] = (T)v;
     }
-    out[i] = (T)v;
-  }
-  if constexpr (ID == VEGAS_MOROKOFF_CAFLISCH) {
-    if (threadIdx.x == 0) {
+  } else if constexpr (ID == VEGAS_PRODUCT_PEAK) {
+    for (int i = tid; i < 2 * DMAX; i += nt) {
+      const int j = i % DMAX;
+      double v = 0.0;
+      if (j < d) v = i < DMAX ? 1.0 / (raw[j] * raw[j]) : raw[d + j];
+      out[i] = (T)v;
+    }
+  } else if constexpr (ID == VEGAS_OSCILLATORY) {
+    for (int i = tid; i < 4 + DMAX; i += nt) {
+      double v = 0.0;
+      if (i == 0) v = 6.283185307179586 * raw[0];
+      else if (i >= 4 && i - 4 < d) v = raw[1 + (i - 4)];
+      out[i] = (T)v;
+    }
+  } else if constexpr (ID == VEGAS_MOROKOFF_CAFLISCH) {
+    if (tid == 0) {
       out[0] = (T)pow(1.0 + 1.0 / d, (double)d);
       out[1] = (T)(1.0 / d);
+      out[2] = out[3] = T(0);
     }
+  } else if constexpr (ID == VEGAS_MAP_DENSITY) {
+    for (int i = tid; i < np; i += nt) out[i] = (T)raw[i];
   }
+}
+
+// One padded row of DMAX parameters from 16-byte aligned shared memory, as
+// 16-byte vector loads.
+template <typename T, int DMAX>
+__device__ __forceinline__ void load_row(const T* __restrict__ p, T (&out)[DMAX]) {
+  if constexpr (sizeof(T) == 4 && DMAX % 4 == 0) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int i = 0; i < DMAX / 4; ++i) {
+      const float4 v = q[i];
+      out[4 * i] = v.x;
+      out[4 * i + 1] = v.y;
+      out[4 * i + 2] = v.z;
+      out[4 * i + 3] = v.w;
+    }
+  } else if constexpr (sizeof(T) == 8 && DMAX % 2 == 0) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int i = 0; i < DMAX / 2; ++i) {
+      const double2 v = q[i];
+      out[2 * i] = v.x;
+      out[2 * i + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < DMAX; ++i) out[i] = p[i];
+  }
+}
+
+// f(x) with the derived parameters p (shared memory) and the scalars s0, s1,
+// K loaded into registers once per thread.
+template <int ID, typename T, int DMAX>
+__device__ __forceinline__ T integrand(const T (&x)[DMAX], int d, const T* __restrict__ p, int np, T s0, T s1,
+                                       int K) {
+  if constexpr (ID == VEGAS_GAUSS_SUM) {
+    const T* mu = p + 4;
+    T acc = T(0);
+    for (int k = 0; k < K; ++k, mu += DMAX) {
+      T m[DMAX];
+      load_row<T, DMAX>(mu, m);
+      T r2 = T(0);
+#pragma unroll
+      for (int j = 0; j < DMAX; ++j) {
+        const T dx = x[j] - m[j];  // padded axes hold x = mu = 0
+        r2 = fma(dx, dx, r2);
+      }
+      if constexpr (sizeof(T) == 8) acc += exp(r2 * s1);
+      else acc += exp2f(r2 * s1);
+    }
+    return s0 * acc;
+  } else if constexpr (ID == VEGAS_PRODUCT_PEAK) {
+    // product of the denominators in groups of four, one division per group
+    T r = T(1), den = T(1);
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j) {
+      if (j < d) {
+        const T dx = x[j] - p[DMAX + j];
+        den *= fma(dx, dx, p[j]);
+      }
+      if ((j & 3) == 3 || j == DMAX - 1) {
+        r = r / den;
+        den = T(1);
+      }
+    }
+    return r;
+  } else if constexpr (ID == VEGAS_OSCILLATORY) {
+    T arg = s0;
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j) arg = fma(p[4 + j], x[j], arg);
+    return cos(arg);
+  } else if constexpr (ID == VEGAS_SIN_EXP) {
+    if constexpr (sizeof(T) == 8) return sin(x[0]) + exp(x[1 % DMAX]);
+    else return sinf(x[0]) + expf(x[1 % DMAX]);
+  } else if constexpr (ID == VEGAS_LINEAR) {
+    T s = T(0);
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j) s += x[j];
+    return s;
+  } else if constexpr (ID == VEGAS_COSINE) {
+    T r = T(1);
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j)
+      if (j < d) r *= cos(x[j]);
+    return r;
+  } else if constexpr (ID == VEGAS_EXPONENTIAL) {
+    T s = T(0);
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j) s = fma(x[j], x[j], s);
+    if constexpr (sizeof(T) == 8) return exp(s);
+    else return expf(s);
+  } else if constexpr (ID == VEGAS_ROOS_ARNOLD) {
+    T r = T(1);
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j)
+      if (j < d) r *= fabs(fma(T(4), x[j], T(-2)));
+    return r;
+  } else if constexpr (ID == VEGAS_MOROKOFF_CAFLISCH) {
+    T r = s0;
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j)
+      if (j < d) r *= pow(x[j], s1);
+    return r;
+  } else {  // VEGAS_MAP_DENSITY
+    const int G = np / d - 1;
+    T r = T(1);
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j) {
+      if (j < d) {
+        const T* e = p + j * (G + 1);
+        int lo = 0, hi = G - 1;  // largest i in [0, G-1] with e[i] <= x
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (e[mid] <= x[j]) lo = mid;
+          else hi = mid - 1;
+        }
+        r *= T(1) / (T(G) * (e[lo + 1] - e[lo]));
+      }
+    }
+    return r;
+  }
+}
+
+// Philox4x32-10 with the round keys precomputed on the host (kernel
+// parameters): rk0[r] = key0 + r * 0x9E3779B9, rk1[r] = key1 + r * 0xBB67AE85.
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const uint32_t* rk0, const uint32_t* rk1) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ rk0[round], lo1, hi0 ^ c.w ^ rk1[round], lo0);
+  }
+  return c;
 }
 
 // Point of evaluation j in cube h: Philox coordinates, z = (c + u) N_g / s,
 // interval i = min(floor z, N_g - 1), x = e_i + (z - i) dx_i, J = prod N_g dx_i.
+// Axes beyond d are set to x = 0 (the padded integrand parameters match).
 template <typename T, int DMAX>
-__device__ __forceinline__ void make_point(const FillArgs& a, uint32_t h, int64_t j, const T* __restrict__ gz,
+__device__ __forceinline__ void make_point(const FillArgs& a, uint32_t h, int64_t j,
                                            const TabEntry<T>* __restrict__ tab, T (&x)[DMAX], int (&bin)[DMAX],
                                            T& J) {
   const int G = a.G;
@@ -119,24 +291,24 @@ __device__ __forceinline__ void make_point(const FillArgs& a, uint32_t h, int64_
   const uint32_t jlo = (uint32_t)j, jhi = (uint32_t)((uint64_t)j >> 32);
 #pragma unroll
   for (int k = 0; k < DMAX; ++k) {
+    x[k] = T(0);
+    bin[k] = 0;
     if (k < a.d) {
       const uint32_t q = (uint32_t)(((uint64_t)rest * a.magic[k]) >> a.shift[k]);  // rest / s_k
       const uint32_t ck = rest - q * a.nstrat[k];
       rest = q;
       T z;
       if constexpr (sizeof(T) == 8) {
-        if ((k & 1) == 0)
-          r = philox4x32_10(make_uint4(jlo, jhi, a.iter, (a.pid << 16) | (uint32_t)(k >> 1)), a.key0, a.key1);
+        if ((k & 1) == 0) r = philox_rk(make_uint4(jlo, jhi, a.iter, (a.pid << 16) | (uint32_t)(k >> 1)), a.rk0, a.rk1);
         const uint32_t whi = (k & 1) ? r.z : r.x, wlo = (k & 1) ? r.w : r.y;
         const uint64_t bits = (((uint64_t)whi << 32) | wlo) >> 11;
         const double u = __dmul_rn(__ull2double_rn(bits), 0x1p-53);
-        z = __dmul_rn(__dadd_rn((double)ck, u), gz[k]);
+        z = __dmul_rn(__dadd_rn((double)ck, u), a.gz64[k]);
       } else {
-        if ((k & 3) == 0)
-          r = philox4x32_10(make_uint4(jlo, jhi, a.iter, (a.pid << 16) | (uint32_t)(k >> 2)), a.key0, a.key1);
+        if ((k & 3) == 0) r = philox_rk(make_uint4(jlo, jhi, a.iter, (a.pid << 16) | (uint32_t)(k >> 2)), a.rk0, a.rk1);
         const uint32_t w = (k & 3) == 0 ? r.x : (k & 3) == 1 ? r.y : (k & 3) == 2 ? r.z : r.w;
         const float u = __fmul_rn(__uint2float_rn(w >> 8), 0x1p-24f);
-        z = __fmul_rn(__fadd_rn((float)ck, u), gz[k]);
+        z = __fmul_rn(__fadd_rn((float)ck, u), a.gz32[k]);
       }
       int i = (int)z;  // z >= 0: truncation is floor
       i = i < G - 1 ? i : G - 1;
@@ -144,7 +316,7 @@ __device__ __forceinline__ void make_point(const FillArgs& a, uint32_t h, int64_
       const TabEntry<T> te = tab[k * G + i];
       x[k] = fma(dz, te.dx, te.e);
       J = J * te.jk;
-      bin[k] = k * G + i;
+      bin[k] = i;
     }
   }
 }
@@ -152,21 +324,26 @@ __device__ __forceinline__ void make_point(const FillArgs& a, uint32_t h, int64_
 template <int ID, typename T, int DMAX>
 __global__ void __launch_bounds__(kFillThreads) fill_kernel(const __grid_constant__ FillArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int d = a.d, G = a.G, dG = a.d * a.G;
+  const bool two_phase = a.hist_mode == kHistTwoPhase;
   TabEntry<T>* tab = a.table_smem ? (TabEntry<T>*)(smem + a.sm_table) : (TabEntry<T>*)a.gtable;
-  T* hist_s = (T*)(smem + a.sm_hist);
+  T* hist_s = (T*)(smem + a.sm_hist);                 // direct mode: shared histogram of T
+  uint32_t* hist_u = (uint32_t*)(smem + a.sm_hist);   // two-phase: fixed-point tile histogram
+  ff* hist_acc = (ff*)(smem + a.sm_hacc);             // two-phase: float-float CTA histogram
+  unsigned char* bins_s = smem + a.sm_bins;           // two-phase: interval of every evaluation and axis
+  float* wv_s = (float*)(smem + a.sm_wv);             // two-phase: map weight of every evaluation
   double* hist_g = a.hist_part + (size_t)blockIdx.x * dG;
   T* prm = (T*)(smem + a.sm_params);
-  int64_t* off_s = (int64_t*)(smem + a.sm_off);
+  int* off_r = (int*)(smem + a.sm_off);               // cube offsets relative to the tile, clamped
   T* invn = (T*)(smem + a.sm_invn);
   T* vals = (T*)(smem + a.sm_vals);
   int* longlist = (int*)(smem + a.sm_long);
-  T* gz = (T*)(smem + a.sm_misc);
-  int* misc = (int*)(smem + a.sm_misc + kMaxDim * sizeof(T));  // [0] long count, [1] cubes in tile
-  double* red = (double*)(smem + a.sm_misc + kMaxDim * sizeof(T) + 16);
+  int* misc = (int*)(smem + a.sm_misc);               // [0] long count, [1] cubes in tile
+  float* wmax = (float*)(smem + a.sm_misc + 16);      // [8] per-warp max of the map weight
+  double* red = (double*)(smem + a.sm_misc + 64);
 
-  // ---- prologue: map table, histogram, parameters, z scales ----
+  // ---- prologue: map table, histograms, parameters ----
   if (a.table_smem) {
     for (int b = tid; b < dG; b += kFillThreads) {
       const int k = b / G, i = b - k * G;
@@ -175,18 +352,22 @@ __global__ void __launch_bounds__(kFillThreads) fill_kernel(const __grid_constan
       tab[b] = TabEntry<T>{(T)e0, (T)dx, (T)jk, T(0)};
     }
   }
-  if (a.hist_smem)
+  if (a.hist_mode == kHistShared)
     for (int b = tid; b < dG; b += kFillThreads) hist_s[b] = T(0);
-  prep_params<ID, T>(a.params_raw, a.np_raw, d, prm);
-  if (tid < d) {
-    if constexpr (sizeof(T) == 8) gz[tid] = __ddiv_rn((double)G, (double)a.nstrat[tid]);
-    else gz[tid] = __fdiv_rn((float)G, (float)a.nstrat[tid]);
-  }
+  if (two_phase)
+    for (int b = tid; b < dG; b += kFillThreads) {
+      hist_u[b] = 0u;
+      hist_acc[b] = ff{0.0f, 0.0f};
+    }
+  prep_params<ID, T, DMAX>(a.params_raw, a.np_raw, d, prm);
   __syncthreads();
+  const T ps0 = prm[0], ps1 = prm[1];
+  const int pK = (ID == VEGAS_GAUSS_SUM) ? (int)prm[2] : 0;
 
   Acc<T> acc_i, acc_v;
   float lmax = -__int_as_float(0x7f800000);
   bool bad = false;
+  float inv_scale = 0.0f;  // two-phase: 1/scale of the tile histogram waiting to be folded
 
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
     const int64_t j0 = (int64_t)tile * kTile;
@@ -194,17 +375,25 @@ __global__ void __launch_bounds__(kFillThreads) fill_kernel(const __grid_constan
     const int h0 = a.tile_first[tile];
     const int64_t jend = j0 + len;
 
+    // ---- fold the previous tile's fixed-point histogram ----
+    if (two_phase && inv_scale > 0.0f) {
+      for (int b = tid; b < dG; b += kFillThreads) {
+        const uint32_t q = hist_u[b];
+        if (q) {
+          hist_acc[b] = ff_add(hist_acc[b], __fmul_rn((float)q, inv_scale));
+          hist_u[b] = 0u;
+        }
+      }
+    }
     // ---- offsets and 1/n_h of the cubes the tile can meet ----
     for (int c = tid; c <= kMaxCubesPerTile; c += kFillThreads) {
       const int64_t h = (int64_t)h0 + c;
       const int64_t o0 = h <= a.NH ? a.offsets[h] : INT64_MAX;
-      off_s[c] = o0;
+      const int64_t rel = o0 - j0;
+      off_r[c] = rel < -1 ? -1 : (rel > kTile + 1 ? kTile + 1 : (int)rel);
       if (c < kMaxCubesPerTile) {
         T inv = T(0);
-        if (o0 < jend) {
-          const int64_t o1 = a.offsets[h + 1];
-          inv = T(1) / (T)(o1 - o0);
-        }
+        if (o0 < jend) inv = T(1) / (T)(a.offsets[h + 1] - o0);
         invn[c] = inv;
       }
     }
@@ -215,57 +404,100 @@ __global__ void __launch_bounds__(kFillThreads) fill_kernel(const __grid_constan
     }
     __syncthreads();
 
-    // ---- evaluations: point, map, integrand, J f, map weights ----
+    // ---- phase A: point, map, integrand, J f; map weights ----
     const int jl0 = tid * kSamplesPerThread;
+    float my_max = 0.0f;
     if (jl0 < len) {
-      const int64_t jfirst = j0 + jl0;
       int lo = 0, hi = kMaxCubesPerTile - 1;
       while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (off_s[mid] <= jfirst) lo = mid;
+        if (off_r[mid] <= jl0) lo = mid;
         else hi = mid - 1;
       }
       int c = lo;
 #pragma unroll 1
       for (int s = 0; s < kSamplesPerThread; ++s) {
         const int jl = jl0 + s;
-        if (jl >= len) break;
-        const int64_t j = j0 + jl;
-        while (off_s[c + 1] <= j) ++c;
-        T x[DMAX];
-        int bin[DMAX];
-        T J;
-        make_point<T, DMAX>(a, (uint32_t)(h0 + c), j, gz, tab, x, bin, J);
-        const T f = integrand<ID, T, DMAX>(x, d, prm, a.np_derived);
-        if (!isfinite(f)) bad = true;
-        const T v = J * f;
-        vals[jl] = v;
-        const T wv = v * v * invn[c];
+        if (jl < len) {
+          while (off_r[c + 1] <= jl) ++c;
+          T x[DMAX];
+          int bin[DMAX];
+          T J;
+          make_point<T, DMAX>(a, (uint32_t)(h0 + c), j0 + jl, tab, x, bin, J);
+          const T f = integrand<ID, T, DMAX>(x, d, prm, a.np_derived, ps0, ps1, pK);
+          if (!isfinite(f)) bad = true;
+          const T v = J * f;
+          vals[jl] = v;
+          const T wv = v * v * invn[c];
+          if (two_phase) {
+            wv_s[jl] = (float)wv;
+            my_max = fmaxf(my_max, (float)wv);
 #pragma unroll
-        for (int k = 0; k < DMAX; ++k) {
-          if (k < d) {
-            if (a.hist_smem) atomicAdd(hist_s + bin[k], wv);
-            else atomicAdd(hist_g + bin[k], (double)wv);
+            for (int k = 0; k < DMAX; ++k)
+              if (k < d) bins_s[(size_t)jl * d + k] = (unsigned char)bin[k];
+          } else {
+#pragma unroll
+            for (int k = 0; k < DMAX; ++k) {
+              if (k < d) {
+                if (a.hist_mode == kHistShared) atomicAdd(hist_s + k * G + bin[k], wv);
+                else atomicAdd(hist_g + k * G + bin[k], (double)wv);
+              }
+            }
           }
+          if (jl == len - 1) misc[1] = c + 1;
         }
-        if (jl == len - 1) misc[1] = c + 1;
       }
     }
+    if (two_phase) {
+      for (int o = 16; o > 0; o >>= 1) my_max = fmaxf(my_max, __shfl_xor_sync(0xffffffffu, my_max, o));
+      if (lane == 0) wmax[warp] = my_max;
+    }
     __syncthreads();
+
+    // ---- phase B (two-phase histogram): fixed-point shared integer atomics ----
+    if (two_phase) {
+      float tmax = 0.0f;
+#pragma unroll
+      for (int w = 0; w < kFillThreads / 32; ++w) tmax = fmaxf(tmax, wmax[w]);
+      if (tmax > 0.0f && isfinite(tmax)) {
+        // tmax < 2^et and a bin gets at most kTile <= 2^kTileLog2 weights of
+        // the tile, so with scale = 2^(31 - kTileLog2 - et) every bin total
+        // stays below 2^31 (plus the rounding of kTile values)
+        int et;
+        frexpf(tmax, &et);
+        const int se = min(31 - kTileLog2 - et, 126);
+        const float scale = ldexpf(1.0f, se);
+        inv_scale = ldexpf(1.0f, -se);
+        if (jl0 < len) {
+#pragma unroll 1
+          for (int s = 0; s < kSamplesPerThread; ++s) {
+            const int jl = jl0 + s;
+            if (jl < len) {
+              const uint32_t q = (uint32_t)__float2uint_rn(wv_s[jl] * scale);
+              if (q) {
+                for (int k = 0; k < d; ++k) atomicAdd(hist_u + k * G + bins_s[(size_t)jl * d + k], q);
+              }
+            }
+          }
+        }
+      } else {
+        inv_scale = 0.0f;
+      }
+    }
 
     // ---- cube statistics ----
     const int ncub = misc[1];
     // one cube segment done: a cube inside the tile is final, one crossing an
     // edge becomes a Carry for the fix-up kernel
     auto finish = [&](int c, int L, auto mean, T m2) {
-      const int64_t o0 = off_s[c], o1 = off_s[c + 1];
-      const bool before = o0 < j0, after = o1 > jend;
+      const int r0 = off_r[c], r1 = off_r[c + 1];
+      const bool before = r0 < 0, after = r1 > len;
       const int h = h0 + c;
       if (before || after) {
         a.carries[2 * tile + (before ? 0 : 1)] = Carry{h, L, to_double(mean), (double)m2};
         return;
       }
-      const int64_t n = o1 - o0;
+      const int n = r1 - r0;
       float ell;
       acc_i.add(mean);
       if constexpr (sizeof(T) == 8) {
@@ -284,8 +516,7 @@ __global__ void __launch_bounds__(kFillThreads) fill_kernel(const __grid_constan
     };
 
     for (int c = tid; c < ncub; c += kFillThreads) {
-      const int64_t o0 = off_s[c], o1 = off_s[c + 1];
-      const int r0 = (int)max(o0 - j0, (int64_t)0), r1 = (int)min(o1 - j0, (int64_t)len);
+      const int r0 = max(off_r[c], 0), r1 = min(off_r[c + 1], len);
       const int L = r1 - r0;
       if (L > kLongSegment) {
         longlist[atomicAdd(&misc[0], 1)] = c;
@@ -317,11 +548,9 @@ __global__ void __launch_bounds__(kFillThreads) fill_kernel(const __grid_constan
     }
     __syncthreads();
     const int nlong = misc[0];
-    const int warp = tid >> 5, lane = tid & 31;
     for (int e = warp; e < nlong; e += kFillThreads / 32) {
       const int c = longlist[e];
-      const int64_t o0 = off_s[c], o1 = off_s[c + 1];
-      const int r0 = (int)max(o0 - j0, (int64_t)0), r1 = (int)min(o1 - j0, (int64_t)len);
+      const int r0 = max(off_r[c], 0), r1 = min(off_r[c + 1], len);
       const int L = r1 - r0;
       if constexpr (sizeof(T) == 8) {
         double s = 0.0;
@@ -362,10 +591,17 @@ __global__ void __launch_bounds__(kFillThreads) fill_kernel(const __grid_constan
     a.cta_part[2 * blockIdx.x + 1] = sv;
   }
   for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-  if ((tid & 31) == 0) atomicMax(a.ellmax_key, float_key(lmax));
+  if (lane == 0) atomicMax(a.ellmax_key, float_key(lmax));
   if (__syncthreads_or(bad) && tid == 0) atomicOr(a.flags, 1);
-  if (a.hist_smem)
+  if (a.hist_mode == kHistShared)
     for (int b = tid; b < dG; b += kFillThreads) hist_g[b] = (double)hist_s[b];
+  if (two_phase) {
+    for (int b = tid; b < dG; b += kFillThreads) {
+      ff acc = hist_acc[b];
+      if (inv_scale > 0.0f) acc = ff_add(acc, __fmul_rn((float)hist_u[b], inv_scale));
+      hist_g[b] = ff_to_double(acc);
+    }
+  }
 }
 
 }  // namespace vg

@@ -68,27 +68,52 @@ ScratchLayout scratch_layout(int d, int G, int64_t neval, int sms) {
   return L;
 }
 
-// Shared-memory regions of the fill kernel.  The map table and the histogram
-// go to shared memory when they fit the budget; otherwise the table is read
-// from global memory and the histogram is accumulated with global atomics.
-int smem_layout(FillArgs& a, size_t tsz, int np_derived) {
+// Shared-memory regions of the fill kernel.  The map-weight histogram goes to
+// shared memory when it fits the budget.  FP32 with N_g <= 256 uses the
+// two-phase fixed-point form; otherwise the histogram is of the evaluation
+// type.  When the histogram does not fit, a per-CTA global histogram takes
+// FP64 atomic adds.  The map table goes to shared memory when it also fits;
+// otherwise the kernel reads it from global memory.
+int smem_layout(FillArgs& a, size_t tsz, int nprm, bool fp32) {
   const int dG = a.d * a.G;
-  const size_t fixed = align_up(np_derived * tsz) + align_up(sizeof(int64_t) * (kMaxCubesPerTile + 1)) +
-                       align_up(tsz * kMaxCubesPerTile) + align_up(tsz * kTile) +
-                       align_up(sizeof(int) * kMaxCubesPerTile) + align_up(kMaxDim * tsz + 16 + 8 * 32);
+  const size_t base = align_up(nprm * tsz) + align_up(sizeof(int) * (kMaxCubesPerTile + 1)) +
+                      align_up(tsz * kMaxCubesPerTile) + align_up(tsz * kTile) +
+                      align_up(sizeof(int) * kMaxCubesPerTile) + align_up(64 + 8 * 32);
   const size_t budget = 160 * 1024;
-  const size_t table = align_up((size_t)dG * 4 * tsz), hist = align_up((size_t)dG * tsz);
-  a.hist_smem = fixed + hist <= budget;
-  a.table_smem = a.hist_smem && fixed + hist + table <= budget;
+  const size_t table = align_up((size_t)dG * 4 * tsz);
+  const size_t two_phase = align_up((size_t)dG * 4) + align_up((size_t)dG * 8) +
+                           align_up((size_t)kTile * a.d) + align_up(sizeof(float) * kTile);
+  const size_t shared_hist = align_up((size_t)dG * tsz);
+  size_t hist;
+  if (fp32 && a.G <= 256 && base + two_phase <= budget) {
+    a.hist_mode = kHistTwoPhase;
+    hist = two_phase;
+  } else if (base + shared_hist <= budget) {
+    a.hist_mode = kHistShared;
+    hist = shared_hist;
+  } else {
+    a.hist_mode = kHistGlobal;
+    hist = 0;
+  }
+  a.table_smem = base + hist + table <= budget;
   size_t off = 0;
-  a.sm_table = (int)off; off += a.table_smem ? table : 0;
-  a.sm_hist = (int)off;  off += a.hist_smem ? hist : 0;
-  a.sm_params = (int)off; off += align_up(np_derived * tsz);
-  a.sm_off = (int)off;   off += align_up(sizeof(int64_t) * (kMaxCubesPerTile + 1));
-  a.sm_invn = (int)off;  off += align_up(tsz * kMaxCubesPerTile);
-  a.sm_vals = (int)off;  off += align_up(tsz * kTile);
-  a.sm_long = (int)off;  off += align_up(sizeof(int) * kMaxCubesPerTile);
-  a.sm_misc = (int)off;  off += align_up(kMaxDim * tsz + 16 + 8 * 32);
+  a.sm_table = (int)off;  off += a.table_smem ? table : 0;
+  a.sm_hist = (int)off;
+  if (a.hist_mode == kHistTwoPhase) {
+    off += align_up((size_t)dG * 4);
+    a.sm_hacc = (int)off; off += align_up((size_t)dG * 8);
+    a.sm_bins = (int)off; off += align_up((size_t)kTile * a.d);
+    a.sm_wv = (int)off;   off += align_up(sizeof(float) * kTile);
+  } else {
+    off += a.hist_mode == kHistShared ? shared_hist : 0;
+    a.sm_hacc = a.sm_bins = a.sm_wv = (int)off;
+  }
+  a.sm_params = (int)off; off += align_up(nprm * tsz);
+  a.sm_off = (int)off;    off += align_up(sizeof(int) * (kMaxCubesPerTile + 1));
+  a.sm_invn = (int)off;   off += align_up(tsz * kMaxCubesPerTile);
+  a.sm_vals = (int)off;   off += align_up(tsz * kTile);
+  a.sm_long = (int)off;   off += align_up(sizeof(int) * kMaxCubesPerTile);
+  a.sm_misc = (int)off;   off += align_up(64 + 8 * 32);
   a.sm_total = (int)off;
   return off <= 227 * 1024 ? VEGAS_OK : VEGAS_EINVAL;
 }
@@ -240,7 +265,10 @@ int fill_impl(const vegas_geometry* g, int precision, int integrand, const doubl
   }
   if (neval < 2 * NH || neval > kMaxEval) return VEGAS_EINVAL;
   const int npd = derived_param_count(integrand, d, nullptr, nparams);
-  if (npd < 0 || npd > kMaxDerivedParams) return VEGAS_EINVAL;
+  if (npd < 0) return VEGAS_EINVAL;
+  const int dmax = dmax_for(d);
+  const int nprm = derived_smem_count(integrand, d, dmax, (int)nparams);
+  if (nprm > kMaxDerivedParams) return VEGAS_EINVAL;
 
   const int sms = num_sms();
   if (sms <= 0) return VEGAS_ECUDA;
@@ -278,11 +306,18 @@ int fill_impl(const vegas_geometry* g, int precision, int integrand, const doubl
   for (int k = 0; k < d; ++k) {
     a.nstrat[k] = (uint32_t)g->nstrat[k];
     magic_div(a.nstrat[k], a.magic[k], a.shift[k]);
+    // z = (c + u) * N_g / s_k: the scale rounded once, in each precision
+    a.gz64[k] = (double)G / (double)g->nstrat[k];
+    volatile float gf = (float)G, sf = (float)g->nstrat[k];
+    a.gz32[k] = gf / sf;
+  }
+  for (int r = 0; r < 10; ++r) {
+    a.rk0[r] = a.key0 + (uint32_t)r * 0x9E3779B9u;
+    a.rk1[r] = a.key1 + (uint32_t)r * 0xBB67AE85u;
   }
   const size_t tsz = precision == VEGAS_FP64 ? sizeof(double) : sizeof(float);
-  if (smem_layout(a, tsz, npd) != VEGAS_OK) return VEGAS_EINVAL;
+  if (smem_layout(a, tsz, nprm, precision == VEGAS_FP32) != VEGAS_OK) return VEGAS_EINVAL;
 
-  const int dmax = dmax_for(d);
   const int per_sm = precision == VEGAS_FP64 ? fill_occupancy_f64(integrand, dmax, a.sm_total)
                                              : fill_occupancy_f32(integrand, dmax, a.sm_total);
   if (per_sm <= 0) return VEGAS_ECUDA;
@@ -291,7 +326,8 @@ int fill_impl(const vegas_geometry* g, int precision, int integrand, const doubl
   tile_first_kernel<<<(L.ntiles + 255) / 256, 256, 0, s>>>(d_offsets, a.NH, L.ntiles, (int32_t*)(sc + L.tile_first),
                                                             a.ellmax_key);
   VG_CHECK(cudaGetLastError());
-  if (!a.hist_smem) VG_CHECK(cudaMemsetAsync(a.hist_part, 0, sizeof(double) * (size_t)grid * d * G, s));
+  if (a.hist_mode == kHistGlobal)
+    VG_CHECK(cudaMemsetAsync(a.hist_part, 0, sizeof(double) * (size_t)grid * d * G, s));
   if (!a.table_smem) {
     const int n = d * G;
     if (precision == VEGAS_FP64) table_kernel<double><<<(n + 255) / 256, 256, 0, s>>>(d_edges, d, G, (TabEntry<double>*)a.gtable);

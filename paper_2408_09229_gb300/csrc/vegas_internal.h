@@ -13,6 +13,12 @@ constexpr int kMaxBins = 4096;
 constexpr int kFillThreads = 256;
 constexpr int kSamplesPerThread = 4;
 constexpr int kTile = kFillThreads * kSamplesPerThread;  // evaluations per tile
+constexpr int kTileLog2 = 10;                            // kTile = 2^kTileLog2
+static_assert(kTile == (1 << kTileLog2), "tile size is a power of two");
+// how the fill accumulates the map weights
+constexpr int kHistShared = 0;    // shared-memory histogram of the evaluation type, atomic adds
+constexpr int kHistGlobal = 1;    // per-CTA global histogram, FP64 atomic adds (large d * N_g)
+constexpr int kHistTwoPhase = 2;  // FP32: fixed-point tile histogram with shared integer atomics
 constexpr int kMaxCubesPerTile = kTile / 2 + 3;          // n_h >= 2 bounds the cubes a tile meets
 constexpr int kLongSegment = 32;                         // longer cube segments go to a warp
 constexpr int kMaxDerivedParams = 8192;
@@ -35,7 +41,8 @@ struct FillArgs {
   int64_t neval;
   uint32_t key0, key1, iter, pid;
   float half_beta;
-  int table_smem, hist_smem;  // 1: map table / map-weight histogram in shared memory
+  int table_smem;  // 1: map table in shared memory
+  int hist_mode;   // kHistShared, kHistGlobal or kHistTwoPhase
   int np_derived;
   const double* edges;     // [d][G+1] FP64
   const int64_t* offsets;  // [NH+1]
@@ -52,8 +59,11 @@ struct FillArgs {
   double* hist_part;    // [grid][d*G]
   void* gtable;         // global map table when it does not fit in shared memory
   uint32_t nstrat[kMaxDim], magic[kMaxDim], shift[kMaxDim];
+  double gz64[kMaxDim];     // N_g / s_k, rounded in FP64
+  float gz32[kMaxDim];      // N_g / s_k, rounded in FP32
+  uint32_t rk0[10], rk1[10];  // Philox round keys
   // shared-memory byte offsets of the regions
-  int sm_table, sm_hist, sm_params, sm_off, sm_invn, sm_vals, sm_long, sm_misc, sm_total;
+  int sm_table, sm_hist, sm_hacc, sm_bins, sm_wv, sm_params, sm_off, sm_invn, sm_vals, sm_long, sm_misc, sm_total;
 };
 
 // launchers (one per precision, defined in vegas_fill_f64.cu / vegas_fill_f32.cu)
