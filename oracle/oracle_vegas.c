@@ -394,8 +394,17 @@ static void point_coordinates_f64(const orc_config *cfg, uint64_t seed, int t, i
   }
 }
 
-static void point_coordinates_f32(const orc_config *cfg, uint64_t seed, int t, int64_t j, float *u) {
-  /* R2: in FP32 mode coordinate k takes word k%4 of block k/4 and keeps 24 bits */
+/* R2/R3, FP32 mode: coordinate k takes word k%4 of block k/4.  With
+ * b = 23 - ceil(log2 s_k) fraction bits, the integer v = c_k 2^b + (w >> (32-b))
+ * is below 2^23, so c_k + u = v 2^-b is exact in float; the point is then
+ * z = RN32((c_k + u) N_g/s_k).  Writes v as a float (exact). */
+static int frac_bits(int s) {
+  int l = 0;
+  while ((1 << l) < s) ++l;
+  return 23 - l;
+}
+
+static void point_words_f32(const orc_config *cfg, uint64_t seed, int t, int64_t j, const int *c, float *v) {
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   uint32_t out[4];
   for (int k = 0; k < cfg->dim; ++k) {
@@ -404,7 +413,9 @@ static void point_coordinates_f32(const orc_config *cfg, uint64_t seed, int t, i
                          (cfg->problem_id << 16) | (uint32_t)(k / 4)};
       orc_philox4x32_10(ctr, key, out);
     }
-    u[k] = (float)(out[k % 4] >> 8) * 0x1p-24f;
+    int b = frac_bits(cfg->nstrat[k]);
+    uint32_t iv = ((uint32_t)c[k] << b) | (out[k % 4] >> (32 - b));
+    v[k] = (float)iv;
   }
 }
 
@@ -421,7 +432,7 @@ int orc_fill_range(const orc_config *cfg, int integrand, const double *params, i
   double *jac = (double *)malloc(sizeof(double) * (size_t)d * G);
   for (int k = 0; k < d; ++k) {
     gz[k] = (double)G / (double)cfg->nstrat[k];
-    gz32[k] = fdiv((float)G, (float)cfg->nstrat[k]);
+    gz32[k] = ldexpf(fdiv((float)G, (float)cfg->nstrat[k]), -frac_bits(cfg->nstrat[k]));
     for (int i = 0; i < G; ++i) {
       const double *e = edges + (size_t)k * (G + 1);
       width[(size_t)k * G + i] = e[i + 1] - e[i];
@@ -455,13 +466,13 @@ int orc_fill_range(const orc_config *cfg, int integrand, const double *params, i
     for (int64_t j = a; j < b; ++j) {
       /* getPoint: uniform point y in the cube, then the map x(y) (Eq. (3)) */
       double J = 1.0;
-      if (cfg->points_f32) point_coordinates_f32(cfg, seed, t, j, u32);
+      if (cfg->points_f32) point_words_f32(cfg, seed, t, j, c, u32);
       else point_coordinates_f64(cfg, seed, t, j, u);
       for (int k = 0; k < d; ++k) {
         double z, dz;
         int i;
         if (cfg->points_f32) {
-          float zf = fmul(fadd((float)c[k], u32[k]), gz32[k]);
+          float zf = fmul(u32[k], gz32[k]);
           i = (int)floorf(zf);
           if (i > G - 1) i = G - 1;
           dz = (double)fsub(zf, (float)i);
@@ -516,21 +527,21 @@ int orc_cube_stats(const orc_config *cfg, int integrand, const double *params, i
   int64_t rest = h;
   for (int k = 0; k < d; ++k) {
     gz[k] = (double)G / (double)cfg->nstrat[k];
-    gz32[k] = fdiv((float)G, (float)cfg->nstrat[k]);
+    gz32[k] = ldexpf(fdiv((float)G, (float)cfg->nstrat[k]), -frac_bits(cfg->nstrat[k]));
     c[k] = (int)(rest % cfg->nstrat[k]);
     rest /= cfg->nstrat[k];
   }
   int status = 0;
   for (int64_t j = offs[0]; j < offs[1]; ++j) {
     double J = 1.0;
-    if (one.points_f32) point_coordinates_f32(&one, seed, t, j, u32);
+    if (one.points_f32) point_words_f32(&one, seed, t, j, c, u32);
     else point_coordinates_f64(&one, seed, t, j, u);
     for (int k = 0; k < d; ++k) {
       const double *e = edges + (size_t)k * (G + 1);
       double dz;
       int i;
       if (one.points_f32) {
-        float zf = fmul(fadd((float)c[k], u32[k]), gz32[k]);
+        float zf = fmul(u32[k], gz32[k]);
         i = (int)floorf(zf);
         if (i > G - 1) i = G - 1;
         dz = (double)fsub(zf, (float)i);

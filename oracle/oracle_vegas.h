@@ -87,7 +87,8 @@ typedef struct {
   int nbins;            /* N_g */
   const int *nstrat;    /* s_k, k < d; number of cubes N_h = prod s_k */
   double alpha, beta;
-  int points_f32;       /* 0: 53-bit coordinates and FP64 z; 1: 24-bit coordinates and FP32 z (R3) */
+  int points_f32;       /* 0: 53-bit coordinates and FP64 z; 1: FP32 z from 23-bit exact c + u (R3);
+                           FP32 mode needs nstrat <= 2^16 */
   uint32_t problem_id;  /* enters the Philox counter (R2) */
 } orc_config;
 

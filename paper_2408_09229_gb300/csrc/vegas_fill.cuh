@@ -144,6 +144,19 @@ __device__ void prep_params(const double* __restrict__ raw, int np, int d, T* ou
   }
 }
 
+// 2^x with the special-function unit (ex2.approx.ftz: about 2 ulp, results
+// below 2^-126 flush to zero)
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// log2 with the special-function unit, for the FP32 form's allocation
+// weight: the counts are a reproducible function of the weight's bits, so the
+// weight itself only has to be deterministic.
+__device__ __forceinline__ float log2_fast(float x) { return __log2f(x); }
+
 // One padded row of DMAX parameters from 16-byte aligned shared memory, as
 // 16-byte vector loads.
 template <typename T, int DMAX>
@@ -190,7 +203,7 @@ __device__ __forceinline__ T integrand(const T (&x)[DMAX], int d, const T* __res
         r2 = fma(dx, dx, r2);
       }
       if constexpr (sizeof(T) == 8) acc += exp(r2 * s1);
-      else acc += exp2f(r2 * s1);
+      else acc += ex2_approx(r2 * s1);
     }
     return s0 * acc;
   } else if constexpr (ID == VEGAS_PRODUCT_PEAK) {
@@ -270,22 +283,45 @@ __device__ __forceinline__ T integrand(const T (&x)[DMAX], int d, const T* __res
 __device__ __forceinline__ uint4 philox_rk(uint4 c, const uint32_t* rk0, const uint32_t* rk1) {
 #pragma unroll
   for (int round = 0; round < 10; ++round) {
-    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-    c = make_uint4(hi1 ^ c.y ^ rk0[round], lo1, hi0 ^ c.w ^ rk1[round], lo0);
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x, p1 = (uint64_t)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk0[round], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ rk1[round],
+                   (uint32_t)p0);
   }
   return c;
 }
 
-// Point of evaluation j in cube h: Philox coordinates, z = (c + u) N_g / s,
-// interval i = min(floor z, N_g - 1), x = e_i + (z - i) dx_i, J = prod N_g dx_i.
-// Axes beyond d are set to x = 0 (the padded integrand parameters match).
+// Coordinates c_k of cube h (axis 0 fastest), by multiplication with the
+// magic reciprocals.  In the FP32 form they are kept as the high bits of a
+// float in [2^23, 2^24): 0x4B000000 | c_k << b_k, with b_k fraction bits.
 template <typename T, int DMAX>
-__device__ __forceinline__ void make_point(const FillArgs& a, uint32_t h, int64_t j,
+__device__ __forceinline__ void decode_cube(const FillArgs& a, uint32_t h, uint32_t (&cb)[DMAX]) {
+  uint32_t rest = h;
+#pragma unroll
+  for (int k = 0; k < DMAX; ++k) {
+    cb[k] = 0u;
+    if (k < a.d) {
+      const uint32_t q = (uint32_t)(((uint64_t)rest * a.magic[k]) >> a.shift[k]);  // rest / s_k
+      const uint32_t ck = rest - q * a.nstrat[k];
+      rest = q;
+      if constexpr (sizeof(T) == 8) cb[k] = ck;
+      else cb[k] = 0x4B000000u | (ck << a.fbits[k]);
+    }
+  }
+}
+
+// Point of evaluation j in the cube with coordinates cb: Philox words, the
+// position z = (c + u) N_g / s_k, interval i = min(floor z, N_g - 1), the
+// point x = e_i + (z - i) dx_i and the Jacobian J = prod N_g dx_i.
+//   FP64: u has 53 bits; z = RN(RN(c + u) * g) in FP64.
+//   FP32: v = c 2^b + (w >> (32 - b)) < 2^23, so c + u = v 2^-b is exact; the
+//         float 2^23 + v is assembled from bits, and z = RN(v g 2^-b) is one
+//         fused multiply-add with the exact constant -2^23 g 2^-b.
+// Axes beyond d get x = 0 (the padded integrand parameters match).
+template <typename T, int DMAX>
+__device__ __forceinline__ void make_point(const FillArgs& a, const uint32_t (&cb)[DMAX], int64_t j,
                                            const TabEntry<T>* __restrict__ tab, T (&x)[DMAX], int (&bin)[DMAX],
                                            T& J) {
   const int G = a.G;
-  uint32_t rest = h;
   J = T(1);
   uint4 r = make_uint4(0u, 0u, 0u, 0u);
   const uint32_t jlo = (uint32_t)j, jhi = (uint32_t)((uint64_t)j >> 32);
@@ -294,25 +330,26 @@ __device__ __forceinline__ void make_point(const FillArgs& a, uint32_t h, int64_
     x[k] = T(0);
     bin[k] = 0;
     if (k < a.d) {
-      const uint32_t q = (uint32_t)(((uint64_t)rest * a.magic[k]) >> a.shift[k]);  // rest / s_k
-      const uint32_t ck = rest - q * a.nstrat[k];
-      rest = q;
-      T z;
+      int i;
+      T dz;
       if constexpr (sizeof(T) == 8) {
         if ((k & 1) == 0) r = philox_rk(make_uint4(jlo, jhi, a.iter, (a.pid << 16) | (uint32_t)(k >> 1)), a.rk0, a.rk1);
         const uint32_t whi = (k & 1) ? r.z : r.x, wlo = (k & 1) ? r.w : r.y;
         const uint64_t bits = (((uint64_t)whi << 32) | wlo) >> 11;
         const double u = __dmul_rn(__ull2double_rn(bits), 0x1p-53);
-        z = __dmul_rn(__dadd_rn((double)ck, u), a.gz64[k]);
+        const double z = __dmul_rn(__dadd_rn((double)cb[k], u), a.gz64[k]);
+        i = (int)z;  // z >= 0: truncation is floor
+        i = i < G - 1 ? i : G - 1;
+        dz = z - (double)i;  // exact
       } else {
         if ((k & 3) == 0) r = philox_rk(make_uint4(jlo, jhi, a.iter, (a.pid << 16) | (uint32_t)(k >> 2)), a.rk0, a.rk1);
         const uint32_t w = (k & 3) == 0 ? r.x : (k & 3) == 1 ? r.y : (k & 3) == 2 ? r.z : r.w;
-        const float u = __fmul_rn(__uint2float_rn(w >> 8), 0x1p-24f);
-        z = __fmul_rn(__fadd_rn((float)ck, u), a.gz32[k]);
+        const float big = __uint_as_float(cb[k] | (w >> (32 - a.fbits[k])));  // 2^23 + v
+        const float z = fmaf(big, a.gzb32[k], a.gzn32[k]);                     // RN(v g 2^-b)
+        const float fl = fminf(floorf(z), (float)(G - 1));
+        dz = z - fl;  // exact
+        i = __float_as_int(fl + 8388608.0f) & 0x7FFFFF;
       }
-      int i = (int)z;  // z >= 0: truncation is floor
-      i = i < G - 1 ? i : G - 1;
-      const T dz = z - (T)i;  // exact
       const TabEntry<T> te = tab[k * G + i];
       x[k] = fma(dz, te.dx, te.e);
       J = J * te.jk;
@@ -331,7 +368,8 @@ __global__ void __launch_bounds__(kFillThreads) fill_kernel(const __grid_constan
   T* hist_s = (T*)(smem + a.sm_hist);                 // direct mode: shared histogram of T
   uint32_t* hist_u = (uint32_t*)(smem + a.sm_hist);   // two-phase: fixed-point tile histogram
   ff* hist_acc = (ff*)(smem + a.sm_hacc);             // two-phase: float-float CTA histogram
-  unsigned char* bins_s = smem + a.sm_bins;           // two-phase: interval of every evaluation and axis
+  uint32_t* binw = (uint32_t*)(smem + a.sm_bins);     // two-phase: intervals of an evaluation, 4 per word
+  const int nw = (d + 3) >> 2;
   float* wv_s = (float*)(smem + a.sm_wv);             // two-phase: map weight of every evaluation
   double* hist_g = a.hist_part + (size_t)blockIdx.x * dG;
   T* prm = (T*)(smem + a.sm_params);
@@ -339,6 +377,7 @@ __global__ void __launch_bounds__(kFillThreads) fill_kernel(const __grid_constan
   T* invn = (T*)(smem + a.sm_invn);
   T* vals = (T*)(smem + a.sm_vals);
   int* longlist = (int*)(smem + a.sm_long);
+  int* startc = (int*)(smem + a.sm_start);            // cube of every thread's first evaluation
   int* misc = (int*)(smem + a.sm_misc);               // [0] long count, [1] cubes in tile
   float* wmax = (float*)(smem + a.sm_misc + 16);      // [8] per-warp max of the map weight
   double* red = (double*)(smem + a.sm_misc + 64);
@@ -393,7 +432,10 @@ __global__ void __launch_bounds__(kFillThreads) fill_kernel(const __grid_constan
       off_r[c] = rel < -1 ? -1 : (rel > kTile + 1 ? kTile + 1 : (int)rel);
       if (c < kMaxCubesPerTile) {
         T inv = T(0);
-        if (o0 < jend) inv = T(1) / (T)(a.offsets[h + 1] - o0);
+        if (o0 < jend) {
+          if constexpr (sizeof(T) == 8) inv = 1.0 / (double)(a.offsets[h + 1] - o0);
+          else inv = __fdividef(1.0f, (float)(a.offsets[h + 1] - o0));
+        }
         invn[c] = inv;
       }
     }
@@ -403,27 +445,36 @@ __global__ void __launch_bounds__(kFillThreads) fill_kernel(const __grid_constan
       a.carries[2 * tile + 1] = Carry{-1, 0, 0.0, 0.0};
     }
     __syncthreads();
+    // every cube tells the threads whose first evaluation it holds
+    for (int c = tid; c < kMaxCubesPerTile; c += kFillThreads) {
+      const int r0 = max(off_r[c], 0), r1 = min(off_r[c + 1], len);
+      if (r0 < r1) {
+        for (int t = (r0 + kSamplesPerThread - 1) / kSamplesPerThread; t * kSamplesPerThread < r1; ++t) startc[t] = c;
+        if (r1 == len) misc[1] = c + 1;  // cubes met by the tile
+      }
+    }
+    __syncthreads();
 
     // ---- phase A: point, map, integrand, J f; map weights ----
     const int jl0 = tid * kSamplesPerThread;
     float my_max = 0.0f;
     if (jl0 < len) {
-      int lo = 0, hi = kMaxCubesPerTile - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (off_r[mid] <= jl0) lo = mid;
-        else hi = mid - 1;
-      }
-      int c = lo;
+      int c = startc[tid];
+      int c_decoded = -1;
+      uint32_t cb[DMAX];
 #pragma unroll 1
       for (int s = 0; s < kSamplesPerThread; ++s) {
         const int jl = jl0 + s;
         if (jl < len) {
           while (off_r[c + 1] <= jl) ++c;
+          if (c != c_decoded) {  // consecutive evaluations often share a cube
+            decode_cube<T, DMAX>(a, (uint32_t)(h0 + c), cb);
+            c_decoded = c;
+          }
           T x[DMAX];
           int bin[DMAX];
           T J;
-          make_point<T, DMAX>(a, (uint32_t)(h0 + c), j0 + jl, tab, x, bin, J);
+          make_point<T, DMAX>(a, cb, j0 + jl, tab, x, bin, J);
           const T f = integrand<ID, T, DMAX>(x, d, prm, a.np_derived, ps0, ps1, pK);
           if (!isfinite(f)) bad = true;
           const T v = J * f;
@@ -433,8 +484,15 @@ __global__ void __launch_bounds__(kFillThreads) fill_kernel(const __grid_constan
             wv_s[jl] = (float)wv;
             my_max = fmaxf(my_max, (float)wv);
 #pragma unroll
-            for (int k = 0; k < DMAX; ++k)
-              if (k < d) bins_s[(size_t)jl * d + k] = (unsigned char)bin[k];
+            for (int w = 0; w < (DMAX + 3) / 4; ++w) {
+              if (4 * w < d) {
+                uint32_t word = 0u;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                  if (4 * w + q < DMAX) word |= (uint32_t)bin[4 * w + q] << (8 * q);
+                binw[jl * nw + w] = word;
+              }
+            }
           } else {
 #pragma unroll
             for (int k = 0; k < DMAX; ++k) {
@@ -444,7 +502,6 @@ __global__ void __launch_bounds__(kFillThreads) fill_kernel(const __grid_constan
               }
             }
           }
-          if (jl == len - 1) misc[1] = c + 1;
         }
       }
     }
@@ -475,7 +532,13 @@ __global__ void __launch_bounds__(kFillThreads) fill_kernel(const __grid_constan
             if (jl < len) {
               const uint32_t q = (uint32_t)__float2uint_rn(wv_s[jl] * scale);
               if (q) {
-                for (int k = 0; k < d; ++k) atomicAdd(hist_u + k * G + bins_s[(size_t)jl * d + k], q);
+                for (int w = 0; w < nw; ++w) {
+                  const uint32_t word = binw[jl * nw + w];
+                  const int kk = 4 * w;
+#pragma unroll
+                  for (int b = 0; b < 4; ++b)
+                    if (kk + b < d) atomicAdd(hist_u + (kk + b) * G + ((word >> (8 * b)) & 255u), q);
+                }
               }
             }
           }
@@ -502,10 +565,13 @@ __global__ void __launch_bounds__(kFillThreads) fill_kernel(const __grid_constan
       acc_i.add(mean);
       if constexpr (sizeof(T) == 8) {
         acc_v.add(m2 / ((double)n * (double)(n - 1)));
+        // the FP64 form keeps the reproducible log2, so that the counts of a
+        // free-running FP64 run follow the CPU reference bit for bit
         ell = __fmul_rn(a.half_beta, log2r(m2 / (double)(n - 1)));
       } else {
-        acc_v.add(m2 / ((float)n * (float)(n - 1)));
-        ell = __fmul_rn(a.half_beta, log2r(__fdiv_rn(m2, (float)(n - 1))));
+        const float nf = (float)n;
+        acc_v.add(__fdividef(m2, nf * (nf - 1.0f)));
+        ell = a.half_beta * log2_fast(__fdividef(m2, nf - 1.0f));
       }
       a.ell[h] = ell;
       lmax = fmaxf(lmax, ell);
@@ -522,28 +588,22 @@ __global__ void __launch_bounds__(kFillThreads) fill_kernel(const __grid_constan
         longlist[atomicAdd(&misc[0], 1)] = c;
         continue;
       }
+      // one pass over the segment, shifted by its first value: mean = v0 + s/L,
+      // M2 = q - s^2/L with s, q the sums of (v - v0) and (v - v0)^2; the shift
+      // keeps q within (L + 1) M2, so the cancellation costs a few ulps
+      const T v0 = vals[r0];
+      T sd = T(0), qd = T(0);
+      for (int r = r0 + 1; r < r1; ++r) {
+        const T dv = vals[r] - v0;
+        sd += dv;
+        qd = fma(dv, dv, qd);
+      }
       if constexpr (sizeof(T) == 8) {
-        double s = 0.0;
-        for (int r = r0; r < r1; ++r) s += vals[r];
-        const double mean = s / (double)L;
-        double q = 0.0;
-        for (int r = r0; r < r1; ++r) {
-          const double dv = vals[r] - mean;
-          q = fma(dv, dv, q);
-        }
-        finish(c, L, mean, q);
+        const double sl = sd / (double)L;
+        finish(c, L, v0 + sl, fmax(fma(-sd, sl, qd), 0.0));
       } else {
-        ff s{0.0f, 0.0f};
-        for (int r = r0; r < r1; ++r) s = ff_add(s, vals[r]);
-        const float Lf = (float)L;
-        const float mh = __fdiv_rn(s.hi, Lf);
-        const float ml = __fdiv_rn(__fadd_rn(fmaf(-mh, Lf, s.hi), s.lo), Lf);
-        float q = 0.0f;
-        for (int r = r0; r < r1; ++r) {
-          const float dv = vals[r] - mh;
-          q = fmaf(dv, dv, q);
-        }
-        finish(c, L, ff{mh, ml}, q);
+        const float sl = __fdividef(sd, (float)L);
+        finish(c, L, ff{v0, sl}, fmaxf(fmaf(-sd, sl, qd), 0.0f));
       }
     }
     __syncthreads();

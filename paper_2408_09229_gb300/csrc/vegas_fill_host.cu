@@ -78,11 +78,13 @@ int smem_layout(FillArgs& a, size_t tsz, int nprm, bool fp32) {
   const int dG = a.d * a.G;
   const size_t base = align_up(nprm * tsz) + align_up(sizeof(int) * (kMaxCubesPerTile + 1)) +
                       align_up(tsz * kMaxCubesPerTile) + align_up(tsz * kTile) +
-                      align_up(sizeof(int) * kMaxCubesPerTile) + align_up(64 + 8 * 32);
+                      align_up(sizeof(int) * kMaxCubesPerTile) + align_up(sizeof(int) * kFillThreads) +
+                      align_up(64 + 8 * 32);
   const size_t budget = 160 * 1024;
   const size_t table = align_up((size_t)dG * 4 * tsz);
-  const size_t two_phase = align_up((size_t)dG * 4) + align_up((size_t)dG * 8) +
-                           align_up((size_t)kTile * a.d) + align_up(sizeof(float) * kTile);
+  const size_t bin_words = (size_t)kTile * 4 * ((a.d + 3) / 4);
+  const size_t two_phase = align_up((size_t)dG * 4) + align_up((size_t)dG * 8) + align_up(bin_words) +
+                           align_up(sizeof(float) * kTile);
   const size_t shared_hist = align_up((size_t)dG * tsz);
   size_t hist;
   if (fp32 && a.G <= 256 && base + two_phase <= budget) {
@@ -102,7 +104,7 @@ int smem_layout(FillArgs& a, size_t tsz, int nprm, bool fp32) {
   if (a.hist_mode == kHistTwoPhase) {
     off += align_up((size_t)dG * 4);
     a.sm_hacc = (int)off; off += align_up((size_t)dG * 8);
-    a.sm_bins = (int)off; off += align_up((size_t)kTile * a.d);
+    a.sm_bins = (int)off; off += align_up(bin_words);
     a.sm_wv = (int)off;   off += align_up(sizeof(float) * kTile);
   } else {
     off += a.hist_mode == kHistShared ? shared_hist : 0;
@@ -113,6 +115,7 @@ int smem_layout(FillArgs& a, size_t tsz, int nprm, bool fp32) {
   a.sm_invn = (int)off;   off += align_up(tsz * kMaxCubesPerTile);
   a.sm_vals = (int)off;   off += align_up(tsz * kTile);
   a.sm_long = (int)off;   off += align_up(sizeof(int) * kMaxCubesPerTile);
+  a.sm_start = (int)off;  off += align_up(sizeof(int) * kFillThreads);
   a.sm_misc = (int)off;   off += align_up(64 + 8 * 32);
   a.sm_total = (int)off;
   return off <= 227 * 1024 ? VEGAS_OK : VEGAS_EINVAL;
@@ -308,8 +311,13 @@ int fill_impl(const vegas_geometry* g, int precision, int integrand, const doubl
     magic_div(a.nstrat[k], a.magic[k], a.shift[k]);
     // z = (c + u) * N_g / s_k: the scale rounded once, in each precision
     a.gz64[k] = (double)G / (double)g->nstrat[k];
+    uint32_t l = 0;
+    while ((1u << l) < (uint32_t)g->nstrat[k]) ++l;
+    a.fbits[k] = 23u - l;
     volatile float gf = (float)G, sf = (float)g->nstrat[k];
-    a.gz32[k] = gf / sf;
+    const float g32 = gf / sf;
+    a.gzb32[k] = std::ldexp(g32, -(int)a.fbits[k]);
+    a.gzn32[k] = -8388608.0f * a.gzb32[k];
   }
   for (int r = 0; r < 10; ++r) {
     a.rk0[r] = a.key0 + (uint32_t)r * 0x9E3779B9u;

@@ -60,10 +60,13 @@ struct FillArgs {
   void* gtable;         // global map table when it does not fit in shared memory
   uint32_t nstrat[kMaxDim], magic[kMaxDim], shift[kMaxDim];
   double gz64[kMaxDim];     // N_g / s_k, rounded in FP64
-  float gz32[kMaxDim];      // N_g / s_k, rounded in FP32
+  float gzb32[kMaxDim];     // RN32(N_g / s_k) 2^-b_k
+  float gzn32[kMaxDim];     // -2^23 RN32(N_g / s_k) 2^-b_k
+  uint32_t fbits[kMaxDim];  // b_k = 23 - ceil(log2 s_k): fraction bits of an FP32 coordinate
   uint32_t rk0[10], rk1[10];  // Philox round keys
   // shared-memory byte offsets of the regions
-  int sm_table, sm_hist, sm_hacc, sm_bins, sm_wv, sm_params, sm_off, sm_invn, sm_vals, sm_long, sm_misc, sm_total;
+  int sm_table, sm_hist, sm_hacc, sm_bins, sm_wv, sm_params, sm_off, sm_invn, sm_vals, sm_long, sm_start, sm_misc,
+      sm_total;
 };
 
 // launchers (one per precision, defined in vegas_fill_f64.cu / vegas_fill_f32.cu)

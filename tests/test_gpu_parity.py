@@ -8,7 +8,7 @@ below, each derived in DESIGN.md ("Tolerances"):
     that rounding bound; I_t 1e-12; map weights 1e-12; sigma_t^2
     1e-10 (the centred moments inherit the cancellation of near-equal
     samples); refined edges 1e-13 absolute; allocation weights ell within
-    4 float ulps.
+    4 float ulps (the FP64 form evaluates them with the reproducible log2).
   FP32 path against the oracle on the same FP32 points: I_t 2e-5 relative,
     sigma_t^2 2e-3 relative, cube means 5e-4 relative of the largest mean.
 Inputs are seeded and synthetic; sizes span several tiles (1024 evaluations)

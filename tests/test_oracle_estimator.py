@@ -152,3 +152,28 @@ def test_first_iteration_uniform_map_is_plain_stratified_mc(orc):
     assert r["est"] == pytest.approx(r["mean"].mean(), rel=1e-15)
     # linear integrand: cube (a, b) has mean ~ centre sum; 9 cubes over [0,1]^2 -> ~1
     assert abs(r["est"] - 1.0) < 5 * math.sqrt(r["var"])
+
+
+@pytest.mark.parametrize("name,iid,d,params", [
+    ("ridge d=4", W.GAUSS_SUM, 4, W.ridge4_params()),
+    ("product peak d=5", W.PRODUCT_PEAK, 5, W.product_peak(5, seed=1)),
+    ("roos-arnold d=10", W.ROOS_ARNOLD, 10, []),
+    ("sin-exp d=2 many strata", W.SIN_EXP, 2, []),
+])
+def test_fp32_points_closed_form(orc, name, iid, d, params):
+    """FP32-mode points (23-bit exact c + u, FP32 z) still sample every cube uniformly:
+    the estimate stays within 4 sigma of the closed form, including with 2^9 strata per axis"""
+    neval = 200_000
+    cfg = orc.Config(d, 50, orc.default_nstrat(neval, d), 0.5, 0.75, points_f32=True)
+    r = orc.integrate(cfg, iid, params, neval, 6, seed=4)
+    assert abs(r["estimate"] - W.exact(iid, d, params)) < 4 * r["sigma"]
+
+
+def test_fp32_points_uniform_in_a_cube(orc):
+    # one cube of a 1-d map with 7 strata: the linear integrand's cube mean is the stratum centre
+    cfg = orc.Config(1, 10, 7, 0.5, 0.75, points_f32=True)
+    edges = cfg.uniform_edges()
+    for h in range(7):
+        m, q = orc.cube_stats(cfg, W.LINEAR, [], 0, 5, edges, h, h * 20_000, 20_000)
+        assert m == pytest.approx((h + 0.5) / 7, abs=4 * math.sqrt((1 / 7) ** 2 / 12 / 20_000))
+        assert q / 19_999 == pytest.approx((1 / 7) ** 2 / 12, rel=0.05)
