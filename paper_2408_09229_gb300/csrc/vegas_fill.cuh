@@ -346,9 +346,9 @@ __device__ __forceinline__ void make_point(const FillArgs& a, const uint32_t (&c
         const uint32_t w = (k & 3) == 0 ? r.x : (k & 3) == 1 ? r.y : (k & 3) == 2 ? r.z : r.w;
         const float big = __uint_as_float(cb[k] | (w >> (32 - a.fbits[k])));  // 2^23 + v
         const float z = fmaf(big, a.gzb32[k], a.gzn32[k]);                     // RN(v g 2^-b)
-        const float fl = fminf(floorf(z), (float)(G - 1));
-        dz = z - fl;  // exact
-        i = __float_as_int(fl + 8388608.0f) & 0x7FFFFF;
+        i = (int)z;  // z >= 0: truncation is floor
+        i = i < G - 1 ? i : G - 1;
+        dz = z - (float)i;  // exact
       }
       const TabEntry<T> te = tab[k * G + i];
       x[k] = fma(dz, te.dx, te.e);
