@@ -147,7 +147,7 @@ def run_ours(args, rank, world):
         return v, r, outer_ms, it_ms, fill_ms
 
     if args.profile:
-        v, r, outer_ms, it_ms, fill_ms = timed_run(V.FP32)
+        v, r, outer_ms, it_ms, fill_ms = timed_run(V.FP32 if args.precision == "fp32" else V.FP64)
         if rank == 0:
             print(json.dumps({"profile": True, "evals_per_s": NEVAL * args.steps / (float(np.sum(it_ms)) / 1e3),
                               "fill_ms": [float(x) for x in fill_ms], "iteration_ms": [float(x) for x in it_ms],
@@ -280,7 +280,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--profile", action="store_true",
-                    help="profiling run: only the warm-up and timed FP32 iterations, a short JSON line")
+                    help="profiling run: only the warm-up and timed iterations of one form, a short JSON line")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+                    help="the form a --profile run times")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(kAllocThreads) block_sum_kernel(const float* _
   const float emax = key_float(*key);
   const int64_t base = (int64_t)blockIdx.x * kBlockCubes;
   uint64_t s = 0;
+#pragma unroll 8
   for (int i = threadIdx.x; i < kBlockCubes; i += kAllocThreads) {
     const int64_t h = base + i;
     if (h < n) s += weight_of(ell, h, uni, emax);
@@ -133,25 +134,41 @@ __device__ __forceinline__ uint64_t share_floor(uint64_t R, uint64_t Qh, uint64_
   return c;
 }
 
-// pass 3: block scan of q and the offsets off_h = 2h + floor(R Q_h / Q)
+// pass 3: block scan of q and the offsets off_h = 2h + floor(R Q_h / Q).
+// The weights come in and the offsets go out through shared memory, so that
+// global accesses are coalesced while every thread works on a run of
+// kAllocItems consecutive cubes.  Padding keeps the runs free of bank conflicts.
+__device__ __forceinline__ int pad32(int x) { return x + (x >> 5); }  // 4-byte words
+__device__ __forceinline__ int pad16(int x) { return x + (x >> 4); }  // 8-byte words
+
 __global__ void __launch_bounds__(kAllocThreads) offsets_kernel(const float* __restrict__ ell, int64_t n,
                                                                 int64_t neval, const int* key, int uniform,
                                                                 const uint64_t* __restrict__ bpre,
                                                                 int64_t* __restrict__ offsets) {
   __shared__ uint64_t warp_tot[kAllocThreads / 32];
+  __shared__ int64_t stage[kBlockCubes + kBlockCubes / 16];
+  __shared__ double r_over_q_s;
+  uint32_t* qs = reinterpret_cast<uint32_t*>(stage);  // the weights, before the offsets reuse the space
   const bool uni = is_uniform(key, uniform);
   const float emax = uni ? 0.0f : key_float(*key);
   const int64_t nb = (n + kBlockCubes - 1) / kBlockCubes;
   const uint64_t R = (uint64_t)(neval - 2 * n);
   const uint64_t Q = uni ? (uint64_t)n : bpre[nb];
-  const double r_over_q = (double)R / (double)Q;
-  const int64_t base = (int64_t)blockIdx.x * kBlockCubes + (int64_t)threadIdx.x * kAllocItems;
+  // FP64 is scarce on this GPU: one division per block, none per cube
+  if (threadIdx.x == 0) r_over_q_s = (double)R / (double)Q;
+  const int64_t block0 = (int64_t)blockIdx.x * kBlockCubes;
+  const int64_t base = block0 + (int64_t)threadIdx.x * kAllocItems;
+#pragma unroll 4
+  for (int i = threadIdx.x; i < kBlockCubes; i += kAllocThreads) {
+    const int64_t h = block0 + i;
+    qs[pad32(i)] = (h < n) ? (uni ? 1u : quant_weight(ell[h], emax)) : 0u;
+  }
+  __syncthreads();
   uint32_t q[kAllocItems];
   uint64_t tsum = 0;
 #pragma unroll
   for (int i = 0; i < kAllocItems; ++i) {
-    const int64_t h = base + i;
-    q[i] = (h < n) ? (uni ? 1u : quant_weight(ell[h], emax)) : 0u;
+    q[i] = qs[pad32(threadIdx.x * kAllocItems + i)];
     tsum += q[i];
   }
   // exclusive scan of the thread sums across the block
@@ -163,16 +180,44 @@ __global__ void __launch_bounds__(kAllocThreads) offsets_kernel(const float* __r
     if (lane >= o) x += y;
   }
   if (lane == 31) warp_tot[w] = x;
-  __syncthreads();
+  __syncthreads();  // also: every thread has read its weights from qs
   uint64_t wbefore = 0;
   for (int k = 0; k < w; ++k) wbefore += warp_tot[k];
   uint64_t Qh = (uni ? (uint64_t)blockIdx.x * kBlockCubes : bpre[blockIdx.x]) + wbefore + (x - tsum);
+  // the thread's first share exactly, then share_{h+1} = share_h + floor((rem_h + R q_h) / Q)
+  // with rem_h = R Q_h - share_h Q carried exactly; FP32 estimates every step and
+  // integer compares correct it, so no step needs FP64
+  uint64_t share = share_floor(R, Qh, Q, r_over_q_s);
+  uint64_t rem = (uint64_t)((unsigned __int128)R * Qh - (unsigned __int128)share * Q);
+  const float inv_q = 1.0f / ((float)(uint32_t)(Q >> 32) * 4294967296.0f + (float)(uint32_t)Q);
 #pragma unroll
   for (int i = 0; i < kAllocItems; ++i) {
     const int64_t h = base + i;
-    if (h < n) offsets[h] = 2 * h + (int64_t)share_floor(R, Qh, Q, r_over_q);
-    Qh += q[i];
+    stage[pad16(threadIdx.x * kAllocItems + i)] = 2 * h + (int64_t)share;
+    const uint64_t X = rem + R * (uint64_t)q[i];  // < 2^57
+    // X to float from its 32-bit halves (32-bit conversions, no FP64 pipe)
+    const float xf = fmaf((float)(uint32_t)(X >> 32), 4294967296.0f, (float)(uint32_t)X);
+    uint64_t inc = (uint64_t)(uint32_t)fminf(xf * inv_q, 4294967040.0f);
+    if (inc > (1ull << 20)) {  // a heavy cube: the FP32 estimate is too coarse
+      inc = share_floor(X, 1, Q, (double)X / (double)Q);
+    } else {
+      unsigned __int128 t = (unsigned __int128)inc * Q;
+      for (int it = 0; it < 8 && t > X; ++it) {
+        --inc;
+        t -= Q;
+      }
+      for (int it = 0; it < 8 && t + Q <= X; ++it) {
+        ++inc;
+        t += Q;
+      }
+    }
+    share += inc;
+    rem = X - inc * Q;
   }
+  __syncthreads();
+#pragma unroll 4
+  for (int i = threadIdx.x; i < kBlockCubes; i += kAllocThreads)
+    if (block0 + i < n) offsets[block0 + i] = stage[pad16(i)];
   if (base <= n - 1 && n - 1 < base + kAllocItems) offsets[n] = neval;  // the thread of the last cube
 }
 
@@ -186,22 +231,31 @@ extern "C" size_t vegas_allocate_scratch_bytes(int64_t ncubes) {
   return alloc_layout(ncubes).total;
 }
 
-extern "C" int vegas_allocate(const float* d_ell, int64_t ncubes, int64_t neval, int uniform, int64_t* d_offsets,
-                              void* d_scratch, size_t scratch_bytes, void* stream) {
+namespace vg {
+// d_key: the order-preserving key of max ell when the caller already has it
+// (the fill computes it), or NULL to compute it here
+int allocate_impl(const float* d_ell, int64_t ncubes, int64_t neval, int uniform, int64_t* d_offsets,
+                  void* d_scratch, size_t scratch_bytes, cudaStream_t s, const int* d_key) {
   if (ncubes < 1 || ncubes >= (int64_t(1) << 31) || neval < 2 * ncubes || neval > kMaxEval) return VEGAS_EINVAL;
   if (!d_offsets || !d_scratch || (!uniform && !d_ell)) return VEGAS_EINVAL;
   const AllocScratch L = alloc_layout(ncubes);
   if (scratch_bytes < L.total) return VEGAS_ENOSPACE;
-  cudaStream_t s = (cudaStream_t)stream;
   unsigned char* sc = (unsigned char*)d_scratch;
-  int* key = (int*)(sc + L.key);
+  int* own_key = (int*)(sc + L.key);
   uint64_t* bsum = (uint64_t*)(sc + L.bsum);
-  key_init_kernel<<<1, 1, 0, s>>>(key);
-  VG_CHECK(cudaGetLastError());
-  if (!uniform) {
-    const int grid = (int)std::min<int64_t>((ncubes + 255) / 256, 4096);
-    max_kernel<<<grid, 256, 0, s>>>(d_ell, ncubes, key);
+  const int* key = own_key;
+  if (d_key && !uniform) {
+    key = d_key;
+  } else {
+    key_init_kernel<<<1, 1, 0, s>>>(own_key);
     VG_CHECK(cudaGetLastError());
+    if (!uniform) {
+      const int grid = (int)std::min<int64_t>((ncubes + 255) / 256, 4096);
+      max_kernel<<<grid, 256, 0, s>>>(d_ell, ncubes, own_key);
+      VG_CHECK(cudaGetLastError());
+    }
+  }
+  if (!uniform) {
     block_sum_kernel<<<(unsigned)L.nblocks, kAllocThreads, 0, s>>>(d_ell, ncubes, key, 0, bsum);
     VG_CHECK(cudaGetLastError());
     block_scan_kernel<<<1, 1024, 0, s>>>(bsum, L.nblocks);
@@ -210,6 +264,13 @@ extern "C" int vegas_allocate(const float* d_ell, int64_t ncubes, int64_t neval,
   offsets_kernel<<<(unsigned)L.nblocks, kAllocThreads, 0, s>>>(d_ell, ncubes, neval, key, uniform, bsum, d_offsets);
   VG_CHECK(cudaGetLastError());
   return VEGAS_OK;
+}
+}  // namespace vg
+
+extern "C" int vegas_allocate(const float* d_ell, int64_t ncubes, int64_t neval, int uniform, int64_t* d_offsets,
+                              void* d_scratch, size_t scratch_bytes, void* stream) {
+  return vg::allocate_impl(d_ell, ncubes, neval, uniform, d_offsets, d_scratch, scratch_bytes, (cudaStream_t)stream,
+                           nullptr);
 }
 
 // ---------------------------------------------------------------------------

@@ -46,6 +46,7 @@ struct vegas_s {
   double* h_out = nullptr;  // pinned [4]
   // carried-over stratification
   bool ell_valid = false;
+  const int* fill_key = nullptr;  // max-ell key left in the fill scratch by the last fill, or NULL
   std::vector<int32_t> ell_nstrat;
   int64_t iter_counter = 0;
   // timing
@@ -255,6 +256,7 @@ extern "C" int vegas_reset_map(vegas_handle h) {
   DeviceGuard g(h->device);
   VG_CHECK(cudaStreamSynchronize(h->stream()));
   h->ell_valid = false;
+  h->fill_key = nullptr;
   h->iter_counter = 0;
   return upload_uniform_edges(h);
 }
@@ -291,6 +293,7 @@ extern "C" int vegas_integrate(vegas_handle h, int integrand, const double* para
   const size_t fill_need = vegas_fill_scratch_bytes(&geo, neval);
   const size_t alloc_need = vegas_allocate_scratch_bytes(NH);
   if (fill_need == 0 || alloc_need == 0) return VEGAS_EINVAL;
+  if (fill_need > h->fill_scratch_cap) h->fill_key = nullptr;  // the scratch is about to move
   if ((rc = grow_bytes(h->d_fill_scratch, h->fill_scratch_cap, fill_need)) != VEGAS_OK) return rc;
   if ((rc = grow_bytes(h->d_alloc_scratch, h->alloc_scratch_cap, alloc_need)) != VEGAS_OK) return rc;
   if (nparams > 0 && (rc = grow(h->d_params, h->params_cap, nparams)) != VEGAS_OK) return rc;
@@ -319,13 +322,14 @@ extern "C" int vegas_integrate(vegas_handle h, int integrand, const double* para
   for (int it = 0; it < nitn; ++it) {
     cudaEvent_t* e = &h->ev[4 * it];
     VG_CHECK(cudaEventRecord(e[0], s));
-    rc = vegas_allocate(h->d_ell, NH, neval, (uniform || h->beta == 0.0) ? 1 : 0, h->d_offsets, h->d_alloc_scratch,
-                        h->alloc_scratch_cap, s);
+    rc = vg::allocate_impl(h->d_ell, NH, neval, (uniform || h->beta == 0.0) ? 1 : 0, h->d_offsets,
+                           h->d_alloc_scratch, h->alloc_scratch_cap, s, h->fill_key);
     if (rc != VEGAS_OK) return rc;
     rc = vg::fill_impl(&geo, h->precision, integrand, h->d_params, nparams, neval, seed, (int32_t)h->iter_counter, 0u,
                        h->beta, h->d_edges[h->cur], h->d_offsets, h->d_ell, h->d_bins, h->d_result, nullptr, nullptr,
                        h->d_flags, h->d_fill_scratch, h->fill_scratch_cap, s, e[1], e[2]);
     if (rc != VEGAS_OK) return rc;
+    h->fill_key = vg::fill_ellmax_key(&geo, neval, h->d_fill_scratch);
     rc = vegas_refine(d, G, h->alpha, h->d_bins, h->d_edges[h->cur], h->d_edges[1 - h->cur], s);
     if (rc != VEGAS_OK) return rc;
     h->cur = 1 - h->cur;
@@ -447,6 +451,7 @@ extern "C" int vegas_set_state(vegas_handle h, const void* buf, size_t bytes) {
   h->cur = 0;
   VG_CHECK(cudaMemcpy(h->d_edges[0], p + sizeof hd, sizeof(double) * ne, cudaMemcpyHostToDevice));
   h->ell_valid = false;
+  h->fill_key = nullptr;
   if (nc > 0) {
     const int rc = ensure_cubes(h, nc + 1);
     if (rc != VEGAS_OK) return rc;

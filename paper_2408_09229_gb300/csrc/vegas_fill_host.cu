@@ -217,13 +217,24 @@ __global__ void results_kernel(const double* __restrict__ cta_part, int ncta, co
   }
 }
 
-// map weights: sum the per-CTA histograms in CTA order
-__global__ void bins_kernel(const double* __restrict__ hist_part, int ncta, int dG, double* bins) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= dG) return;
+// map weights: sum the per-CTA histograms.  A block owns 32 bins (one per
+// lane); its 8 warps take every 8th CTA, and the 8 warp sums are added in
+// warp order, so the order is fixed.
+__global__ void __launch_bounds__(256) bins_kernel(const double* __restrict__ hist_part, int ncta, int dG,
+                                                   double* bins) {
+  __shared__ double part[8][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int b = blockIdx.x * 32 + lane;
   double s = 0.0;
-  for (int c = 0; c < ncta; ++c) s += hist_part[(size_t)c * dG + b];
-  bins[b] = s;
+  if (b < dG)
+    for (int c = w; c < ncta; c += 8) s += hist_part[(size_t)c * dG + b];
+  part[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && b < dG) {
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += part[k][lane];
+    bins[b] = t;
+  }
 }
 
 // magic multiplier for n / s with n < 2^31 (Granlund & Montgomery, PLDI'94,
@@ -352,7 +363,7 @@ int fill_impl(const vegas_geometry* g, int precision, int integrand, const doubl
   VG_CHECK(cudaGetLastError());
   results_kernel<<<1, 256, 0, s>>>(a.cta_part, grid, fix_part, L.nfix, a.NH, d_result);
   VG_CHECK(cudaGetLastError());
-  bins_kernel<<<(d * G + 255) / 256, 256, 0, s>>>(a.hist_part, grid, d * G, d_bins);
+  bins_kernel<<<(d * G + 31) / 32, 256, 0, s>>>(a.hist_part, grid, d * G, d_bins);
   VG_CHECK(cudaGetLastError());
   return VEGAS_OK;
 }
@@ -368,3 +379,10 @@ extern "C" int vegas_fill(const vegas_geometry* g, int precision, int integrand,
                    stream, nullptr, nullptr);
 }
 
+
+namespace vg {
+const int* fill_ellmax_key(const vegas_geometry* g, int64_t neval, const void* d_scratch) {
+  const ScratchLayout L = scratch_layout(g->dim, g->nbins, neval, num_sms());
+  return (const int*)((const unsigned char*)d_scratch + L.ellmax);
+}
+}  // namespace vg

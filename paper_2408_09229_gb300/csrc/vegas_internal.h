@@ -80,6 +80,10 @@ int fill_impl(const vegas_geometry* g, int precision, int integrand, const doubl
               const double* d_edges, const int64_t* d_offsets, float* d_ell, double* d_bins, double* d_result,
               double* d_cube_mean, double* d_cube_m2, int* d_flags, void* d_scratch, size_t scratch_bytes,
               void* stream, cudaEvent_t ev_before, cudaEvent_t ev_after);
+int allocate_impl(const float* d_ell, int64_t ncubes, int64_t neval, int uniform, int64_t* d_offsets,
+                  void* d_scratch, size_t scratch_bytes, cudaStream_t s, const int* d_key);
+// device address of the fill's max-ell key inside its scratch area
+const int* fill_ellmax_key(const vegas_geometry* g, int64_t neval, const void* d_scratch);
 int launch_record_combine(const double* d_result, int t, double* d_est, double* d_sig, int skip, double* d_out,
                           cudaStream_t s);
 
