@@ -57,19 +57,44 @@ __device__ __forceinline__ uint64_t weight_of(const float* __restrict__ ell, int
   return uni ? 1ull : (uint64_t)quant_weight(ell[h], emax);
 }
 
+// the quantised weights of cubes [base, base + kAllocItems): four 16-byte
+// loads issued together when the run is whole and aligned, scalar loads else
+__device__ __forceinline__ void load_weights(const float* __restrict__ ell, int64_t base, int64_t n, bool uni,
+                                             float emax, uint32_t (&q)[kAllocItems]) {
+  if (uni) {
+#pragma unroll
+    for (int i = 0; i < kAllocItems; ++i) q[i] = base + i < n ? 1u : 0u;
+    return;
+  }
+  if (base + kAllocItems <= n && ((reinterpret_cast<uintptr_t>(ell + base) & 15) == 0)) {
+    const float4* p = reinterpret_cast<const float4*>(ell + base);
+    float4 v[kAllocItems / 4];
+#pragma unroll
+    for (int i = 0; i < kAllocItems / 4; ++i) v[i] = __ldg(p + i);
+#pragma unroll
+    for (int i = 0; i < kAllocItems / 4; ++i) {
+      q[4 * i] = quant_weight(v[i].x, emax);
+      q[4 * i + 1] = quant_weight(v[i].y, emax);
+      q[4 * i + 2] = quant_weight(v[i].z, emax);
+      q[4 * i + 3] = quant_weight(v[i].w, emax);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < kAllocItems; ++i) q[i] = base + i < n ? quant_weight(ell[base + i], emax) : 0u;
+  }
+}
+
 // pass 1: sum of q over each block of kBlockCubes cubes
 __global__ void __launch_bounds__(kAllocThreads) block_sum_kernel(const float* __restrict__ ell, int64_t n,
                                                                   const int* key, int uniform, uint64_t* bsum) {
   __shared__ uint64_t red[kAllocThreads / 32];
   const bool uni = is_uniform(key, uniform);
   const float emax = key_float(*key);
-  const int64_t base = (int64_t)blockIdx.x * kBlockCubes;
+  uint32_t q[kAllocItems];
+  load_weights(ell, (int64_t)blockIdx.x * kBlockCubes + (int64_t)threadIdx.x * kAllocItems, n, uni, emax, q);
   uint64_t s = 0;
-#pragma unroll 8
-  for (int i = threadIdx.x; i < kBlockCubes; i += kAllocThreads) {
-    const int64_t h = base + i;
-    if (h < n) s += weight_of(ell, h, uni, emax);
-  }
+#pragma unroll
+  for (int i = 0; i < kAllocItems; ++i) s += q[i];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -135,10 +160,9 @@ __device__ __forceinline__ uint64_t share_floor(uint64_t R, uint64_t Qh, uint64_
 }
 
 // pass 3: block scan of q and the offsets off_h = 2h + floor(R Q_h / Q).
-// The weights come in and the offsets go out through shared memory, so that
-// global accesses are coalesced while every thread works on a run of
-// kAllocItems consecutive cubes.  Padding keeps the runs free of bank conflicts.
-__device__ __forceinline__ int pad32(int x) { return x + (x >> 5); }  // 4-byte words
+// Every thread works on a run of kAllocItems consecutive cubes; the offsets
+// go out through shared memory so that the global stores are coalesced.
+// Padding keeps the runs free of bank conflicts.
 __device__ __forceinline__ int pad16(int x) { return x + (x >> 4); }  // 8-byte words
 
 __global__ void __launch_bounds__(kAllocThreads) offsets_kernel(const float* __restrict__ ell, int64_t n,
@@ -148,7 +172,6 @@ __global__ void __launch_bounds__(kAllocThreads) offsets_kernel(const float* __r
   __shared__ uint64_t warp_tot[kAllocThreads / 32];
   __shared__ int64_t stage[kBlockCubes + kBlockCubes / 16];
   __shared__ double r_over_q_s;
-  uint32_t* qs = reinterpret_cast<uint32_t*>(stage);  // the weights, before the offsets reuse the space
   const bool uni = is_uniform(key, uniform);
   const float emax = uni ? 0.0f : key_float(*key);
   const int64_t nb = (n + kBlockCubes - 1) / kBlockCubes;
@@ -158,19 +181,11 @@ __global__ void __launch_bounds__(kAllocThreads) offsets_kernel(const float* __r
   if (threadIdx.x == 0) r_over_q_s = (double)R / (double)Q;
   const int64_t block0 = (int64_t)blockIdx.x * kBlockCubes;
   const int64_t base = block0 + (int64_t)threadIdx.x * kAllocItems;
-#pragma unroll 4
-  for (int i = threadIdx.x; i < kBlockCubes; i += kAllocThreads) {
-    const int64_t h = block0 + i;
-    qs[pad32(i)] = (h < n) ? (uni ? 1u : quant_weight(ell[h], emax)) : 0u;
-  }
-  __syncthreads();
   uint32_t q[kAllocItems];
+  load_weights(ell, base, n, uni, emax, q);
   uint64_t tsum = 0;
 #pragma unroll
-  for (int i = 0; i < kAllocItems; ++i) {
-    q[i] = qs[pad32(threadIdx.x * kAllocItems + i)];
-    tsum += q[i];
-  }
+  for (int i = 0; i < kAllocItems; ++i) tsum += q[i];
   // exclusive scan of the thread sums across the block
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint64_t x = tsum;
@@ -180,7 +195,7 @@ __global__ void __launch_bounds__(kAllocThreads) offsets_kernel(const float* __r
     if (lane >= o) x += y;
   }
   if (lane == 31) warp_tot[w] = x;
-  __syncthreads();  // also: every thread has read its weights from qs
+  __syncthreads();
   uint64_t wbefore = 0;
   for (int k = 0; k < w; ++k) wbefore += warp_tot[k];
   uint64_t Qh = (uni ? (uint64_t)blockIdx.x * kBlockCubes : bpre[blockIdx.x]) + wbefore + (x - tsum);

@@ -293,13 +293,13 @@ __device__ __forceinline__ uint4 philox_rk(uint4 c, const uint32_t* rk0, const u
 // Coordinates c_k of cube h (axis 0 fastest), by multiplication with the
 // magic reciprocals.  In the FP32 form they are kept as the high bits of a
 // float in [2^23, 2^24): 0x4B000000 | c_k << b_k, with b_k fraction bits.
-template <typename T, int DMAX>
+template <typename T, int DMAX, bool EXACT>
 __device__ __forceinline__ void decode_cube(const FillArgs& a, uint32_t h, uint32_t (&cb)[DMAX]) {
   uint32_t rest = h;
 #pragma unroll
   for (int k = 0; k < DMAX; ++k) {
     cb[k] = 0u;
-    if (k < a.d) {
+    if (EXACT || k < a.d) {
       const uint32_t q = (uint32_t)(((uint64_t)rest * a.magic[k]) >> a.shift[k]);  // rest / s_k
       const uint32_t ck = rest - q * a.nstrat[k];
       rest = q;
@@ -317,7 +317,7 @@ __device__ __forceinline__ void decode_cube(const FillArgs& a, uint32_t h, uint3
 //         float 2^23 + v is assembled from bits, and z = RN(v g 2^-b) is one
 //         fused multiply-add with the exact constant -2^23 g 2^-b.
 // Axes beyond d get x = 0 (the padded integrand parameters match).
-template <typename T, int DMAX>
+template <typename T, int DMAX, bool EXACT>
 __device__ __forceinline__ void make_point(const FillArgs& a, const uint32_t (&cb)[DMAX], int64_t j,
                                            const TabEntry<T>* __restrict__ tab, T (&x)[DMAX], int (&bin)[DMAX],
                                            T& J) {
@@ -329,7 +329,7 @@ __device__ __forceinline__ void make_point(const FillArgs& a, const uint32_t (&c
   for (int k = 0; k < DMAX; ++k) {
     x[k] = T(0);
     bin[k] = 0;
-    if (k < a.d) {
+    if (EXACT || k < a.d) {
       int i;
       T dz;
       if constexpr (sizeof(T) == 8) {
@@ -358,13 +358,15 @@ __device__ __forceinline__ void make_point(const FillArgs& a, const uint32_t (&c
   }
 }
 
-template <int ID, typename T, int DMAX>
+// EXACT: d == DMAX and the map table is in shared memory, so the per-axis
+// bounds checks vanish and the table reads are shared-memory loads.
+template <int ID, typename T, int DMAX, bool EXACT>
 __global__ void __launch_bounds__(kFillThreads) fill_kernel(const __grid_constant__ FillArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int d = a.d, G = a.G, dG = a.d * a.G;
+  const int d = EXACT ? DMAX : a.d, G = a.G, dG = d * a.G;
   const bool two_phase = a.hist_mode == kHistTwoPhase;
-  TabEntry<T>* tab = a.table_smem ? (TabEntry<T>*)(smem + a.sm_table) : (TabEntry<T>*)a.gtable;
+  TabEntry<T>* tab = (EXACT || a.table_smem) ? (TabEntry<T>*)(smem + a.sm_table) : (TabEntry<T>*)a.gtable;
   T* hist_s = (T*)(smem + a.sm_hist);                 // direct mode: shared histogram of T
   uint32_t* hist_u = (uint32_t*)(smem + a.sm_hist);   // two-phase: fixed-point tile histogram
   ff* hist_acc = (ff*)(smem + a.sm_hacc);             // two-phase: float-float CTA histogram
@@ -383,7 +385,7 @@ __global__ void __launch_bounds__(kFillThreads) fill_kernel(const __grid_constan
   double* red = (double*)(smem + a.sm_misc + 64);
 
   // ---- prologue: map table, histograms, parameters ----
-  if (a.table_smem) {
+  if (EXACT || a.table_smem) {
     for (int b = tid; b < dG; b += kFillThreads) {
       const int k = b / G, i = b - k * G;
       const double e0 = a.edges[k * (G + 1) + i], e1 = a.edges[k * (G + 1) + i + 1];
@@ -468,13 +470,13 @@ __global__ void __launch_bounds__(kFillThreads) fill_kernel(const __grid_constan
         if (jl < len) {
           while (off_r[c + 1] <= jl) ++c;
           if (c != c_decoded) {  // consecutive evaluations often share a cube
-            decode_cube<T, DMAX>(a, (uint32_t)(h0 + c), cb);
+            decode_cube<T, DMAX, EXACT>(a, (uint32_t)(h0 + c), cb);
             c_decoded = c;
           }
           T x[DMAX];
           int bin[DMAX];
           T J;
-          make_point<T, DMAX>(a, cb, j0 + jl, tab, x, bin, J);
+          make_point<T, DMAX, EXACT>(a, cb, j0 + jl, tab, x, bin, J);
           const T f = integrand<ID, T, DMAX>(x, d, prm, a.np_derived, ps0, ps1, pK);
           if (!isfinite(f)) bad = true;
           const T v = J * f;

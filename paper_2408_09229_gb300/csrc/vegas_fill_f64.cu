@@ -6,7 +6,7 @@ namespace {
 
 template <int ID, int DMAX>
 int launch_one(FillArgs& a, int grid, cudaStream_t s) {
-  auto k = fill_kernel<ID, double, DMAX>;
+  auto k = fill_kernel<ID, double, DMAX, false>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, a.sm_total);
   if (e != cudaSuccess) return VEGAS_ECUDA;
   k<<<grid, kFillThreads, a.sm_total, s>>>(a);
@@ -15,7 +15,7 @@ int launch_one(FillArgs& a, int grid, cudaStream_t s) {
 
 template <int ID, int DMAX>
 int occupancy_one(int smem) {
-  auto k = fill_kernel<ID, double, DMAX>;
+  auto k = fill_kernel<ID, double, DMAX, false>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kFillThreads, smem) != cudaSuccess) return 0;

@@ -337,8 +337,12 @@ int fill_impl(const vegas_geometry* g, int precision, int integrand, const doubl
   const size_t tsz = precision == VEGAS_FP64 ? sizeof(double) : sizeof(float);
   if (smem_layout(a, tsz, nprm, precision == VEGAS_FP32) != VEGAS_OK) return VEGAS_EINVAL;
 
-  const int per_sm = precision == VEGAS_FP64 ? fill_occupancy_f64(integrand, dmax, a.sm_total)
-                                             : fill_occupancy_f32(integrand, dmax, a.sm_total);
+  const bool exact = d == dmax && (dmax == 4 || dmax == 8) && a.table_smem;
+  const int per_sm = precision == VEGAS_FP64
+                         ? (exact ? fill_occupancy_f64_exact(integrand, dmax, a.sm_total)
+                                  : fill_occupancy_f64(integrand, dmax, a.sm_total))
+                         : (exact ? fill_occupancy_f32_exact(integrand, dmax, a.sm_total)
+                                  : fill_occupancy_f32(integrand, dmax, a.sm_total));
   if (per_sm <= 0) return VEGAS_ECUDA;
   const int grid = std::max(1, std::min(L.grid_max, per_sm * sms));
 
@@ -354,8 +358,9 @@ int fill_impl(const vegas_geometry* g, int precision, int integrand, const doubl
     VG_CHECK(cudaGetLastError());
   }
   if (ev_before) VG_CHECK(cudaEventRecord(ev_before, s));
-  const int rc = precision == VEGAS_FP64 ? launch_fill_f64(integrand, dmax, a, grid, s)
-                                         : launch_fill_f32(integrand, dmax, a, grid, s);
+  const int rc = precision == VEGAS_FP64
+                     ? (exact ? launch_fill_f64_exact(integrand, dmax, a, grid, s) : launch_fill_f64(integrand, dmax, a, grid, s))
+                     : (exact ? launch_fill_f32_exact(integrand, dmax, a, grid, s) : launch_fill_f32(integrand, dmax, a, grid, s));
   if (rc != VEGAS_OK) return rc;
   if (ev_after) VG_CHECK(cudaEventRecord(ev_after, s));
   double* fix_part = (double*)(sc + L.fix_part);

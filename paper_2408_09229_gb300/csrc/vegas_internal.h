@@ -74,6 +74,11 @@ int launch_fill_f64(int integrand, int dmax, FillArgs& a, int grid, cudaStream_t
 int launch_fill_f32(int integrand, int dmax, FillArgs& a, int grid, cudaStream_t s);
 int fill_occupancy_f64(int integrand, int dmax, int smem);
 int fill_occupancy_f32(int integrand, int dmax, int smem);
+// d == dmax (4 or 8) and the map table in shared memory
+int launch_fill_f64_exact(int integrand, int dmax, FillArgs& a, int grid, cudaStream_t s);
+int launch_fill_f32_exact(int integrand, int dmax, FillArgs& a, int grid, cudaStream_t s);
+int fill_occupancy_f64_exact(int integrand, int dmax, int smem);
+int fill_occupancy_f32_exact(int integrand, int dmax, int smem);
 
 int fill_impl(const vegas_geometry* g, int precision, int integrand, const double* d_params, int64_t nparams,
               int64_t neval, uint64_t seed, int32_t iteration, uint32_t problem_id, double beta,
