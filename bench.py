@@ -38,8 +38,11 @@ METRIC = "evals/s and time to 1e-4 rel. error, chosen form vs plain VEGAS+, 1 GB
 D, NBINS, NSTRAT, ALPHA, BETA, NEVAL, NITN, SEED, K_PEAKS, SIGMA = 8, 50, 9, 0.5, 0.75, 100_000_000, 15, 0, 5, 0.05
 WORKLOAD = ("plain VEGAS+ d=8, ridge of 5 Gaussians (s=0.05) on the diagonal, Ng=50, 9^8 cubes, "
             "1e8 evals/iteration, beta=0.75, alpha=0.5, Philox seed 0")
-# MEASURED_PEAKS-independent nominal SM facts of GB300 (152 SMs, 128 FP32 lanes per SM, 2070 MHz max)
+# nominal SM facts of GB300 (152 SMs, 128 FP32 lanes per SM, 2070 MHz maximum SM clock)
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) of one launch of the dominant kernel on this workload, from the ncu capture
+# summarised in profiles/fill_kernel_ridge8_fp32.md: the per-cube offsets and weights, set by the data layout
+FILL_TRAFFIC_BYTES = (346.26 + 146.93) * 1e6
 
 
 def fp32_ops_per_eval(d=D, K=K_PEAKS):
@@ -215,8 +218,9 @@ def run_ours(args, rank, world):
         "time_to_rtol": {"rtol": 1e-4, "fp32_form": ttr32, "plain_fp64": ttr64},
         "e2e": {"value": NEVAL * args.steps * world / t_e2e, "unit": "evals/s",
                 "h2d_bytes_per_step": 8 * len(params), "d2h_bytes_per_step": 8 * 4 + 2 * 8 + 4},
-        "roofline": {"bound": "alu", "kernel": "fill_kernel<GAUSS_SUM, float, 8>", "achieved": achieved,
-                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+        "roofline": {"bound": "alu", "kernel": "fill_kernel<GAUSS_SUM, float, 8, exact>", "achieved": achieved,
+                     "peak": peak, "unit": "Tops/s (FP32-pipe operations, FMA = 1)", "frac": achieved / peak,
+                     "traffic": FILL_TRAFFIC_BYTES,
                      "ops_per_eval": ops, "fill_ms": fill_mean32 * 1e3,
                      "peak_basis": "FP32 FMA pipe: 128 lanes x %d SMs x 2070 MHz (max SM clock)" % sms,
                      "probe_ops_per_sm_clk": {"ffma": rates[0], "dfma": rates[1], "mufu_ex2": rates[2],

@@ -216,7 +216,8 @@ __global__ void __launch_bounds__(kAllocThreads) offsets_kernel(const float* __r
     if (inc > (1ull << 20)) {  // a heavy cube: the FP32 estimate is too coarse
       inc = share_floor(X, 1, Q, (double)X / (double)Q);
     } else {
-      unsigned __int128 t = (unsigned __int128)inc * Q;
+      // inc is within one of floor(X/Q) <= 2^20, so inc Q <= X + Q < 2^58: 64 bits suffice
+      uint64_t t = inc * Q;
       for (int it = 0; it < 8 && t > X; ++it) {
         --inc;
         t -= Q;

