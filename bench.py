@@ -133,15 +133,15 @@ def run_ours(args, rank, world):
     stream = torch.cuda.Stream()
     params = W.ridge8_params()
 
-    def timed_run(precision):
+    def timed_run(precision, iid=W.GAUSS_SUM, prm=params):
         v = V.Vegas(D, NBINS, NSTRAT, ALPHA, BETA, precision=precision, stream=stream)
-        v.integrate(W.GAUSS_SUM, params, NEVAL, args.warmup, seed=SEED + rank)
+        v.integrate(iid, prm, NEVAL, args.warmup, seed=SEED + rank)
         torch.cuda.synchronize()
         barrier(world)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        r = v.integrate(W.GAUSS_SUM, params, NEVAL, args.steps, seed=SEED + rank)
+        r = v.integrate(iid, prm, NEVAL, args.steps, seed=SEED + rank)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier(world)
@@ -164,6 +164,16 @@ def run_ours(args, rank, world):
     time.sleep(0.3)
     v32, r32, outer32, it32, fill32 = timed_run(V.FP32)
     v64, r64, outer64, it64, fill64 = timed_run(V.FP64)
+    # the second integrand of the same configuration: the product peak
+    pp = W.product_peak8_params()
+    pp_exact = W.exact(W.PRODUCT_PEAK, D, pp)
+    pp_lines = {}
+    for name, prec in (("fp32_form", V.FP32), ("plain_fp64", V.FP64)):
+        _, rp, _, itp, flp = timed_run(prec, W.PRODUCT_PEAK, pp)
+        pp_lines[name] = {"value": NEVAL * args.steps * world / max_over_ranks(float(np.sum(itp)) / 1e3, world),
+                          "unit": "evals/s", "ms_per_step": float(np.mean(itp)), "fill_ms": float(np.mean(flp)),
+                          "rel_err": rp["sigma"] / abs(rp["estimate"]),
+                          "pulls_from_exact": (rp["estimate"] - pp_exact) / rp["sigma"]}
     stop.set()
     th.join(timeout=10)
     clocks = summarize_clocks(clock_lines)
@@ -204,7 +214,9 @@ def run_ours(args, rank, world):
     ops = fp32_ops_per_eval()
     achieved = ops * NEVAL / fill_mean32 / 1e12
     peak = FP32_LANES_PER_SM * sms * 2070e6 / 1e12
-    launches_per_it = 12
+    # per steady iteration: allocation 3 (q sums, their scan, offsets; the max of the weights comes from
+    # the fill), fill 5 (tile search, fill, fix-up, results, map weights), refinement 1, combination 1
+    launches_per_it = 10
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_dev32 / args.steps * 1e3, "higher_is_better": True,
@@ -215,6 +227,8 @@ def run_ours(args, rank, world):
         "plain_fp64": {"value": evals / t_dev64, "unit": "evals/s", "ms_per_step": t_dev64 / args.steps * 1e3,
                        "estimate": r64["estimate"], "sigma": r64["sigma"]},
         "result_fp32": {"estimate": r32["estimate"], "sigma": r32["sigma"], "chi2_dof": r32["chi2_dof"]},
+        "product_peak": dict(pp_lines, workload="product peak prod 1/(c^-2 + (x - w)^2), c ~ U[5,15], "
+                                                "w ~ U[0.2,0.8], seed 0; same d, cubes and evaluations"),
         "time_to_rtol": {"rtol": 1e-4, "fp32_form": ttr32, "plain_fp64": ttr64},
         "e2e": {"value": NEVAL * args.steps * world / t_e2e, "unit": "evals/s",
                 "h2d_bytes_per_step": 8 * len(params), "d2h_bytes_per_step": 8 * 4 + 2 * 8 + 4},

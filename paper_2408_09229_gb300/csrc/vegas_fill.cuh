@@ -99,7 +99,7 @@ __host__ __device__ inline int derived_smem_count(int integrand, int d, int dmax
 // Turn the caller's parameters into the derived form read by vg::integrand:
 //   GAUSS_SUM         [A, c, K, 0, mu rows of DMAX]  c = -1/(2 s^2) (FP64, exp),
 //                                                    c = -log2(e)/(2 s^2) (FP32, exp2)
-//   PRODUCT_PEAK      [c_i^-2 (DMAX), w (DMAX)]
+//   PRODUCT_PEAK      [c_i^-2 (DMAX), w (DMAX)]   padded axes: c^-2 = 1, w = 0
 //   OSCILLATORY       [2 pi u, 0, 0, 0, a (DMAX)]
 //   MOROKOFF_CAFLISCH [(1+1/d)^d, 1/d, 0, 0]
 //   MAP_DENSITY       [edges (d*(G'+1))]
@@ -122,7 +122,7 @@ __device__ void prep_params(const double* __restrict__ raw, int np, int d, T* ou
   } else if constexpr (ID == VEGAS_PRODUCT_PEAK) {
     for (int i = tid; i < 2 * DMAX; i += nt) {
       const int j = i % DMAX;
-      double v = 0.0;
+      double v = i < DMAX ? 1.0 : 0.0;  // padded axes: c^-2 = 1, w = 0
       if (j < d) v = i < DMAX ? 1.0 / (raw[j] * raw[j]) : raw[d + j];
       out[i] = (T)v;
     }
@@ -157,6 +157,31 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // weight itself only has to be deterministic.
 __device__ __forceinline__ float log2_fast(float x) { return __log2f(x); }
 
+// Packed FP32 pairs (sm_100-family f32x2 arithmetic): one instruction does two
+// independent IEEE single operations with round-to-nearest.  Each lane
+// rounds as the scalar operation would.  The fill is issue-bound, so this
+// halves the issue cost of the paired arithmetic.
+__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
+  return ((uint64_t)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+}
+__device__ __forceinline__ float lo2(uint64_t v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float hi2(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
 // One padded row of DMAX parameters from 16-byte aligned shared memory, as
 // 16-byte vector loads.
 template <typename T, int DMAX>
@@ -190,7 +215,27 @@ __device__ __forceinline__ void load_row(const T* __restrict__ p, T (&out)[DMAX]
 template <int ID, typename T, int DMAX>
 __device__ __forceinline__ T integrand(const T (&x)[DMAX], int d, const T* __restrict__ p, int np, T s0, T s1,
                                        int K) {
-  if constexpr (ID == VEGAS_GAUSS_SUM) {
+  if constexpr (ID == VEGAS_GAUSS_SUM && sizeof(T) == 4 && DMAX % 4 == 0) {
+    // FP32: the squared distance in packed pairs of axes, then one exp2 per peak
+    uint64_t xp[DMAX / 2];
+#pragma unroll
+    for (int i = 0; i < DMAX / 2; ++i) xp[i] = pk2(x[2 * i], x[2 * i + 1]);
+    const float4* mu = reinterpret_cast<const float4*>(p + 4);
+    float acc = 0.0f;
+    for (int k = 0; k < K; ++k, mu += DMAX / 4) {
+      uint64_t r2 = 0ull;  // (+0, +0)
+#pragma unroll
+      for (int i = 0; i < DMAX / 4; ++i) {
+        const float4 m = mu[i];
+        const uint64_t d0 = sub2(xp[2 * i], pk2(m.x, m.y));
+        r2 = fma2(d0, d0, r2);
+        const uint64_t d1 = sub2(xp[2 * i + 1], pk2(m.z, m.w));
+        r2 = fma2(d1, d1, r2);
+      }
+      acc += ex2_approx((lo2(r2) + hi2(r2)) * s1);
+    }
+    return s0 * acc;
+  } else if constexpr (ID == VEGAS_GAUSS_SUM) {
     const T* mu = p + 4;
     T acc = T(0);
     for (int k = 0; k < K; ++k, mu += DMAX) {
@@ -206,6 +251,20 @@ __device__ __forceinline__ T integrand(const T (&x)[DMAX], int d, const T* __res
       else acc += ex2_approx(r2 * s1);
     }
     return s0 * acc;
+  } else if constexpr (ID == VEGAS_PRODUCT_PEAK && sizeof(T) == 4 && DMAX % 4 == 0) {
+    // FP32: denominators of two axes per packed operation, one division per four axes
+    float r = 1.0f;
+#pragma unroll
+    for (int g = 0; g < DMAX / 4; ++g) {
+      const float4 c2 = reinterpret_cast<const float4*>(p)[g];
+      const float4 w = reinterpret_cast<const float4*>(p + DMAX)[g];
+      const uint64_t d0 = sub2(pk2(x[4 * g], x[4 * g + 1]), pk2(w.x, w.y));
+      const uint64_t d1 = sub2(pk2(x[4 * g + 2], x[4 * g + 3]), pk2(w.z, w.w));
+      const uint64_t e0 = fma2(d0, d0, pk2(c2.x, c2.y)), e1 = fma2(d1, d1, pk2(c2.z, c2.w));
+      const uint64_t e = mul2(e0, e1);  // padded axes: x = w = 0 and c^-2 = 1, a factor of 1
+      r = r / (lo2(e) * hi2(e));
+    }
+    return r;
   } else if constexpr (ID == VEGAS_PRODUCT_PEAK) {
     // product of the denominators in groups of four, one division per group
     T r = T(1), den = T(1);
