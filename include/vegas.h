@@ -263,6 +263,104 @@ VEGAS_API int vegas_combine(const double *d_it_est, const double *d_it_sigma, in
                   void *stream);
 
 /* ======================================================================== */
+/* Level 3: a batch of independent integrals                                */
+/* ======================================================================== */
+/* The paper runs one integral per launch (Algorithm 1).  A batch runs the same
+ * iteration for many independent integrals at once: each step of Algorithm 1
+ * is one launch over the work of every integral still running, the fill is
+ * one persistent launch over all their evaluation tiles (Algorithm 2 per
+ * integral), and one iteration of the whole batch is replayed as a captured
+ * CUDA graph.  Every integral keeps its own map (N_g intervals per axis, the
+ * same N_g for the batch), its own strata and counts (Sec. 2.1.2) and its own
+ * combination of iterations (Eqs. (8)-(9)).  Evaluation is FP32 (the
+ * VEGAS_FP32 form); sums across cubes and everything after the fill are FP64.
+ * Integral p draws its points with problem_id = p in the Philox counter, from
+ * the batch's one seed, so its evaluations equal those of vegas_fill with
+ * problem_id = p on the same map and counts.  Sums over CTAs are taken with
+ * atomic adds, so results are reproducible to FP64 rounding, not bit for bit.
+ * Limits: 1 <= nproblems <= 4096; per integral 1 <= dim <= 16 and the
+ * families GAUSS_SUM, PRODUCT_PEAK, OSCILLATORY; 2 <= nbins <= 256. */
+typedef struct vegas_batch_s *vegas_batch;
+
+typedef struct {
+  int32_t dim;           /* d of this integral, 1..16                                  */
+  int32_t integrand;     /* VEGAS_GAUSS_SUM, VEGAS_PRODUCT_PEAK or VEGAS_OSCILLATORY   */
+  const double *params;  /* host array, layout of the family (copied at create)         */
+  int64_t nparams;
+  int64_t neval;         /* evaluations per iteration, 2 N_h <= neval < 2^31            */
+  int32_t nstrat;        /* strata per axis (<= 65536); <= 0: the largest s with
+                            s^d <= neval/2                                              */
+  int32_t pad;
+} vegas_problem;
+
+typedef struct {
+  double estimate, sigma, chi2_dof; /* Eqs. (8)-(9) over the recorded iterations >= skip  */
+  int32_t n_used;                   /* iterations in the weighted mean                    */
+  int32_t nitn_run;                 /* iterations recorded since create or reset          */
+  int32_t converged;                /* 1: sigma <= rtol |estimate| was reached            */
+  int32_t status;                   /* VEGAS_OK, VEGAS_ENONFINITE, or VEGAS_ECUDA when a
+                                       cube split across tiles was not reassembled        */
+} vegas_problem_result;
+
+/* Create a batch of nproblems integrals on the current CUDA device, with
+ * N_g = nbins, map damping alpha >= 0, stratification damping beta in [0,1]
+ * and one Philox seed.  Copies the parameters, sizes and allocates every
+ * device buffer (per integral: map, counts, allocation weights, tile records)
+ * and uploads uniform maps.  Errors: EINVAL (an argument or a problem out of
+ * range; nothing is allocated), ENOMEM, ECUDA. */
+VEGAS_API int vegas_batch_create(const vegas_problem *problems, int32_t nproblems, int32_t nbins, double alpha,
+                                 double beta, uint64_t seed, vegas_batch *out);
+VEGAS_API int vegas_batch_destroy(vegas_batch b);
+/* Stream of later calls (NULL: the legacy default stream).  The graph is
+ * captured on a stream of the batch's own and launched on this one. */
+VEGAS_API int vegas_batch_set_stream(vegas_batch b, void *stream);
+/* Iterations with index < skip stay out of the combination (default 0). */
+VEGAS_API int vegas_batch_set_skip(vegas_batch b, int32_t skip);
+/* Launch shape of the fill: variant 0 (64 registers a thread, up to 4 CTAs
+ * per SM) or 1 (128 registers, up to 2), ctas_per_sm (<= 0: as many as fit)
+ * and chunk_tiles, the consecutive 1024-evaluation tiles a CTA takes from the
+ * work counter at a time.  Errors: EINVAL. */
+VEGAS_API int vegas_batch_set_launch(vegas_batch b, int32_t variant, int32_t ctas_per_sm, int32_t chunk_tiles);
+/* Time one iteration of the batch under each candidate launch shape (both
+ * variants, every resident-CTA count, chunk_tiles in {1, 4, 16}), keep the
+ * fastest, and reset the batch (vegas_batch_reset).  The chosen shape and its
+ * iteration time go to the non-NULL outputs.  Errors: ECUDA. */
+VEGAS_API int vegas_batch_tune(vegas_batch b, int32_t *variant, int32_t *ctas_per_sm, int32_t *chunk_tiles,
+                               float *ms);
+/* Uniform maps, uniform counts, no recorded iterations, iteration counter 0. */
+VEGAS_API int vegas_batch_reset(vegas_batch b);
+/* Run up to nitn iterations.  Every integral without an error takes part
+ * until its combined sigma <= rtol |estimate| (rtol > 0, checked after each
+ * iteration with index >= skip); the call returns early when none is left.
+ * results[nproblems] (host, may be NULL) receives each integral's combination
+ * over all its recorded iterations; nitn_run the iterations run by this call;
+ * ms the wall time of those iterations on the device (CUDA events).
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+VEGAS_API int vegas_batch_integrate(vegas_batch b, int32_t nitn, double rtol, vegas_problem_result *results,
+                                    int32_t *nitn_run, float *ms);
+/* Copy one integral's state to the host.  what selects the array and count
+ * is the capacity of host_out in elements:
+ *   VEGAS_BATCH_EDGES    double [d][N_g+1]  the current map
+ *   VEGAS_BATCH_OFFSETS  int64  [N_h+1]     offsets of the last allocation
+ *   VEGAS_BATCH_ELL      float  [N_h]       allocation weights of the last fill
+ *   VEGAS_BATCH_BINS     double [d][N_g]    map weights of the last fill
+ *   VEGAS_BATCH_ITER_EST double [nitn_run]  I_t of every recorded iteration
+ *   VEGAS_BATCH_ITER_SIG double [nitn_run]  sigma_t
+ *   VEGAS_BATCH_INFO     int64  [4]         d, strata per axis, N_h, nitn_run
+ * Errors: EINVAL (unknown what, problem out of range), ENOSPACE (count too
+ * small), ECUDA. */
+enum vegas_batch_field {
+  VEGAS_BATCH_EDGES = 0,
+  VEGAS_BATCH_OFFSETS = 1,
+  VEGAS_BATCH_ELL = 2,
+  VEGAS_BATCH_BINS = 3,
+  VEGAS_BATCH_ITER_EST = 4,
+  VEGAS_BATCH_ITER_SIG = 5,
+  VEGAS_BATCH_INFO = 6
+};
+VEGAS_API int vegas_batch_get(vegas_batch b, int32_t problem, int32_t what, void *host_out, int64_t count);
+
+/* ======================================================================== */
 /* Measurement support                                                      */
 /* ======================================================================== */
 /* Measure issue rates of the arithmetic pipes on the current device with

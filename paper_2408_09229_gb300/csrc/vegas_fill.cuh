@@ -375,13 +375,15 @@ __device__ __forceinline__ void decode_cube(const FillArgs& a, uint32_t h, uint3
 //   FP32: v = c 2^b + (w >> (32 - b)) < 2^23, so c + u = v 2^-b is exact; the
 //         float 2^23 + v is assembled from bits, and z = RN(v g 2^-b) is one
 //         fused multiply-add with the exact constant -2^23 g 2^-b.
-// Axes beyond d get x = 0 (the padded integrand parameters match).
+// Axes beyond d get x = 0 (the padded integrand parameters match).  J0 is the
+// starting value of the Jacobian product: the value scale of the FP32 form.
 template <typename T, int DMAX, bool EXACT>
-__device__ __forceinline__ void make_point(const FillArgs& a, const uint32_t (&cb)[DMAX], int64_t j,
+__device__ __forceinline__ void make_point(const FillArgs& a, const uint32_t* __restrict__ rk0,
+                                           const uint32_t* __restrict__ rk1, const uint32_t (&cb)[DMAX], int64_t j,
                                            const TabEntry<T>* __restrict__ tab, T (&x)[DMAX], int (&bin)[DMAX],
-                                           T& J) {
+                                           T& J, T J0) {
   const int G = a.G;
-  J = T(1);
+  J = J0;
   uint4 r = make_uint4(0u, 0u, 0u, 0u);
   const uint32_t jlo = (uint32_t)j, jhi = (uint32_t)((uint64_t)j >> 32);
 #pragma unroll
@@ -392,7 +394,7 @@ __device__ __forceinline__ void make_point(const FillArgs& a, const uint32_t (&c
       int i;
       T dz;
       if constexpr (sizeof(T) == 8) {
-        if ((k & 1) == 0) r = philox_rk(make_uint4(jlo, jhi, a.iter, (a.pid << 16) | (uint32_t)(k >> 1)), a.rk0, a.rk1);
+        if ((k & 1) == 0) r = philox_rk(make_uint4(jlo, jhi, a.iter, (a.pid << 16) | (uint32_t)(k >> 1)), rk0, rk1);
         const uint32_t whi = (k & 1) ? r.z : r.x, wlo = (k & 1) ? r.w : r.y;
         const uint64_t bits = (((uint64_t)whi << 32) | wlo) >> 11;
         const double u = __dmul_rn(__ull2double_rn(bits), 0x1p-53);
@@ -401,7 +403,7 @@ __device__ __forceinline__ void make_point(const FillArgs& a, const uint32_t (&c
         i = i < G - 1 ? i : G - 1;
         dz = z - (double)i;  // exact
       } else {
-        if ((k & 3) == 0) r = philox_rk(make_uint4(jlo, jhi, a.iter, (a.pid << 16) | (uint32_t)(k >> 2)), a.rk0, a.rk1);
+        if ((k & 3) == 0) r = philox_rk(make_uint4(jlo, jhi, a.iter, (a.pid << 16) | (uint32_t)(k >> 2)), rk0, rk1);
         const uint32_t w = (k & 3) == 0 ? r.x : (k & 3) == 1 ? r.y : (k & 3) == 2 ? r.z : r.w;
         const float big = __uint_as_float(cb[k] | (w >> (32 - a.fbits[k])));  // 2^23 + v
         const float z = fmaf(big, a.gzb32[k], a.gzn32[k]);                     // RN(v g 2^-b)
@@ -417,6 +419,377 @@ __device__ __forceinline__ void make_point(const FillArgs& a, const uint32_t (&c
   }
 }
 
+// Shared-memory views of the fill and the per-thread running state; one tile
+// of evaluations is processed by fill_tile, which both the single-integral and
+// the batched kernels call.
+template <typename T>
+struct FillShared {
+  TabEntry<T>* tab;
+  T* hist_s;          // direct mode: shared histogram of T
+  uint32_t* hist_u;   // two-phase: fixed-point tile histogram
+  ff* hist_acc;       // two-phase: float-float CTA histogram
+  uint32_t* binw;     // two-phase: intervals of an evaluation, 4 per word
+  float* wv_s;        // two-phase: map weight of every evaluation
+  T* prm;
+  int* off_r;         // cube offsets relative to the tile, clamped
+  T* invn;
+  T* vals;
+  int* longlist;
+  int* startc;        // cube of every thread's first evaluation
+  int* misc;          // [0] long count, [1] cubes in tile
+  float* wmax;        // [8] per-warp max of the map weight
+  double* red;
+};
+
+template <typename T>
+__device__ __forceinline__ FillShared<T> fill_shared(unsigned char* smem, const FillArgs& a, bool table_in_smem) {
+  FillShared<T> S;
+  S.tab = table_in_smem ? (TabEntry<T>*)(smem + a.sm_table) : (TabEntry<T>*)a.gtable;
+  S.hist_s = (T*)(smem + a.sm_hist);
+  S.hist_u = (uint32_t*)(smem + a.sm_hist);
+  S.hist_acc = (ff*)(smem + a.sm_hacc);
+  S.binw = (uint32_t*)(smem + a.sm_bins);
+  S.wv_s = (float*)(smem + a.sm_wv);
+  S.prm = (T*)(smem + a.sm_params);
+  S.off_r = (int*)(smem + a.sm_off);
+  S.invn = (T*)(smem + a.sm_invn);
+  S.vals = (T*)(smem + a.sm_vals);
+  S.longlist = (int*)(smem + a.sm_long);
+  S.startc = (int*)(smem + a.sm_start);
+  S.misc = (int*)(smem + a.sm_misc);
+  S.wmax = (float*)(smem + a.sm_misc + 16);
+  S.red = (double*)(smem + a.sm_misc + 64);
+  return S;
+}
+
+template <typename T>
+struct FillState {
+  Acc<T> acc_i, acc_v;
+  float lmax = -__builtin_huge_valf();
+  bool bad = false;
+  float inv_scale = 0.0f;  // two-phase: 1/scale of the tile histogram waiting to be folded
+  int vexp = 0;            // FP32: the evaluations carry J f 2^-vexp
+  T J0 = T(1);             // 2^-vexp
+};
+
+// Power-of-two value scale of the FP32 form.  Cube sums of (J f)^2 must stay
+// in FP32 range; a product peak in d = 12 reaches |f| = prod c_i^2 ~ 1e28.
+// From a bound B of |f| (prod c_i^2 for PRODUCT_PEAK, |A| K for GAUSS_SUM),
+// e = floor(log2(B) / 2), so the scaled peak value is about sqrt(B).  The
+// scaling is exact, so it changes no rounding until the FP64 outputs, where
+// 2^e (sums of J f) and 2^2e (sums of its square) are multiplied back.  Host
+// and device compute it the same way: products of frexp mantissas.
+__host__ __device__ inline int value_exponent(int integrand, int d, const double* raw, int np) {
+  double m = 1.0;
+  int E = 0, k = 0;
+  if (integrand == VEGAS_PRODUCT_PEAK && np >= d) {
+    for (int i = 0; i < d; ++i) {
+      m *= frexp(fabs(raw[i]), &k);
+      E += k;
+      m = frexp(m, &k);
+      E += k;
+    }
+    E = 2 * E;  // B = (prod c_i)^2 = m^2 2^(2E) with m in [0.5, 1)
+    m = frexp(m * m, &k);
+    E += k;
+  } else if (integrand == VEGAS_GAUSS_SUM && np >= 3) {
+    m = frexp(fabs(raw[0]) * raw[2], &E);
+  } else {
+    return 0;
+  }
+  if (!(m > 0.0) || !(m < 1.0)) return 0;  // a zero, infinite or NaN bound: no scale
+  const int e = (E - 1) >> 1;              // B in [2^(E-1), 2^E)
+  return e < 0 ? 0 : (e > 120 ? 120 : e);
+}
+
+// map table {e, dx, N_g dx} from the FP64 edges, and zeroed histograms
+template <typename T>
+__device__ __forceinline__ void fill_prologue(const FillArgs& a, const FillShared<T>& S, int d, bool table_in_smem) {
+  const int G = a.G, dG = d * G, tid = threadIdx.x;
+  if (table_in_smem) {
+    for (int b = tid; b < dG; b += kFillThreads) {
+      const int k = b / G, i = b - k * G;
+      const double e0 = a.edges[k * (G + 1) + i], e1 = a.edges[k * (G + 1) + i + 1];
+      const double dx = __dsub_rn(e1, e0), jk = __dmul_rn((double)G, dx);
+      S.tab[b] = TabEntry<T>{(T)e0, (T)dx, (T)jk, T(0)};
+    }
+  }
+  if (a.hist_mode == kHistShared)
+    for (int b = tid; b < dG; b += kFillThreads) S.hist_s[b] = T(0);
+  if (a.hist_mode == kHistTwoPhase)
+    for (int b = tid; b < dG; b += kFillThreads) {
+      S.hist_u[b] = 0u;
+      S.hist_acc[b] = ff{0.0f, 0.0f};
+    }
+}
+
+// One tile of kTile evaluations of integral a (tile index local to a).  rk0 /
+// rk1: the Philox round keys (kernel parameters, so that they are
+// constant-bank operands).
+template <int ID, typename T, int DMAX, bool EXACT>
+__device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __restrict__ rk0,
+                                          const uint32_t* __restrict__ rk1, const FillShared<T>& S,
+                                          FillState<T>& st, int tile, T ps0, T ps1, int pK, double* hist_g) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int d = EXACT ? DMAX : a.d, G = a.G, dG = d * a.G;
+  const bool two_phase = a.hist_mode == kHistTwoPhase;
+  const int nw = (d + 3) >> 2;
+  TabEntry<T>* tab = S.tab;
+  T* hist_s = S.hist_s;
+  uint32_t* hist_u = S.hist_u;
+  ff* hist_acc = S.hist_acc;
+  uint32_t* binw = S.binw;
+  float* wv_s = S.wv_s;
+  T* prm = S.prm;
+  int* off_r = S.off_r;
+  T* invn = S.invn;
+  T* vals = S.vals;
+  int* longlist = S.longlist;
+  int* startc = S.startc;
+  int* misc = S.misc;
+  float* wmax = S.wmax;
+  auto& acc_i = st.acc_i;
+  auto& acc_v = st.acc_v;
+  float& lmax = st.lmax;
+  bool& bad = st.bad;
+  float& inv_scale = st.inv_scale;
+  const int64_t j0 = (int64_t)tile * kTile;
+  const int len = (int)min((int64_t)kTile, a.neval - j0);
+  const int h0 = a.tile_first[tile];
+  const int64_t jend = j0 + len;
+
+  // ---- fold the previous tile's fixed-point histogram ----
+  if (two_phase && inv_scale > 0.0f) {
+    for (int b = tid; b < dG; b += kFillThreads) {
+      const uint32_t q = hist_u[b];
+      if (q) {
+        hist_acc[b] = ff_add(hist_acc[b], __fmul_rn((float)q, inv_scale));
+        hist_u[b] = 0u;
+      }
+    }
+  }
+  // ---- offsets and 1/n_h of the cubes the tile can meet ----
+  for (int c = tid; c <= kMaxCubesPerTile; c += kFillThreads) {
+    const int64_t h = (int64_t)h0 + c;
+    const int64_t o0 = h <= a.NH ? a.offsets[h] : INT64_MAX;
+    const int64_t rel = o0 - j0;
+    off_r[c] = rel < -1 ? -1 : (rel > kTile + 1 ? kTile + 1 : (int)rel);
+    if (c < kMaxCubesPerTile) {
+      T inv = T(0);
+      if (o0 < jend) {
+        if constexpr (sizeof(T) == 8) inv = 1.0 / (double)(a.offsets[h + 1] - o0);
+        else inv = __fdividef(1.0f, (float)(a.offsets[h + 1] - o0));
+      }
+      invn[c] = inv;
+    }
+  }
+  if (tid == 0) {
+    misc[0] = 0;
+    a.carries[2 * tile] = Carry{-1, 0, 0.0, 0.0};
+    a.carries[2 * tile + 1] = Carry{-1, 0, 0.0, 0.0};
+  }
+  __syncthreads();
+  // every cube tells the threads whose first evaluation it holds
+  for (int c = tid; c < kMaxCubesPerTile; c += kFillThreads) {
+    const int r0 = max(off_r[c], 0), r1 = min(off_r[c + 1], len);
+    if (r0 < r1) {
+      for (int t = (r0 + kSamplesPerThread - 1) / kSamplesPerThread; t * kSamplesPerThread < r1; ++t) startc[t] = c;
+      if (r1 == len) misc[1] = c + 1;  // cubes met by the tile
+    }
+  }
+  __syncthreads();
+
+  // ---- phase A: point, map, integrand, J f; map weights ----
+  const int jl0 = tid * kSamplesPerThread;
+  float my_max = 0.0f;
+  if (jl0 < len) {
+    int c = startc[tid];
+    int c_decoded = -1;
+    uint32_t cb[DMAX];
+#pragma unroll 1
+    for (int s = 0; s < kSamplesPerThread; ++s) {
+      const int jl = jl0 + s;
+      if (jl < len) {
+        while (off_r[c + 1] <= jl) ++c;
+        if (c != c_decoded) {  // consecutive evaluations often share a cube
+          decode_cube<T, DMAX, EXACT>(a, (uint32_t)(h0 + c), cb);
+          c_decoded = c;
+        }
+        T x[DMAX];
+        int bin[DMAX];
+        T J;
+        make_point<T, DMAX, EXACT>(a, rk0, rk1, cb, j0 + jl, tab, x, bin, J, st.J0);
+        const T f = integrand<ID, T, DMAX>(x, d, prm, a.np_derived, ps0, ps1, pK);
+        if (!isfinite(f)) bad = true;
+        const T v = J * f;
+        vals[jl] = v;
+        const T wv = v * v * invn[c];
+        if (two_phase) {
+          wv_s[jl] = (float)wv;
+          my_max = fmaxf(my_max, (float)wv);
+#pragma unroll
+          for (int w = 0; w < (DMAX + 3) / 4; ++w) {
+            if (4 * w < d) {
+              uint32_t word = 0u;
+#pragma unroll
+              for (int q = 0; q < 4; ++q)
+                if (4 * w + q < DMAX) word |= (uint32_t)bin[4 * w + q] << (8 * q);
+              binw[jl * nw + w] = word;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < DMAX; ++k) {
+            if (k < d) {
+              if (a.hist_mode == kHistShared) atomicAdd(hist_s + k * G + bin[k], wv);
+              else atomicAdd(hist_g + k * G + bin[k], (double)wv);
+            }
+          }
+        }
+      }
+    }
+  }
+  if (two_phase) {
+    for (int o = 16; o > 0; o >>= 1) my_max = fmaxf(my_max, __shfl_xor_sync(0xffffffffu, my_max, o));
+    if (lane == 0) wmax[warp] = my_max;
+  }
+  __syncthreads();
+
+  // ---- phase B (two-phase histogram): fixed-point shared integer atomics ----
+  if (two_phase) {
+    float tmax = 0.0f;
+#pragma unroll
+    for (int w = 0; w < kFillThreads / 32; ++w) tmax = fmaxf(tmax, wmax[w]);
+    if (tmax > 0.0f && isfinite(tmax)) {
+      // tmax < 2^et and a bin gets at most kTile <= 2^kTileLog2 weights of
+      // the tile, so with scale = 2^(31 - kTileLog2 - et) every bin total
+      // stays below 2^31 (plus the rounding of kTile values)
+      int et;
+      frexpf(tmax, &et);
+      const int se = min(31 - kTileLog2 - et, 126);
+      const float scale = ldexpf(1.0f, se);
+      inv_scale = ldexpf(1.0f, -se);
+      if (jl0 < len) {
+#pragma unroll 1
+        for (int s = 0; s < kSamplesPerThread; ++s) {
+          const int jl = jl0 + s;
+          if (jl < len) {
+            const uint32_t q = (uint32_t)__float2uint_rn(wv_s[jl] * scale);
+            if (q) {
+              for (int w = 0; w < nw; ++w) {
+                const uint32_t word = binw[jl * nw + w];
+                const int kk = 4 * w;
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                  if (kk + b < d) atomicAdd(hist_u + (kk + b) * G + ((word >> (8 * b)) & 255u), q);
+              }
+            }
+          }
+        }
+      }
+    } else {
+      inv_scale = 0.0f;
+    }
+  }
+
+  // ---- cube statistics ----
+  const int ncub = misc[1];
+  // one cube segment done: a cube inside the tile is final, one crossing an
+  // edge becomes a Carry for the fix-up kernel
+  auto finish = [&](int c, int L, auto mean, T m2) {
+    const int r0 = off_r[c], r1 = off_r[c + 1];
+    const bool before = r0 < 0, after = r1 > len;
+    const int h = h0 + c;
+    if (before || after) {
+      a.carries[2 * tile + (before ? 0 : 1)] = Carry{h, L, to_double(mean), (double)m2};
+      return;
+    }
+    const int n = r1 - r0;
+    float ell;
+    acc_i.add(mean);
+    if constexpr (sizeof(T) == 8) {
+      acc_v.add(m2 / ((double)n * (double)(n - 1)));
+      // the FP64 form keeps the reproducible log2, so that the counts of a
+      // free-running FP64 run follow the CPU reference bit for bit
+      ell = __fmul_rn(a.half_beta, log2r(m2 / (double)(n - 1)));
+    } else {
+      const float nf = (float)n;
+      acc_v.add(__fdividef(m2, nf * (nf - 1.0f)));
+      ell = a.half_beta * (log2_fast(__fdividef(m2, nf - 1.0f)) + (float)(2 * st.vexp));
+    }
+    a.ell[h] = ell;
+    lmax = fmaxf(lmax, ell);
+    if (a.cube_mean) {
+      a.cube_mean[h] = ldexp(to_double(mean), st.vexp);
+      a.cube_m2[h] = ldexp((double)m2, 2 * st.vexp);
+    }
+  };
+
+  for (int c = tid; c < ncub; c += kFillThreads) {
+    const int r0 = max(off_r[c], 0), r1 = min(off_r[c + 1], len);
+    const int L = r1 - r0;
+    if (L > kLongSegment) {
+      longlist[atomicAdd(&misc[0], 1)] = c;
+      continue;
+    }
+    // one pass over the segment, shifted by its first value: mean = v0 + s/L,
+    // M2 = q - s^2/L with s, q the sums of (v - v0) and (v - v0)^2; the shift
+    // keeps q within (L + 1) M2, so the cancellation costs a few ulps
+    const T v0 = vals[r0];
+    T sd = T(0), qd = T(0);
+    for (int r = r0 + 1; r < r1; ++r) {
+      const T dv = vals[r] - v0;
+      sd += dv;
+      qd = fma(dv, dv, qd);
+    }
+    if constexpr (sizeof(T) == 8) {
+      const double sl = sd / (double)L;
+      finish(c, L, v0 + sl, fmax(fma(-sd, sl, qd), 0.0));
+    } else {
+      const float sl = __fdividef(sd, (float)L);
+      // mean = v0 + sl as a normalised float-float (TwoSum), so that the
+      // low words summed into the iteration estimate stay rounding errors
+      finish(c, L, ff_add(ff{v0, 0.0f}, sl), fmaxf(fmaf(-sd, sl, qd), 0.0f));
+    }
+  }
+  __syncthreads();
+  const int nlong = misc[0];
+  for (int e = warp; e < nlong; e += kFillThreads / 32) {
+    const int c = longlist[e];
+    const int r0 = max(off_r[c], 0), r1 = min(off_r[c + 1], len);
+    const int L = r1 - r0;
+    if constexpr (sizeof(T) == 8) {
+      double s = 0.0;
+      for (int r = r0 + lane; r < r1; r += 32) s += vals[r];
+      s = warp_sum(s);
+      const double mean = s / (double)L;
+      double q = 0.0;
+      for (int r = r0 + lane; r < r1; r += 32) {
+        const double dv = vals[r] - mean;
+        q = fma(dv, dv, q);
+      }
+      q = warp_sum(q);
+      if (lane == 0) finish(c, L, mean, q);
+    } else {
+      ff s{0.0f, 0.0f};
+      for (int r = r0 + lane; r < r1; r += 32) s = ff_add(s, vals[r]);
+      s = warp_sum(s);
+      const float Lf = (float)L;
+      const float mh = __fdiv_rn(s.hi, Lf);
+      const float ml = __fdiv_rn(__fadd_rn(fmaf(-mh, Lf, s.hi), s.lo), Lf);
+      float q = 0.0f;
+      for (int r = r0 + lane; r < r1; r += 32) {
+        const float dv = vals[r] - mh;
+        q = fmaf(dv, dv, q);
+      }
+      const ff qq = warp_sum(ff{q, 0.0f});
+      if (lane == 0) finish(c, L, ff{mh, ml}, __fadd_rn(qq.hi, qq.lo));
+    }
+  }
+  __syncthreads();
+  }
+
+// Fill of one integral: a persistent grid walks the tiles round-robin.
 // EXACT: d == DMAX and the map table is in shared memory, so the per-axis
 // bounds checks vanish and the table reads are shared-memory loads.  The FP32
 // form with d <= 8 asks for 4 resident CTAs (at most 64 registers): measured
@@ -425,304 +798,41 @@ template <int ID, typename T, int DMAX, bool EXACT>
 __global__ void __launch_bounds__(kFillThreads, (sizeof(T) == 4 && DMAX <= 8) ? 4 : 1)
     fill_kernel(const __grid_constant__ FillArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int d = EXACT ? DMAX : a.d, G = a.G, dG = d * a.G;
-  const bool two_phase = a.hist_mode == kHistTwoPhase;
-  TabEntry<T>* tab = (EXACT || a.table_smem) ? (TabEntry<T>*)(smem + a.sm_table) : (TabEntry<T>*)a.gtable;
-  T* hist_s = (T*)(smem + a.sm_hist);                 // direct mode: shared histogram of T
-  uint32_t* hist_u = (uint32_t*)(smem + a.sm_hist);   // two-phase: fixed-point tile histogram
-  ff* hist_acc = (ff*)(smem + a.sm_hacc);             // two-phase: float-float CTA histogram
-  uint32_t* binw = (uint32_t*)(smem + a.sm_bins);     // two-phase: intervals of an evaluation, 4 per word
-  const int nw = (d + 3) >> 2;
-  float* wv_s = (float*)(smem + a.sm_wv);             // two-phase: map weight of every evaluation
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int d = EXACT ? DMAX : a.d, dG = d * a.G;
+  const bool table_in_smem = EXACT || a.table_smem;
+  const FillShared<T> S = fill_shared<T>(smem, a, table_in_smem);
   double* hist_g = a.hist_part + (size_t)blockIdx.x * dG;
-  T* prm = (T*)(smem + a.sm_params);
-  int* off_r = (int*)(smem + a.sm_off);               // cube offsets relative to the tile, clamped
-  T* invn = (T*)(smem + a.sm_invn);
-  T* vals = (T*)(smem + a.sm_vals);
-  int* longlist = (int*)(smem + a.sm_long);
-  int* startc = (int*)(smem + a.sm_start);            // cube of every thread's first evaluation
-  int* misc = (int*)(smem + a.sm_misc);               // [0] long count, [1] cubes in tile
-  float* wmax = (float*)(smem + a.sm_misc + 16);      // [8] per-warp max of the map weight
-  double* red = (double*)(smem + a.sm_misc + 64);
-
-  // ---- prologue: map table, histograms, parameters ----
-  if (EXACT || a.table_smem) {
-    for (int b = tid; b < dG; b += kFillThreads) {
-      const int k = b / G, i = b - k * G;
-      const double e0 = a.edges[k * (G + 1) + i], e1 = a.edges[k * (G + 1) + i + 1];
-      const double dx = __dsub_rn(e1, e0), jk = __dmul_rn((double)G, dx);
-      tab[b] = TabEntry<T>{(T)e0, (T)dx, (T)jk, T(0)};
-    }
-  }
-  if (a.hist_mode == kHistShared)
-    for (int b = tid; b < dG; b += kFillThreads) hist_s[b] = T(0);
-  if (two_phase)
-    for (int b = tid; b < dG; b += kFillThreads) {
-      hist_u[b] = 0u;
-      hist_acc[b] = ff{0.0f, 0.0f};
-    }
-  prep_params<ID, T, DMAX>(a.params_raw, a.np_raw, d, prm);
+  fill_prologue<T>(a, S, d, table_in_smem);
+  prep_params<ID, T, DMAX>(a.params_raw, a.np_raw, d, S.prm);
   __syncthreads();
-  const T ps0 = prm[0], ps1 = prm[1];
-  const int pK = (ID == VEGAS_GAUSS_SUM) ? (int)prm[2] : 0;
-
-  Acc<T> acc_i, acc_v;
-  float lmax = -__int_as_float(0x7f800000);
-  bool bad = false;
-  float inv_scale = 0.0f;  // two-phase: 1/scale of the tile histogram waiting to be folded
-
-  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-    const int64_t j0 = (int64_t)tile * kTile;
-    const int len = (int)min((int64_t)kTile, a.neval - j0);
-    const int h0 = a.tile_first[tile];
-    const int64_t jend = j0 + len;
-
-    // ---- fold the previous tile's fixed-point histogram ----
-    if (two_phase && inv_scale > 0.0f) {
-      for (int b = tid; b < dG; b += kFillThreads) {
-        const uint32_t q = hist_u[b];
-        if (q) {
-          hist_acc[b] = ff_add(hist_acc[b], __fmul_rn((float)q, inv_scale));
-          hist_u[b] = 0u;
-        }
-      }
-    }
-    // ---- offsets and 1/n_h of the cubes the tile can meet ----
-    for (int c = tid; c <= kMaxCubesPerTile; c += kFillThreads) {
-      const int64_t h = (int64_t)h0 + c;
-      const int64_t o0 = h <= a.NH ? a.offsets[h] : INT64_MAX;
-      const int64_t rel = o0 - j0;
-      off_r[c] = rel < -1 ? -1 : (rel > kTile + 1 ? kTile + 1 : (int)rel);
-      if (c < kMaxCubesPerTile) {
-        T inv = T(0);
-        if (o0 < jend) {
-          if constexpr (sizeof(T) == 8) inv = 1.0 / (double)(a.offsets[h + 1] - o0);
-          else inv = __fdividef(1.0f, (float)(a.offsets[h + 1] - o0));
-        }
-        invn[c] = inv;
-      }
-    }
-    if (tid == 0) {
-      misc[0] = 0;
-      a.carries[2 * tile] = Carry{-1, 0, 0.0, 0.0};
-      a.carries[2 * tile + 1] = Carry{-1, 0, 0.0, 0.0};
-    }
-    __syncthreads();
-    // every cube tells the threads whose first evaluation it holds
-    for (int c = tid; c < kMaxCubesPerTile; c += kFillThreads) {
-      const int r0 = max(off_r[c], 0), r1 = min(off_r[c + 1], len);
-      if (r0 < r1) {
-        for (int t = (r0 + kSamplesPerThread - 1) / kSamplesPerThread; t * kSamplesPerThread < r1; ++t) startc[t] = c;
-        if (r1 == len) misc[1] = c + 1;  // cubes met by the tile
-      }
-    }
-    __syncthreads();
-
-    // ---- phase A: point, map, integrand, J f; map weights ----
-    const int jl0 = tid * kSamplesPerThread;
-    float my_max = 0.0f;
-    if (jl0 < len) {
-      int c = startc[tid];
-      int c_decoded = -1;
-      uint32_t cb[DMAX];
-#pragma unroll 1
-      for (int s = 0; s < kSamplesPerThread; ++s) {
-        const int jl = jl0 + s;
-        if (jl < len) {
-          while (off_r[c + 1] <= jl) ++c;
-          if (c != c_decoded) {  // consecutive evaluations often share a cube
-            decode_cube<T, DMAX, EXACT>(a, (uint32_t)(h0 + c), cb);
-            c_decoded = c;
-          }
-          T x[DMAX];
-          int bin[DMAX];
-          T J;
-          make_point<T, DMAX, EXACT>(a, cb, j0 + jl, tab, x, bin, J);
-          const T f = integrand<ID, T, DMAX>(x, d, prm, a.np_derived, ps0, ps1, pK);
-          if (!isfinite(f)) bad = true;
-          const T v = J * f;
-          vals[jl] = v;
-          const T wv = v * v * invn[c];
-          if (two_phase) {
-            wv_s[jl] = (float)wv;
-            my_max = fmaxf(my_max, (float)wv);
-#pragma unroll
-            for (int w = 0; w < (DMAX + 3) / 4; ++w) {
-              if (4 * w < d) {
-                uint32_t word = 0u;
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                  if (4 * w + q < DMAX) word |= (uint32_t)bin[4 * w + q] << (8 * q);
-                binw[jl * nw + w] = word;
-              }
-            }
-          } else {
-#pragma unroll
-            for (int k = 0; k < DMAX; ++k) {
-              if (k < d) {
-                if (a.hist_mode == kHistShared) atomicAdd(hist_s + k * G + bin[k], wv);
-                else atomicAdd(hist_g + k * G + bin[k], (double)wv);
-              }
-            }
-          }
-        }
-      }
-    }
-    if (two_phase) {
-      for (int o = 16; o > 0; o >>= 1) my_max = fmaxf(my_max, __shfl_xor_sync(0xffffffffu, my_max, o));
-      if (lane == 0) wmax[warp] = my_max;
-    }
-    __syncthreads();
-
-    // ---- phase B (two-phase histogram): fixed-point shared integer atomics ----
-    if (two_phase) {
-      float tmax = 0.0f;
-#pragma unroll
-      for (int w = 0; w < kFillThreads / 32; ++w) tmax = fmaxf(tmax, wmax[w]);
-      if (tmax > 0.0f && isfinite(tmax)) {
-        // tmax < 2^et and a bin gets at most kTile <= 2^kTileLog2 weights of
-        // the tile, so with scale = 2^(31 - kTileLog2 - et) every bin total
-        // stays below 2^31 (plus the rounding of kTile values)
-        int et;
-        frexpf(tmax, &et);
-        const int se = min(31 - kTileLog2 - et, 126);
-        const float scale = ldexpf(1.0f, se);
-        inv_scale = ldexpf(1.0f, -se);
-        if (jl0 < len) {
-#pragma unroll 1
-          for (int s = 0; s < kSamplesPerThread; ++s) {
-            const int jl = jl0 + s;
-            if (jl < len) {
-              const uint32_t q = (uint32_t)__float2uint_rn(wv_s[jl] * scale);
-              if (q) {
-                for (int w = 0; w < nw; ++w) {
-                  const uint32_t word = binw[jl * nw + w];
-                  const int kk = 4 * w;
-#pragma unroll
-                  for (int b = 0; b < 4; ++b)
-                    if (kk + b < d) atomicAdd(hist_u + (kk + b) * G + ((word >> (8 * b)) & 255u), q);
-                }
-              }
-            }
-          }
-        }
-      } else {
-        inv_scale = 0.0f;
-      }
-    }
-
-    // ---- cube statistics ----
-    const int ncub = misc[1];
-    // one cube segment done: a cube inside the tile is final, one crossing an
-    // edge becomes a Carry for the fix-up kernel
-    auto finish = [&](int c, int L, auto mean, T m2) {
-      const int r0 = off_r[c], r1 = off_r[c + 1];
-      const bool before = r0 < 0, after = r1 > len;
-      const int h = h0 + c;
-      if (before || after) {
-        a.carries[2 * tile + (before ? 0 : 1)] = Carry{h, L, to_double(mean), (double)m2};
-        return;
-      }
-      const int n = r1 - r0;
-      float ell;
-      acc_i.add(mean);
-      if constexpr (sizeof(T) == 8) {
-        acc_v.add(m2 / ((double)n * (double)(n - 1)));
-        // the FP64 form keeps the reproducible log2, so that the counts of a
-        // free-running FP64 run follow the CPU reference bit for bit
-        ell = __fmul_rn(a.half_beta, log2r(m2 / (double)(n - 1)));
-      } else {
-        const float nf = (float)n;
-        acc_v.add(__fdividef(m2, nf * (nf - 1.0f)));
-        ell = a.half_beta * log2_fast(__fdividef(m2, nf - 1.0f));
-      }
-      a.ell[h] = ell;
-      lmax = fmaxf(lmax, ell);
-      if (a.cube_mean) {
-        a.cube_mean[h] = to_double(mean);
-        a.cube_m2[h] = (double)m2;
-      }
-    };
-
-    for (int c = tid; c < ncub; c += kFillThreads) {
-      const int r0 = max(off_r[c], 0), r1 = min(off_r[c + 1], len);
-      const int L = r1 - r0;
-      if (L > kLongSegment) {
-        longlist[atomicAdd(&misc[0], 1)] = c;
-        continue;
-      }
-      // one pass over the segment, shifted by its first value: mean = v0 + s/L,
-      // M2 = q - s^2/L with s, q the sums of (v - v0) and (v - v0)^2; the shift
-      // keeps q within (L + 1) M2, so the cancellation costs a few ulps
-      const T v0 = vals[r0];
-      T sd = T(0), qd = T(0);
-      for (int r = r0 + 1; r < r1; ++r) {
-        const T dv = vals[r] - v0;
-        sd += dv;
-        qd = fma(dv, dv, qd);
-      }
-      if constexpr (sizeof(T) == 8) {
-        const double sl = sd / (double)L;
-        finish(c, L, v0 + sl, fmax(fma(-sd, sl, qd), 0.0));
-      } else {
-        const float sl = __fdividef(sd, (float)L);
-        finish(c, L, ff{v0, sl}, fmaxf(fmaf(-sd, sl, qd), 0.0f));
-      }
-    }
-    __syncthreads();
-    const int nlong = misc[0];
-    for (int e = warp; e < nlong; e += kFillThreads / 32) {
-      const int c = longlist[e];
-      const int r0 = max(off_r[c], 0), r1 = min(off_r[c + 1], len);
-      const int L = r1 - r0;
-      if constexpr (sizeof(T) == 8) {
-        double s = 0.0;
-        for (int r = r0 + lane; r < r1; r += 32) s += vals[r];
-        s = warp_sum(s);
-        const double mean = s / (double)L;
-        double q = 0.0;
-        for (int r = r0 + lane; r < r1; r += 32) {
-          const double dv = vals[r] - mean;
-          q = fma(dv, dv, q);
-        }
-        q = warp_sum(q);
-        if (lane == 0) finish(c, L, mean, q);
-      } else {
-        ff s{0.0f, 0.0f};
-        for (int r = r0 + lane; r < r1; r += 32) s = ff_add(s, vals[r]);
-        s = warp_sum(s);
-        const float Lf = (float)L;
-        const float mh = __fdiv_rn(s.hi, Lf);
-        const float ml = __fdiv_rn(__fadd_rn(fmaf(-mh, Lf, s.hi), s.lo), Lf);
-        float q = 0.0f;
-        for (int r = r0 + lane; r < r1; r += 32) {
-          const float dv = vals[r] - mh;
-          q = fmaf(dv, dv, q);
-        }
-        const ff qq = warp_sum(ff{q, 0.0f});
-        if (lane == 0) finish(c, L, ff{mh, ml}, __fadd_rn(qq.hi, qq.lo));
-      }
-    }
-    __syncthreads();
+  const T ps0 = S.prm[0], ps1 = S.prm[1];
+  const int pK = (ID == VEGAS_GAUSS_SUM) ? (int)S.prm[2] : 0;
+  FillState<T> st;
+  if constexpr (sizeof(T) == 4) {
+    st.vexp = a.vexp ? *a.vexp : 0;
+    st.J0 = ldexpf(1.0f, -st.vexp);
   }
+  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x)
+    fill_tile<ID, T, DMAX, EXACT>(a, a.rk0, a.rk1, S, st, tile, ps0, ps1, pK, hist_g);
 
   // ---- epilogue: CTA partial sums, max weight, flags, histogram ----
-  const double si = block_sum(acc_i.value(), red);
-  const double sv = block_sum(acc_v.value(), red);
+  const double si = block_sum(st.acc_i.value(), S.red);
+  const double sv = block_sum(st.acc_v.value(), S.red);
   if (tid == 0) {
     a.cta_part[2 * blockIdx.x] = si;
     a.cta_part[2 * blockIdx.x + 1] = sv;
   }
+  float lmax = st.lmax;
   for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
   if (lane == 0) atomicMax(a.ellmax_key, float_key(lmax));
-  if (__syncthreads_or(bad) && tid == 0) atomicOr(a.flags, 1);
+  if (__syncthreads_or(st.bad) && tid == 0) atomicOr(a.flags, 1);
   if (a.hist_mode == kHistShared)
-    for (int b = tid; b < dG; b += kFillThreads) hist_g[b] = (double)hist_s[b];
-  if (two_phase) {
+    for (int b = tid; b < dG; b += kFillThreads) hist_g[b] = (double)S.hist_s[b];
+  if (a.hist_mode == kHistTwoPhase) {
     for (int b = tid; b < dG; b += kFillThreads) {
-      ff acc = hist_acc[b];
-      if (inv_scale > 0.0f) acc = ff_add(acc, __fmul_rn((float)hist_u[b], inv_scale));
+      ff acc = S.hist_acc[b];
+      if (st.inv_scale > 0.0f) acc = ff_add(acc, __fmul_rn((float)S.hist_u[b], st.inv_scale));
       hist_g[b] = ff_to_double(acc);
     }
   }

@@ -63,9 +63,18 @@ ScratchLayout scratch_layout(int d, int G, int64_t neval, int sms) {
   L.fix_part = off;   off = align_up(off + sizeof(double) * 2 * (size_t)L.nfix);
   L.hist_part = off;  off = align_up(off + sizeof(double) * (size_t)L.grid_max * d * G);
   L.gtable = off;     off = align_up(off + sizeof(TabEntry<double>) * (size_t)d * G);
-  L.ellmax = off;     off = align_up(off + 16);
+  L.ellmax = off;     off = align_up(off + 16);  // max-ell key at +0, FP32 value scale exponent at +4
   L.total = off;
   return L;
+}
+
+// magic multiplier for n / s with n < 2^31 (Granlund & Montgomery, PLDI'94,
+// Thm 4.2): l = ceil(log2 s), m = ceil(2^(31+l) / s), n / s = (n m) >> (31+l)
+void magic_div(uint32_t s, uint32_t& m, uint32_t& shift) {
+  uint32_t l = 0;
+  while ((uint64_t(1) << l) < s) ++l;
+  m = (uint32_t)(((uint64_t(1) << (31 + l)) + s - 1) / s);
+  shift = 31 + l;
 }
 
 // Shared-memory regions of the fill kernel.  The map-weight histogram goes to
@@ -121,11 +130,46 @@ int smem_layout(FillArgs& a, size_t tsz, int nprm, bool fp32) {
   return off <= 227 * 1024 ? VEGAS_OK : VEGAS_EINVAL;
 }
 
-// first cube of every tile: largest h with offsets[h] <= tile * kTile
+}  // namespace
+
+// Per-axis constants (magic reciprocals, z scales, FP32 fraction bits), the
+// Philox round keys and the shared-memory layout of a.  a.d, a.G, a.key0 and
+// a.key1 must be set.
+int fill_args_axes(FillArgs& a, const int32_t* nstrat, int precision, int nprm) {
+  const int G = a.G;
+  for (int k = 0; k < a.d; ++k) {
+    a.nstrat[k] = (uint32_t)nstrat[k];
+    magic_div(a.nstrat[k], a.magic[k], a.shift[k]);
+    // z = (c + u) * N_g / s_k: the scale rounded once, in each precision
+    a.gz64[k] = (double)G / (double)nstrat[k];
+    uint32_t l = 0;
+    while ((1u << l) < (uint32_t)nstrat[k]) ++l;
+    a.fbits[k] = 23u - l;
+    volatile float gf = (float)G, sf = (float)nstrat[k];
+    const float g32 = gf / sf;
+    a.gzb32[k] = std::ldexp(g32, -(int)a.fbits[k]);
+    a.gzn32[k] = -8388608.0f * a.gzb32[k];
+  }
+  for (int r = 0; r < 10; ++r) {
+    a.rk0[r] = a.key0 + (uint32_t)r * 0x9E3779B9u;
+    a.rk1[r] = a.key1 + (uint32_t)r * 0xBB67AE85u;
+  }
+  const size_t tsz = precision == VEGAS_FP64 ? sizeof(double) : sizeof(float);
+  return smem_layout(a, tsz, nprm, precision == VEGAS_FP32);
+}
+
+namespace {
+
+// first cube of every tile: largest h with offsets[h] <= tile * kTile; thread
+// 0 also resets the max-ell key and writes the FP32 value scale exponent
 __global__ void tile_first_kernel(const int64_t* __restrict__ offsets, int NH, int ntiles, int32_t* tile_first,
-                                  int* ellmax_key) {
+                                  int* ellmax_key, int* vexp, int fp32, int integrand, int d,
+                                  const double* __restrict__ params, int np) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t == 0) *ellmax_key = float_key(-__int_as_float(0x7f800000));
+  if (t == 0) {
+    *ellmax_key = float_key(-__int_as_float(0x7f800000));
+    *vexp = fp32 ? value_exponent(integrand, d, params, np) : 0;
+  }
   if (t >= ntiles) return;
   const int64_t j0 = (int64_t)t * kTile;
   int lo = 0, hi = NH - 1;
@@ -156,6 +200,7 @@ __global__ void fixup_kernel(const __grid_constant__ FillArgs a, double* fix_par
   double ai = 0.0, av = 0.0;
   float lmax = -__int_as_float(0x7f800000);
   bool broken = false;
+  const int e = a.vexp ? *a.vexp : 0;
   if (t < a.ntiles) {
     const Carry r = a.carries[2 * t + 1];
     if (r.h >= 0) {
@@ -176,12 +221,14 @@ __global__ void fixup_kernel(const __grid_constant__ FillArgs a, double* fix_par
       if (cnt != (double)n) broken = true;
       ai = mean;
       av = m2 / ((double)n * (double)(n - 1));
-      const float ell = __fmul_rn(a.half_beta, log2r(m2 / (double)(n - 1)));
+      float l2 = log2r(m2 / (double)(n - 1));
+      if (e != 0) l2 += (float)(2 * e);  // the FP32 value scale
+      const float ell = __fmul_rn(a.half_beta, l2);
       a.ell[h] = ell;
       lmax = ell;
       if (a.cube_mean) {
-        a.cube_mean[h] = mean;
-        a.cube_m2[h] = m2;
+        a.cube_mean[h] = ldexp(mean, e);
+        a.cube_m2[h] = ldexp(m2, 2 * e);
       }
     }
   }
@@ -196,9 +243,10 @@ __global__ void fixup_kernel(const __grid_constant__ FillArgs a, double* fix_par
   if (broken) atomicOr(a.flags, 2);
 }
 
-// (I_t, sigma_t^2) = (sum mean_h / N_h, sum M2_h/(n_h(n_h-1)) / N_h^2), Eqs. (5)-(6)
+// (I_t, sigma_t^2) = (sum mean_h / N_h, sum M2_h/(n_h(n_h-1)) / N_h^2), Eqs. (5)-(6);
+// the sums carry the FP32 value scale 2^-vexp, multiplied back here
 __global__ void results_kernel(const double* __restrict__ cta_part, int ncta, const double* __restrict__ fix_part,
-                               int nfix, int NH, double* result) {
+                               int nfix, int NH, const int* __restrict__ vexp, double* result) {
   __shared__ double red[32];
   double si = 0.0, sv = 0.0;
   for (int i = threadIdx.x; i < ncta; i += blockDim.x) {
@@ -212,8 +260,9 @@ __global__ void results_kernel(const double* __restrict__ cta_part, int ncta, co
   si = block_sum(si, red);
   sv = block_sum(sv, red);
   if (threadIdx.x == 0) {
-    result[0] = si / (double)NH;
-    result[1] = sv / ((double)NH * (double)NH);
+    const int e = *vexp;
+    result[0] = ldexp(si / (double)NH, e);
+    result[1] = ldexp(sv / ((double)NH * (double)NH), 2 * e);
   }
 }
 
@@ -221,7 +270,7 @@ __global__ void results_kernel(const double* __restrict__ cta_part, int ncta, co
 // lane); its 8 warps take every 8th CTA, and the 8 warp sums are added in
 // warp order, so the order is fixed.
 __global__ void __launch_bounds__(256) bins_kernel(const double* __restrict__ hist_part, int ncta, int dG,
-                                                   double* bins) {
+                                                   const int* __restrict__ vexp, double* bins) {
   __shared__ double part[8][33];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int b = blockIdx.x * 32 + lane;
@@ -233,18 +282,10 @@ __global__ void __launch_bounds__(256) bins_kernel(const double* __restrict__ hi
   if (w == 0 && b < dG) {
     double t = 0.0;
     for (int k = 0; k < 8; ++k) t += part[k][lane];
-    bins[b] = t;
+    bins[b] = ldexp(t, 2 * *vexp);
   }
 }
 
-// magic multiplier for n / s with n < 2^31 (Granlund & Montgomery, PLDI'94,
-// Thm 4.2): l = ceil(log2 s), m = ceil(2^(31+l) / s), n / s = (n m) >> (31+l)
-void magic_div(uint32_t s, uint32_t& m, uint32_t& shift) {
-  uint32_t l = 0;
-  while ((uint64_t(1) << l) < s) ++l;
-  m = (uint32_t)(((uint64_t(1) << (31 + l)) + s - 1) / s);
-  shift = 31 + l;
-}
 
 }  // namespace
 }  // namespace vg
@@ -303,6 +344,7 @@ int fill_impl(const vegas_geometry* g, int precision, int integrand, const doubl
   a.pid = problem_id;
   a.half_beta = (float)beta * 0.5f;
   a.np_derived = npd;
+  a.iid = integrand;
   a.edges = d_edges;
   a.offsets = d_offsets;
   a.tile_first = (const int32_t*)(sc + L.tile_first);
@@ -317,25 +359,8 @@ int fill_impl(const vegas_geometry* g, int precision, int integrand, const doubl
   a.cta_part = (double*)(sc + L.cta_part);
   a.hist_part = (double*)(sc + L.hist_part);
   a.gtable = sc + L.gtable;
-  for (int k = 0; k < d; ++k) {
-    a.nstrat[k] = (uint32_t)g->nstrat[k];
-    magic_div(a.nstrat[k], a.magic[k], a.shift[k]);
-    // z = (c + u) * N_g / s_k: the scale rounded once, in each precision
-    a.gz64[k] = (double)G / (double)g->nstrat[k];
-    uint32_t l = 0;
-    while ((1u << l) < (uint32_t)g->nstrat[k]) ++l;
-    a.fbits[k] = 23u - l;
-    volatile float gf = (float)G, sf = (float)g->nstrat[k];
-    const float g32 = gf / sf;
-    a.gzb32[k] = std::ldexp(g32, -(int)a.fbits[k]);
-    a.gzn32[k] = -8388608.0f * a.gzb32[k];
-  }
-  for (int r = 0; r < 10; ++r) {
-    a.rk0[r] = a.key0 + (uint32_t)r * 0x9E3779B9u;
-    a.rk1[r] = a.key1 + (uint32_t)r * 0xBB67AE85u;
-  }
-  const size_t tsz = precision == VEGAS_FP64 ? sizeof(double) : sizeof(float);
-  if (smem_layout(a, tsz, nprm, precision == VEGAS_FP32) != VEGAS_OK) return VEGAS_EINVAL;
+  a.vexp = (const int*)(sc + L.ellmax + 4);
+  if (fill_args_axes(a, g->nstrat, precision, nprm) != VEGAS_OK) return VEGAS_EINVAL;
 
   const bool exact = d == dmax && (dmax == 4 || dmax == 8) && a.table_smem;
   const int per_sm = precision == VEGAS_FP64
@@ -347,7 +372,8 @@ int fill_impl(const vegas_geometry* g, int precision, int integrand, const doubl
   const int grid = std::max(1, std::min(L.grid_max, per_sm * sms));
 
   tile_first_kernel<<<(L.ntiles + 255) / 256, 256, 0, s>>>(d_offsets, a.NH, L.ntiles, (int32_t*)(sc + L.tile_first),
-                                                            a.ellmax_key);
+                                                            a.ellmax_key, (int*)a.vexp, precision == VEGAS_FP32,
+                                                            integrand, d, d_params, (int)nparams);
   VG_CHECK(cudaGetLastError());
   if (a.hist_mode == kHistGlobal)
     VG_CHECK(cudaMemsetAsync(a.hist_part, 0, sizeof(double) * (size_t)grid * d * G, s));
@@ -366,9 +392,9 @@ int fill_impl(const vegas_geometry* g, int precision, int integrand, const doubl
   double* fix_part = (double*)(sc + L.fix_part);
   fixup_kernel<<<L.nfix, 256, 0, s>>>(a, fix_part);
   VG_CHECK(cudaGetLastError());
-  results_kernel<<<1, 256, 0, s>>>(a.cta_part, grid, fix_part, L.nfix, a.NH, d_result);
+  results_kernel<<<1, 256, 0, s>>>(a.cta_part, grid, fix_part, L.nfix, a.NH, a.vexp, d_result);
   VG_CHECK(cudaGetLastError());
-  bins_kernel<<<(d * G + 31) / 32, 256, 0, s>>>(a.hist_part, grid, d * G, d_bins);
+  bins_kernel<<<(d * G + 31) / 32, 256, 0, s>>>(a.hist_part, grid, d * G, a.vexp, d_bins);
   VG_CHECK(cudaGetLastError());
   return VEGAS_OK;
 }

@@ -44,6 +44,7 @@ struct FillArgs {
   int table_smem;  // 1: map table in shared memory
   int hist_mode;   // kHistShared, kHistGlobal or kHistTwoPhase
   int np_derived;
+  int iid;  // integrand family (the batched fill dispatches on it per tile)
   const double* edges;     // [d][G+1] FP64
   const int64_t* offsets;  // [NH+1]
   const int32_t* tile_first;
@@ -58,6 +59,7 @@ struct FillArgs {
   double* cta_part;     // [grid][2]
   double* hist_part;    // [grid][d*G]
   void* gtable;         // global map table when it does not fit in shared memory
+  const int* vexp;      // FP32 value scale exponent (see value_exponent), or NULL for 0
   uint32_t nstrat[kMaxDim], magic[kMaxDim], shift[kMaxDim];
   double gz64[kMaxDim];     // N_g / s_k, rounded in FP64
   float gzb32[kMaxDim];     // RN32(N_g / s_k) 2^-b_k
@@ -93,6 +95,7 @@ int launch_record_combine(const double* d_result, int t, double* d_est, double* 
                           cudaStream_t s);
 
 int dmax_for(int d);
+int fill_args_axes(FillArgs& a, const int32_t* nstrat, int precision, int nprm);
 int derived_param_count(int integrand, int d, const double* host_params_or_null, int64_t np);
 
 // status helpers

@@ -38,6 +38,18 @@ class Result(ctypes.Structure):
                 ("it_cap", ctypes.c_int32)]
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("integrand", ctypes.c_int32), ("params", ctypes.c_void_p),
+                ("nparams", ctypes.c_int64), ("neval", ctypes.c_int64), ("nstrat", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+
+class ProblemResult(ctypes.Structure):
+    _fields_ = [("estimate", ctypes.c_double), ("sigma", ctypes.c_double), ("chi2_dof", ctypes.c_double),
+                ("n_used", ctypes.c_int32), ("nitn_run", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("status", ctypes.c_int32)]
+
+
 class Geometry(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("nbins", ctypes.c_int32), ("nstrat", ctypes.POINTER(ctypes.c_int32))]
 
@@ -74,6 +86,17 @@ def _load():
         "vegas_refine": ([i32, i32, f64, P, P, P, P], i32),
         "vegas_combine": ([P, P, i32, i32, P, P], i32),
         "vegas_probe_pipes": ([P], i32),
+        "vegas_batch_create": ([ctypes.POINTER(Problem), i32, i32, f64, f64, u64, ctypes.POINTER(P)], i32),
+        "vegas_batch_destroy": ([P], i32),
+        "vegas_batch_set_stream": ([P, P], i32),
+        "vegas_batch_set_skip": ([P, i32], i32),
+        "vegas_batch_set_launch": ([P, i32, i32, i32], i32),
+        "vegas_batch_tune": ([P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                              ctypes.POINTER(ctypes.c_float)], i32),
+        "vegas_batch_reset": ([P], i32),
+        "vegas_batch_integrate": ([P, i32, f64, ctypes.POINTER(ProblemResult), ctypes.POINTER(i32),
+                                   ctypes.POINTER(ctypes.c_float)], i32),
+        "vegas_batch_get": ([P, i32, i32, P, i64], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -196,6 +219,87 @@ class Vegas:
         e = np.zeros((self.dim, self.nbins + 1))
         _check(lib.vegas_get_edges(self._h, e.ctypes.data_as(ctypes.c_void_p), e.size), "vegas_get_edges")
         return e
+
+
+# ---------------------------------------------------------------------------
+# Level 3: a batch of independent integrals
+# ---------------------------------------------------------------------------
+BATCH_EDGES, BATCH_OFFSETS, BATCH_ELL, BATCH_BINS, BATCH_ITER_EST, BATCH_ITER_SIG, BATCH_INFO = range(7)
+
+
+class Batch:
+    """Independent integrals run together (vegas_batch_create ... vegas_batch_destroy).
+
+    problems: a list of dicts with keys dim, integrand, params, neval and
+    optionally nstrat (0: automatic)."""
+
+    def __init__(self, problems, nbins=50, alpha=0.5, beta=0.75, seed=0, skip=0, stream=None):
+        n = len(problems)
+        arr = (Problem * n)()
+        self._params = []
+        for i, q in enumerate(problems):
+            prm = np.ascontiguousarray(q.get("params", []), dtype=np.float64)
+            self._params.append(prm)
+            arr[i] = Problem(int(q["dim"]), int(q["integrand"]), prm.ctypes.data if prm.size else None, prm.size,
+                             int(q["neval"]), int(q.get("nstrat", 0)), 0)
+        h = ctypes.c_void_p()
+        _check(lib.vegas_batch_create(arr, n, nbins, alpha, beta, int(seed), ctypes.byref(h)), "vegas_batch_create")
+        self._h = h
+        self.n, self.nbins = n, nbins
+        self.dims = [int(q["dim"]) for q in problems]
+        if skip:
+            _check(lib.vegas_batch_set_skip(self._h, skip), "vegas_batch_set_skip")
+        if stream is not None:
+            _check(lib.vegas_batch_set_stream(self._h, _stream_ptr(stream)), "vegas_batch_set_stream")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.vegas_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_launch(self, variant, ctas_per_sm=0, chunk_tiles=4):
+        _check(lib.vegas_batch_set_launch(self._h, variant, ctas_per_sm, chunk_tiles), "vegas_batch_set_launch")
+
+    def tune(self):
+        v, c, k = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        ms = ctypes.c_float()
+        _check(lib.vegas_batch_tune(self._h, ctypes.byref(v), ctypes.byref(c), ctypes.byref(k), ctypes.byref(ms)),
+               "vegas_batch_tune")
+        return {"variant": v.value, "ctas_per_sm": c.value, "chunk_tiles": k.value, "ms": ms.value}
+
+    def reset(self):
+        _check(lib.vegas_batch_reset(self._h), "vegas_batch_reset")
+
+    def integrate(self, nitn, rtol=0.0):
+        res = (ProblemResult * self.n)()
+        nrun = ctypes.c_int32()
+        ms = ctypes.c_float()
+        _check(lib.vegas_batch_integrate(self._h, int(nitn), float(rtol), res, ctypes.byref(nrun), ctypes.byref(ms)),
+               "vegas_batch_integrate")
+        out = [{"estimate": r.estimate, "sigma": r.sigma, "chi2_dof": r.chi2_dof, "n_used": r.n_used,
+                "nitn_run": r.nitn_run, "converged": bool(r.converged), "status": r.status} for r in res]
+        return out, nrun.value, ms.value
+
+    def info(self, p):
+        o = np.zeros(4, dtype=np.int64)
+        _check(lib.vegas_batch_get(self._h, p, BATCH_INFO, o.ctypes.data_as(ctypes.c_void_p), 4), "vegas_batch_get")
+        return {"dim": int(o[0]), "nstrat": int(o[1]), "ncubes": int(o[2]), "nitn_run": int(o[3])}
+
+    def get(self, p, what):
+        inf = self.info(p)
+        d, nh, nrec, G = inf["dim"], inf["ncubes"], inf["nitn_run"], self.nbins
+        shape, dt = {BATCH_EDGES: ((d, G + 1), np.float64), BATCH_OFFSETS: ((nh + 1,), np.int64),
+                     BATCH_ELL: ((nh,), np.float32), BATCH_BINS: ((d, G), np.float64),
+                     BATCH_ITER_EST: ((nrec,), np.float64), BATCH_ITER_SIG: ((nrec,), np.float64)}[what]
+        a = np.zeros(shape, dtype=dt)
+        _check(lib.vegas_batch_get(self._h, p, what, a.ctypes.data_as(ctypes.c_void_p), a.size), "vegas_batch_get")
+        return a
 
 
 # ---------------------------------------------------------------------------

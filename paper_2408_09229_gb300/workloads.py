@@ -153,3 +153,27 @@ def ridge8_params():
 
 def product_peak8_params():
     return product_peak(8, seed=0)
+
+
+def batch_problems(n=256, seed=0, neval_range=(1e5, 1e8), dims=(2, 12), ridge_s=0.1):
+    """n independent integrals for the batched form: d uniform over
+    dims[0]..dims[1], evaluations per iteration log-uniform over neval_range,
+    and the family drawn uniformly from the diagonal ridge (3 peaks of width
+    ridge_s, integral 1), the product peak and the oscillatory integrand, each
+    with parameters from its own seeded generator.  Returns dicts with keys
+    dim, integrand, params, neval, exact."""
+    rng = np.random.default_rng([seed, 0xBA7C])
+    out = []
+    for i in range(n):
+        d = int(rng.integers(dims[0], dims[1] + 1))
+        neval = int(round(10 ** rng.uniform(math.log10(neval_range[0]), math.log10(neval_range[1]))))
+        fam = int(rng.integers(0, 3))
+        if fam == 0:
+            iid, params = GAUSS_SUM, ridge(d, 3, ridge_s)
+        elif fam == 1:
+            iid, params = PRODUCT_PEAK, product_peak(d, seed=seed * 100_003 + i)
+        else:
+            iid, params = OSCILLATORY, oscillatory(d, seed=seed * 100_003 + i)
+        out.append({"dim": d, "integrand": iid, "params": [float(v) for v in params], "neval": neval,
+                    "exact": exact(iid, d, params)})
+    return out
