@@ -123,6 +123,59 @@ def max_over_ranks(x, world, device="cuda"):
     return float(t.item())
 
 
+def stress_d30(V, W, stream, rank):
+    """The high-dimensional workload: d = 30, 6 Gaussian peaks (s = 0.1) on the main and the anti-diagonal,
+    2 strata on axes 0-19 and 1 on axes 20-29 (2^20 cubes), 4e8 evaluations per iteration, 20 iterations,
+    FP32 form (plain VEGAS+; no learned proposal); plain FP64 timed for 2 iterations beside it."""
+    import torch
+    d, neval, nitn = 30, 400_000_000, 20
+    ns = [2] * 20 + [1] * 10
+    params = W.two_diagonal_ridge(d, 0.1)
+    out = {"workload": "d=30, 6 peaks (s=0.1) on two diagonals, strata 2 on axes 0-19, 1 on 20-29, "
+                       "4e8 evals/iteration, Ng=50, beta=0.75, alpha=0.5"}
+    for pname, prec, its in (("fp32_form", V.FP32, nitn), ("plain_fp64", V.FP64, 2)):
+        v = V.Vegas(d, NBINS, 0, ALPHA, BETA, precision=prec, nstrat_axes=ns, stream=stream)
+        v.integrate(W.GAUSS_SUM, params, neval, 1, seed=5)  # sizes the buffers outside the clock
+        v.reset_map()
+        torch.cuda.synchronize()
+        r = v.integrate(W.GAUSS_SUM, params, neval, its, seed=SEED + rank)
+        it_ms, fill_ms = v.timings()
+        out[pname] = {"evals_per_s": neval * its / (float(np.sum(it_ms)) / 1e3), "iterations": its,
+                      "ms_per_iteration": float(np.mean(it_ms)), "fill_ms": float(np.mean(fill_ms)),
+                      "estimate": r["estimate"], "sigma": r["sigma"], "chi2_dof": r["chi2_dof"],
+                      "pull_from_exact": (r["estimate"] - 1.0) / r["sigma"] if r["sigma"] > 0 else None}
+        v.close()
+    return out
+
+
+SWEEP_DEFAULT = {"neval": 10 ** 9, "dim": 8, "nbins": 1024}
+SWEEP_AXES = {"neval": [10 ** 5, 10 ** 6, 10 ** 7, 10 ** 8, 10 ** 9], "dim": [2, 4, 8, 16, 32],
+              "nbins": [16, 64, 256, 1024, 4096]}
+
+
+def fill_sweep(V, W, stream, args):
+    """The paper's vegasFill scaling test (Sec. 4.2, its Table 4): the linear integrand, one parameter
+    changed at a time around evaluations 2e10 over 20 iterations (1e9 per iteration), d = 8, N_g = 1024.
+    Per point: mean fill-kernel and iteration times over the timed iterations, both forms."""
+    import torch
+    rows = []
+    for axis, values in SWEEP_AXES.items():
+        for val in values:
+            cfg = dict(SWEEP_DEFAULT, **{axis: val})
+            for pname, prec in (("fp32_form", V.FP32), ("plain_fp64", V.FP64)):
+                v = V.Vegas(cfg["dim"], cfg["nbins"], 0, ALPHA, BETA, precision=prec, stream=stream)
+                v.integrate(W.LINEAR, [], cfg["neval"], 2, seed=SEED)
+                torch.cuda.synchronize()
+                r = v.integrate(W.LINEAR, [], cfg["neval"], args.steps, seed=SEED + 1)
+                it_ms, fill_ms = v.timings()
+                rows.append({"vary": axis, **cfg, "form": pname, "fill_ms": float(np.mean(fill_ms)),
+                             "iteration_ms": float(np.mean(it_ms)),
+                             "fill_ns_per_eval": float(np.mean(fill_ms)) * 1e6 / cfg["neval"],
+                             "rel_err": abs(r["estimate"] / (cfg["dim"] / 2.0) - 1), "sigma": r["sigma"]})
+                v.close()
+    return {"sweep": "fill scaling, linear integrand", "iterations_timed": args.steps, "rows": rows}
+
+
 BATCH_N, BATCH_CAP, BATCH_ITERS = 256, 30, 3
 
 
@@ -148,9 +201,23 @@ def batched_form(V, W, stream, rank):
     out, n_rtol, ms_rtol = b.integrate(BATCH_CAP, rtol=1e-4)
     t_batch = time.perf_counter() - t0
     pulls = np.array([(r["estimate"] - p["exact"]) / r["sigma"] for r, p in zip(out, probs) if r["sigma"] > 0])
+    names = {W.GAUSS_SUM: "ridge", W.PRODUCT_PEAK: "product_peak", W.OSCILLATORY: "oscillatory"}
+    outliers = [{"i": i, "d": p["dim"], "family": names[p["integrand"]], "neval": p["neval"],
+                 "pull": (r["estimate"] - p["exact"]) / r["sigma"], "rel_err": abs(r["estimate"] / p["exact"] - 1),
+                 "iterations": r["nitn_run"]}
+                for i, (r, p) in enumerate(zip(out, probs)) if r["sigma"] > 0 and
+                abs(r["estimate"] - p["exact"]) > 3 * r["sigma"]]
     evals_batch = sum(r["nitn_run"] * p["neval"] for r, p in zip(out, probs))
     conv_batch = sum(r["converged"] for r in out)
     b.close()
+    # the same integrals through the plain FP64 path, for comparison
+    for o in outliers[:6]:
+        p = probs[o["i"]]
+        v = V.Vegas(p["dim"], NBINS, 0, ALPHA, BETA, precision=V.FP64, rtol=1e-4, stream=stream)
+        r = v.integrate(p["integrand"], p["params"], p["neval"], BATCH_CAP, seed=SEED + rank)
+        o["plain_fp64_pull"] = (r["estimate"] - p["exact"]) / r["sigma"]
+        o["plain_fp64_rel_err"] = abs(r["estimate"] / p["exact"] - 1)
+        v.close()
     # the same integrals one after another through the single-integral handle
     hs = []
     for p in probs:
@@ -186,9 +253,9 @@ def batched_form(V, W, stream, rank):
                                          "converged": conv_batch, "evals": evals_batch},
                              "plain_one_by_one": {"seconds": t_plain, "converged": int(conv_plain),
                                                   "evals": evals_plain}},
-            "pulls_from_exact": {"max_abs": float(np.abs(pulls).max()), "within_3_sigma": int((np.abs(pulls) <= 3).sum()),
-                                 "n": int(len(pulls))},
-            "gpu_launches_per_iteration": 9}
+            "pulls_from_exact": {"within_3_sigma": int((np.abs(pulls) <= 3).sum()), "n": int(len(pulls)),
+                                 "outside_3_sigma": outliers},
+            "gpu_launches_per_iteration": 10}
 
 
 def run_ours(args, rank, world):
@@ -217,6 +284,20 @@ def run_ours(args, rank, world):
         it_ms, fill_ms = v.timings()
         return v, r, outer_ms, it_ms, fill_ms
 
+    if args.sweep:
+        if rank == 0:
+            print(json.dumps(fill_sweep(V, W, stream, args)))
+        return
+    if args.profile_batch:
+        probs = W.batch_problems(args.profile_batch, seed=0, neval_range=(1e5, args.batch_max_neval))
+        b = V.Batch(probs, NBINS, ALPHA, BETA, seed=SEED, stream=stream)
+        b.integrate(args.warmup)
+        _, n, ms = b.integrate(args.steps)
+        total = sum(p["neval"] for p in probs)
+        if rank == 0:
+            print(json.dumps({"profile": "batched", "integrals": len(probs), "evals_per_iteration": total,
+                              "evals_per_s": total * n / (ms / 1e3), "ms_per_iteration": ms / n}))
+        return
     if args.profile:
         v, r, outer_ms, it_ms, fill_ms = timed_run(V.FP32 if args.precision == "fp32" else V.FP64)
         if rank == 0:
@@ -293,6 +374,7 @@ def run_ours(args, rank, world):
         table1[name] = row
 
     batched = batched_form(V, W, stream, rank)
+    stress = stress_d30(V, W, stream, rank)
 
     t_dev32 = max_over_ranks(float(np.sum(it32)) / 1e3, world)
     t_dev64 = max_over_ranks(float(np.sum(it64)) / 1e3, world)
@@ -305,8 +387,9 @@ def run_ours(args, rank, world):
     achieved = ops * NEVAL / fill_mean32 / 1e12
     peak = FP32_LANES_PER_SM * sms * 2070e6 / 1e12
     # per steady iteration: allocation 3 (q sums, their scan, offsets; the max of the weights comes from
-    # the fill), fill 5 (tile search, fill, fix-up, results, map weights), refinement 1, combination 1
-    launches_per_it = 10
+    # the fill), fill 6 (tile search, fill, carry runs, fix-up, results, map weights), refinement 1,
+    # combination 1
+    launches_per_it = 11
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_dev32 / args.steps * 1e3, "higher_is_better": True,
@@ -321,6 +404,7 @@ def run_ours(args, rank, world):
                                                 "w ~ U[0.2,0.8], seed 0; same d, cubes and evaluations"),
         "time_to_rtol": {"rtol": 1e-4, "fp32_form": ttr32, "plain_fp64": ttr64},
         "batched": batched,
+        "stress_d30": stress,
         "paper_table1_context": dict(table1, note="total wall ms of 20 iterations (def configuration) through "
                                      "vegas_integrate; the paper reports 29.0/91.5 ms (Roos&Arnold) and "
                                      "149.4/1123.1 ms (Ridge) for 1e7/1e8 evaluations on one A100 in FP64"),
@@ -395,6 +479,12 @@ def main():
                     help="profiling run: only the warm-up and timed iterations of one form, a short JSON line")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="the form a --profile run times")
+    ap.add_argument("--sweep", action="store_true",
+                    help="fill scaling sweep of the paper's Table 4 parameters on the linear integrand")
+    ap.add_argument("--profile-batch", type=int, default=0, metavar="N",
+                    help="profiling run of the batched form on the first N integrals of the batched workload")
+    ap.add_argument("--batch-max-neval", type=float, default=1e8,
+                    help="upper end of the log-uniform budgets of a --profile-batch run")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

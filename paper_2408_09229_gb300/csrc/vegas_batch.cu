@@ -12,6 +12,7 @@
 //   offsets    allocation pass 3 (counts n_h as offsets, Sec. 2.1.2)
 //   tile_first first cube of every tile; reset the max-ell keys
 //   fill       Algorithm 2 over all tiles (vegas_batch_fill.cuh)
+//   carry_scan runs of tile records of cubes that span tiles, pre-reduced
 //   fixup      cubes that cross tile edges
 //   refine     the map of every running integral, in place (Sec. 2.1.1)
 //   finish     record (I_t, sigma_t), Eqs. (8)-(9), the rtol test, and the
@@ -135,9 +136,29 @@ __global__ void batch_tile_first_kernel(const __grid_constant__ BatchLaunch L) {
   const_cast<int32_t*>(a.tile_first)[t] = lo;
 }
 
+// runs of "before" records reduced from the right within blocks of
+// kCarryBlock consecutive tiles of the work list (carry_suffix)
+__global__ void __launch_bounds__(kCarryBlock) batch_carry_scan_kernel(const __grid_constant__ BatchLaunch L) {
+  const int gt = blockIdx.x * kCarryBlock + threadIdx.x;
+  Carry rec{-1, 0, 0.0, 0.0};
+  bool joins = false;
+  Carry* car = nullptr;
+  int t = 0;
+  if (gt < L.act_tile[L.P]) {
+    const int p = batch_find(L.act_tile, L.P, gt);
+    t = gt - L.act_tile[p];
+    car = L.prob[p].a.carries;
+    rec = car[2 * t];
+    if (rec.h >= 0 && threadIdx.x > 0 && t > 0) joins = car[2 * (t - 1)].h == rec.h;
+  }
+  rec = carry_suffix(rec, joins);
+  if (car && rec.h >= 0) car[2 * t] = rec;
+}
+
 // cubes that cross tile edges (the single-integral fix-up, per integral of
-// the batch); the sums go to the integral's accumulators, one atomic add per
-// warp when the warp's tiles share their integral
+// the batch); the walk reads one pre-reduced record per block of the work
+// list; the sums go to the integral's accumulators, one atomic add per warp
+// when the warp's tiles share their integral
 __global__ void __launch_bounds__(256) batch_fixup_kernel(const __grid_constant__ BatchLaunch L) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   double ai = 0.0, av = 0.0;
@@ -154,16 +175,15 @@ __global__ void __launch_bounds__(256) batch_fixup_kernel(const __grid_constant_
       const int h = r.h;
       const int64_t n = a.offsets[h + 1] - a.offsets[h];
       double cnt = r.cnt, mean = r.mean, m2 = r.m2;
-      for (int u = t + 1; cnt < (double)n && u < a.ntiles; ++u) {
+      const int base = L.act_tile[p];
+      for (int u = t + 1; cnt < (double)n && u < a.ntiles;
+           u = ((base + u) / kCarryBlock + 1) * kCarryBlock - base) {
         const Carry c = a.carries[2 * u];
         if (c.h != h) {
           broken = true;
           break;
         }
-        const double nb = c.cnt, ntot = cnt + nb, delta = c.mean - mean;
-        mean += delta * nb / ntot;
-        m2 += c.m2 + delta * delta * cnt * nb / ntot;
-        cnt = ntot;
+        chan_merge(cnt, mean, m2, c.cnt, c.mean, c.m2);
       }
       if (cnt != (double)n) broken = true;
       ai = mean;
@@ -420,6 +440,8 @@ int enqueue_iteration(vegas_batch_s* b, const BatchLaunch& L, cudaStream_t s) {
   VG_CHECK(cudaGetLastError());
   int rc = launch_batch_fill(b->variant, L, b->fill_grid, b->smem, s);
   if (rc != VEGAS_OK) return rc;
+  batch_carry_scan_kernel<<<ntb, kCarryBlock, 0, s>>>(L);
+  VG_CHECK(cudaGetLastError());
   batch_fixup_kernel<<<ntb, 256, 0, s>>>(L);
   VG_CHECK(cudaGetLastError());
   const size_t rsmem = sizeof(double) * (3 * (size_t)b->G + 1);

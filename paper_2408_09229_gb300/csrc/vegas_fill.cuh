@@ -789,6 +789,69 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
   __syncthreads();
   }
 
+// ---------------------------------------------------------------------------
+// Cubes that cross tile edges.  A cube that starts in tile t and ends in tile
+// t_end leaves an "after" record in slot 2t+1 of tile t and a "before" record
+// in slot 2u of every later tile u <= t_end.  Before the fix-up merges them,
+// the before records are reduced from the right within blocks of
+// kCarryBlock consecutive tiles: slot 2u then holds the merge of u up to the
+// end of its run of same-cube records inside u's block.  The fix-up reads one
+// record per block, so a cube spanning T tiles costs T / kCarryBlock steps
+// instead of T.  The merge is Chan et al.'s pairwise update of
+// (count, mean, M2), which is associative up to rounding.
+// ---------------------------------------------------------------------------
+constexpr int kCarryBlock = 256;
+
+__device__ __forceinline__ void chan_merge(double& cnt, double& mean, double& m2, double nb, double mb, double qb) {
+  const double nt = cnt + nb, delta = mb - mean;
+  mean += delta * nb / nt;
+  m2 += qb + delta * delta * cnt * nb / nt;
+  cnt = nt;
+}
+
+// One thread per tile, blockDim.x == kCarryBlock.  rec: the tile's before
+// record (h < 0: none); joins: the record continues the previous tile's run
+// (same integral and cube, both present).  Returns the run's suffix merge.
+__device__ __forceinline__ Carry carry_suffix(Carry rec, bool joins) {
+  __shared__ int seg[kCarryBlock];
+  __shared__ int wtot[kCarryBlock / 32];
+  __shared__ double sc[2][kCarryBlock], sm[2][kCarryBlock], sq[2][kCarryBlock];
+  const int u = threadIdx.x, lane = u & 31, w = u >> 5;
+  // segment ids: inclusive scan of the run heads
+  int head = (u == 0 || !joins) ? 1 : 0;
+  int x = head;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wtot[w] = x;
+  __syncthreads();
+  for (int k = 0; k < w; ++k) x += wtot[k];
+  seg[u] = x;
+  sc[0][u] = rec.h >= 0 ? (double)rec.cnt : 0.0;
+  sm[0][u] = rec.mean;
+  sq[0][u] = rec.m2;
+  __syncthreads();
+  int cur = 0;
+#pragma unroll 1
+  for (int o = 1; o < kCarryBlock; o <<= 1) {
+    double c = sc[cur][u], m = sm[cur][u], q = sq[cur][u];
+    if (rec.h >= 0 && u + o < kCarryBlock && seg[u + o] == seg[u]) chan_merge(c, m, q, sc[cur][u + o], sm[cur][u + o], sq[cur][u + o]);
+    sc[cur ^ 1][u] = c;
+    sm[cur ^ 1][u] = m;
+    sq[cur ^ 1][u] = q;
+    cur ^= 1;
+    __syncthreads();
+  }
+  if (rec.h >= 0) {
+    rec.cnt = (int32_t)sc[cur][u];
+    rec.mean = sm[cur][u];
+    rec.m2 = sq[cur][u];
+  }
+  return rec;
+}
+
 // Fill of one integral: a persistent grid walks the tiles round-robin.
 // EXACT: d == DMAX and the map table is in shared memory, so the per-axis
 // bounds checks vanish and the table reads are shared-memory loads.  The FP32

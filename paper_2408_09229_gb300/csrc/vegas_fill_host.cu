@@ -191,9 +191,24 @@ __global__ void table_kernel(const double* __restrict__ edges, int d, int G, Tab
   tab[b] = TabEntry<T>{(T)e0, (T)dx, (T)jk, T(0)};
 }
 
-// Merge, in tile order, the parts of every cube that crosses a tile edge.
-// Thread t owns the cube that starts in tile t and ends after it (slot
-// 2t+1); the later parts are the "starts before" slots 2u of tiles u > t.
+// Runs of "before" records reduced from the right within blocks of
+// kCarryBlock tiles (carry_suffix); one thread per tile.
+__global__ void __launch_bounds__(kCarryBlock) carry_scan_kernel(const __grid_constant__ FillArgs a) {
+  const int u = blockIdx.x * kCarryBlock + threadIdx.x;
+  Carry rec{-1, 0, 0.0, 0.0};
+  bool joins = false;
+  if (u < a.ntiles) {
+    rec = a.carries[2 * u];
+    if (rec.h >= 0 && threadIdx.x > 0) joins = a.carries[2 * (u - 1)].h == rec.h;
+  }
+  rec = carry_suffix(rec, joins);
+  if (u < a.ntiles && rec.h >= 0) a.carries[2 * u] = rec;
+}
+
+// Merge the parts of every cube that crosses a tile edge.  Thread t owns the
+// cube that starts in tile t and ends after it (slot 2t+1); the later parts
+// are the "starts before" slots 2u of tiles u > t, pre-reduced per block of
+// kCarryBlock tiles, so the walk reads one record per block.
 __global__ void fixup_kernel(const __grid_constant__ FillArgs a, double* fix_part) {
   __shared__ double red[32];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -207,16 +222,13 @@ __global__ void fixup_kernel(const __grid_constant__ FillArgs a, double* fix_par
       const int h = r.h;
       const int64_t n = a.offsets[h + 1] - a.offsets[h];
       double cnt = r.cnt, mean = r.mean, m2 = r.m2;
-      for (int u = t + 1; cnt < (double)n && u < a.ntiles; ++u) {
+      for (int u = t + 1; cnt < (double)n && u < a.ntiles; u = (u / kCarryBlock + 1) * kCarryBlock) {
         const Carry q = a.carries[2 * u];
         if (q.h != h) {
           broken = true;
           break;
         }
-        const double nb = q.cnt, nt = cnt + nb, delta = q.mean - mean;
-        mean += delta * nb / nt;
-        m2 += q.m2 + delta * delta * cnt * nb / nt;
-        cnt = nt;
+        chan_merge(cnt, mean, m2, q.cnt, q.mean, q.m2);
       }
       if (cnt != (double)n) broken = true;
       ai = mean;
@@ -390,6 +402,8 @@ int fill_impl(const vegas_geometry* g, int precision, int integrand, const doubl
   if (rc != VEGAS_OK) return rc;
   if (ev_after) VG_CHECK(cudaEventRecord(ev_after, s));
   double* fix_part = (double*)(sc + L.fix_part);
+  carry_scan_kernel<<<L.nfix, kCarryBlock, 0, s>>>(a);
+  VG_CHECK(cudaGetLastError());
   fixup_kernel<<<L.nfix, 256, 0, s>>>(a, fix_part);
   VG_CHECK(cudaGetLastError());
   results_kernel<<<1, 256, 0, s>>>(a.cta_part, grid, fix_part, L.nfix, a.NH, a.vexp, d_result);

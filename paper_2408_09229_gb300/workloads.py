@@ -177,3 +177,20 @@ def batch_problems(n=256, seed=0, neval_range=(1e5, 1e8), dims=(2, 12), ridge_s=
         out.append({"dim": d, "integrand": iid, "params": [float(v) for v in params], "neval": neval,
                     "exact": exact(iid, d, params)})
     return out
+
+
+def flow_params(d, seed=0, out_scale=0.0, hidden=64, layers=6):
+    """Seeded parameter vector of the coupling flow of the learned proposal
+    (layout in include/vegas.h, vegas_flow_param_count): He-normal W1, W2,
+    zero b1, b2, and W3, b3 drawn with standard deviation out_scale (0: the
+    identity flow, the usual starting point of training)."""
+    rng = np.random.default_rng([seed, 0xF10E])
+    parts = []
+    for l in range(layers):
+        a = (d + 1) // 2 if l % 2 == 0 else d // 2
+        b = d - a
+        parts += [rng.normal(0.0, math.sqrt(2.0 / a), hidden * a), np.zeros(hidden),
+                  rng.normal(0.0, math.sqrt(2.0 / hidden), hidden * hidden), np.zeros(hidden),
+                  rng.normal(0.0, out_scale / math.sqrt(hidden), 2 * b * hidden) if out_scale else np.zeros(2 * b * hidden),
+                  rng.normal(0.0, out_scale, 2 * b) if out_scale else np.zeros(2 * b)]
+    return np.concatenate(parts).astype(np.float32).astype(np.float64)

@@ -213,6 +213,25 @@ def test_fill_fp32_matches_oracle(V, orc, name, d, G, ns, iid, params, neval):
 # ---------------------------------------------------------------------------
 # map refinement and combination
 # ---------------------------------------------------------------------------
+def test_fill_fp32_d30_two_diagonal_ridge(V, orc):
+    """the d = 30 workload: 6 peaks on two diagonals, 2 strata on axes 0-19 and 1 on 20-29 (2^20 cubes),
+    FP32 form against the oracle on the same FP32 points, map and counts"""
+    d, G, neval = 30, 50, 3_000_001
+    ns = [2] * 20 + [1] * 10
+    params = W.two_diagonal_ridge(d, 0.1)
+    cfg = orc.Config(d, G, ns, 0.5, 0.75, points_f32=True)
+    rng = np.random.default_rng(30)
+    edges = random_edges(rng, d, G)
+    ell = rng.normal(0, 2, cfg.ncubes).astype(np.float32)
+    off = orc.allocate(ell, cfg.ncubes, neval, 0.75)
+    g = gpu_fill(V, cfg, V.FP32, W.GAUSS_SUM, params, neval, 2, 30, edges, off, want_cubes=False)
+    r = orc.iteration(cfg, W.GAUSS_SUM, params, neval, 2, 30, edges, off)
+    assert g["flags"] == 0
+    assert g["est"] == pytest.approx(r["est"], rel=2e-5)
+    assert g["var"] == pytest.approx(r["var"], rel=2e-3)
+    assert np.allclose(g["bins"], r["bins"], rtol=0, atol=1e-3 * r["bins"].max())
+
+
 @pytest.mark.parametrize("d,G,alpha", [(1, 2, 0.5), (4, 50, 0.5), (8, 50, 1.5), (3, 1024, 0.5), (2, 4096, 1.0)])
 def test_refine_matches_oracle(V, orc, d, G, alpha):
     rng = np.random.default_rng(G + d)
@@ -300,6 +319,31 @@ def test_integrate_closed_form(V, name, iid, d, params, neval, nitn, precision):
     exact = W.exact(iid, d, params)
     assert r["status"] == 0
     assert abs(r["estimate"] - exact) < 4 * r["sigma"], (r["estimate"], r["sigma"], exact)
+
+
+TABLE3 = [  # the paper's Table 3 at its dimensions
+    ("(1) sine exponential", W.SIN_EXP, 2, []),
+    ("(2) linear", W.LINEAR, 10, []),
+    ("(3) cosine", W.COSINE, 10, []),
+    ("(4) exponential", W.EXPONENTIAL, 10, []),
+    ("(5) roos-arnold", W.ROOS_ARNOLD, 10, []),
+    ("(6) morokoff-caflisch", W.MOROKOFF_CAFLISCH, 8, []),
+    ("(7) gaussian", W.GAUSS_SUM, 4, W.gaussian(4)),
+    ("(8) ridge N=1000", W.GAUSS_SUM, 4, W.paper_ridge(4, 1000)),
+]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name,iid,d,params", TABLE3, ids=[c[0] for c in TABLE3])
+def test_table3_suite_def_configuration(V, name, iid, d, params, precision):
+    """Table 3 integrands under the paper's "def" configuration (Table 2: N_g = 1024, alpha = 0.5,
+    beta = 0.75), 1e6 evaluations per iteration, 10 iterations: within 4 sigma of the closed form"""
+    v = V.Vegas(d, 1024, 0, 0.5, 0.75, precision=precision)
+    r = v.integrate(iid, params, 1_000_000, 10, seed=11)
+    exact = W.exact(iid, d, params)
+    assert r["status"] == 0 and r["nitn_run"] == 10
+    assert abs(r["estimate"] - exact) < 4 * r["sigma"], (r["estimate"], r["sigma"], exact)
+    assert r["sigma"] < 1e-2 * abs(exact)
 
 
 def test_full_size_ridge8_sampled_cubes(V, orc):
