@@ -361,6 +361,71 @@ enum vegas_batch_field {
 VEGAS_API int vegas_batch_get(vegas_batch b, int32_t problem, int32_t what, void *host_out, int64_t count);
 
 /* ======================================================================== */
+/* Level 4: the learned proposal (a coupling flow after the VEGAS map)      */
+/* ======================================================================== */
+/* The paper has no learned component.  The VEGAS+ map (Sec. 2.1.1) samples
+ * x' = M(y); a flow F maps x' to the point x = F(x') where the integrand is
+ * evaluated, and VEGAS+ integrates g(x') = f(F(x')) |det dF/dx'|, whose
+ * integral over the unit cube is that of f.  F is 6 affine coupling layers
+ * (RealNVP) between a logit (clamped to [-20, 20]) and a sigmoid; layer l
+ * conditions on the axes k = l (mod 2) through an MLP a_l -> 64 -> 64 -> 2 b_l
+ * with ReLU, whose outputs 2j and 2j+1 give s_j = 2 tanh(o_2j / 2) and t_j.
+ * The normalising direction N = F^-1 moves z_B to z_B e^s + t; the sampling
+ * direction F moves it to (z_B - t) e^-s.  The MLPs run on the tensor cores
+ * with bf16 weights and activations and FP32 accumulation; the log-
+ * determinant is that of the map actually applied, so g stays unbiased.
+ *
+ * Parameters: one FP32 vector of vegas_flow_param_count(dim) values; per layer
+ * l = 0..5 in order W1 [64][a_l], b1 [64], W2 [64][64], b2 [64],
+ * W3 [2 b_l][64], b3 [2 b_l], row-major, with a_l = ceil(d/2) for even l and
+ * floor(d/2) for odd l, b_l = d - a_l.  2 <= dim <= 32 (the training entry
+ * point: dim <= 16). */
+enum vegas_flow_direction {
+  VEGAS_FLOW_NORMALISE = 0, /* x -> x' = F^-1(x), log|det dF^-1/dx|  */
+  VEGAS_FLOW_SAMPLE = 1     /* x' -> x = F(x'),   log|det dF/dx'|   */
+};
+/* Number of parameters of the flow for dim, or 0 when dim is out of range. */
+VEGAS_API int64_t vegas_flow_param_count(int32_t dim);
+/* Apply the flow to n points d_x_in [n][dim] (device, FP32, in [0,1]) in the
+ * given direction: d_x_out [n][dim] and d_logdet [n] (device).  d_x_out may
+ * equal d_x_in.  Asynchronous on stream.  Errors: EINVAL, ECUDA. */
+VEGAS_API int vegas_flow_apply(int32_t dim, int32_t direction, const float *d_params, const float *d_x_in,
+                               float *d_x_out, float *d_logdet, int64_t n, void *stream);
+/* Training loss and gradient.  For samples d_x [n][dim] with weights
+ * d_w [n] >= 0 of positive sum (|f| over the density that drew them, e.g.
+ * |J f| of a VEGAS+ iteration), loss = - sum_i w_i log|det dF^-1/dx(x_i)| /
+ * sum_i w_i, the weighted negative log-likelihood of the flow's density with
+ * a uniform base (its minimiser makes that density proportional to |f|).
+ * Writes d_grad [param_count] and, if not NULL, d_loss [1] (device).
+ * d_scratch holds vegas_flow_grad_scratch_bytes(dim, n) bytes.  The partial
+ * gradients of blocks of 32 samples are summed in a fixed order.
+ * Errors: EINVAL (dim > 16 included), ENOSPACE, ECUDA. */
+VEGAS_API size_t vegas_flow_grad_scratch_bytes(int32_t dim, int64_t n);
+VEGAS_API int vegas_flow_grad(int32_t dim, const float *d_params, const float *d_x, const float *d_w, int64_t n,
+                              float *d_grad, float *d_loss, void *d_scratch, size_t scratch_bytes, void *stream);
+/* One Adam step (Kingma and Ba) on d_params with d_grad, moments d_m, d_v
+ * (device, zero before step 1), step counting from 1.  Errors: EINVAL, ECUDA. */
+VEGAS_API int vegas_flow_adam(int64_t nparams, float *d_params, const float *d_grad, float *d_m, float *d_v,
+                              int32_t step, float lr, float beta1, float beta2, float eps, void *stream);
+
+/* The learned proposal on a handle.  vegas_set_flow with parameters (host,
+ * vegas_flow_param_count(dim) values) turns it on: every later iteration of
+ * vegas_integrate draws the VEGAS+ points x', maps them to x = F(x'),
+ * evaluates f there and integrates g(x') = f(F(x')) |det dF/dx'| (FP32 form
+ * only; 2 <= dim <= 16).  NULL turns it off.  The Adam moments start at zero.
+ * vegas_set_flow_training: during the next `iterations` iterations, after each
+ * one, run steps_per_iteration Adam steps (learning rate lr) on every k-th
+ * evaluation of that iteration, k = neval / samples, each weighted by
+ * |J f| / n_h, its share of the estimate.  vegas_get_flow copies the current
+ * parameters (nparams = the count, or params NULL) and the last training loss.
+ * The checkpoint of vegas_get_state does not include the flow.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+VEGAS_API int vegas_set_flow(vegas_handle h, const float *params, int64_t nparams);
+VEGAS_API int vegas_set_flow_training(vegas_handle h, int32_t iterations, int32_t steps_per_iteration,
+                                      int32_t samples, float lr);
+VEGAS_API int vegas_get_flow(vegas_handle h, float *params, int64_t nparams, float *last_loss);
+
+/* ======================================================================== */
 /* Measurement support                                                      */
 /* ======================================================================== */
 /* Measure issue rates of the arithmetic pipes on the current device with

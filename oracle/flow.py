@@ -39,9 +39,10 @@ Definitions (the same in the CUDA path):
       W1 [H][a_l], b1 [H], W2 [H][H], b2 [H], W3 [2 b_l][H], b3 [2 b_l],
     row-major; rows 2j and 2j+1 of W3 give s_j and t_j.
 
-bf16=True rounds what the CUDA path stores as bf16 (the weights, the
-conditioner input h and the hidden activations u1, u2) to bf16, round to
-nearest even, from their FP32 values; the arithmetic stays FP64.
+bf16=True rounds what the CUDA path stores as bf16 (the weight matrices,
+the conditioner input h and the hidden activations u1, u2; not the biases)
+to bf16, round to nearest even, from their FP32 values; the arithmetic stays
+FP64.
 """
 import numpy as np
 
@@ -102,7 +103,8 @@ def _sigmoid(z):
 
 def _mlp(layer, h, rnd):
     """conditioner of one layer on a batch h [n][a]: (s, t, cache)"""
-    W1, b1, W2, b2, W3, b3 = (rnd(layer[k]) for k in ("W1", "b1", "W2", "b2", "W3", "b3"))
+    W1, W2, W3 = (rnd(layer[k]) for k in ("W1", "W2", "W3"))
+    b1, b2, b3 = (layer[k] for k in ("b1", "b2", "b3"))  # biases stay FP32 values
     hq = rnd(h)
     a1 = hq @ W1.T + b1
     u1 = rnd(np.maximum(a1, 0.0))

@@ -49,6 +49,19 @@ struct vegas_s {
   const int* fill_key = nullptr;  // max-ell key left in the fill scratch by the last fill, or NULL
   std::vector<int32_t> ell_nstrat;
   int64_t iter_counter = 0;
+  // learned proposal: the flow's parameters (NULL: off), Adam state, the
+  // per-evaluation buffers and the training schedule
+  float* d_flow = nullptr;
+  float *d_flow_m = nullptr, *d_flow_v = nullptr, *d_flow_g = nullptr, *d_flow_loss = nullptr;
+  int64_t flow_np = 0;
+  int flow_step = 0, flow_train_iters = 0, flow_train_steps = 0, flow_train_samples = 0, flow_trained = 0;
+  float flow_lr = 1e-3f;
+  float *d_X = nullptr, *d_logdet = nullptr, *d_values = nullptr;
+  int64_t x_cap = 0, ld_cap = 0, val_cap = 0;
+  float *d_train_x = nullptr, *d_train_w = nullptr;
+  int64_t tx_cap = 0, tw_cap = 0;
+  void* d_grad_scratch = nullptr;
+  size_t grad_scratch_cap = 0;
   // timing
   std::vector<cudaEvent_t> ev;  // 4 per iteration: start, fill start, fill end, end
   int last_nrun = 0;
@@ -160,6 +173,10 @@ void release(vegas_s* h) {
   cudaFree(h->d_it_est);
   cudaFree(h->d_it_sig);
   if (h->h_out) cudaFreeHost(h->h_out);
+  for (float* p : {h->d_flow, h->d_flow_m, h->d_flow_v, h->d_flow_g, h->d_flow_loss, h->d_X, h->d_logdet,
+                   h->d_values, h->d_train_x, h->d_train_w})
+    cudaFree(p);
+  cudaFree(h->d_grad_scratch);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
 }
@@ -316,6 +333,28 @@ extern "C" int vegas_integrate(vegas_handle h, int integrand, const double* para
     VG_CHECK(cudaMemcpyAsync(h->d_params, params, sizeof(double) * (size_t)nparams, cudaMemcpyHostToDevice, s));
   VG_CHECK(cudaMemsetAsync(h->d_flags, 0, sizeof(int), s));
 
+  // learned proposal: per-evaluation buffers and the training sample
+  const bool flow = h->d_flow != nullptr;
+  int64_t train_stride = 1, n_train = 0;
+  if (flow) {
+    if (h->precision != VEGAS_FP32) return VEGAS_EINVAL;
+    if ((rc = grow(h->d_X, h->x_cap, neval * d)) != VEGAS_OK || (rc = grow(h->d_logdet, h->ld_cap, neval)) != VEGAS_OK ||
+        (rc = grow(h->d_values, h->val_cap, neval)) != VEGAS_OK)
+      return rc;
+    if (h->flow_train_iters > h->flow_trained && h->flow_train_samples > 0 && h->flow_train_steps > 0) {
+      train_stride = std::max<int64_t>(1, neval / h->flow_train_samples);
+      n_train = (neval + train_stride - 1) / train_stride;
+      if ((rc = grow(h->d_train_x, h->tx_cap, n_train * d)) != VEGAS_OK ||
+          (rc = grow(h->d_train_w, h->tw_cap, n_train)) != VEGAS_OK)
+        return rc;
+      const size_t gs = vegas_flow_grad_scratch_bytes(d, n_train);
+      if (gs == 0) return VEGAS_EINVAL;
+      if ((rc = grow_bytes(h->d_grad_scratch, h->grad_scratch_cap, gs)) != VEGAS_OK) return rc;
+    } else if (h->flow_train_iters > h->flow_trained) {
+      h->flow_trained = h->flow_train_iters;  // nothing to train with
+    }
+  }
+
   // the stratification of an earlier call carries over only on the same cubes
   bool uniform = !(h->ell_valid && h->ell_nstrat == ns);
   int nrun = 0;
@@ -325,9 +364,29 @@ extern "C" int vegas_integrate(vegas_handle h, int integrand, const double* para
     rc = vg::allocate_impl(h->d_ell, NH, neval, (uniform || h->beta == 0.0) ? 1 : 0, h->d_offsets,
                            h->d_alloc_scratch, h->alloc_scratch_cap, s, h->fill_key);
     if (rc != VEGAS_OK) return rc;
-    rc = vg::fill_impl(&geo, h->precision, integrand, h->d_params, nparams, neval, seed, (int32_t)h->iter_counter, 0u,
-                       h->beta, h->d_edges[h->cur], h->d_offsets, h->d_ell, h->d_bins, h->d_result, nullptr, nullptr,
-                       h->d_flags, h->d_fill_scratch, h->fill_scratch_cap, s, e[1], e[2]);
+    const bool train = flow && h->flow_trained < h->flow_train_iters;
+    if (flow) {
+      // points x' of the VEGAS+ map, x = F(x') and |det dF/dx'|, then g = f(x) |det| tabulated by evaluation
+      vg::FillExtra ex_points{nullptr, h->d_X, nullptr, 0};
+      rc = vg::fill_impl(&geo, VEGAS_FP32, vg::kIntegrandPoints, nullptr, 0, neval, seed, (int32_t)h->iter_counter,
+                         0u, h->beta, h->d_edges[h->cur], h->d_offsets, h->d_ell, h->d_bins, h->d_result, nullptr,
+                         nullptr, h->d_flags, h->d_fill_scratch, h->fill_scratch_cap, s, nullptr, nullptr, &ex_points);
+      if (rc != VEGAS_OK) return rc;
+      if ((rc = vg::flow_apply(d, VEGAS_FLOW_SAMPLE, h->d_flow, h->d_X, h->d_X, h->d_logdet, neval, s)) != VEGAS_OK)
+        return rc;
+      if ((rc = vg::flow_eval(integrand, d, h->d_params, nparams, h->d_X, h->d_logdet, h->d_values, neval, s)) !=
+          VEGAS_OK)
+        return rc;
+      vg::FillExtra ex_tab{h->d_values, nullptr, train ? h->d_train_w : nullptr, (int)train_stride};
+      rc = vg::fill_impl(&geo, VEGAS_FP32, vg::kIntegrandTabulated, nullptr, 0, neval, seed,
+                         (int32_t)h->iter_counter, 0u, h->beta, h->d_edges[h->cur], h->d_offsets, h->d_ell, h->d_bins,
+                         h->d_result, nullptr, nullptr, h->d_flags, h->d_fill_scratch, h->fill_scratch_cap, s, e[1],
+                         e[2], &ex_tab);
+    } else {
+      rc = vg::fill_impl(&geo, h->precision, integrand, h->d_params, nparams, neval, seed, (int32_t)h->iter_counter,
+                         0u, h->beta, h->d_edges[h->cur], h->d_offsets, h->d_ell, h->d_bins, h->d_result, nullptr,
+                         nullptr, h->d_flags, h->d_fill_scratch, h->fill_scratch_cap, s, e[1], e[2]);
+    }
     if (rc != VEGAS_OK) return rc;
     h->fill_key = vg::fill_ellmax_key(&geo, neval, h->d_fill_scratch);
     rc = vegas_refine(d, G, h->alpha, h->d_bins, h->d_edges[h->cur], h->d_edges[1 - h->cur], s);
@@ -335,6 +394,19 @@ extern "C" int vegas_integrate(vegas_handle h, int integrand, const double* para
     h->cur = 1 - h->cur;
     rc = vg::launch_record_combine(h->d_result, it, h->d_it_est, h->d_it_sig, h->skip, h->d_out, s);
     if (rc != VEGAS_OK) return rc;
+    if (train) {
+      // Adam steps on the weighted samples of this iteration (x = F(x'), weight |J f| / n_h)
+      if ((rc = vg::flow_gather(h->d_X, d, train_stride, n_train, h->d_train_x, s)) != VEGAS_OK) return rc;
+      for (int k = 0; k < h->flow_train_steps; ++k) {
+        rc = vegas_flow_grad(d, h->d_flow, h->d_train_x, h->d_train_w, n_train, h->d_flow_g, h->d_flow_loss,
+                             h->d_grad_scratch, h->grad_scratch_cap, s);
+        if (rc != VEGAS_OK) return rc;
+        rc = vegas_flow_adam(h->flow_np, h->d_flow, h->d_flow_g, h->d_flow_m, h->d_flow_v, ++h->flow_step, h->flow_lr,
+                             0.9f, 0.999f, 1e-8f, s);
+        if (rc != VEGAS_OK) return rc;
+      }
+      h->flow_trained++;
+    }
     VG_CHECK(cudaEventRecord(e[3], s));
     h->iter_counter++;
     uniform = false;
@@ -485,4 +557,58 @@ extern "C" const char* vegas_strerror(int status) {
     case VEGAS_ENOSPACE: return "scratch or output buffer too small";
     default: return "unknown status";
   }
+}
+
+// ---------------------------------------------------------------------------
+// learned proposal
+// ---------------------------------------------------------------------------
+extern "C" int vegas_set_flow(vegas_handle h, const float* params, int64_t nparams) {
+  if (!h) return VEGAS_EINVAL;
+  DeviceGuard g(h->device);
+  VG_CHECK(cudaStreamSynchronize(h->stream()));
+  if (!params) {
+    for (float** p : {&h->d_flow, &h->d_flow_m, &h->d_flow_v, &h->d_flow_g, &h->d_flow_loss}) {
+      cudaFree(*p);
+      *p = nullptr;
+    }
+    h->flow_np = 0;
+    return VEGAS_OK;
+  }
+  if (h->dim < 2 || h->dim > 16 || nparams != vegas_flow_param_count(h->dim)) return VEGAS_EINVAL;
+  if (!h->d_flow) {
+    const size_t b = sizeof(float) * (size_t)nparams;
+    if (cudaMalloc((void**)&h->d_flow, b) != cudaSuccess || cudaMalloc((void**)&h->d_flow_m, b) != cudaSuccess ||
+        cudaMalloc((void**)&h->d_flow_v, b) != cudaSuccess || cudaMalloc((void**)&h->d_flow_g, b) != cudaSuccess ||
+        cudaMalloc((void**)&h->d_flow_loss, sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      return VEGAS_ENOMEM;
+    }
+  }
+  h->flow_np = nparams;
+  VG_CHECK(cudaMemcpy(h->d_flow, params, sizeof(float) * (size_t)nparams, cudaMemcpyHostToDevice));
+  VG_CHECK(cudaMemset(h->d_flow_m, 0, sizeof(float) * (size_t)nparams));
+  VG_CHECK(cudaMemset(h->d_flow_v, 0, sizeof(float) * (size_t)nparams));
+  VG_CHECK(cudaMemset(h->d_flow_loss, 0, sizeof(float)));
+  h->flow_step = 0;
+  return VEGAS_OK;
+}
+
+extern "C" int vegas_set_flow_training(vegas_handle h, int32_t iterations, int32_t steps_per_iteration,
+                                       int32_t samples, float lr) {
+  if (!h || iterations < 0 || steps_per_iteration < 0 || samples < 0 || !(lr > 0.0f)) return VEGAS_EINVAL;
+  h->flow_train_iters = iterations;
+  h->flow_train_steps = steps_per_iteration;
+  h->flow_train_samples = samples;
+  h->flow_lr = lr;
+  h->flow_trained = 0;
+  return VEGAS_OK;
+}
+
+extern "C" int vegas_get_flow(vegas_handle h, float* params, int64_t nparams, float* last_loss) {
+  if (!h || !h->d_flow || (params && nparams != h->flow_np)) return VEGAS_EINVAL;
+  DeviceGuard g(h->device);
+  VG_CHECK(cudaStreamSynchronize(h->stream()));
+  if (params) VG_CHECK(cudaMemcpy(params, h->d_flow, sizeof(float) * (size_t)nparams, cudaMemcpyDeviceToHost));
+  if (last_loss) VG_CHECK(cudaMemcpy(last_loss, h->d_flow_loss, sizeof(float), cudaMemcpyDeviceToHost));
+  return VEGAS_OK;
 }

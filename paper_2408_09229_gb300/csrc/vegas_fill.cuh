@@ -619,10 +619,23 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
         int bin[DMAX];
         T J;
         make_point<T, DMAX, EXACT>(a, rk0, rk1, cb, j0 + jl, tab, x, bin, J, st.J0);
-        const T f = integrand<ID, T, DMAX>(x, d, prm, a.np_derived, ps0, ps1, pK);
+        if constexpr (ID == kIntegrandPoints) {  // the points only, for an outside evaluation
+#pragma unroll
+          for (int k = 0; k < DMAX; ++k)
+            if (k < d) a.points_out[(j0 + jl) * d + k] = (float)x[k];
+          continue;
+        }
+        T f;
+        if constexpr (ID == kIntegrandTabulated) f = (T)a.values[j0 + jl];
+        else f = integrand<ID, T, DMAX>(x, d, prm, a.np_derived, ps0, ps1, pK);
         if (!isfinite(f)) bad = true;
         const T v = J * f;
         vals[jl] = v;
+        if constexpr (ID == kIntegrandTabulated) {
+          // training weights |J f| / n_h of every train_stride-th evaluation
+          const int64_t j = j0 + jl;
+          if (a.train_w && j % a.train_stride == 0) a.train_w[j / a.train_stride] = fabsf((float)v) * (float)invn[c];
+        }
         const T wv = v * v * invn[c];
         if (two_phase) {
           wv_s[jl] = (float)wv;
@@ -654,6 +667,7 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
     if (lane == 0) wmax[warp] = my_max;
   }
   __syncthreads();
+  if constexpr (ID == kIntegrandPoints) return;
 
   // ---- phase B (two-phase histogram): fixed-point shared integer atomics ----
   if (two_phase) {
@@ -878,6 +892,7 @@ __global__ void __launch_bounds__(kFillThreads, (sizeof(T) == 4 && DMAX <= 8) ? 
   }
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x)
     fill_tile<ID, T, DMAX, EXACT>(a, a.rk0, a.rk1, S, st, tile, ps0, ps1, pK, hist_g);
+  if constexpr (ID == kIntegrandPoints) return;
 
   // ---- epilogue: CTA partial sums, max weight, flags, histogram ----
   const double si = block_sum(st.acc_i.value(), S.red);

@@ -35,6 +35,8 @@ int dispatch_id(int integrand, F&& f) {
     case VEGAS_ROOS_ARNOLD: return f(std::integral_constant<int, VEGAS_ROOS_ARNOLD>{});
     case VEGAS_MOROKOFF_CAFLISCH: return f(std::integral_constant<int, VEGAS_MOROKOFF_CAFLISCH>{});
     case VEGAS_MAP_DENSITY: return f(std::integral_constant<int, VEGAS_MAP_DENSITY>{});
+    case kIntegrandTabulated: return f(std::integral_constant<int, kIntegrandTabulated>{});
+    case kIntegrandPoints: return f(std::integral_constant<int, kIntegrandPoints>{});
     default: return -1;
   }
 }

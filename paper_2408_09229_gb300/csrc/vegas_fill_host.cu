@@ -30,6 +30,8 @@ int derived_param_count(int integrand, int d, const double* host_params, int64_t
     case VEGAS_ROOS_ARNOLD: return np == 0 ? 0 : -1;
     case VEGAS_MOROKOFF_CAFLISCH: return np == 0 ? 2 : -1;
     case VEGAS_MAP_DENSITY: return (np % d == 0 && np / d >= 2) ? (int)np : -1;
+    case kIntegrandTabulated:
+    case kIntegrandPoints: return np == 0 ? 0 : -1;
     default: return -1;
   }
 }
@@ -314,7 +316,14 @@ int fill_impl(const vegas_geometry* g, int precision, int integrand, const doubl
               int64_t neval, uint64_t seed, int32_t iteration, uint32_t problem_id, double beta,
               const double* d_edges, const int64_t* d_offsets, float* d_ell, double* d_bins, double* d_result,
               double* d_cube_mean, double* d_cube_m2, int* d_flags, void* d_scratch, size_t scratch_bytes,
-              void* stream, cudaEvent_t ev_before, cudaEvent_t ev_after) {
+              void* stream, cudaEvent_t ev_before, cudaEvent_t ev_after, const FillExtra* extra) {
+  const bool internal = integrand == kIntegrandTabulated || integrand == kIntegrandPoints;
+  if (internal) {
+    if (precision != VEGAS_FP32 || !extra) return VEGAS_EINVAL;
+    if (integrand == kIntegrandTabulated && (!extra->values || (extra->train_w && extra->train_stride < 1)))
+      return VEGAS_EINVAL;
+    if (integrand == kIntegrandPoints && !extra->points) return VEGAS_EINVAL;
+  }
   if (!g || !g->nstrat || g->dim < 1 || g->dim > kMaxDim || g->nbins < 2 || g->nbins > kMaxBins)
     return VEGAS_EINVAL;
   if (precision != VEGAS_FP64 && precision != VEGAS_FP32) return VEGAS_EINVAL;
@@ -372,9 +381,15 @@ int fill_impl(const vegas_geometry* g, int precision, int integrand, const doubl
   a.hist_part = (double*)(sc + L.hist_part);
   a.gtable = sc + L.gtable;
   a.vexp = (const int*)(sc + L.ellmax + 4);
+  if (extra) {
+    a.values = extra->values;
+    a.points_out = extra->points;
+    a.train_w = extra->train_w;
+    a.train_stride = extra->train_stride > 0 ? extra->train_stride : 1;
+  }
   if (fill_args_axes(a, g->nstrat, precision, nprm) != VEGAS_OK) return VEGAS_EINVAL;
 
-  const bool exact = d == dmax && (dmax == 4 || dmax == 8) && a.table_smem;
+  const bool exact = d == dmax && (dmax == 4 || dmax == 8) && a.table_smem && !internal;
   const int per_sm = precision == VEGAS_FP64
                          ? (exact ? fill_occupancy_f64_exact(integrand, dmax, a.sm_total)
                                   : fill_occupancy_f64(integrand, dmax, a.sm_total))
@@ -401,6 +416,7 @@ int fill_impl(const vegas_geometry* g, int precision, int integrand, const doubl
                      : (exact ? launch_fill_f32_exact(integrand, dmax, a, grid, s) : launch_fill_f32(integrand, dmax, a, grid, s));
   if (rc != VEGAS_OK) return rc;
   if (ev_after) VG_CHECK(cudaEventRecord(ev_after, s));
+  if (integrand == kIntegrandPoints) return VEGAS_OK;  // no sums: the points are the output
   double* fix_part = (double*)(sc + L.fix_part);
   carry_scan_kernel<<<L.nfix, kCarryBlock, 0, s>>>(a);
   VG_CHECK(cudaGetLastError());

@@ -1,0 +1,263 @@
+// vegas_flow.cuh -- the learned proposal's coupling flow on the tensor cores.
+//
+// Not part of cuVegas (arXiv 2408.09229): the VEGAS+ map M of Sec. 2.1.1
+// samples x' = M(y), and the flow F maps x' to the point x = F(x') where the
+// integrand is evaluated; the estimator then integrates
+// g(x') = f(F(x')) |det dF/dx'|, whose integral equals that of f, so the
+// iteration of Algorithms 1-2 runs unchanged on g.  F is a stack of affine
+// coupling layers (RealNVP, Dinh et al., ICLR 2017) between a logit and a
+// sigmoid:
+//   z = clamp(logit(x), -Z, Z);  layer l conditions on the axes k = l (mod 2)
+//   and moves the others: s, t = MLP_l(z[A_l]) with s soft-clamped to
+//   S tanh(./S); normalising direction z[B] = z[B] e^s + t, sampling
+//   direction z[B] = (z[B] - t) e^-s; then x = sigmoid(z).  The
+//   log-determinant is sum s plus the two wrap terms log sigmoid'(z).
+// MLP_l: a_l -> 64 -> 64 -> 2 b_l with ReLU; output row 2j is s_j, 2j+1 t_j.
+//
+// GEMMs run on the tensor cores with mma.sync m16n8k16 (bf16 operands, FP32
+// accumulation).  A warp owns 16 samples.  The accumulator fragment of one
+// layer is, after ReLU and conversion, the A fragment of the next, so the
+// hidden activations never leave registers in the forward direction.
+// Weights are bf16 in shared memory, rows padded so that the fragment loads
+// of a warp hit 32 distinct banks.
+#pragma once
+#include <cuda_bf16.h>
+#include <cstdint>
+
+#include "vegas_internal.h"
+
+namespace vg {
+
+constexpr int kFlowLayers = 6;
+constexpr int kFlowHidden = 64;
+constexpr float kFlowSClamp = 2.0f;
+constexpr float kFlowZClamp = 20.0f;
+constexpr int kFlowMaxDim = 32;
+// shared-memory leading dimensions (bf16 elements): 12, 36 and 20 words
+constexpr int kLdK16 = 24, kLdK64 = 72, kLdK32 = 40;
+
+struct FlowLayer {
+  int a, b, no;                        // conditioning axes, moved axes, outputs padded to 8 (2b <= no)
+  int oW1, ob1, oW2, ob2, oW3, ob3;    // offsets in the FP32 parameter vector
+  int sW1, sb1, sW2, sb2, sW3, sb3;    // byte offsets of the layer's bf16 / f32 copies in shared memory
+};
+
+struct FlowArgs {
+  int d, nparams, smem_weights;  // bytes of the staged weights (all layers)
+  FlowLayer lay[kFlowLayers];
+  const float* params;
+};
+
+// ---- mma.sync helpers ------------------------------------------------------
+__device__ __forceinline__ void mma16816(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// B fragment of a [n][k] row-major bf16 matrix (k contiguous), tile at (n0, k0)
+__device__ __forceinline__ void load_b(const __nv_bfloat16* __restrict__ B, int ld, int n0, int k0, uint32_t& b0,
+                                       uint32_t& b1) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const __nv_bfloat16* p = B + (n0 + g) * ld + k0 + 2 * t;
+  b0 = *reinterpret_cast<const uint32_t*>(p);
+  b1 = *reinterpret_cast<const uint32_t*>(p + 8);
+}
+
+// A fragment of a [m][k] row-major bf16 matrix, tile at (m0, k0)
+__device__ __forceinline__ void load_a(const __nv_bfloat16* __restrict__ A, int ld, int m0, int k0, uint32_t (&a)[4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const __nv_bfloat16* p = A + (m0 + g) * ld + k0 + 2 * t;
+  a[0] = *reinterpret_cast<const uint32_t*>(p);
+  a[1] = *reinterpret_cast<const uint32_t*>(p + 8 * ld);
+  a[2] = *reinterpret_cast<const uint32_t*>(p + 8);
+  a[3] = *reinterpret_cast<const uint32_t*>(p + 8 * ld + 8);
+}
+
+__device__ __forceinline__ float flow_logit(float x) {
+  const float z = logf(x) - log1pf(-x);
+  return fminf(fmaxf(z, -kFlowZClamp), kFlowZClamp);
+}
+// log sigmoid'(z) = -|z| - 2 log(1 + e^-|z|)
+__device__ __forceinline__ float flow_log_sig_prime(float z) {
+  const float az = fabsf(z);
+  return -az - 2.0f * log1pf(expf(-az));
+}
+__device__ __forceinline__ float flow_sigmoid(float z) { return 1.0f / (1.0f + expf(-z)); }
+
+// Stage every layer's weights in shared memory as bf16 (biases FP32); zero
+// padding rows and columns.  Called by the whole CTA.
+__device__ inline void flow_stage_weights(const FlowArgs& fa, unsigned char* sm) {
+  for (int l = 0; l < kFlowLayers; ++l) {
+    const FlowLayer& L = fa.lay[l];
+    const float* P = fa.params;
+    __nv_bfloat16* W1 = reinterpret_cast<__nv_bfloat16*>(sm + L.sW1);
+    __nv_bfloat16* W2 = reinterpret_cast<__nv_bfloat16*>(sm + L.sW2);
+    __nv_bfloat16* W3 = reinterpret_cast<__nv_bfloat16*>(sm + L.sW3);
+    float* b1 = reinterpret_cast<float*>(sm + L.sb1);
+    float* b2 = reinterpret_cast<float*>(sm + L.sb2);
+    float* b3 = reinterpret_cast<float*>(sm + L.sb3);
+    for (int i = threadIdx.x; i < kFlowHidden * kLdK16; i += blockDim.x) {
+      const int r = i / kLdK16, c = i - r * kLdK16;
+      W1[i] = __float2bfloat16_rn(c < L.a ? P[L.oW1 + r * L.a + c] : 0.0f);
+    }
+    for (int i = threadIdx.x; i < kFlowHidden * kLdK64; i += blockDim.x) {
+      const int r = i / kLdK64, c = i - r * kLdK64;
+      W2[i] = __float2bfloat16_rn(c < kFlowHidden ? P[L.oW2 + r * kFlowHidden + c] : 0.0f);
+    }
+    for (int i = threadIdx.x; i < L.no * kLdK64; i += blockDim.x) {
+      const int r = i / kLdK64, c = i - r * kLdK64;
+      W3[i] = __float2bfloat16_rn((r < 2 * L.b && c < kFlowHidden) ? P[L.oW3 + r * kFlowHidden + c] : 0.0f);
+    }
+    for (int i = threadIdx.x; i < kFlowHidden; i += blockDim.x) {
+      b1[i] = P[L.ob1 + i];
+      b2[i] = P[L.ob2 + i];
+    }
+    for (int i = threadIdx.x; i < L.no; i += blockDim.x) b3[i] = i < 2 * L.b ? P[L.ob3 + i] : 0.0f;
+  }
+}
+
+// The conditioner of layer L on the warp's 16 rows: from the A fragments of
+// h (one k-step: a <= 16), the output fragments o[nt][4] for nt < no/8.
+// u1 and u2 stay in registers.
+template <int NT3>
+__device__ __forceinline__ void flow_mlp(const FlowLayer& L, const unsigned char* sm, const uint32_t (&ha)[4],
+                                         float (&o)[NT3][4]) {
+  const int lane = threadIdx.x & 31, t = lane & 3;
+  const __nv_bfloat16* W1 = reinterpret_cast<const __nv_bfloat16*>(sm + L.sW1);
+  const __nv_bfloat16* W2 = reinterpret_cast<const __nv_bfloat16*>(sm + L.sW2);
+  const __nv_bfloat16* W3 = reinterpret_cast<const __nv_bfloat16*>(sm + L.sW3);
+  const float* b1 = reinterpret_cast<const float*>(sm + L.sb1);
+  const float* b2 = reinterpret_cast<const float*>(sm + L.sb2);
+  const float* b3 = reinterpret_cast<const float*>(sm + L.sb3);
+  float acc[8][4];
+  // layer 1: h (16 x 16) W1^T -> 16 x 64
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const float2 bb = *reinterpret_cast<const float2*>(b1 + nt * 8 + 2 * t);
+    acc[nt][0] = bb.x; acc[nt][1] = bb.y; acc[nt][2] = bb.x; acc[nt][3] = bb.y;
+    uint32_t b0, bq;
+    load_b(W1, kLdK16, nt * 8, 0, b0, bq);
+    mma16816(acc[nt], ha[0], ha[1], ha[2], ha[3], b0, bq);
+  }
+  // ReLU, bf16: the A fragments of u1 (4 k-steps of 16)
+  uint32_t ua[4][4];
+#pragma unroll
+  for (int ks = 0; ks < 4; ++ks) {
+    ua[ks][0] = pack_bf16(fmaxf(acc[2 * ks][0], 0.0f), fmaxf(acc[2 * ks][1], 0.0f));
+    ua[ks][1] = pack_bf16(fmaxf(acc[2 * ks][2], 0.0f), fmaxf(acc[2 * ks][3], 0.0f));
+    ua[ks][2] = pack_bf16(fmaxf(acc[2 * ks + 1][0], 0.0f), fmaxf(acc[2 * ks + 1][1], 0.0f));
+    ua[ks][3] = pack_bf16(fmaxf(acc[2 * ks + 1][2], 0.0f), fmaxf(acc[2 * ks + 1][3], 0.0f));
+  }
+  // layer 2: u1 (16 x 64) W2^T -> 16 x 64
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const float2 bb = *reinterpret_cast<const float2*>(b2 + nt * 8 + 2 * t);
+    acc[nt][0] = bb.x; acc[nt][1] = bb.y; acc[nt][2] = bb.x; acc[nt][3] = bb.y;
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      uint32_t b0, bq;
+      load_b(W2, kLdK64, nt * 8, ks * 16, b0, bq);
+      mma16816(acc[nt], ua[ks][0], ua[ks][1], ua[ks][2], ua[ks][3], b0, bq);
+    }
+  }
+#pragma unroll
+  for (int ks = 0; ks < 4; ++ks) {
+    ua[ks][0] = pack_bf16(fmaxf(acc[2 * ks][0], 0.0f), fmaxf(acc[2 * ks][1], 0.0f));
+    ua[ks][1] = pack_bf16(fmaxf(acc[2 * ks][2], 0.0f), fmaxf(acc[2 * ks][3], 0.0f));
+    ua[ks][2] = pack_bf16(fmaxf(acc[2 * ks + 1][0], 0.0f), fmaxf(acc[2 * ks + 1][1], 0.0f));
+    ua[ks][3] = pack_bf16(fmaxf(acc[2 * ks + 1][2], 0.0f), fmaxf(acc[2 * ks + 1][3], 0.0f));
+  }
+  // layer 3: u2 (16 x 64) W3^T -> 16 x no
+#pragma unroll
+  for (int nt = 0; nt < NT3; ++nt) {
+    if (nt * 8 < L.no) {
+      const float2 bb = *reinterpret_cast<const float2*>(b3 + nt * 8 + 2 * t);
+      o[nt][0] = bb.x; o[nt][1] = bb.y; o[nt][2] = bb.x; o[nt][3] = bb.y;
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        uint32_t b0, bq;
+        load_b(W3, kLdK64, nt * 8, ks * 16, b0, bq);
+        mma16816(o[nt], ua[ks][0], ua[ks][1], ua[ks][2], ua[ks][3], b0, bq);
+      }
+    }
+  }
+}
+
+// One coupling layer on the warp's 16 rows held in z (row-major [16][zld]
+// FP32, shared memory).  dir = +1 normalising, -1 sampling.  ld0 / ld1
+// accumulate sum s of rows g and g+8 (g = lane / 4) over this lane's pairs.
+template <int NT3>
+__device__ __forceinline__ void flow_layer(const FlowLayer& L, int l, const unsigned char* sm, float* z, int zld,
+                                           int dir, float& ld0, float& ld1) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int par = l & 1;
+  // h = z[A]: column c of h is axis 2c + par; columns >= a are zero
+  uint32_t ha[4];
+  {
+    const int c0 = 2 * t, c1 = 2 * t + 1, c2 = 2 * t + 8, c3 = 2 * t + 9;
+    auto hv = [&](int row, int c) { return c < L.a ? z[row * zld + 2 * c + par] : 0.0f; };
+    ha[0] = pack_bf16(hv(g, c0), hv(g, c1));
+    ha[1] = pack_bf16(hv(g + 8, c0), hv(g + 8, c1));
+    ha[2] = pack_bf16(hv(g, c2), hv(g, c3));
+    ha[3] = pack_bf16(hv(g + 8, c2), hv(g + 8, c3));
+  }
+  float o[NT3][4];
+  flow_mlp<NT3>(L, sm, ha, o);
+  __syncwarp();
+  // pair m = 4 nt + t holds (s_m, t_m) for rows g and g+8; it moves axis 2m + 1 - par
+#pragma unroll
+  for (int nt = 0; nt < NT3; ++nt) {
+    const int m = 4 * nt + t;
+    if (nt * 8 < L.no && m < L.b) {
+      const int k = 2 * m + 1 - par;
+      const float s0 = kFlowSClamp * tanhf(o[nt][0] / kFlowSClamp), t0 = o[nt][1];
+      const float s1 = kFlowSClamp * tanhf(o[nt][2] / kFlowSClamp), t1 = o[nt][3];
+      float& z0 = z[g * zld + k];
+      float& z1 = z[(g + 8) * zld + k];
+      if (dir > 0) {
+        z0 = fmaf(z0, expf(s0), t0);
+        z1 = fmaf(z1, expf(s1), t1);
+        ld0 += s0;
+        ld1 += s1;
+      } else {
+        z0 = (z0 - t0) * expf(-s0);
+        z1 = (z1 - t1) * expf(-s1);
+        ld0 -= s0;
+        ld1 -= s1;
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// The whole flow on the warp's 16 rows: z holds logit(x) on entry and the
+// final z on exit; returns in lanes t == 0 the coupling part of the
+// log-determinant of rows g (r0) and g + 8 (r1).
+template <int NT3>
+__device__ __forceinline__ void flow_rows(const FlowArgs& fa, const unsigned char* sm, float* z, int zld, int dir,
+                                          float& r0, float& r1) {
+  float ld0 = 0.0f, ld1 = 0.0f;
+  for (int i = 0; i < kFlowLayers; ++i) {
+    const int l = dir > 0 ? i : kFlowLayers - 1 - i;
+    flow_layer<NT3>(fa.lay[l], l, sm, z, zld, dir, ld0, ld1);
+  }
+  ld0 += __shfl_xor_sync(0xffffffffu, ld0, 1);
+  ld0 += __shfl_xor_sync(0xffffffffu, ld0, 2);
+  ld1 += __shfl_xor_sync(0xffffffffu, ld1, 1);
+  ld1 += __shfl_xor_sync(0xffffffffu, ld1, 2);
+  r0 = ld0;
+  r1 = ld1;
+}
+
+int flow_layout(int d, FlowArgs& fa);
+
+}  // namespace vg

@@ -25,6 +25,11 @@ constexpr int kMaxDerivedParams = 8192;
 constexpr int kAllocThreads = 256;
 constexpr int kAllocItems = 16;  // cubes per thread in the allocation scan
 constexpr int64_t kMaxEval = (int64_t(1) << 31) - 1;
+// internal integrand identifiers of the fill (not in the public enumeration):
+// tabulated values f_j = values[j] by evaluation index, and a points-only
+// pass that writes the evaluation points and nothing else
+constexpr int kIntegrandTabulated = 100;
+constexpr int kIntegrandPoints = 101;
 
 // Per-tile record of a cube that crosses a tile edge: the tile's part of its
 // evaluations as (count, mean, centred second moment).
@@ -60,6 +65,10 @@ struct FillArgs {
   double* hist_part;    // [grid][d*G]
   void* gtable;         // global map table when it does not fit in shared memory
   const int* vexp;      // FP32 value scale exponent (see value_exponent), or NULL for 0
+  const float* values;  // kIntegrandTabulated: f of evaluation j
+  float* points_out;    // kIntegrandPoints: [neval][d] evaluation points
+  float* train_w;       // kIntegrandTabulated: |J f| / n_h of evaluations j = i * train_stride, or NULL
+  int train_stride;
   uint32_t nstrat[kMaxDim], magic[kMaxDim], shift[kMaxDim];
   double gz64[kMaxDim];     // N_g / s_k, rounded in FP64
   float gzb32[kMaxDim];     // RN32(N_g / s_k) 2^-b_k
@@ -82,11 +91,19 @@ int launch_fill_f32_exact(int integrand, int dmax, FillArgs& a, int grid, cudaSt
 int fill_occupancy_f64_exact(int integrand, int dmax, int smem);
 int fill_occupancy_f32_exact(int integrand, int dmax, int smem);
 
+// buffers of the internal integrands (kIntegrandTabulated, kIntegrandPoints)
+struct FillExtra {
+  const float* values;
+  float* points;
+  float* train_w;
+  int train_stride;
+};
+
 int fill_impl(const vegas_geometry* g, int precision, int integrand, const double* d_params, int64_t nparams,
               int64_t neval, uint64_t seed, int32_t iteration, uint32_t problem_id, double beta,
               const double* d_edges, const int64_t* d_offsets, float* d_ell, double* d_bins, double* d_result,
               double* d_cube_mean, double* d_cube_m2, int* d_flags, void* d_scratch, size_t scratch_bytes,
-              void* stream, cudaEvent_t ev_before, cudaEvent_t ev_after);
+              void* stream, cudaEvent_t ev_before, cudaEvent_t ev_after, const FillExtra* extra = nullptr);
 int allocate_impl(const float* d_ell, int64_t ncubes, int64_t neval, int uniform, int64_t* d_offsets,
                   void* d_scratch, size_t scratch_bytes, cudaStream_t s, const int* d_key);
 // device address of the fill's max-ell key inside its scratch area
@@ -95,6 +112,12 @@ int launch_record_combine(const double* d_result, int t, double* d_est, double* 
                           cudaStream_t s);
 
 int dmax_for(int d);
+// learned proposal (vegas_flow.cu)
+int flow_apply(int d, int direction, const float* d_params, const float* d_xin, float* d_xout, float* d_logdet,
+               int64_t n, cudaStream_t s);
+int flow_eval(int integrand, int d, const double* d_params, int64_t nparams, const float* X, const float* logdet,
+              float* values, int64_t n, cudaStream_t s);
+int flow_gather(const float* X, int d, int64_t stride, int64_t m, float* xs, cudaStream_t s);
 int fill_args_axes(FillArgs& a, const int32_t* nstrat, int precision, int nprm);
 int derived_param_count(int integrand, int d, const double* host_params_or_null, int64_t np);
 

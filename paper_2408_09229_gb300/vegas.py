@@ -97,6 +97,15 @@ def _load():
         "vegas_batch_integrate": ([P, i32, f64, ctypes.POINTER(ProblemResult), ctypes.POINTER(i32),
                                    ctypes.POINTER(ctypes.c_float)], i32),
         "vegas_batch_get": ([P, i32, i32, P, i64], i32),
+        "vegas_flow_param_count": ([i32], i64),
+        "vegas_set_flow": ([P, P, i64], i32),
+        "vegas_set_flow_training": ([P, i32, i32, i32, ctypes.c_float], i32),
+        "vegas_get_flow": ([P, P, i64, P], i32),
+        "vegas_flow_apply": ([i32, i32, P, P, P, P, i64, P], i32),
+        "vegas_flow_grad_scratch_bytes": ([i32, i64], sz),
+        "vegas_flow_grad": ([i32, P, P, P, i64, P, P, P, sz, P], i32),
+        "vegas_flow_adam": ([i64, P, P, P, P, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                             P], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -214,6 +223,26 @@ class Vegas:
     def set_state(self, blob):
         buf = ctypes.create_string_buffer(blob, len(blob))
         _check(lib.vegas_set_state(self._h, buf, len(blob)), "vegas_set_state")
+
+    def set_flow(self, params):
+        """the learned proposal's flow parameters (FP32 vector), or None to turn it off"""
+        if params is None:
+            _check(lib.vegas_set_flow(self._h, None, 0), "vegas_set_flow")
+            return
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        self._flow = p
+        _check(lib.vegas_set_flow(self._h, p.ctypes.data_as(ctypes.c_void_p), p.size), "vegas_set_flow")
+
+    def set_flow_training(self, iterations, steps_per_iteration, samples, lr=1e-3):
+        _check(lib.vegas_set_flow_training(self._h, iterations, steps_per_iteration, samples, lr),
+               "vegas_set_flow_training")
+
+    def get_flow(self):
+        n = lib.vegas_flow_param_count(self.dim)
+        p = np.zeros(n, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(lib.vegas_get_flow(self._h, p.ctypes.data_as(ctypes.c_void_p), n, ctypes.byref(loss)), "vegas_get_flow")
+        return p, loss.value
 
     def edges(self):
         e = np.zeros((self.dim, self.nbins + 1))
@@ -356,6 +385,37 @@ def refine(dim, nbins, alpha, bins, edges_in, edges_out, stream=None):
 def combine(it_est, it_sig, skip, out, stream=None):
     _check(lib.vegas_combine(_ptr(it_est), _ptr(it_sig), it_est.numel(), int(skip), _ptr(out), _stream_ptr(stream)),
            "vegas_combine")
+
+
+# ---------------------------------------------------------------------------
+# Level 4: the learned proposal's coupling flow, on torch CUDA tensors (FP32)
+# ---------------------------------------------------------------------------
+FLOW_NORMALISE, FLOW_SAMPLE = 0, 1
+
+
+def flow_param_count(dim):
+    return lib.vegas_flow_param_count(dim)
+
+
+def flow_apply(dim, direction, params, x_in, x_out, logdet, stream=None):
+    """vegas_flow_apply: x_in / x_out [n][dim], logdet [n], params [flow_param_count(dim)]"""
+    _check(lib.vegas_flow_apply(dim, direction, _ptr(params), _ptr(x_in), _ptr(x_out), _ptr(logdet),
+                                x_in.shape[0], _stream_ptr(stream)), "vegas_flow_apply")
+
+
+def flow_grad_scratch_bytes(dim, n):
+    return lib.vegas_flow_grad_scratch_bytes(dim, int(n))
+
+
+def flow_grad(dim, params, x, w, grad, loss, scratch, stream=None):
+    """vegas_flow_grad: the weighted negative log-likelihood of samples x [n][dim] with weights w [n]"""
+    _check(lib.vegas_flow_grad(dim, _ptr(params), _ptr(x), _ptr(w), x.shape[0], _ptr(grad), _ptr(loss),
+                               _ptr(scratch), scratch.numel(), _stream_ptr(stream)), "vegas_flow_grad")
+
+
+def flow_adam(params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib.vegas_flow_adam(params.numel(), _ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(step), lr, beta1,
+                               beta2, eps, _stream_ptr(stream)), "vegas_flow_adam")
 
 
 def probe_pipes():

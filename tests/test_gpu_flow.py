@@ -1,0 +1,215 @@
+"""The learned proposal's coupling flow on the GPU (vegas_flow_*), against
+the oracle (oracle/flow.py) and against its own invariants.
+
+Tolerances.  The CUDA path rounds the weights, the conditioner input and the
+hidden activations to bf16 (8 significant bits) and accumulates in FP32; the
+oracle rounds the same quantities to bf16 and computes in FP64.  The two
+then differ only where an FP32 rounding moves a value across a bf16 rounding
+boundary, which changes one hidden unit by one bf16 ulp (2^-8 relative):
+outputs agree to ~1e-5 typically and to 5e-3 at worst.  The backward pass also
+rounds the gradients of the layer outputs and hidden units to bf16, so the
+gradient of each parameter block agrees with the oracle's FP64 gradient to a
+few percent of its norm.  Checks that need no tolerance argument: the
+change of variables (Monte Carlo within 5 standard errors), the round trip,
+Adam against its definition, and that training lowers the loss.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle import flow as F  # noqa: E402
+from paper_2408_09229_gb300 import workloads as W  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def V():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2408_09229_gb300 import vegas
+    assert torch.cuda.is_available()
+    return vegas
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).cuda()
+
+
+def gpu_apply(V, d, direction, th, x):
+    xi = dev(x)
+    xo = torch.empty_like(xi)
+    ld = torch.empty(x.shape[0], dtype=torch.float32, device="cuda")
+    V.flow_apply(d, direction, dev(th), xi, xo, ld)
+    torch.cuda.synchronize()
+    return xo.cpu().numpy().astype(np.float64), ld.cpu().numpy().astype(np.float64)
+
+
+def test_param_count_matches_layout(V):
+    for d in range(2, 33):
+        assert V.flow_param_count(d) == F.param_count(d)
+    assert V.flow_param_count(1) == 0 and V.flow_param_count(33) == 0
+
+
+@pytest.mark.parametrize("d", [2, 5, 12, 16, 30])
+def test_apply_matches_oracle(V, d):
+    th = W.flow_params(d, seed=d, out_scale=0.05)
+    n = 1037  # 64 full warp chunks and a ragged one
+    x = np.random.default_rng(d).uniform(0.01, 0.99, (n, d)).astype(np.float32).astype(np.float64)
+    for direction, fn in ((V.FLOW_NORMALISE, F.normalise), (V.FLOW_SAMPLE, F.sample)):
+        gx, gl = gpu_apply(V, d, direction, th, x)
+        ox, ol = fn(th, x, d, bf16_path=True)
+        ex, el = np.abs(gx - ox), np.abs(gl - ol)
+        assert np.median(ex) < 2e-5 and ex.max() < 5e-3, (direction, np.median(ex), ex.max())
+        assert np.median(el) < 2e-4 and el.max() < 5e-2, (direction, np.median(el), el.max())
+        # the flow moves the points: the comparison is not of two identities
+        assert np.abs(ox - x).max() > 0.02
+
+
+def test_identity_flow_on_gpu(V):
+    d = 7
+    th = W.flow_params(d, seed=1, out_scale=0.0)
+    x = np.random.default_rng(0).uniform(0.001, 0.999, (500, d)).astype(np.float32).astype(np.float64)
+    gx, gl = gpu_apply(V, d, V.FLOW_SAMPLE, th, x)
+    assert np.abs(gx - x).max() < 1e-6 and np.abs(gl).max() < 1e-5
+
+
+def test_round_trip_and_logdet_sign(V):
+    d = 12
+    th = W.flow_params(d, seed=3, out_scale=0.05)
+    x = np.random.default_rng(4).uniform(0.01, 0.99, (4096, d))
+    xp, ln = gpu_apply(V, d, V.FLOW_NORMALISE, th, x)
+    xb, ls = gpu_apply(V, d, V.FLOW_SAMPLE, th, xp)
+    err = np.abs(xb - x.astype(np.float32))
+    assert np.quantile(err, 0.99) < 1e-5 and err.max() < 1e-2
+    assert np.quantile(np.abs(ls + ln), 0.99) < 1e-4
+
+
+@pytest.mark.parametrize("d", [3, 12])
+def test_change_of_variables_on_gpu(V, d):
+    """the GPU's sampling map with its own log-determinant: the integral of |det dF/dx'| over the cube is 1
+    and a Gaussian keeps its integral (Monte Carlo within 5 standard errors)"""
+    th = W.flow_params(d, seed=7, out_scale=0.05)
+    n = 1 << 22
+    xp = torch.rand((n, d), dtype=torch.float32, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    xo = torch.empty_like(xp)
+    ld = torch.empty(n, dtype=torch.float32, device="cuda")
+    V.flow_apply(d, V.FLOW_SAMPLE, dev(th), xp, xo, ld)
+    jac = torch.exp(ld.double())
+    m, s = float(jac.mean()), float(jac.std())
+    assert abs(m - 1.0) < 5 * s / math.sqrt(n) and s > 0.02
+    mu, sg = 0.45, 0.3
+    f = torch.exp(-((xo.double() - mu) ** 2).sum(dim=1) / (2 * sg * sg)) * jac
+    one = math.sqrt(math.pi / 2) * sg * (math.erf((1 - mu) / (sg * math.sqrt(2))) + math.erf(mu / (sg * math.sqrt(2))))
+    assert abs(float(f.mean()) - one ** d) < 5 * float(f.std()) / math.sqrt(n)
+
+
+@pytest.mark.parametrize("d,n", [(5, 1000), (12, 777)])
+def test_gradient_matches_oracle(V, d, n):
+    th = W.flow_params(d, seed=11 + d, out_scale=0.05)
+    rng = np.random.default_rng(d)
+    x = rng.uniform(0.02, 0.98, (n, d)).astype(np.float32).astype(np.float64)
+    w = rng.exponential(1.0, n).astype(np.float32).astype(np.float64)
+    grad = torch.zeros(th.size, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    scratch = torch.empty(V.flow_grad_scratch_bytes(d, n), dtype=torch.uint8, device="cuda")
+    V.flow_grad(d, dev(th), dev(x), dev(w), grad, loss, scratch)
+    torch.cuda.synchronize()
+    L, g = F.grad(th, x, w, d, bf16_path=True)
+    assert float(loss[0]) == pytest.approx(L, rel=2e-3, abs=2e-3)
+    gg = grad.cpu().numpy().astype(np.float64)
+    off = 0
+    for l in range(F.LAYERS):
+        for name, shape in F.layer_sizes(d, l):
+            k = int(np.prod(shape))
+            a, b = gg[off:off + k], g[off:off + k]
+            assert np.linalg.norm(a - b) <= 0.05 * np.linalg.norm(b) + 1e-6, (l, name)
+            off += k
+
+
+def test_adam_matches_definition(V):
+    rng = np.random.default_rng(2)
+    n = 10_001
+    th, g = rng.normal(size=n), rng.normal(size=n)
+    m, v = rng.normal(size=n) * 0.1, rng.uniform(0, 0.1, n)
+    tt, gt, mt, vt = dev(th), dev(g), dev(m), dev(v)
+    V.flow_adam(tt, gt, mt, vt, 7, lr=2e-3, beta1=0.9, beta2=0.99, eps=1e-6)
+    torch.cuda.synchronize()
+    want, wm, wv = F.adam(th, g, m, v, 7, lr=2e-3, beta1=0.9, beta2=0.99, eps=1e-6)
+    assert np.allclose(tt.cpu().numpy(), want, rtol=1e-5, atol=1e-6)
+    assert np.allclose(mt.cpu().numpy(), wm, rtol=1e-5, atol=1e-7)
+    assert np.allclose(vt.cpu().numpy(), wv, rtol=1e-5, atol=1e-8)
+
+
+def test_training_on_gpu_lowers_the_loss(V):
+    """GPU forward/backward and Adam on samples of a diagonal ridge in d = 2 (the oracle's training pin)"""
+    d, n = 2, 4096
+    rng = np.random.default_rng(7)
+    xs = rng.uniform(0, 1, (n, d))
+    w = np.exp(-((xs[:, 0] - xs[:, 1]) ** 2) / (2 * 0.05 ** 2))
+    th = dev(W.flow_params(d, seed=1))
+    m, v = torch.zeros_like(th), torch.zeros_like(th)
+    grad = torch.zeros_like(th)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    scratch = torch.empty(V.flow_grad_scratch_bytes(d, n), dtype=torch.uint8, device="cuda")
+    X, Wt = dev(xs), dev(w)
+    losses = []
+    for step in range(1, 201):
+        V.flow_grad(d, th, X, Wt, grad, loss, scratch)
+        V.flow_adam(th, grad, m, v, step, lr=3e-3)
+        if step in (1, 200):
+            torch.cuda.synchronize()
+            losses.append(float(loss[0]))
+    assert losses[1] < losses[0] - 0.3
+    # the oracle's loss of the GPU-trained parameters agrees
+    assert F.loss(th.cpu().numpy().astype(np.float64), xs, w, d) < losses[0] - 0.3
+
+
+# ---------------------------------------------------------------------------
+# the flow inside the VEGAS+ iteration (vegas_set_flow / vegas_set_flow_training)
+# ---------------------------------------------------------------------------
+def test_identity_flow_reproduces_plain_vegas(V):
+    """with F = identity the points, counts and weights are those of the plain FP32 form up to the FP32
+    rounding of logit / sigmoid, so every iteration agrees to ~1e-5"""
+    d, neval = 4, 200_000
+    p = W.ridge(4, 3, 0.1)
+    plain = V.Vegas(d, 50, 0, 0.5, 0.75, precision=V.FP32).integrate(W.GAUSS_SUM, p, neval, 5, seed=3)
+    v = V.Vegas(d, 50, 0, 0.5, 0.75, precision=V.FP32)
+    v.set_flow(W.flow_params(d, seed=0, out_scale=0.0))
+    r = v.integrate(W.GAUSS_SUM, p, neval, 5, seed=3)
+    assert np.allclose(r["it_est"], plain["it_est"], rtol=1e-4)
+    assert np.allclose(r["it_sig"], plain["it_sig"], rtol=1e-3)
+
+
+@pytest.mark.parametrize("name,iid,d,params", [
+    ("ridge d6", W.GAUSS_SUM, 6, W.ridge(6, 3, 0.1)),
+    ("product peak d5", W.PRODUCT_PEAK, 5, W.product_peak(5, seed=2)),
+    ("oscillatory d4", W.OSCILLATORY, 4, W.oscillatory(4, seed=1)),
+])
+def test_random_flow_keeps_the_estimate_unbiased(V, name, iid, d, params):
+    """any flow: g = f(F(x')) |det dF/dx'| has the integral of f"""
+    v = V.Vegas(d, 50, 0, 0.5, 0.75, precision=V.FP32)
+    v.set_flow(W.flow_params(d, seed=5, out_scale=0.05))
+    r = v.integrate(iid, params, 300_000, 8, seed=1)
+    exact = W.exact(iid, d, params)
+    assert r["status"] == 0
+    assert abs(r["estimate"] - exact) < 5 * r["sigma"], (r["estimate"], r["sigma"], exact)
+
+
+def test_online_training_in_the_loop(V):
+    """training between iterations lowers the flow's loss and keeps the estimate unbiased"""
+    d, neval = 4, 200_000
+    p = W.ridge(4, 3, 0.05)
+    v = V.Vegas(d, 50, 0, 0.5, 0.75, precision=V.FP32)
+    v.set_flow(W.flow_params(d, seed=2))
+    v.set_flow_training(iterations=4, steps_per_iteration=50, samples=8192, lr=2e-3)
+    v.integrate(W.GAUSS_SUM, p, neval, 1, seed=4)
+    _, loss1 = v.get_flow()
+    r = v.integrate(W.GAUSS_SUM, p, neval, 9, seed=5)
+    th, loss2 = v.get_flow()
+    assert loss2 < loss1
+    assert np.abs(th - W.flow_params(d, seed=2)).max() > 1e-3
+    assert abs(r["estimate"] - 1.0) < 5 * r["sigma"]
