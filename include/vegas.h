@@ -397,6 +397,8 @@ VEGAS_API int vegas_flow_apply(int32_t dim, int32_t direction, const float *d_pa
  * sum_i w_i, the weighted negative log-likelihood of the flow's density with
  * a uniform base (its minimiser makes that density proportional to |f|).
  * Writes d_grad [param_count] and, if not NULL, d_loss [1] (device).
+ * Weights that are negative or not finite count as 0; with no positive weight
+ * the gradient is 0 and the loss 0.
  * d_scratch holds vegas_flow_grad_scratch_bytes(dim, n) bytes.  The partial
  * gradients of blocks of 32 samples are summed in a fixed order.
  * Errors: EINVAL (dim > 16 included), ENOSPACE, ECUDA. */
@@ -414,15 +416,18 @@ VEGAS_API int vegas_flow_adam(int64_t nparams, float *d_params, const float *d_g
  * evaluates f there and integrates g(x') = f(F(x')) |det dF/dx'| (FP32 form
  * only; 2 <= dim <= 16).  NULL turns it off.  The Adam moments start at zero.
  * vegas_set_flow_training: during the next `iterations` iterations, after each
- * one, run steps_per_iteration Adam steps (learning rate lr) on every k-th
- * evaluation of that iteration, k = neval / samples, each weighted by
- * |J f| / n_h, its share of the estimate.  vegas_get_flow copies the current
+ * one, run steps_per_iteration Adam steps (learning rate lr) on minibatches of
+ * `batch` consecutive rows of a sample of that iteration: every k-th
+ * evaluation, k = neval / samples, weighted by (|J f| / n_h)^p, with |J f| /
+ * n_h its share of the estimate and p ramping linearly from temper (0 < temper
+ * <= 1; below 1 the first targets are broader than |f|) to 1 over the
+ * training iterations.  vegas_get_flow copies the current
  * parameters (nparams = the count, or params NULL) and the last training loss.
  * The checkpoint of vegas_get_state does not include the flow.
  * Errors: EINVAL, ENOMEM, ECUDA. */
 VEGAS_API int vegas_set_flow(vegas_handle h, const float *params, int64_t nparams);
 VEGAS_API int vegas_set_flow_training(vegas_handle h, int32_t iterations, int32_t steps_per_iteration,
-                                      int32_t samples, float lr);
+                                      int32_t samples, int32_t batch, float lr, float temper);
 VEGAS_API int vegas_get_flow(vegas_handle h, float *params, int64_t nparams, float *last_loss);
 
 /* ======================================================================== */

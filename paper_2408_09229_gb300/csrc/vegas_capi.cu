@@ -55,7 +55,8 @@ struct vegas_s {
   float *d_flow_m = nullptr, *d_flow_v = nullptr, *d_flow_g = nullptr, *d_flow_loss = nullptr;
   int64_t flow_np = 0;
   int flow_step = 0, flow_train_iters = 0, flow_train_steps = 0, flow_train_samples = 0, flow_trained = 0;
-  float flow_lr = 1e-3f;
+  int flow_batch = 4096;
+  float flow_lr = 1e-3f, flow_temper = 1.0f;
   float *d_X = nullptr, *d_logdet = nullptr, *d_values = nullptr;
   int64_t x_cap = 0, ld_cap = 0, val_cap = 0;
   float *d_train_x = nullptr, *d_train_w = nullptr;
@@ -347,7 +348,7 @@ extern "C" int vegas_integrate(vegas_handle h, int integrand, const double* para
       if ((rc = grow(h->d_train_x, h->tx_cap, n_train * d)) != VEGAS_OK ||
           (rc = grow(h->d_train_w, h->tw_cap, n_train)) != VEGAS_OK)
         return rc;
-      const size_t gs = vegas_flow_grad_scratch_bytes(d, n_train);
+      const size_t gs = vegas_flow_grad_scratch_bytes(d, std::min<int64_t>(n_train, h->flow_batch));
       if (gs == 0) return VEGAS_EINVAL;
       if ((rc = grow_bytes(h->d_grad_scratch, h->grad_scratch_cap, gs)) != VEGAS_OK) return rc;
     } else if (h->flow_train_iters > h->flow_trained) {
@@ -367,7 +368,7 @@ extern "C" int vegas_integrate(vegas_handle h, int integrand, const double* para
     const bool train = flow && h->flow_trained < h->flow_train_iters;
     if (flow) {
       // points x' of the VEGAS+ map, x = F(x') and |det dF/dx'|, then g = f(x) |det| tabulated by evaluation
-      vg::FillExtra ex_points{nullptr, h->d_X, nullptr, 0};
+      vg::FillExtra ex_points{nullptr, h->d_X, nullptr, 0, 1.0f};
       rc = vg::fill_impl(&geo, VEGAS_FP32, vg::kIntegrandPoints, nullptr, 0, neval, seed, (int32_t)h->iter_counter,
                          0u, h->beta, h->d_edges[h->cur], h->d_offsets, h->d_ell, h->d_bins, h->d_result, nullptr,
                          nullptr, h->d_flags, h->d_fill_scratch, h->fill_scratch_cap, s, nullptr, nullptr, &ex_points);
@@ -377,7 +378,12 @@ extern "C" int vegas_integrate(vegas_handle h, int integrand, const double* para
       if ((rc = vg::flow_eval(integrand, d, h->d_params, nparams, h->d_X, h->d_logdet, h->d_values, neval, s)) !=
           VEGAS_OK)
         return rc;
-      vg::FillExtra ex_tab{h->d_values, nullptr, train ? h->d_train_w : nullptr, (int)train_stride};
+      // the temper exponent ramps linearly to 1 over the training iterations: broad targets first
+      const float power =
+          h->flow_train_iters > 1
+              ? h->flow_temper + (1.0f - h->flow_temper) * (float)h->flow_trained / (float)(h->flow_train_iters - 1)
+              : 1.0f;
+      vg::FillExtra ex_tab{h->d_values, nullptr, train ? h->d_train_w : nullptr, (int)train_stride, power};
       rc = vg::fill_impl(&geo, VEGAS_FP32, vg::kIntegrandTabulated, nullptr, 0, neval, seed,
                          (int32_t)h->iter_counter, 0u, h->beta, h->d_edges[h->cur], h->d_offsets, h->d_ell, h->d_bins,
                          h->d_result, nullptr, nullptr, h->d_flags, h->d_fill_scratch, h->fill_scratch_cap, s, e[1],
@@ -397,9 +403,12 @@ extern "C" int vegas_integrate(vegas_handle h, int integrand, const double* para
     if (train) {
       // Adam steps on the weighted samples of this iteration (x = F(x'), weight |J f| / n_h)
       if ((rc = vg::flow_gather(h->d_X, d, train_stride, n_train, h->d_train_x, s)) != VEGAS_OK) return rc;
+      // minibatches: consecutive windows of the sample, cycling
+      const int64_t nb = std::min<int64_t>(n_train, h->flow_batch);
       for (int k = 0; k < h->flow_train_steps; ++k) {
-        rc = vegas_flow_grad(d, h->d_flow, h->d_train_x, h->d_train_w, n_train, h->d_flow_g, h->d_flow_loss,
-                             h->d_grad_scratch, h->grad_scratch_cap, s);
+        const int64_t off = ((int64_t)k * nb) % (n_train - nb + 1);
+        rc = vegas_flow_grad(d, h->d_flow, h->d_train_x + off * d, h->d_train_w + off, nb, h->d_flow_g,
+                             h->d_flow_loss, h->d_grad_scratch, h->grad_scratch_cap, s);
         if (rc != VEGAS_OK) return rc;
         rc = vegas_flow_adam(h->flow_np, h->d_flow, h->d_flow_g, h->d_flow_m, h->d_flow_v, ++h->flow_step, h->flow_lr,
                              0.9f, 0.999f, 1e-8f, s);
@@ -594,8 +603,12 @@ extern "C" int vegas_set_flow(vegas_handle h, const float* params, int64_t npara
 }
 
 extern "C" int vegas_set_flow_training(vegas_handle h, int32_t iterations, int32_t steps_per_iteration,
-                                       int32_t samples, float lr) {
-  if (!h || iterations < 0 || steps_per_iteration < 0 || samples < 0 || !(lr > 0.0f)) return VEGAS_EINVAL;
+                                       int32_t samples, int32_t batch, float lr, float temper) {
+  if (!h || iterations < 0 || steps_per_iteration < 0 || samples < 0 || batch < 1 || !(lr > 0.0f) ||
+      !(temper > 0.0f && temper <= 1.0f))
+    return VEGAS_EINVAL;
+  h->flow_batch = batch;
+  h->flow_temper = temper;
   h->flow_train_iters = iterations;
   h->flow_train_steps = steps_per_iteration;
   h->flow_train_samples = samples;

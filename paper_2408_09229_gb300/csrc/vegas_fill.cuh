@@ -632,9 +632,10 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
         const T v = J * f;
         vals[jl] = v;
         if constexpr (ID == kIntegrandTabulated) {
-          // training weights |J f| / n_h of every train_stride-th evaluation
+          // training weights (|J f| / n_h)^p of every train_stride-th evaluation
           const int64_t j = j0 + jl;
-          if (a.train_w && j % a.train_stride == 0) a.train_w[j / a.train_stride] = fabsf((float)v) * (float)invn[c];
+          if (a.train_w && j % a.train_stride == 0)
+            a.train_w[j / a.train_stride] = powf(fabsf((float)v) * (float)invn[c], a.train_power);
         }
         const T wv = v * v * invn[c];
         if (two_phase) {

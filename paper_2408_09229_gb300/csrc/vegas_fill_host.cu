@@ -386,6 +386,7 @@ int fill_impl(const vegas_geometry* g, int precision, int integrand, const doubl
     a.points_out = extra->points;
     a.train_w = extra->train_w;
     a.train_stride = extra->train_stride > 0 ? extra->train_stride : 1;
+    a.train_power = extra->train_power;
   }
   if (fill_args_axes(a, g->nstrat, precision, nprm) != VEGAS_OK) return VEGAS_EINVAL;
 

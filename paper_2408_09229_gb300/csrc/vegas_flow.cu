@@ -160,7 +160,7 @@ extern "C" int vegas_flow_apply(int32_t dim, int32_t direction, const float* d_p
 
 // ===========================================================================
 // Training: loss = - sum_i w_i log|det dN/dx(x_i)| / sum_i w_i and its
-// gradient.  A CTA of 2 warps takes 32 samples: the forward pass in the
+// gradient.  A CTA of 4 warps takes 64 samples: the forward pass in the
 // normalising direction keeps z before every layer; the backward pass
 // recomputes each layer's conditioner and runs its six GEMMs on the tensor
 // cores (bf16 operands, FP32 accumulation):
@@ -173,9 +173,9 @@ extern "C" int vegas_flow_apply(int32_t dim, int32_t direction, const float* d_p
 namespace vg {
 namespace {
 
-constexpr int kGradWarps = 2;
+constexpr int kGradWarps = 4;
 constexpr int kGradRows = 16 * kGradWarps;  // samples per CTA
-constexpr int kLdR = kGradRows + 8;         // leading dimension of sample-major (transposed) tiles: 20 words
+constexpr int kLdR = kGradRows + 8;         // leading dimension of sample-major (transposed) tiles: 36 words
 
 struct GradLayout {
   int wnat;               // natural weights of all layers (flow_stage_weights)
@@ -277,12 +277,17 @@ __global__ void __launch_bounds__(kGradWarps * 32) flow_grad_kernel(const __grid
   float* zs = at<float>(sm, G.zs);
   float* gz = at<float>(sm, G.gz);
   float* wn = at<float>(sm, G.wn);
-  const float inv = (float)(1.0 / *wsum);
+  // weights that are not finite count as 0; with no positive weight every gradient is 0
+  const double ws = *wsum;
+  const float inv = (ws > 0.0 && ws < INFINITY) ? (float)(1.0 / ws) : 0.0f;
   for (int i = tid; i < R * d; i += blockDim.x) {
     const int r = i / d, k = i - r * d;
     zs[r * zld + k] = flow_logit(r < rows ? x[(r0 + r) * d + k] : 0.5f);
   }
-  for (int r = tid; r < R; r += blockDim.x) wn[r] = r < rows ? w[r0 + r] * inv : 0.0f;
+  for (int r = tid; r < R; r += blockDim.x) {
+    const float wr = r < rows ? w[r0 + r] : 0.0f;
+    wn[r] = (isfinite(wr) && wr > 0.0f) ? wr * inv : 0.0f;
+  }
   __syncthreads();
   // ---- forward (normalising): keep z before every layer ----
   float lsum0 = 0.0f, lsum1 = 0.0f;  // sum s of this lane's pairs, rows g and g+8 of its warp
@@ -539,7 +544,10 @@ __global__ void __launch_bounds__(kGradWarps * 32) flow_grad_kernel(const __grid
 __global__ void flow_wsum_kernel(const float* __restrict__ w, int64_t n, double* out) {
   __shared__ double red[32];
   double s = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += (double)w[i];
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const float wi = w[i];
+    if (isfinite(wi) && wi > 0.0f) s += (double)wi;
+  }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();

@@ -67,8 +67,9 @@ struct FillArgs {
   const int* vexp;      // FP32 value scale exponent (see value_exponent), or NULL for 0
   const float* values;  // kIntegrandTabulated: f of evaluation j
   float* points_out;    // kIntegrandPoints: [neval][d] evaluation points
-  float* train_w;       // kIntegrandTabulated: |J f| / n_h of evaluations j = i * train_stride, or NULL
+  float* train_w;       // kIntegrandTabulated: (|J f| / n_h)^train_power of evaluations j = i * train_stride
   int train_stride;
+  float train_power;
   uint32_t nstrat[kMaxDim], magic[kMaxDim], shift[kMaxDim];
   double gz64[kMaxDim];     // N_g / s_k, rounded in FP64
   float gzb32[kMaxDim];     // RN32(N_g / s_k) 2^-b_k
@@ -97,6 +98,7 @@ struct FillExtra {
   float* points;
   float* train_w;
   int train_stride;
+  float train_power;
 };
 
 int fill_impl(const vegas_geometry* g, int precision, int integrand, const double* d_params, int64_t nparams,

@@ -172,16 +172,18 @@ def test_training_on_gpu_lowers_the_loss(V):
 # the flow inside the VEGAS+ iteration (vegas_set_flow / vegas_set_flow_training)
 # ---------------------------------------------------------------------------
 def test_identity_flow_reproduces_plain_vegas(V):
-    """with F = identity the points, counts and weights are those of the plain FP32 form up to the FP32
-    rounding of logit / sigmoid, so every iteration agrees to ~1e-5"""
+    """with F = identity the points and weights of the first iteration are those of the plain FP32 form up
+    to the FP32 rounding of logit / sigmoid (1e-6); later iterations start from allocation weights that
+    differ in their last bits, so their counts differ and they agree statistically"""
     d, neval = 4, 200_000
     p = W.ridge(4, 3, 0.1)
     plain = V.Vegas(d, 50, 0, 0.5, 0.75, precision=V.FP32).integrate(W.GAUSS_SUM, p, neval, 5, seed=3)
     v = V.Vegas(d, 50, 0, 0.5, 0.75, precision=V.FP32)
     v.set_flow(W.flow_params(d, seed=0, out_scale=0.0))
     r = v.integrate(W.GAUSS_SUM, p, neval, 5, seed=3)
-    assert np.allclose(r["it_est"], plain["it_est"], rtol=1e-4)
-    assert np.allclose(r["it_sig"], plain["it_sig"], rtol=1e-3)
+    assert r["it_est"][0] == pytest.approx(plain["it_est"][0], rel=1e-6)
+    assert r["it_sig"][0] == pytest.approx(plain["it_sig"][0], rel=1e-4)
+    assert np.all(np.abs(r["it_est"] - plain["it_est"]) < 3 * plain["it_sig"])
 
 
 @pytest.mark.parametrize("name,iid,d,params", [
@@ -205,7 +207,8 @@ def test_online_training_in_the_loop(V):
     p = W.ridge(4, 3, 0.05)
     v = V.Vegas(d, 50, 0, 0.5, 0.75, precision=V.FP32)
     v.set_flow(W.flow_params(d, seed=2))
-    v.set_flow_training(iterations=4, steps_per_iteration=50, samples=8192, lr=2e-3)
+    v.set_flow_training(iterations=4, steps_per_iteration=50, samples=8192, batch=2048, lr=2e-3, temper=0.5)
+    v.set_skip(4)  # the estimate combines the iterations after training
     v.integrate(W.GAUSS_SUM, p, neval, 1, seed=4)
     _, loss1 = v.get_flow()
     r = v.integrate(W.GAUSS_SUM, p, neval, 9, seed=5)
