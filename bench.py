@@ -329,6 +329,19 @@ def run_ours(args, rank, world):
         if rank == 0:
             print(json.dumps(fill_sweep(V, W, stream, args)))
         return
+    if args.profile_flow:
+        d, neval = 12, 10_000_000
+        v = V.Vegas(d, NBINS, 0, ALPHA, BETA, precision=V.FP32, stream=stream)
+        v.set_flow(W.flow_params(d, seed=0, out_scale=0.05))
+        prm = W.ridge(d, 4, 0.03)
+        v.integrate(W.GAUSS_SUM, prm, neval, args.warmup, seed=SEED)
+        r = v.integrate(W.GAUSS_SUM, prm, neval, args.steps, seed=SEED + 1)
+        it_ms, fill_ms = v.timings()
+        if rank == 0:
+            print(json.dumps({"profile": "learned proposal", "evals_per_s": neval * args.steps / (float(np.sum(it_ms)) / 1e3),
+                              "iteration_ms": [float(x) for x in it_ms], "fill_ms": [float(x) for x in fill_ms],
+                              "estimate": r["estimate"], "sigma": r["sigma"]}))
+        return
     if args.profile_batch:
         probs = W.batch_problems(args.profile_batch, seed=0, neval_range=(1e5, args.batch_max_neval))
         b = V.Batch(probs, NBINS, ALPHA, BETA, seed=SEED, stream=stream)
@@ -524,6 +537,8 @@ def main():
                     help="the form a --profile run times")
     ap.add_argument("--sweep", action="store_true",
                     help="fill scaling sweep of the paper's Table 4 parameters on the linear integrand")
+    ap.add_argument("--profile-flow", action="store_true",
+                    help="profiling run of the learned proposal: d = 12 ridge, 1e7 evaluations, a fixed flow")
     ap.add_argument("--profile-batch", type=int, default=0, metavar="N",
                     help="profiling run of the batched form on the first N integrals of the batched workload")
     ap.add_argument("--batch-max-neval", type=float, default=1e8,

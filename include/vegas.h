@@ -279,7 +279,9 @@ VEGAS_API int vegas_combine(const double *d_it_est, const double *d_it_sigma, in
  * problem_id = p on the same map and counts.  Sums over CTAs are taken with
  * atomic adds, so results are reproducible to FP64 rounding, not bit for bit.
  * Limits: 1 <= nproblems <= 4096; per integral 1 <= dim <= 16 and the
- * families GAUSS_SUM, PRODUCT_PEAK, OSCILLATORY; 2 <= nbins <= 256. */
+ * families GAUSS_SUM, PRODUCT_PEAK, OSCILLATORY; 2 <= nbins <= 256; an
+ * integral with more than 8 axes has at most 256 strata per axis and, for
+ * GAUSS_SUM, at most 8 peaks. */
 typedef struct vegas_batch_s *vegas_batch;
 
 typedef struct {

@@ -566,6 +566,9 @@ extern "C" int vegas_batch_create(const vegas_problem* problems, int32_t nproble
     h.dmax = dmax_for(h.d);
     h.nprm = derived_smem_count(h.iid, h.d, h.dmax, (int)q.nparams);
     if (h.nprm > kMaxDerivedParams) return VEGAS_EINVAL;
+    // integrals wider than 8 axes run the streamed point path
+    if (h.dmax >= 16 && (h.nstrat > 256 || !stream_family(h.iid, h.iid == VEGAS_GAUSS_SUM ? (int)((q.nparams - 3) / h.d) : 0)))
+      return VEGAS_EINVAL;
     h.params.assign(q.params, q.params + q.nparams);
     tiles += h.ntiles;
     blocks += h.nblocks;

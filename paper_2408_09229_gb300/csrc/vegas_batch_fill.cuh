@@ -40,33 +40,37 @@ __device__ __forceinline__ void batch_prep(const FillArgs& sa, int dmax, float* 
 }
 
 template <int ID, int DMAX>
-__device__ __forceinline__ void batch_tile_one(const FillArgs& sa, const BatchLaunch& L, const FillShared<float>& S,
+__device__ __forceinline__ void batch_tile_one(const FillArgs& sa, const BatchLaunch& L, unsigned char* smem,
                                                FillState<float>& st, int tile) {
+  // the shared-memory views are rebuilt per tile (a few adds) instead of being held across the loop
+  const FillShared<float> S = fill_shared<float>(smem, sa, true);
   const float ps0 = S.prm[0], ps1 = S.prm[1];
   const int pK = (ID == VEGAS_GAUSS_SUM) ? (int)S.prm[2] : 0;
-  fill_tile<ID, float, DMAX, false>(sa, L.rk0, L.rk1, S, st, tile, ps0, ps1, pK, nullptr);
+  // 16-axis integrals take the streamed point path (64 registers, no spills)
+  fill_tile<ID, float, DMAX, false, (DMAX >= 16)>(sa, L.rk0, L.rk1, S, st, tile, ps0, ps1, pK, nullptr);
 }
 
-__device__ __forceinline__ void batch_tile(const FillArgs& sa, int dmax, const BatchLaunch& L,
-                                           const FillShared<float>& S, FillState<float>& st, int tile) {
+__device__ __forceinline__ void batch_tile(const FillArgs& sa, int dmax, const BatchLaunch& L, unsigned char* smem,
+                                           FillState<float>& st, int tile) {
   switch (sa.iid * 4 + (dmax == 4 ? 0 : dmax == 8 ? 1 : 2)) {
-    case VEGAS_GAUSS_SUM * 4 + 0: batch_tile_one<VEGAS_GAUSS_SUM, 4>(sa, L, S, st, tile); break;
-    case VEGAS_GAUSS_SUM * 4 + 1: batch_tile_one<VEGAS_GAUSS_SUM, 8>(sa, L, S, st, tile); break;
-    case VEGAS_GAUSS_SUM * 4 + 2: batch_tile_one<VEGAS_GAUSS_SUM, 16>(sa, L, S, st, tile); break;
-    case VEGAS_PRODUCT_PEAK * 4 + 0: batch_tile_one<VEGAS_PRODUCT_PEAK, 4>(sa, L, S, st, tile); break;
-    case VEGAS_PRODUCT_PEAK * 4 + 1: batch_tile_one<VEGAS_PRODUCT_PEAK, 8>(sa, L, S, st, tile); break;
-    case VEGAS_PRODUCT_PEAK * 4 + 2: batch_tile_one<VEGAS_PRODUCT_PEAK, 16>(sa, L, S, st, tile); break;
-    case VEGAS_OSCILLATORY * 4 + 0: batch_tile_one<VEGAS_OSCILLATORY, 4>(sa, L, S, st, tile); break;
-    case VEGAS_OSCILLATORY * 4 + 1: batch_tile_one<VEGAS_OSCILLATORY, 8>(sa, L, S, st, tile); break;
-    default: batch_tile_one<VEGAS_OSCILLATORY, 16>(sa, L, S, st, tile); break;
+    case VEGAS_GAUSS_SUM * 4 + 0: batch_tile_one<VEGAS_GAUSS_SUM, 4>(sa, L, smem, st, tile); break;
+    case VEGAS_GAUSS_SUM * 4 + 1: batch_tile_one<VEGAS_GAUSS_SUM, 8>(sa, L, smem, st, tile); break;
+    case VEGAS_GAUSS_SUM * 4 + 2: batch_tile_one<VEGAS_GAUSS_SUM, 16>(sa, L, smem, st, tile); break;
+    case VEGAS_PRODUCT_PEAK * 4 + 0: batch_tile_one<VEGAS_PRODUCT_PEAK, 4>(sa, L, smem, st, tile); break;
+    case VEGAS_PRODUCT_PEAK * 4 + 1: batch_tile_one<VEGAS_PRODUCT_PEAK, 8>(sa, L, smem, st, tile); break;
+    case VEGAS_PRODUCT_PEAK * 4 + 2: batch_tile_one<VEGAS_PRODUCT_PEAK, 16>(sa, L, smem, st, tile); break;
+    case VEGAS_OSCILLATORY * 4 + 0: batch_tile_one<VEGAS_OSCILLATORY, 4>(sa, L, smem, st, tile); break;
+    case VEGAS_OSCILLATORY * 4 + 1: batch_tile_one<VEGAS_OSCILLATORY, 8>(sa, L, smem, st, tile); break;
+    default: batch_tile_one<VEGAS_OSCILLATORY, 16>(sa, L, smem, st, tile); break;
   }
 }
 
 // the CTA's share of integral p: iteration sums, largest ell, flags and the
 // map-weight histogram go to p's global accumulators
-__device__ __forceinline__ void batch_flush(const BatchLaunch& L, int p, const FillArgs& sa,
-                                            const FillShared<float>& S, const FillState<float>& st) {
+__device__ __forceinline__ void batch_flush(const BatchLaunch& L, int p, const FillArgs& sa, unsigned char* smem,
+                                            const FillState<float>& st) {
   const int tid = threadIdx.x;
+  const FillShared<float> S = fill_shared<float>(smem, sa, true);
   const double si = block_sum(st.acc_i.value(), S.red);
   const double sv = block_sum(st.acc_v.value(), S.red);
   if (tid == 0) {
@@ -96,7 +100,6 @@ __global__ void __launch_bounds__(kFillThreads, MINB) batch_fill_kernel(const __
   const int tid = threadIdx.x;
   const int total = L.act_tile[L.P];
   int cur = -1, dmax = 4;
-  FillShared<float> S;
   FillState<float> st;
   for (;;) {
     if (tid == 0) s_chunk = (int)atomicAdd(L.counter, 1u);
@@ -108,26 +111,28 @@ __global__ void __launch_bounds__(kFillThreads, MINB) batch_fill_kernel(const __
     for (int gt = (int)t0; gt < t1; ++gt) {
       const int p = batch_find(L.act_tile, L.P, gt);
       if (p != cur) {
-        if (cur >= 0) batch_flush(L, cur, sa, S, st);
+        if (cur >= 0) batch_flush(L, cur, sa, smem, st);
         // load integral p: arguments, map table, derived parameters, zeroed histogram
         const uint32_t* src = reinterpret_cast<const uint32_t*>(&L.prob[p].a);
         uint32_t* dst = reinterpret_cast<uint32_t*>(&sa);
         for (int i = tid; i < (int)(sizeof(FillArgs) / 4); i += kFillThreads) dst[i] = src[i];
         __syncthreads();
         dmax = L.prob[p].dmax;
-        S = fill_shared<float>(smem, sa, true);
-        fill_prologue<float>(sa, S, sa.d, true);
-        batch_prep(sa, dmax, S.prm);
+        {
+          const FillShared<float> S = fill_shared<float>(smem, sa, true);
+          fill_prologue<float>(sa, S, sa.d, true);
+          batch_prep(sa, dmax, S.prm);
+        }
         st = FillState<float>{};
         st.vexp = sa.vexp ? *sa.vexp : 0;
         st.J0 = ldexpf(1.0f, -st.vexp);
         cur = p;
         __syncthreads();
       }
-      batch_tile(sa, dmax, L, S, st, gt - L.act_tile[p]);
+      batch_tile(sa, dmax, L, smem, st, gt - L.act_tile[p]);
     }
   }
-  if (cur >= 0) batch_flush(L, cur, sa, S, st);
+  if (cur >= 0) batch_flush(L, cur, sa, smem, st);
 }
 
 template <int MINB>

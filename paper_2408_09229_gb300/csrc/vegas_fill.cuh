@@ -87,8 +87,12 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 
 // Number of shared-memory elements of the derived parameters.  The Gaussian
 // centres are padded to rows of DMAX so that a row loads as vectors.
+__host__ __device__ inline int gauss_kp(int K) { return (K + 3) & ~3; }  // peaks padded to 4
 __host__ __device__ inline int derived_smem_count(int integrand, int d, int dmax, int np) {
-  if (integrand == VEGAS_GAUSS_SUM) return 4 + ((np - 3) / d) * dmax;
+  if (integrand == VEGAS_GAUSS_SUM) {
+    const int K = (np - 3) / d;
+    return 4 + K * dmax + (dmax >= 16 ? dmax * gauss_kp(K) : 0);
+  }
   if (integrand == VEGAS_PRODUCT_PEAK) return 2 * dmax;
   if (integrand == VEGAS_OSCILLATORY) return 4 + dmax;
   if (integrand == VEGAS_MOROKOFF_CAFLISCH) return 4;
@@ -98,6 +102,8 @@ __host__ __device__ inline int derived_smem_count(int integrand, int d, int dmax
 
 // Turn the caller's parameters into the derived form read by vg::integrand:
 //   GAUSS_SUM         [A, c, K, 0, mu rows of DMAX]  c = -1/(2 s^2) (FP64, exp),
+//                     for DMAX >= 16 followed by the centres by axis,
+//                     [DMAX][K padded to 4], for the streamed point path
 //                                                    c = -log2(e)/(2 s^2) (FP32, exp2)
 //   PRODUCT_PEAK      [c_i^-2 (DMAX), w (DMAX)]   padded axes: c^-2 = 1, w = 0
 //   OSCILLATORY       [2 pi u, 0, 0, 0, a (DMAX)]
@@ -108,6 +114,13 @@ __device__ void prep_params(const double* __restrict__ raw, int np, int d, T* ou
   const int tid = threadIdx.x, nt = blockDim.x;
   if constexpr (ID == VEGAS_GAUSS_SUM) {
     const int K = (np - 3) / d;
+    if constexpr (DMAX >= 16) {
+      const int KP = gauss_kp(K);
+      for (int i = tid; i < DMAX * KP; i += nt) {
+        const int k = i / KP, q = i - k * KP;
+        out[4 + K * DMAX + i] = (T)((k < d && q < K) ? raw[3 + q * d + k] : 0.0);
+      }
+    }
     for (int i = tid; i < 4 + K * DMAX; i += nt) {
       double v = 0.0;
       if (i == 0) v = raw[0];
@@ -419,6 +432,154 @@ __device__ __forceinline__ void make_point(const FillArgs& a, const uint32_t* __
   }
 }
 
+// ---------------------------------------------------------------------------
+// Streamed FP32 point path for wide maps (DMAX >= 16).  The array path holds
+// the cube digits, the coordinates and the intervals of all axes in registers
+// (172 and 254 registers a thread at 16 and 32 axes).  The streamed path makes
+// the point four axes at a time (one Philox call) and folds every coordinate
+// into the integrand's running sums or products at once, so a thread holds
+// only those: it fits in 64 registers.  The cube digits come packed, 8 bits
+// an axis (every s_k <= 256), and the intervals go straight to the packed
+// words of the two-phase histogram.  Families: the Gaussian sum with at most
+// kStreamMaxPeaks peaks, and every family whose value is a sum or a product
+// over the axes.
+// ---------------------------------------------------------------------------
+constexpr int kStreamMaxPeaks = 8;
+
+__host__ __device__ inline bool stream_family(int integrand, int K) {
+  switch (integrand) {
+    case VEGAS_GAUSS_SUM: return K <= kStreamMaxPeaks;
+    case VEGAS_PRODUCT_PEAK:
+    case VEGAS_OSCILLATORY:
+    case VEGAS_LINEAR:
+    case VEGAS_COSINE:
+    case VEGAS_EXPONENTIAL:
+    case VEGAS_ROOS_ARNOLD:
+    case VEGAS_MOROKOFF_CAFLISCH:
+    case kIntegrandTabulated:
+    case kIntegrandPoints: return true;
+    default: return false;
+  }
+}
+
+// digits c_k of cube h, 8 bits each, four axes a word
+template <int DMAX>
+__device__ __forceinline__ void decode_packed(const FillArgs& a, uint32_t h, uint32_t (&cw)[DMAX / 4]) {
+  uint32_t rest = h;
+#pragma unroll
+  for (int g = 0; g < DMAX / 4; ++g) {
+    uint32_t w = 0u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = 4 * g + q;
+      if (k < a.d) {
+        const uint32_t qq = (uint32_t)(((uint64_t)rest * a.magic[k]) >> a.shift[k]);
+        w |= (rest - qq * a.nstrat[k]) << (8 * q);
+        rest = qq;
+      }
+    }
+    cw[g] = w;
+  }
+}
+
+// Point j of the cube with digits cw, its Jacobian J (from J0) and f there.
+// binw_row receives the packed intervals (4 axes a word); xout, if not NULL,
+// the coordinates.
+template <int ID, int DMAX>
+__device__ __forceinline__ float stream_point_eval(const FillArgs& a, const uint32_t* __restrict__ rk0,
+                                                   const uint32_t* __restrict__ rk1, const uint32_t (&cw)[DMAX / 4],
+                                                   int64_t j, const TabEntry<float>* __restrict__ tab,
+                                                   const float* __restrict__ prm, float s0, float s1, int K,
+                                                   float& J, uint32_t* __restrict__ binw_row,
+                                                   float* __restrict__ xout) {
+  const int d = a.d, G = a.G;
+  const uint32_t jlo = (uint32_t)j, jhi = (uint32_t)((uint64_t)j >> 32);
+  float r2[kStreamMaxPeaks];
+#pragma unroll
+  for (int q = 0; q < kStreamMaxPeaks; ++q) r2[q] = 0.0f;
+  float acc = (ID == VEGAS_OSCILLATORY) ? s0 : 0.0f;
+  float prod = 1.0f;
+  const int KP = gauss_kp(K);
+  const float* muT = prm + 4 + K * DMAX;
+  const int ng = (d + 3) >> 2;
+#pragma unroll 1
+  for (int g = 0; g < ng; ++g) {
+    const uint4 r = philox_rk(make_uint4(jlo, jhi, a.iter, (a.pid << 16) | (uint32_t)g), rk0, rk1);
+    uint32_t word = 0u;
+    float den = 1.0f;
+    uint32_t dig = 0u;
+#pragma unroll
+    for (int gg = 0; gg < DMAX / 4; ++gg)
+      if (gg == g) dig = cw[gg];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = 4 * g + q;
+      if (k < d) {
+        const uint32_t w = q == 0 ? r.x : q == 1 ? r.y : q == 2 ? r.z : r.w;
+        const uint32_t fb = a.fbits[k];
+        const float big = __uint_as_float(0x4B000000u | (((dig >> (8 * q)) & 255u) << fb) | (w >> (32 - fb)));
+        const float z = fmaf(big, a.gzb32[k], a.gzn32[k]);
+        int i = (int)z;
+        i = i < G - 1 ? i : G - 1;
+        const float dz = z - (float)i;
+        const TabEntry<float> te = tab[k * G + i];
+        const float x = fmaf(dz, te.dx, te.e);
+        J = J * te.jk;
+        word |= (uint32_t)i << (8 * q);
+        if (xout) xout[k] = x;
+        if constexpr (ID == VEGAS_GAUSS_SUM) {
+          const float4* m4 = reinterpret_cast<const float4*>(muT + k * KP);
+#pragma unroll
+          for (int p4 = 0; p4 < kStreamMaxPeaks / 4; ++p4) {
+            if (4 * p4 < KP) {
+              const float4 m = m4[p4];
+              const float e0 = x - m.x, e1 = x - m.y, e2 = x - m.z, e3 = x - m.w;
+              r2[4 * p4] = fmaf(e0, e0, r2[4 * p4]);
+              r2[4 * p4 + 1] = fmaf(e1, e1, r2[4 * p4 + 1]);
+              r2[4 * p4 + 2] = fmaf(e2, e2, r2[4 * p4 + 2]);
+              r2[4 * p4 + 3] = fmaf(e3, e3, r2[4 * p4 + 3]);
+            }
+          }
+        } else if constexpr (ID == VEGAS_PRODUCT_PEAK) {
+          const float e = x - prm[DMAX + k];
+          den *= fmaf(e, e, prm[k]);
+        } else if constexpr (ID == VEGAS_OSCILLATORY) {
+          acc = fmaf(prm[4 + k], x, acc);
+        } else if constexpr (ID == VEGAS_LINEAR) {
+          acc += x;
+        } else if constexpr (ID == VEGAS_COSINE) {
+          prod *= cosf(x);
+        } else if constexpr (ID == VEGAS_EXPONENTIAL) {
+          acc = fmaf(x, x, acc);
+        } else if constexpr (ID == VEGAS_ROOS_ARNOLD) {
+          prod *= fabsf(fmaf(4.0f, x, -2.0f));
+        } else if constexpr (ID == VEGAS_MOROKOFF_CAFLISCH) {
+          prod *= powf(x, s1);
+        }
+      }
+    }
+    if (binw_row) binw_row[g] = word;
+    if constexpr (ID == VEGAS_PRODUCT_PEAK) prod = prod / den;  // one division per four axes
+  }
+  if constexpr (ID == VEGAS_GAUSS_SUM) {
+    float sum = 0.0f;
+#pragma unroll
+    for (int q = 0; q < kStreamMaxPeaks; ++q)
+      if (q < K) sum += ex2_approx(r2[q] * s1);
+    return s0 * sum;
+  } else if constexpr (ID == VEGAS_OSCILLATORY) {
+    return cosf(acc);
+  } else if constexpr (ID == VEGAS_LINEAR) {
+    return acc;
+  } else if constexpr (ID == VEGAS_EXPONENTIAL) {
+    return expf(acc);
+  } else if constexpr (ID == VEGAS_MOROKOFF_CAFLISCH) {
+    return s0 * prod;
+  } else {  // PRODUCT_PEAK, COSINE, ROOS_ARNOLD; tabulated and points: unused
+    return prod;
+  }
+}
+
 // Shared-memory views of the fill and the per-thread running state; one tile
 // of evaluations is processed by fill_tile, which both the single-integral and
 // the batched kernels call.
@@ -525,8 +686,9 @@ __device__ __forceinline__ void fill_prologue(const FillArgs& a, const FillShare
 
 // One tile of kTile evaluations of integral a (tile index local to a).  rk0 /
 // rk1: the Philox round keys (kernel parameters, so that they are
-// constant-bank operands).
-template <int ID, typename T, int DMAX, bool EXACT>
+// constant-bank operands).  STREAM: the streamed point path (FP32, DMAX >= 16,
+// two-phase histogram, s_k <= 256).
+template <int ID, typename T, int DMAX, bool EXACT, bool STREAM = false>
 __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __restrict__ rk0,
                                           const uint32_t* __restrict__ rk1, const FillShared<T>& S,
                                           FillState<T>& st, int tile, T ps0, T ps1, int pK, double* hist_g) {
@@ -602,7 +764,42 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
   // ---- phase A: point, map, integrand, J f; map weights ----
   const int jl0 = tid * kSamplesPerThread;
   float my_max = 0.0f;
-  if (jl0 < len) {
+  if constexpr (STREAM) {
+    static_assert(sizeof(T) == 4 && DMAX >= 16, "the streamed path is FP32 and wide");
+    if (jl0 < len) {
+      int c = startc[tid];
+      int c_decoded = -1;
+      uint32_t cw[DMAX / 4];
+#pragma unroll 1
+      for (int s = 0; s < kSamplesPerThread; ++s) {
+        const int jl = jl0 + s;
+        if (jl < len) {
+          while (off_r[c + 1] <= jl) ++c;
+          if (c != c_decoded) {
+            decode_packed<DMAX>(a, (uint32_t)(h0 + c), cw);
+            c_decoded = c;
+          }
+          float J = st.J0;
+          float* xo = (ID == kIntegrandPoints) ? a.points_out + (j0 + jl) * d : nullptr;
+          float f = stream_point_eval<ID, DMAX>(a, rk0, rk1, cw, j0 + jl, tab, prm, ps0, ps1, pK, J,
+                                                binw + jl * nw, xo);
+          if constexpr (ID == kIntegrandPoints) continue;
+          if constexpr (ID == kIntegrandTabulated) f = a.values[j0 + jl];
+          if (!isfinite(f)) bad = true;
+          const float v = J * f;
+          vals[jl] = v;
+          if constexpr (ID == kIntegrandTabulated) {
+            const int64_t j = j0 + jl;
+            if (a.train_w && j % a.train_stride == 0)
+              a.train_w[j / a.train_stride] = powf(fabsf(v) * (float)invn[c], a.train_power);
+          }
+          const float wv = v * v * (float)invn[c];
+          wv_s[jl] = wv;
+          my_max = fmaxf(my_max, wv);
+        }
+      }
+    }
+  } else if (jl0 < len) {
     int c = startc[tid];
     int c_decoded = -1;
     uint32_t cb[DMAX];
@@ -872,8 +1069,8 @@ __device__ __forceinline__ Carry carry_suffix(Carry rec, bool joins) {
 // bounds checks vanish and the table reads are shared-memory loads.  The FP32
 // form with d <= 8 asks for 4 resident CTAs (at most 64 registers): measured
 // 7 % faster than 3 CTAs with more registers.  Wider or FP64 forms would spill.
-template <int ID, typename T, int DMAX, bool EXACT>
-__global__ void __launch_bounds__(kFillThreads, (sizeof(T) == 4 && DMAX <= 8) ? 4 : 1)
+template <int ID, typename T, int DMAX, bool EXACT, bool STREAM = false>
+__global__ void __launch_bounds__(kFillThreads, (sizeof(T) == 4 && (DMAX <= 8 || STREAM)) ? 4 : 1)
     fill_kernel(const __grid_constant__ FillArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, lane = tid & 31;
@@ -892,7 +1089,7 @@ __global__ void __launch_bounds__(kFillThreads, (sizeof(T) == 4 && DMAX <= 8) ? 
     st.J0 = ldexpf(1.0f, -st.vexp);
   }
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x)
-    fill_tile<ID, T, DMAX, EXACT>(a, a.rk0, a.rk1, S, st, tile, ps0, ps1, pK, hist_g);
+    fill_tile<ID, T, DMAX, EXACT, STREAM>(a, a.rk0, a.rk1, S, st, tile, ps0, ps1, pK, hist_g);
   if constexpr (ID == kIntegrandPoints) return;
 
   // ---- epilogue: CTA partial sums, max weight, flags, histogram ----

@@ -391,11 +391,16 @@ int fill_impl(const vegas_geometry* g, int precision, int integrand, const doubl
   if (fill_args_axes(a, g->nstrat, precision, nprm) != VEGAS_OK) return VEGAS_EINVAL;
 
   const bool exact = d == dmax && (dmax == 4 || dmax == 8) && a.table_smem && !internal;
+  // the streamed point path: FP32, 16 or 32 axes, two-phase histogram, at most 256 strata an axis
+  bool streamed = precision == VEGAS_FP32 && dmax >= 16 && a.hist_mode == kHistTwoPhase &&
+                stream_family(integrand, integrand == VEGAS_GAUSS_SUM ? (int)((nparams - 3) / d) : 0);
+  for (int k = 0; k < d && streamed; ++k) streamed = g->nstrat[k] <= 256;
   const int per_sm = precision == VEGAS_FP64
                          ? (exact ? fill_occupancy_f64_exact(integrand, dmax, a.sm_total)
                                   : fill_occupancy_f64(integrand, dmax, a.sm_total))
                          : (exact ? fill_occupancy_f32_exact(integrand, dmax, a.sm_total)
-                                  : fill_occupancy_f32(integrand, dmax, a.sm_total));
+                                  : streamed ? fill_occupancy_f32_stream(integrand, dmax, a.sm_total)
+                                           : fill_occupancy_f32(integrand, dmax, a.sm_total));
   if (per_sm <= 0) return VEGAS_ECUDA;
   const int grid = std::max(1, std::min(L.grid_max, per_sm * sms));
 
@@ -414,7 +419,9 @@ int fill_impl(const vegas_geometry* g, int precision, int integrand, const doubl
   if (ev_before) VG_CHECK(cudaEventRecord(ev_before, s));
   const int rc = precision == VEGAS_FP64
                      ? (exact ? launch_fill_f64_exact(integrand, dmax, a, grid, s) : launch_fill_f64(integrand, dmax, a, grid, s))
-                     : (exact ? launch_fill_f32_exact(integrand, dmax, a, grid, s) : launch_fill_f32(integrand, dmax, a, grid, s));
+                     : (exact    ? launch_fill_f32_exact(integrand, dmax, a, grid, s)
+                        : streamed ? launch_fill_f32_stream(integrand, dmax, a, grid, s)
+                                 : launch_fill_f32(integrand, dmax, a, grid, s));
   if (rc != VEGAS_OK) return rc;
   if (ev_after) VG_CHECK(cudaEventRecord(ev_after, s));
   if (integrand == kIntegrandPoints) return VEGAS_OK;  // no sums: the points are the output

@@ -91,6 +91,9 @@ int launch_fill_f64_exact(int integrand, int dmax, FillArgs& a, int grid, cudaSt
 int launch_fill_f32_exact(int integrand, int dmax, FillArgs& a, int grid, cudaStream_t s);
 int fill_occupancy_f64_exact(int integrand, int dmax, int smem);
 int fill_occupancy_f32_exact(int integrand, int dmax, int smem);
+// DMAX 16 or 32 with the streamed point path (FP32, two-phase histogram, s_k <= 256)
+int launch_fill_f32_stream(int integrand, int dmax, FillArgs& a, int grid, cudaStream_t s);
+int fill_occupancy_f32_stream(int integrand, int dmax, int smem);
 
 // buffers of the internal integrands (kIntegrandTabulated, kIntegrandPoints)
 struct FillExtra {

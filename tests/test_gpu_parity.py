@@ -213,6 +213,35 @@ def test_fill_fp32_matches_oracle(V, orc, name, d, G, ns, iid, params, neval):
 # ---------------------------------------------------------------------------
 # map refinement and combination
 # ---------------------------------------------------------------------------
+STREAM_CASES = [  # FP32 with 9..32 axes: the streamed point path (s_k <= 256, two-phase histogram)
+    ("ridge d12 K6", 12, 50, 2, W.GAUSS_SUM, W.ridge(12, 6, 0.15), 30_011),
+    ("ridge d16 K8", 16, 40, 1, W.GAUSS_SUM, W.ridge(16, 8, 0.2), 9_000),
+    ("product peak d12", 12, 50, [2, 1, 3] * 4, W.PRODUCT_PEAK, W.product_peak(12, 4), 25_000),
+    ("oscillatory d20", 20, 30, 1, W.OSCILLATORY, W.oscillatory(20, 3), 6_001),
+    ("roos-arnold d10", 10, 20, 2, W.ROOS_ARNOLD, [], 12_345),
+    ("cosine d16", 16, 8, 1, W.COSINE, [], 5_000),
+    ("exponential d9", 9, 16, 2, W.EXPONENTIAL, [], 4_097),
+    ("morokoff d11", 11, 10, 2, W.MOROKOFF_CAFLISCH, [], 8_192),
+    ("linear d32", 32, 4, 1, W.LINEAR, [], 3_333),
+]
+
+
+@pytest.mark.parametrize("name,d,G,ns,iid,params,neval", STREAM_CASES, ids=[c[0] for c in STREAM_CASES])
+def test_fill_fp32_streamed_matches_oracle(V, orc, name, d, G, ns, iid, params, neval):
+    cfg = orc.Config(d, G, ns, 0.5, 0.75, points_f32=True)
+    rng = np.random.default_rng(len(name) + 7)
+    edges = random_edges(rng, d, G)
+    ell = rng.normal(0, 5, cfg.ncubes).astype(np.float32)
+    off = orc.allocate(ell, cfg.ncubes, neval, 0.75)
+    g = gpu_fill(V, cfg, V.FP32, iid, params, neval, 1, 77, edges, off)
+    r = orc.iteration(cfg, iid, params, neval, 1, 77, edges, off)
+    assert g["flags"] == 0
+    assert g["est"] == pytest.approx(r["est"], rel=2e-5)
+    assert g["var"] == pytest.approx(r["var"], rel=2e-3)
+    assert np.allclose(g["mean"], r["mean"], rtol=0, atol=5e-4 * np.abs(r["mean"]).max())
+    assert np.allclose(g["bins"], r["bins"], rtol=0, atol=1e-3 * r["bins"].max())
+
+
 def test_fill_fp32_d30_two_diagonal_ridge(V, orc):
     """the d = 30 workload: 6 peaks on two diagonals, 2 strata on axes 0-19 and 1 on 20-29 (2^20 cubes),
     FP32 form against the oracle on the same FP32 points, map and counts"""
