@@ -126,17 +126,24 @@ def max_over_ranks(x, world, device="cuda"):
 def stress_d30(V, W, stream, rank):
     """The high-dimensional workload: d = 30, 6 Gaussian peaks (s = 0.1) on the main and the anti-diagonal,
     2 strata on axes 0-19 and 1 on axes 20-29 (2^20 cubes), 4e8 evaluations per iteration, 20 iterations,
-    FP32 form (plain VEGAS+; no learned proposal); plain FP64 timed for 2 iterations beside it."""
+    FP32 form: plain VEGAS+ and with the learned proposal (trained online over the first 10 iterations,
+    the estimate combining the last 10); plain FP64 timed for 2 iterations beside them."""
     import torch
     d, neval, nitn = 30, 400_000_000, 20
     ns = [2] * 20 + [1] * 10
     params = W.two_diagonal_ridge(d, 0.1)
     out = {"workload": "d=30, 6 peaks (s=0.1) on two diagonals, strata 2 on axes 0-19, 1 on 20-29, "
                        "4e8 evals/iteration, Ng=50, beta=0.75, alpha=0.5"}
-    for pname, prec, its in (("fp32_form", V.FP32, nitn), ("plain_fp64", V.FP64, 2)):
+    for pname, prec, its in (("fp32_form", V.FP32, nitn), ("learned_proposal", V.FP32, nitn), ("plain_fp64", V.FP64, 2)):
         v = V.Vegas(d, NBINS, 0, ALPHA, BETA, precision=prec, nstrat_axes=ns, stream=stream)
+        if pname == "learned_proposal":
+            v.set_flow(W.flow_params(d, seed=0))
         v.integrate(W.GAUSS_SUM, params, neval, 1, seed=5)  # sizes the buffers outside the clock
         v.reset_map()
+        if pname == "learned_proposal":
+            v.set_flow(W.flow_params(d, seed=0))  # untrained again: the sizing call above ran no training
+            v.set_flow_training(**FLOW_TRAIN)
+            v.set_skip(FLOW_TRAIN["iterations"])
         torch.cuda.synchronize()
         r = v.integrate(W.GAUSS_SUM, params, neval, its, seed=SEED + rank)
         it_ms, fill_ms = v.timings()
@@ -328,6 +335,17 @@ def run_ours(args, rank, world):
     if args.sweep:
         if rank == 0:
             print(json.dumps(fill_sweep(V, W, stream, args)))
+        return
+    if args.profile_stress:
+        d, neval = 30, int(args.profile_stress)
+        v = V.Vegas(d, NBINS, 0, ALPHA, BETA, precision=V.FP32, nstrat_axes=[2] * 20 + [1] * 10, stream=stream)
+        prm = W.two_diagonal_ridge(d, 0.1)
+        v.integrate(W.GAUSS_SUM, prm, neval, args.warmup, seed=SEED)
+        r = v.integrate(W.GAUSS_SUM, prm, neval, args.steps, seed=SEED + 1)
+        it_ms, fill_ms = v.timings()
+        if rank == 0:
+            print(json.dumps({"profile": "d30 stress", "evals_per_s": neval * args.steps / (float(np.sum(it_ms)) / 1e3),
+                              "iteration_ms": [float(x) for x in it_ms], "fill_ms": [float(x) for x in fill_ms]}))
         return
     if args.profile_flow:
         d, neval = 12, 10_000_000
@@ -537,6 +555,8 @@ def main():
                     help="the form a --profile run times")
     ap.add_argument("--sweep", action="store_true",
                     help="fill scaling sweep of the paper's Table 4 parameters on the linear integrand")
+    ap.add_argument("--profile-stress", type=float, default=0.0, metavar="NEVAL",
+                    help="profiling run of the d = 30 workload (FP32 form) at NEVAL evaluations per iteration")
     ap.add_argument("--profile-flow", action="store_true",
                     help="profiling run of the learned proposal: d = 12 ridge, 1e7 evaluations, a fixed flow")
     ap.add_argument("--profile-batch", type=int, default=0, metavar="N",

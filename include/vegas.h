@@ -380,8 +380,7 @@ VEGAS_API int vegas_batch_get(vegas_batch b, int32_t problem, int32_t what, void
  * Parameters: one FP32 vector of vegas_flow_param_count(dim) values; per layer
  * l = 0..5 in order W1 [64][a_l], b1 [64], W2 [64][64], b2 [64],
  * W3 [2 b_l][64], b3 [2 b_l], row-major, with a_l = ceil(d/2) for even l and
- * floor(d/2) for odd l, b_l = d - a_l.  2 <= dim <= 32 (the training entry
- * point: dim <= 16). */
+ * floor(d/2) for odd l, b_l = d - a_l.  2 <= dim <= 32. */
 enum vegas_flow_direction {
   VEGAS_FLOW_NORMALISE = 0, /* x -> x' = F^-1(x), log|det dF^-1/dx|  */
   VEGAS_FLOW_SAMPLE = 1     /* x' -> x = F(x'),   log|det dF/dx'|   */
@@ -403,7 +402,7 @@ VEGAS_API int vegas_flow_apply(int32_t dim, int32_t direction, const float *d_pa
  * the gradient is 0 and the loss 0.
  * d_scratch holds vegas_flow_grad_scratch_bytes(dim, n) bytes.  The partial
  * gradients of blocks of 32 samples are summed in a fixed order.
- * Errors: EINVAL (dim > 16 included), ENOSPACE, ECUDA. */
+ * Errors: EINVAL, ENOSPACE, ECUDA. */
 VEGAS_API size_t vegas_flow_grad_scratch_bytes(int32_t dim, int64_t n);
 VEGAS_API int vegas_flow_grad(int32_t dim, const float *d_params, const float *d_x, const float *d_w, int64_t n,
                               float *d_grad, float *d_loss, void *d_scratch, size_t scratch_bytes, void *stream);
@@ -416,7 +415,7 @@ VEGAS_API int vegas_flow_adam(int64_t nparams, float *d_params, const float *d_g
  * vegas_flow_param_count(dim) values) turns it on: every later iteration of
  * vegas_integrate draws the VEGAS+ points x', maps them to x = F(x'),
  * evaluates f there and integrates g(x') = f(F(x')) |det dF/dx'| (FP32 form
- * only; 2 <= dim <= 16).  NULL turns it off.  The Adam moments start at zero.
+ * only; 2 <= dim <= 32).  NULL turns it off.  The Adam moments start at zero.
  * vegas_set_flow_training: during the next `iterations` iterations, after each
  * one, run steps_per_iteration Adam steps (learning rate lr) on minibatches of
  * `batch` consecutive rows of a sample of that iteration: every k-th

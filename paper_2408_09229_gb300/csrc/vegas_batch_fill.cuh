@@ -84,9 +84,15 @@ __device__ __forceinline__ void batch_flush(const BatchLaunch& L, int p, const F
   double* bins = L.prob[p].bins;
   const int dG = sa.d * sa.G;
   for (int b = tid; b < dG; b += kFillThreads) {
-    ff acc = S.hist_acc[b];
-    if (st.inv_scale > 0.0f) acc = ff_add(acc, __fmul_rn((float)S.hist_u[b], st.inv_scale));
-    const double v = ff_to_double(acc);
+    const float pend = st.inv_scale > 0.0f ? __fmul_rn((float)S.hist_u[b], st.inv_scale) : 0.0f;
+    double v;
+    if (sa.acc32) {
+      v = (double)S.hist_accf[b] + (double)pend;
+    } else {
+      ff acc = S.hist_acc[b];
+      if (st.inv_scale > 0.0f) acc = ff_add(acc, pend);
+      v = ff_to_double(acc);
+    }
     if (v != 0.0) atomicAdd(bins + b, ldexp(v, 2 * st.vexp));
   }
   __syncthreads();

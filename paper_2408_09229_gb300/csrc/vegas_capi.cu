@@ -583,7 +583,7 @@ extern "C" int vegas_set_flow(vegas_handle h, const float* params, int64_t npara
     h->flow_np = 0;
     return VEGAS_OK;
   }
-  if (h->dim < 2 || h->dim > 16 || nparams != vegas_flow_param_count(h->dim)) return VEGAS_EINVAL;
+  if (h->dim < 2 || h->dim > 32 || nparams != vegas_flow_param_count(h->dim)) return VEGAS_EINVAL;
   if (!h->d_flow) {
     const size_t b = sizeof(float) * (size_t)nparams;
     if (cudaMalloc((void**)&h->d_flow, b) != cudaSuccess || cudaMalloc((void**)&h->d_flow_m, b) != cudaSuccess ||

@@ -446,6 +446,17 @@ __device__ __forceinline__ void make_point(const FillArgs& a, const uint32_t* __
 // ---------------------------------------------------------------------------
 constexpr int kStreamMaxPeaks = 8;
 
+// Slot of tile evaluation jl in the per-evaluation arrays written by one
+// thread and read back by the same thread (map weights, packed intervals).
+// Thread t owns evaluations 4t..4t+3, so storing them at jl would put the
+// lanes of a warp 4 (or 4 * words) apart and make them collide on a few
+// shared-memory banks; slot (jl mod 4) * 256 + jl / 4 puts them on
+// consecutive words.  The packed intervals add word w * kTile.
+__device__ __forceinline__ int tix(int jl) {
+  static_assert(kSamplesPerThread == 4 && kFillThreads == 256, "slot layout");
+  return ((jl & 3) << 8) | (jl >> 2);
+}
+
 __host__ __device__ inline bool stream_family(int integrand, int K) {
   switch (integrand) {
     case VEGAS_GAUSS_SUM: return K <= kStreamMaxPeaks;
@@ -483,14 +494,15 @@ __device__ __forceinline__ void decode_packed(const FillArgs& a, uint32_t h, uin
 }
 
 // Point j of the cube with digits cw, its Jacobian J (from J0) and f there.
-// binw_row receives the packed intervals (4 axes a word); xout, if not NULL,
+// binw_col receives the packed intervals (4 or 2 axes a word, word w at
+// binw_col[w * kTile]); xout, if not NULL,
 // the coordinates.
 template <int ID, int DMAX>
 __device__ __forceinline__ float stream_point_eval(const FillArgs& a, const uint32_t* __restrict__ rk0,
                                                    const uint32_t* __restrict__ rk1, const uint32_t (&cw)[DMAX / 4],
                                                    int64_t j, const TabEntry<float>* __restrict__ tab,
                                                    const float* __restrict__ prm, float s0, float s1, int K,
-                                                   float& J, uint32_t* __restrict__ binw_row,
+                                                   float& J, uint32_t* __restrict__ binw_col,
                                                    float* __restrict__ xout) {
   const int d = a.d, G = a.G;
   const uint32_t jlo = (uint32_t)j, jhi = (uint32_t)((uint64_t)j >> 32);
@@ -505,7 +517,7 @@ __device__ __forceinline__ float stream_point_eval(const FillArgs& a, const uint
 #pragma unroll 1
   for (int g = 0; g < ng; ++g) {
     const uint4 r = philox_rk(make_uint4(jlo, jhi, a.iter, (a.pid << 16) | (uint32_t)g), rk0, rk1);
-    uint32_t word = 0u;
+    uint32_t word = 0u, w16a = 0u, w16b = 0u;
     float den = 1.0f;
     uint32_t dig = 0u;
 #pragma unroll
@@ -526,6 +538,8 @@ __device__ __forceinline__ float stream_point_eval(const FillArgs& a, const uint
         const float x = fmaf(dz, te.dx, te.e);
         J = J * te.jk;
         word |= (uint32_t)i << (8 * q);
+        if (q < 2) w16a |= (uint32_t)i << (16 * q);
+        else w16b |= (uint32_t)i << (16 * (q - 2));
         if (xout) xout[k] = x;
         if constexpr (ID == VEGAS_GAUSS_SUM) {
           const float4* m4 = reinterpret_cast<const float4*>(muT + k * KP);
@@ -558,7 +572,14 @@ __device__ __forceinline__ float stream_point_eval(const FillArgs& a, const uint
         }
       }
     }
-    if (binw_row) binw_row[g] = word;
+    if (binw_col) {
+      if (a.bin_shift == 3) {
+        binw_col[g * kTile] = word;
+      } else {
+        binw_col[2 * g * kTile] = w16a;
+        if (4 * g + 2 < d) binw_col[(2 * g + 1) * kTile] = w16b;
+      }
+    }
     if constexpr (ID == VEGAS_PRODUCT_PEAK) prod = prod / den;  // one division per four axes
   }
   if constexpr (ID == VEGAS_GAUSS_SUM) {
@@ -588,8 +609,9 @@ struct FillShared {
   TabEntry<T>* tab;
   T* hist_s;          // direct mode: shared histogram of T
   uint32_t* hist_u;   // two-phase: fixed-point tile histogram
-  ff* hist_acc;       // two-phase: float-float CTA histogram
-  uint32_t* binw;     // two-phase: intervals of an evaluation, 4 per word
+  ff* hist_acc;       // two-phase: float-float CTA histogram (acc32 == 0)
+  float* hist_accf;   // two-phase: FP32 CTA histogram (acc32 == 1), the same bytes
+  uint32_t* binw;     // two-phase: intervals of an evaluation, 4 or 2 per word
   float* wv_s;        // two-phase: map weight of every evaluation
   T* prm;
   int* off_r;         // cube offsets relative to the tile, clamped
@@ -609,6 +631,7 @@ __device__ __forceinline__ FillShared<T> fill_shared(unsigned char* smem, const 
   S.hist_s = (T*)(smem + a.sm_hist);
   S.hist_u = (uint32_t*)(smem + a.sm_hist);
   S.hist_acc = (ff*)(smem + a.sm_hacc);
+  S.hist_accf = (float*)(smem + a.sm_hacc);
   S.binw = (uint32_t*)(smem + a.sm_bins);
   S.wv_s = (float*)(smem + a.sm_wv);
   S.prm = (T*)(smem + a.sm_params);
@@ -680,7 +703,8 @@ __device__ __forceinline__ void fill_prologue(const FillArgs& a, const FillShare
   if (a.hist_mode == kHistTwoPhase)
     for (int b = tid; b < dG; b += kFillThreads) {
       S.hist_u[b] = 0u;
-      S.hist_acc[b] = ff{0.0f, 0.0f};
+      if (a.acc32) S.hist_accf[b] = 0.0f;
+      else S.hist_acc[b] = ff{0.0f, 0.0f};
     }
 }
 
@@ -695,7 +719,9 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int d = EXACT ? DMAX : a.d, G = a.G, dG = d * a.G;
   const bool two_phase = a.hist_mode == kHistTwoPhase;
-  const int nw = (d + 3) >> 2;
+  // intervals per packed word: 4 (8 bits) or 2 (16 bits); the exact-d path runs with N_g <= 256 only
+  const int bpw = EXACT ? 4 : (32 >> a.bin_shift);
+  const int nw = (d + bpw - 1) / bpw;
   TabEntry<T>* tab = S.tab;
   T* hist_s = S.hist_s;
   uint32_t* hist_u = S.hist_u;
@@ -725,7 +751,8 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
     for (int b = tid; b < dG; b += kFillThreads) {
       const uint32_t q = hist_u[b];
       if (q) {
-        hist_acc[b] = ff_add(hist_acc[b], __fmul_rn((float)q, inv_scale));
+        if (a.acc32) S.hist_accf[b] += __fmul_rn((float)q, inv_scale);
+        else hist_acc[b] = ff_add(hist_acc[b], __fmul_rn((float)q, inv_scale));
         hist_u[b] = 0u;
       }
     }
@@ -782,7 +809,7 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
           float J = st.J0;
           float* xo = (ID == kIntegrandPoints) ? a.points_out + (j0 + jl) * d : nullptr;
           float f = stream_point_eval<ID, DMAX>(a, rk0, rk1, cw, j0 + jl, tab, prm, ps0, ps1, pK, J,
-                                                binw + jl * nw, xo);
+                                                binw + tix(jl), xo);
           if constexpr (ID == kIntegrandPoints) continue;
           if constexpr (ID == kIntegrandTabulated) f = a.values[j0 + jl];
           if (!isfinite(f)) bad = true;
@@ -794,7 +821,7 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
               a.train_w[j / a.train_stride] = powf(fabsf(v) * (float)invn[c], a.train_power);
           }
           const float wv = v * v * (float)invn[c];
-          wv_s[jl] = wv;
+          wv_s[tix(jl)] = wv;
           my_max = fmaxf(my_max, wv);
         }
       }
@@ -836,16 +863,27 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
         }
         const T wv = v * v * invn[c];
         if (two_phase) {
-          wv_s[jl] = (float)wv;
+          wv_s[tix(jl)] = (float)wv;
           my_max = fmaxf(my_max, (float)wv);
+          if (bpw == 4) {
 #pragma unroll
-          for (int w = 0; w < (DMAX + 3) / 4; ++w) {
-            if (4 * w < d) {
-              uint32_t word = 0u;
+            for (int w = 0; w < (DMAX + 3) / 4; ++w) {
+              if (4 * w < d) {
+                uint32_t word = 0u;
 #pragma unroll
-              for (int q = 0; q < 4; ++q)
-                if (4 * w + q < DMAX) word |= (uint32_t)bin[4 * w + q] << (8 * q);
-              binw[jl * nw + w] = word;
+                for (int q = 0; q < 4; ++q)
+                  if (4 * w + q < DMAX) word |= (uint32_t)bin[4 * w + q] << (8 * q);
+                binw[w * kTile + tix(jl)] = word;
+              }
+            }
+          } else {
+#pragma unroll
+            for (int w = 0; w < (DMAX + 1) / 2; ++w) {
+              if (2 * w < d) {
+                uint32_t word = (uint32_t)bin[2 * w];
+                if (2 * w + 1 < DMAX) word |= (uint32_t)bin[2 * w + 1] << 16;
+                binw[w * kTile + tix(jl)] = word;
+              }
             }
           }
         } else {
@@ -886,14 +924,23 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
         for (int s = 0; s < kSamplesPerThread; ++s) {
           const int jl = jl0 + s;
           if (jl < len) {
-            const uint32_t q = (uint32_t)__float2uint_rn(wv_s[jl] * scale);
+            const uint32_t q = (uint32_t)__float2uint_rn(wv_s[tix(jl)] * scale);
             if (q) {
-              for (int w = 0; w < nw; ++w) {
-                const uint32_t word = binw[jl * nw + w];
-                const int kk = 4 * w;
+              if (bpw == 4) {
+                for (int w = 0; w < nw; ++w) {
+                  const uint32_t word = binw[w * kTile + tix(jl)];
+                  const int kk = 4 * w;
 #pragma unroll
-                for (int b = 0; b < 4; ++b)
-                  if (kk + b < d) atomicAdd(hist_u + (kk + b) * G + ((word >> (8 * b)) & 255u), q);
+                  for (int b = 0; b < 4; ++b)
+                    if (kk + b < d) atomicAdd(hist_u + (kk + b) * G + ((word >> (8 * b)) & 255u), q);
+                }
+              } else {
+                for (int w = 0; w < nw; ++w) {
+                  const uint32_t word = binw[w * kTile + tix(jl)];
+                  const int kk = 2 * w;
+                  atomicAdd(hist_u + kk * G + (word & 0xFFFFu), q);
+                  if (kk + 1 < d) atomicAdd(hist_u + (kk + 1) * G + (word >> 16), q);
+                }
               }
             }
           }
@@ -1107,9 +1154,14 @@ __global__ void __launch_bounds__(kFillThreads, (sizeof(T) == 4 && (DMAX <= 8 ||
     for (int b = tid; b < dG; b += kFillThreads) hist_g[b] = (double)S.hist_s[b];
   if (a.hist_mode == kHistTwoPhase) {
     for (int b = tid; b < dG; b += kFillThreads) {
-      ff acc = S.hist_acc[b];
-      if (st.inv_scale > 0.0f) acc = ff_add(acc, __fmul_rn((float)S.hist_u[b], st.inv_scale));
-      hist_g[b] = ff_to_double(acc);
+      const float pend = st.inv_scale > 0.0f ? __fmul_rn((float)S.hist_u[b], st.inv_scale) : 0.0f;
+      if (a.acc32) {
+        hist_g[b] = (double)S.hist_accf[b] + (double)pend;
+      } else {
+        ff acc = S.hist_acc[b];
+        if (st.inv_scale > 0.0f) acc = ff_add(acc, pend);
+        hist_g[b] = ff_to_double(acc);
+      }
     }
   }
 }

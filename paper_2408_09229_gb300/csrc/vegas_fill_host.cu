@@ -93,14 +93,28 @@ int smem_layout(FillArgs& a, size_t tsz, int nprm, bool fp32) {
                       align_up(64 + 8 * 32);
   const size_t budget = 160 * 1024;
   const size_t table = align_up((size_t)dG * 4 * tsz);
-  const size_t bin_words = (size_t)kTile * 4 * ((a.d + 3) / 4);
-  const size_t two_phase = align_up((size_t)dG * 4) + align_up((size_t)dG * 8) + align_up(bin_words) +
-                           align_up(sizeof(float) * kTile);
+  // two-phase: interval indices packed 8 bits (N_g <= 256) or 16 bits wide
+  a.bin_shift = a.G <= 256 ? 3 : 4;
+  const int per_word = 32 >> a.bin_shift;
+  const size_t bin_words = (size_t)kTile * 4 * ((a.d + per_word - 1) / per_word);
+  const size_t two_phase_ff = align_up((size_t)dG * 4) + align_up((size_t)dG * 8) + align_up(bin_words) +
+                              align_up(sizeof(float) * kTile);
+  const size_t two_phase_32 = align_up((size_t)dG * 4) + align_up((size_t)dG * 4) + align_up(bin_words) +
+                              align_up(sizeof(float) * kTile);
   const size_t shared_hist = align_up((size_t)dG * tsz);
   size_t hist;
-  if (fp32 && a.G <= 256 && base + two_phase <= budget) {
+  a.acc32 = 0;
+  // the two-phase form folds all d N_g intervals of the CTA histogram once per
+  // tile (kTile evaluations): measured faster than shared FP32 atomics for
+  // N_g <= 256 and for d N_g <= 2048, slower beyond (d = 8, N_g = 1024: 2.3x)
+  const bool two_phase_ok = fp32 && (a.G <= 256 || dG <= 2048);
+  if (two_phase_ok && base + two_phase_ff <= budget) {
     a.hist_mode = kHistTwoPhase;
-    hist = two_phase;
+    hist = two_phase_ff;
+  } else if (two_phase_ok && base + two_phase_32 <= budget) {
+    a.hist_mode = kHistTwoPhase;
+    a.acc32 = 1;
+    hist = two_phase_32;
   } else if (base + shared_hist <= budget) {
     a.hist_mode = kHistShared;
     hist = shared_hist;
@@ -114,7 +128,7 @@ int smem_layout(FillArgs& a, size_t tsz, int nprm, bool fp32) {
   a.sm_hist = (int)off;
   if (a.hist_mode == kHistTwoPhase) {
     off += align_up((size_t)dG * 4);
-    a.sm_hacc = (int)off; off += align_up((size_t)dG * 8);
+    a.sm_hacc = (int)off; off += align_up((size_t)dG * (a.acc32 ? 4 : 8));
     a.sm_bins = (int)off; off += align_up(bin_words);
     a.sm_wv = (int)off;   off += align_up(sizeof(float) * kTile);
   } else {
@@ -390,7 +404,7 @@ int fill_impl(const vegas_geometry* g, int precision, int integrand, const doubl
   }
   if (fill_args_axes(a, g->nstrat, precision, nprm) != VEGAS_OK) return VEGAS_EINVAL;
 
-  const bool exact = d == dmax && (dmax == 4 || dmax == 8) && a.table_smem && !internal;
+  const bool exact = d == dmax && (dmax == 4 || dmax == 8) && a.table_smem && !internal && G <= 256;
   // the streamed point path: FP32, 16 or 32 axes, two-phase histogram, at most 256 strata an axis
   bool streamed = precision == VEGAS_FP32 && dmax >= 16 && a.hist_mode == kHistTwoPhase &&
                 stream_family(integrand, integrand == VEGAS_GAUSS_SUM ? (int)((nparams - 3) / d) : 0);

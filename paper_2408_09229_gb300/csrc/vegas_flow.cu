@@ -160,7 +160,8 @@ extern "C" int vegas_flow_apply(int32_t dim, int32_t direction, const float* d_p
 
 // ===========================================================================
 // Training: loss = - sum_i w_i log|det dN/dx(x_i)| / sum_i w_i and its
-// gradient.  A CTA of 4 warps takes 64 samples: the forward pass in the
+// gradient.  A CTA of 4 warps takes 64 samples (2 warps and 32 samples above
+// 16 axes, for shared memory): the forward pass in the
 // normalising direction keeps z before every layer; the backward pass
 // recomputes each layer's conditioner and runs its six GEMMs on the tensor
 // cores (bf16 operands, FP32 accumulation):
@@ -173,9 +174,10 @@ extern "C" int vegas_flow_apply(int32_t dim, int32_t direction, const float* d_p
 namespace vg {
 namespace {
 
-constexpr int kGradWarps = 4;
-constexpr int kGradRows = 16 * kGradWarps;  // samples per CTA
-constexpr int kLdR = kGradRows + 8;         // leading dimension of sample-major (transposed) tiles: 36 words
+// W warps a CTA, 16 W samples; W = 4 up to 16 axes, 2 above (shared memory)
+__host__ __device__ constexpr int grad_rows(int W) { return 16 * W; }
+__host__ __device__ constexpr int grad_ldr(int W) { return 16 * W + 8; }  // sample-major tiles: 20 or 36 words
+inline int grad_warps(int d) { return d <= 16 ? 4 : 2; }
 
 struct GradLayout {
   int wnat;               // natural weights of all layers (flow_stage_weights)
@@ -185,13 +187,14 @@ struct GradLayout {
   int wn;                 // [R] f32 normalised weights
   int H, HT, U1, U1T, U2, U2T, GO, GOT;
   int bias;               // [64 + 64 + 32] f32 bias-gradient accumulators
-  int red;                // [kGradWarps] f32
+  int red;                // [W] f32
   int total;
   int ldo;                // leading dimension of GO (no padded to 16 or 32, + 8)
 };
 
-GradLayout grad_layout(const FlowArgs& fa) {
+GradLayout grad_layout(const FlowArgs& fa, int W) {
   GradLayout G{};
+  const int kGradRows = grad_rows(W), kLdR = grad_ldr(W);
   const int zld = flow_zld(fa.d);
   int nomax = 8;
   for (int l = 0; l < kFlowLayers; ++l) nomax = std::max(nomax, fa.lay[l].no);
@@ -219,7 +222,7 @@ GradLayout grad_layout(const FlowArgs& fa) {
   G.GO = take(sizeof(__nv_bfloat16) * kGradRows * G.ldo);
   G.GOT = take(sizeof(__nv_bfloat16) * 32 * kLdR);
   G.bias = take(sizeof(float) * (64 + 64 + 32));
-  G.red = take(sizeof(float) * kGradWarps);
+  G.red = take(sizeof(float) * W);
   G.total = (int)o;
   return G;
 }
@@ -232,12 +235,12 @@ __device__ __forceinline__ T* at(unsigned char* sm, int off) {
 // C[M x N] = A[M x K] B^T with A [M][lda] and B [N][ldb] bf16 row-major (K
 // contiguous); the 16 x 8 tiles are dealt to the CTA's warps; epi(row, col,
 // v0, v1) receives each thread's pairs (col, col + 1).
-template <typename Epi>
+template <int W, typename Epi>
 __device__ __forceinline__ void cta_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M,
                                          int N, int K, Epi&& epi) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const int mt = M / 16, nt = N / 8;
-  for (int tile = warp; tile < mt * nt; tile += kGradWarps) {
+  for (int tile = warp; tile < mt * nt; tile += W) {
     const int m0 = (tile / nt) * 16, n0 = (tile % nt) * 8;
     float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     for (int k0 = 0; k0 < K; k0 += 16) {
@@ -261,7 +264,8 @@ __device__ __forceinline__ float sum_over_g(float v) {
 
 __device__ __forceinline__ void st_bf16(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 
-__global__ void __launch_bounds__(kGradWarps * 32) flow_grad_kernel(const __grid_constant__ FlowArgs fa,
+template <int W>
+__global__ void __launch_bounds__(W * 32) flow_grad_kernel(const __grid_constant__ FlowArgs fa,
                                                                    GradLayout G, const float* __restrict__ x,
                                                                    const float* __restrict__ w,
                                                                    const double* __restrict__ wsum, int64_t n,
@@ -269,7 +273,8 @@ __global__ void __launch_bounds__(kGradWarps * 32) flow_grad_kernel(const __grid
                                                                    float* __restrict__ lpart) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-  const int d = fa.d, zld = flow_zld(d), R = kGradRows;
+  constexpr int R = grad_rows(W), kLdR = grad_ldr(W);
+  const int d = fa.d, zld = flow_zld(d);
   const int64_t r0 = (int64_t)blockIdx.x * R;
   const int rows = (int)min((int64_t)R, n - r0);
   unsigned char* wsm = sm + G.wnat;
@@ -331,7 +336,7 @@ __global__ void __launch_bounds__(kGradWarps * 32) flow_grad_kernel(const __grid
     __syncthreads();
     if (tid == 0) {
       float s = 0.0f;
-      for (int k = 0; k < kGradWarps; ++k) s += red[k];
+      for (int k = 0; k < W; ++k) s += red[k];
       lpart[blockIdx.x] = s;
     }
   }
@@ -460,9 +465,9 @@ __global__ void __launch_bounds__(kGradWarps * 32) flow_grad_kernel(const __grid
         if (nt * 8 < L.no && m < L.b) {
           const int k = 2 * m + 1 - par;
           const int ra = m0 + g, rb = m0 + g + 8;
-          const float s0 = kFlowSClamp * tanhf(o[nt][0] / kFlowSClamp);
-          const float s1 = kFlowSClamp * tanhf(o[nt][2] / kFlowSClamp);
-          const float e0 = expf(s0), e1 = expf(s1);
+          const float s0 = flow_soft_clamp(o[nt][0]);
+          const float s1 = flow_soft_clamp(o[nt][2]);
+          const float e0 = __expf(s0), e1 = __expf(s1);
           const float gza = gz[ra * zld + k], gzb = gz[rb * zld + k];
           const float dsa = -wn[ra] + gza * zi[ra * zld + k] * e0;
           const float dsb = -wn[rb] + gzb * zi[rb * zld + k] * e1;
@@ -487,7 +492,7 @@ __global__ void __launch_bounds__(kGradWarps * 32) flow_grad_kernel(const __grid
     }
     __syncthreads();
     // dW3 = GO^T U2: [no x R] [R x 64]
-    cta_gemm(GOT, kLdR, U2T, kLdR, (L.no + 15) / 16 * 16, 64, R, [&](int r, int c, float v0, float v1) {
+    cta_gemm<W>(GOT, kLdR, U2T, kLdR, (L.no + 15) / 16 * 16, 64, R, [&](int r, int c, float v0, float v1) {
       if (r < 2 * L.b) {
         gp[L.oW3 + r * 64 + c] = v0;
         gp[L.oW3 + r * 64 + c + 1] = v1;
@@ -495,7 +500,7 @@ __global__ void __launch_bounds__(kGradWarps * 32) flow_grad_kernel(const __grid
     });
     __syncthreads();
     // gU2 = GO W3: [R x kpad] [kpad x 64] (the warp's own rows); GA2 = gU2 * (U2 > 0) into U2 / U2T
-    cta_gemm(GO, G.ldo, W3T, G.ldo, R, 64, kpad, [&](int r, int c, float v0, float v1) {
+    cta_gemm<W>(GO, G.ldo, W3T, G.ldo, R, 64, kpad, [&](int r, int c, float v0, float v1) {
       const float m0v = __bfloat162float(U2[r * kLdK64 + c]) > 0.0f ? v0 : 0.0f;
       const float m1v = __bfloat162float(U2[r * kLdK64 + c + 1]) > 0.0f ? v1 : 0.0f;
       st_bf16(U2 + r * kLdK64 + c, m0v); st_bf16(U2 + r * kLdK64 + c + 1, m1v);
@@ -505,13 +510,13 @@ __global__ void __launch_bounds__(kGradWarps * 32) flow_grad_kernel(const __grid
     });
     __syncthreads();
     // dW2 = GA2^T U1: [64 x R] [R x 64]
-    cta_gemm(U2T, kLdR, U1T, kLdR, 64, 64, R, [&](int r, int c, float v0, float v1) {
+    cta_gemm<W>(U2T, kLdR, U1T, kLdR, 64, 64, R, [&](int r, int c, float v0, float v1) {
       gp[L.oW2 + r * 64 + c] = v0;
       gp[L.oW2 + r * 64 + c + 1] = v1;
     });
     __syncthreads();
     // gU1 = GA2 W2: [R x 64] [64 x 64]; GA1 = gU1 * (U1 > 0) into U1 / U1T
-    cta_gemm(U2, kLdK64, W2T, kLdK64, R, 64, 64, [&](int r, int c, float v0, float v1) {
+    cta_gemm<W>(U2, kLdK64, W2T, kLdK64, R, 64, 64, [&](int r, int c, float v0, float v1) {
       const float m0v = __bfloat162float(U1[r * kLdK64 + c]) > 0.0f ? v0 : 0.0f;
       const float m1v = __bfloat162float(U1[r * kLdK64 + c + 1]) > 0.0f ? v1 : 0.0f;
       st_bf16(U1 + r * kLdK64 + c, m0v); st_bf16(U1 + r * kLdK64 + c + 1, m1v);
@@ -521,12 +526,12 @@ __global__ void __launch_bounds__(kGradWarps * 32) flow_grad_kernel(const __grid
     });
     __syncthreads();
     // dW1 = GA1^T H: [64 x R] [R x 16]
-    cta_gemm(U1T, kLdR, HT, kLdR, 64, 16, R, [&](int r, int c, float v0, float v1) {
+    cta_gemm<W>(U1T, kLdR, HT, kLdR, 64, 16, R, [&](int r, int c, float v0, float v1) {
       if (c < L.a) gp[L.oW1 + r * L.a + c] = v0;
       if (c + 1 < L.a) gp[L.oW1 + r * L.a + c + 1] = v1;
     });
     // gH = GA1 W1: [R x 64] [64 x 16]; the conditioning axes take it
-    cta_gemm(U1, kLdK64, W1T, kLdK64, R, 16, 64, [&](int r, int c, float v0, float v1) {
+    cta_gemm<W>(U1, kLdK64, W1T, kLdK64, R, 16, 64, [&](int r, int c, float v0, float v1) {
       if (c < L.a) gz[r * zld + 2 * c + par] += v0;
       if (c + 1 < L.a) gz[r * zld + 2 * (c + 1) + par] += v1;
     });
@@ -594,7 +599,8 @@ struct GradScratch {
 
 GradScratch grad_scratch(const FlowArgs& fa, int64_t n) {
   GradScratch S{};
-  S.nblk = (int)((n + kGradRows - 1) / kGradRows);
+  const int R = grad_rows(grad_warps(fa.d));
+  S.nblk = (int)((n + R - 1) / R);
   size_t o = 0;
   S.wsum = o; o = al16(o + sizeof(double));
   S.lpart = o; o = al16(o + sizeof(float) * S.nblk);
@@ -615,13 +621,14 @@ extern "C" size_t vegas_flow_grad_scratch_bytes(int32_t dim, int64_t n) {
 extern "C" int vegas_flow_grad(int32_t dim, const float* d_params, const float* d_x, const float* d_w, int64_t n,
                                float* d_grad, float* d_loss, void* d_scratch, size_t scratch_bytes, void* stream) {
   FlowArgs fa{};
-  if (flow_layout(dim, fa) != VEGAS_OK || dim > 16 || n < 1 || n > (int64_t(1) << 31) || !d_params || !d_x || !d_w || !d_grad ||
+  if (flow_layout(dim, fa) != VEGAS_OK || n < 1 || n > (int64_t(1) << 31) || !d_params || !d_x || !d_w || !d_grad ||
       !d_scratch)
     return VEGAS_EINVAL;
   fa.params = d_params;
   const GradScratch S = grad_scratch(fa, n);
   if (scratch_bytes < S.total) return VEGAS_ENOSPACE;
-  const GradLayout G = grad_layout(fa);
+  const int W = grad_warps(dim);
+  const GradLayout G = grad_layout(fa, W);
   if (G.total > 227 * 1024) return VEGAS_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned char* sc = (unsigned char*)d_scratch;
@@ -630,8 +637,13 @@ extern "C" int vegas_flow_grad(int32_t dim, const float* d_params, const float* 
   float* gpart = (float*)(sc + S.gpart);
   flow_wsum_kernel<<<1, 1024, 0, s>>>(d_w, n, wsum);
   VG_CHECK(cudaGetLastError());
-  VG_CHECK(cudaFuncSetAttribute(flow_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G.total));
-  flow_grad_kernel<<<S.nblk, kGradWarps * 32, G.total, s>>>(fa, G, d_x, d_w, wsum, n, gpart, lpart);
+  if (W == 4) {
+    VG_CHECK(cudaFuncSetAttribute(flow_grad_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, G.total));
+    flow_grad_kernel<4><<<S.nblk, 4 * 32, G.total, s>>>(fa, G, d_x, d_w, wsum, n, gpart, lpart);
+  } else {
+    VG_CHECK(cudaFuncSetAttribute(flow_grad_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, G.total));
+    flow_grad_kernel<2><<<S.nblk, 2 * 32, G.total, s>>>(fa, G, d_x, d_w, wsum, n, gpart, lpart);
+  }
   VG_CHECK(cudaGetLastError());
   flow_reduce_kernel<<<(fa.nparams + 255) / 256, 256, 0, s>>>(gpart, lpart, S.nblk, fa.nparams, d_grad, d_loss);
   return cuda_status(cudaGetLastError());
@@ -673,7 +685,7 @@ __global__ void __launch_bounds__(256) flow_eval_kernel(const float* __restrict_
 #pragma unroll
     for (int k = 0; k < DMAX; ++k) x[k] = k < d ? X[j * d + k] : 0.0f;
     const float f = integrand<ID, float, DMAX>(x, d, prm, np_derived, s0, s1, K);
-    values[j] = f * expf(logdet[j]);
+    values[j] = f * __expf(logdet[j]);
   }
 }
 

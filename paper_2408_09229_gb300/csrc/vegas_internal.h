@@ -48,6 +48,8 @@ struct FillArgs {
   float half_beta;
   int table_smem;  // 1: map table in shared memory
   int hist_mode;   // kHistShared, kHistGlobal or kHistTwoPhase
+  int bin_shift;   // two-phase: log2 of the bits of a packed interval index (3: 8 bits, N_g <= 256; 4: 16 bits)
+  int acc32;       // two-phase: 1 when the CTA histogram accumulates in FP32 (large d * N_g), 0 for float-float
   int np_derived;
   int iid;  // integrand family (the batched fill dispatches on it per tile)
   const double* edges;     // [d][G+1] FP64

@@ -107,7 +107,7 @@ def test_change_of_variables_on_gpu(V, d):
     assert abs(float(f.mean()) - one ** d) < 5 * float(f.std()) / math.sqrt(n)
 
 
-@pytest.mark.parametrize("d,n", [(5, 1000), (12, 777)])
+@pytest.mark.parametrize("d,n", [(5, 1000), (12, 777), (30, 333)])
 def test_gradient_matches_oracle(V, d, n):
     th = W.flow_params(d, seed=11 + d, out_scale=0.05)
     rng = np.random.default_rng(d)

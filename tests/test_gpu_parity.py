@@ -223,7 +223,21 @@ STREAM_CASES = [  # FP32 with 9..32 axes: the streamed point path (s_k <= 256, t
     ("exponential d9", 9, 16, 2, W.EXPONENTIAL, [], 4_097),
     ("morokoff d11", 11, 10, 2, W.MOROKOFF_CAFLISCH, [], 8_192),
     ("linear d32", 32, 4, 1, W.LINEAR, [], 3_333),
+    # N_g = 256 at 16 axes: d * N_g = 4096 intervals in the two-phase histogram
+    ("ridge d16 G256", 16, 256, 1, W.GAUSS_SUM, W.ridge(16, 3, 0.2), 20_000),
 ]
+
+WIDE_G_CASES = [  # FP32 with N_g > 256: 16-bit packed intervals (d N_g <= 2048) or shared FP32 atomics
+    ("linear d2 G1024 two-phase", 2, 1024, 40, W.LINEAR, [], 40_000),
+    ("product peak d3 G600 two-phase", 3, 600, 9, W.PRODUCT_PEAK, W.product_peak(3, 2), 20_001),
+    ("ridge d4 G1024 shared atomics", 4, 1024, 10, W.GAUSS_SUM, W.ridge(4, 3, 0.05), 40_000),
+    ("roos-arnold d10 G1024 shared atomics", 10, 1024, 2, W.ROOS_ARNOLD, [], 12_345),
+]
+
+
+@pytest.mark.parametrize("name,d,G,ns,iid,params,neval", WIDE_G_CASES, ids=[c[0] for c in WIDE_G_CASES])
+def test_fill_fp32_wide_map_matches_oracle(V, orc, name, d, G, ns, iid, params, neval):
+    test_fill_fp32_streamed_matches_oracle(V, orc, name, d, G, ns, iid, params, neval)
 
 
 @pytest.mark.parametrize("name,d,G,ns,iid,params,neval", STREAM_CASES, ids=[c[0] for c in STREAM_CASES])
