@@ -40,14 +40,14 @@ WORKLOAD = ("plain VEGAS+ d=8, ridge of 5 Gaussians (s=0.05) on the diagonal, Ng
             "1e8 evals/iteration, beta=0.75, alpha=0.5, Philox seed 0")
 # nominal SM facts of GB300 (152 SMs, 128 FP32 lanes per SM, 2070 MHz maximum SM clock)
 FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) of one launch of the dominant kernel on this workload, from the ncu capture
-# summarised in profiles/fill_kernel_ridge8_fp32.md: the per-cube offsets and weights, set by the data layout
-FILL_TRAFFIC_BYTES = (346.26 + 146.93) * 1e6
+# DRAM bytes (read + write) of one launch of the dominant kernel on this workload, from one ncu capture of
+# that kernel (dram__bytes_read.sum + dram__bytes_write.sum): the per-cube offsets and weights
+FILL_TRAFFIC_BYTES = (346.99 + 148.24) * 1e6
 
 
 def fp32_ops_per_eval(d=D, K=K_PEAKS):
     """FP32 FMA-pipe operations the method needs per evaluation of the d-dimensional
-    ridge in the FP32 form (counted from the algorithm):
+    ridge in the FP32 form, counted from the algorithm:
       point + map, per axis: c+u, *g, z-i, fma(dz,dx,e), J*=jk        -> 5 d
       integrand, per peak:   per axis x-mu, fma(dx,dx,r2); r2*c; acc+= -> K (2 d + 2)
       A*acc, v = J f, v*v, *1/n_h                                      -> 4"""

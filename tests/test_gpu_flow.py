@@ -202,17 +202,23 @@ def test_random_flow_keeps_the_estimate_unbiased(V, name, iid, d, params):
 
 
 def test_online_training_in_the_loop(V):
-    """training between iterations lowers the flow's loss and keeps the estimate unbiased"""
+    """training between iterations lowers the flow's loss; the trained proposal integrates the ridge with a
+    lower variance per iteration than plain VEGAS+ and an estimate within 5 sigma.  (A flow trained too
+    briefly under-covers the peaks' tails: each iteration stays unbiased, but its sigma_t then correlates
+    with I_t and the inverse-variance combination of Eq. (8) leans low; enough training avoids that.)"""
     d, neval = 4, 200_000
     p = W.ridge(4, 3, 0.05)
     v = V.Vegas(d, 50, 0, 0.5, 0.75, precision=V.FP32)
     v.set_flow(W.flow_params(d, seed=2))
-    v.set_flow_training(iterations=4, steps_per_iteration=50, samples=8192, batch=2048, lr=2e-3, temper=0.5)
-    v.set_skip(4)  # the estimate combines the iterations after training
+    v.set_flow_training(iterations=8, steps_per_iteration=100, samples=32768, batch=4096, lr=1e-3, temper=0.5)
+    v.set_skip(7)  # the estimate combines the iterations after training
     v.integrate(W.GAUSS_SUM, p, neval, 1, seed=4)
     _, loss1 = v.get_flow()
-    r = v.integrate(W.GAUSS_SUM, p, neval, 9, seed=5)
+    r = v.integrate(W.GAUSS_SUM, p, neval, 15, seed=5)
     th, loss2 = v.get_flow()
     assert loss2 < loss1
     assert np.abs(th - W.flow_params(d, seed=2)).max() > 1e-3
-    assert abs(r["estimate"] - 1.0) < 5 * r["sigma"]
+    assert abs(r["estimate"] - 1.0) < 5 * r["sigma"], (r["estimate"], r["sigma"], r["chi2_dof"])
+    plain = V.Vegas(d, 50, 0, 0.5, 0.75, precision=V.FP32).integrate(W.GAUSS_SUM, p, neval, 15, seed=5)
+    rel = lambda q: np.median(q["it_sig"][7:] / q["it_est"][7:])  # noqa: E731
+    assert rel(r) < 0.7 * rel(plain)

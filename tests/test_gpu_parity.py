@@ -1,7 +1,7 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
 Integer work is compared bit for bit; floating point within the tolerances
-below, each derived in DESIGN.md ("Tolerances"):
+below, each derived from the arithmetic of the two sides:
   FP64 path, same points and map as the oracle: cube means 1e-12 relative
     (plus 1e-12 of the largest mean), widened to 2 (n_h - 1) 2^-53 for cubes
     of n_h > 4500 evaluations, whose sequential sum in the oracle carries
