@@ -155,7 +155,7 @@ def stress_d30(V, W, stream, rank):
     return out
 
 
-FLOW_TRAIN = dict(iterations=10, steps_per_iteration=200, samples=65536, batch=4096, lr=1e-3, temper=0.5)
+FLOW_TRAIN = dict(iterations=10, steps_per_iteration=200, samples=65536, batch=4096, lr=1e-3, temper=0.5, floor=0.03)
 
 
 def learned_proposal(V, W, stream, rank):

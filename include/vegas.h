@@ -422,13 +422,19 @@ VEGAS_API int vegas_flow_adam(int64_t nparams, float *d_params, const float *d_g
  * evaluation, k = neval / samples, weighted by (|J f| / n_h)^p, with |J f| /
  * n_h its share of the estimate and p ramping linearly from temper (0 < temper
  * <= 1; below 1 the first targets are broader than |f|) to 1 over the
- * training iterations.  vegas_get_flow copies the current
+ * training iterations.  floor >= 0 mixes uniform points into the training
+ * set, one row in four, each weighted floor * 3 * the mean sample weight: the
+ * loss gains floor times the cross-entropy of the uniform density, whose
+ * minimiser is the density (target + floor * its mean) / (1 + floor).  Its
+ * log barrier keeps the flow's density off zero on every region of the cube,
+ * including regions that the flow's own samples no longer reach.  0 turns it
+ * off (the training set is the samples alone).  vegas_get_flow copies the current
  * parameters (nparams = the count, or params NULL) and the last training loss.
  * The checkpoint of vegas_get_state does not include the flow.
  * Errors: EINVAL, ENOMEM, ECUDA. */
 VEGAS_API int vegas_set_flow(vegas_handle h, const float *params, int64_t nparams);
 VEGAS_API int vegas_set_flow_training(vegas_handle h, int32_t iterations, int32_t steps_per_iteration,
-                                      int32_t samples, int32_t batch, float lr, float temper);
+                                      int32_t samples, int32_t batch, float lr, float temper, float floor);
 VEGAS_API int vegas_get_flow(vegas_handle h, float *params, int64_t nparams, float *last_loss);
 
 /* ======================================================================== */

@@ -56,7 +56,7 @@ struct vegas_s {
   int64_t flow_np = 0;
   int flow_step = 0, flow_train_iters = 0, flow_train_steps = 0, flow_train_samples = 0, flow_trained = 0;
   int flow_batch = 4096;
-  float flow_lr = 1e-3f, flow_temper = 1.0f;
+  float flow_lr = 1e-3f, flow_temper = 1.0f, flow_floor = 0.0f;
   float *d_X = nullptr, *d_logdet = nullptr, *d_values = nullptr;
   int64_t x_cap = 0, ld_cap = 0, val_cap = 0;
   float *d_train_x = nullptr, *d_train_w = nullptr;
@@ -336,7 +336,7 @@ extern "C" int vegas_integrate(vegas_handle h, int integrand, const double* para
 
   // learned proposal: per-evaluation buffers and the training sample
   const bool flow = h->d_flow != nullptr;
-  int64_t train_stride = 1, n_train = 0;
+  int64_t train_stride = 1, n_train = 0, train_rows = 0;
   if (flow) {
     if (h->precision != VEGAS_FP32) return VEGAS_EINVAL;
     if ((rc = grow(h->d_X, h->x_cap, neval * d)) != VEGAS_OK || (rc = grow(h->d_logdet, h->ld_cap, neval)) != VEGAS_OK ||
@@ -345,10 +345,12 @@ extern "C" int vegas_integrate(vegas_handle h, int integrand, const double* para
     if (h->flow_train_iters > h->flow_trained && h->flow_train_samples > 0 && h->flow_train_steps > 0) {
       train_stride = std::max<int64_t>(1, neval / h->flow_train_samples);
       n_train = (neval + train_stride - 1) / train_stride;
-      if ((rc = grow(h->d_train_x, h->tx_cap, n_train * d)) != VEGAS_OK ||
-          (rc = grow(h->d_train_w, h->tw_cap, n_train)) != VEGAS_OK)
+      train_rows = vg::flow_train_rows(n_train, h->flow_floor);
+      // d_train_w: the training set's weights [train_rows], the fill's raw weights [n_train], their sum (a double)
+      if ((rc = grow(h->d_train_x, h->tx_cap, train_rows * d)) != VEGAS_OK ||
+          (rc = grow(h->d_train_w, h->tw_cap, train_rows + n_train + 4)) != VEGAS_OK)
         return rc;
-      const size_t gs = vegas_flow_grad_scratch_bytes(d, std::min<int64_t>(n_train, h->flow_batch));
+      const size_t gs = vegas_flow_grad_scratch_bytes(d, std::min<int64_t>(train_rows, h->flow_batch));
       if (gs == 0) return VEGAS_EINVAL;
       if ((rc = grow_bytes(h->d_grad_scratch, h->grad_scratch_cap, gs)) != VEGAS_OK) return rc;
     } else if (h->flow_train_iters > h->flow_trained) {
@@ -383,7 +385,8 @@ extern "C" int vegas_integrate(vegas_handle h, int integrand, const double* para
           h->flow_train_iters > 1
               ? h->flow_temper + (1.0f - h->flow_temper) * (float)h->flow_trained / (float)(h->flow_train_iters - 1)
               : 1.0f;
-      vg::FillExtra ex_tab{h->d_values, nullptr, train ? h->d_train_w : nullptr, (int)train_stride, power};
+      vg::FillExtra ex_tab{h->d_values, nullptr, train ? h->d_train_w + train_rows : nullptr, (int)train_stride,
+                           power};
       rc = vg::fill_impl(&geo, VEGAS_FP32, vg::kIntegrandTabulated, nullptr, 0, neval, seed,
                          (int32_t)h->iter_counter, 0u, h->beta, h->d_edges[h->cur], h->d_offsets, h->d_ell, h->d_bins,
                          h->d_result, nullptr, nullptr, h->d_flags, h->d_fill_scratch, h->fill_scratch_cap, s, e[1],
@@ -401,12 +404,16 @@ extern "C" int vegas_integrate(vegas_handle h, int integrand, const double* para
     rc = vg::launch_record_combine(h->d_result, it, h->d_it_est, h->d_it_sig, h->skip, h->d_out, s);
     if (rc != VEGAS_OK) return rc;
     if (train) {
-      // Adam steps on the weighted samples of this iteration (x = F(x'), weight |J f| / n_h)
-      if ((rc = vg::flow_gather(h->d_X, d, train_stride, n_train, h->d_train_x, s)) != VEGAS_OK) return rc;
-      // minibatches: consecutive windows of the sample, cycling
-      const int64_t nb = std::min<int64_t>(n_train, h->flow_batch);
+      // Adam steps on the weighted samples of this iteration (x = F(x'), weight |J f| / n_h), with uniform
+      // points of the floor mixed in
+      double* wsum = (double*)(h->d_train_w + ((train_rows + n_train + 1) & ~(int64_t)1));
+      if ((rc = vg::flow_gather(h->d_X, d, train_stride, n_train, h->d_train_w + train_rows, h->flow_floor, seed,
+                                (uint32_t)h->iter_counter, wsum, h->d_train_x, h->d_train_w, s)) != VEGAS_OK)
+        return rc;
+      // minibatches: consecutive windows of the training set, cycling
+      const int64_t nb = std::min<int64_t>(train_rows, h->flow_batch);
       for (int k = 0; k < h->flow_train_steps; ++k) {
-        const int64_t off = ((int64_t)k * nb) % (n_train - nb + 1);
+        const int64_t off = ((int64_t)k * nb) % (train_rows - nb + 1);
         rc = vegas_flow_grad(d, h->d_flow, h->d_train_x + off * d, h->d_train_w + off, nb, h->d_flow_g,
                              h->d_flow_loss, h->d_grad_scratch, h->grad_scratch_cap, s);
         if (rc != VEGAS_OK) return rc;
@@ -603,10 +610,11 @@ extern "C" int vegas_set_flow(vegas_handle h, const float* params, int64_t npara
 }
 
 extern "C" int vegas_set_flow_training(vegas_handle h, int32_t iterations, int32_t steps_per_iteration,
-                                       int32_t samples, int32_t batch, float lr, float temper) {
+                                       int32_t samples, int32_t batch, float lr, float temper, float floor) {
   if (!h || iterations < 0 || steps_per_iteration < 0 || samples < 0 || batch < 1 || !(lr > 0.0f) ||
-      !(temper > 0.0f && temper <= 1.0f))
+      !(temper > 0.0f && temper <= 1.0f) || !(floor >= 0.0f))
     return VEGAS_EINVAL;
+  h->flow_floor = floor;
   h->flow_batch = batch;
   h->flow_temper = temper;
   h->flow_train_iters = iterations;

@@ -27,7 +27,7 @@ int flow_layout(int d, FlowArgs& fa) {
     FlowLayer& L = fa.lay[l];
     L.a = (l % 2 == 0) ? (d + 1) / 2 : d / 2;
     L.b = d - L.a;
-    L.no = (2 * L.b + 7) / 8 * 8;
+    L.no = (2 * L.b + 15) / 16 * 16;  // outputs padded to 16: the n-tiles of W3 load in pairs
     L.oW1 = off; off += kFlowHidden * L.a;
     L.ob1 = off; off += kFlowHidden;
     L.oW2 = off; off += kFlowHidden * kFlowHidden;
@@ -735,16 +735,56 @@ int flow_eval(int integrand, int d, const double* d_params, int64_t nparams, con
 }
 
 // training rows: xs[i] = X[i * stride]
+// The training set of one iteration: rows r = 0 .. rows-1 in a period of P.
+// Row r with r mod P < P-1 is sample i = (r / P)(P-1) + r mod P, the point of
+// evaluation i * stride and its weight w_i (zero weight past the last sample);
+// with a floor lambda > 0 row r with r mod P = P-1 is uniform point u = r / P,
+// a Philox4x32-10 draw keyed by (seed, iteration), with weight
+// lambda (P-1) mean(w).  Every window of consecutive rows then carries floor
+// weight lambda times its data weight, on average, spread over the whole cube.
 __global__ void flow_gather_kernel(const float* __restrict__ X, int d, int64_t stride, int64_t m,
-                                   float* __restrict__ xs) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= m * d) return;
-  const int64_t r = i / d, k = i - r * d;
-  xs[i] = X[r * stride * d + k];
+                                   const float* __restrict__ w, const double* __restrict__ wsum, float lambda, int P,
+                                   uint32_t k0, uint32_t k1, int64_t rows, float* __restrict__ xs,
+                                   float* __restrict__ ws) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  const int64_t q = r / P, ph = r - q * P;
+  if (lambda > 0.0f && ph == P - 1) {
+    const double wbar = m > 0 ? *wsum / (double)m : 0.0;
+    ws[r] = (float)((double)lambda * (double)(P - 1) * wbar);
+    for (int k0c = 0; k0c < d; k0c += 4) {
+      const uint4 b = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), (uint32_t)k0c, 0x464C4F57u), k0, k1);
+      const uint32_t u[4] = {b.x, b.y, b.z, b.w};
+      for (int t = 0; t < 4 && k0c + t < d; ++t)
+        xs[r * d + k0c + t] = ((float)(u[t] >> 8) + 0.5f) * 0x1p-24f;  // in (0, 1)
+    }
+    return;
+  }
+  const int64_t i = lambda > 0.0f ? q * (P - 1) + ph : r;
+  if (i < m) {
+    ws[r] = w[i];
+    for (int k = 0; k < d; ++k) xs[r * d + k] = X[i * stride * d + k];
+  } else {
+    ws[r] = 0.0f;
+    for (int k = 0; k < d; ++k) xs[r * d + k] = 0.5f;
+  }
 }
 
-int flow_gather(const float* X, int d, int64_t stride, int64_t m, float* xs, cudaStream_t s) {
-  flow_gather_kernel<<<(unsigned)((m * d + 255) / 256), 256, 0, s>>>(X, d, stride, m, xs);
+int64_t flow_train_rows(int64_t m, float lambda) {
+  if (!(lambda > 0.0f)) return m;
+  return (m + kFloorPeriod - 2) / (kFloorPeriod - 1) * kFloorPeriod;
+}
+
+int flow_gather(const float* X, int d, int64_t stride, int64_t m, const float* w, float lambda, uint64_t seed,
+                uint32_t iter, double* wsum, float* xs, float* ws, cudaStream_t s) {
+  const int64_t rows = flow_train_rows(m, lambda);
+  if (lambda > 0.0f) {
+    flow_wsum_kernel<<<1, 1024, 0, s>>>(w, m, wsum);
+    VG_CHECK(cudaGetLastError());
+  }
+  const uint32_t k0 = (uint32_t)seed ^ 0x3C6EF372u, k1 = (uint32_t)(seed >> 32) ^ iter;
+  flow_gather_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(X, d, stride, m, w, wsum, lambda, kFloorPeriod,
+                                                                    k0, k1, rows, xs, ws);
   return cuda_status(cudaGetLastError());
 }
 

@@ -72,6 +72,21 @@ __device__ __forceinline__ void load_b(const __nv_bfloat16* __restrict__ B, int 
   b1 = *reinterpret_cast<const uint32_t*>(p + 8);
 }
 
+// B fragments of two adjacent n-tiles (n0 and n0 + 8) at k0 with one
+// ldmatrix.x4: lanes 0-7 address rows n0..n0+7 at k0, lanes 8-15 the same
+// rows at k0 + 8, lanes 16-31 rows n0+8..n0+15; each 8x8 tile lands in the
+// B-fragment layout of m16n8k16 (thread i holds row i/4, columns 2(i%4)+{0,1}).
+// Row pitches are multiples of 16 bytes and k0 a multiple of 8.
+__device__ __forceinline__ void load_b2(const __nv_bfloat16* __restrict__ B, int ld, int n0, int k0, uint32_t& b00,
+                                        uint32_t& b01, uint32_t& b10, uint32_t& b11) {
+  const int lane = threadIdx.x & 31;
+  const int row = n0 + (lane & 7) + ((lane >> 4) << 3), col = k0 + ((lane >> 3) & 1) * 8;
+  const uint32_t addr = (uint32_t)__cvta_generic_to_shared(B + row * ld + col);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(b00), "=r"(b01), "=r"(b10), "=r"(b11)
+               : "r"(addr));
+}
+
 // A fragment of a [m][k] row-major bf16 matrix, tile at (m0, k0)
 __device__ __forceinline__ void load_a(const __nv_bfloat16* __restrict__ A, int ld, int m0, int k0, uint32_t (&a)[4]) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
@@ -150,12 +165,15 @@ __device__ __forceinline__ void flow_mlp(const FlowLayer& L, const unsigned char
   float acc[8][4];
   // layer 1: h (16 x 16) W1^T -> 16 x 64
 #pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
+  for (int nt = 0; nt < 8; nt += 2) {
     const float2 bb = *reinterpret_cast<const float2*>(b1 + nt * 8 + 2 * t);
+    const float2 bc = *reinterpret_cast<const float2*>(b1 + nt * 8 + 8 + 2 * t);
     acc[nt][0] = bb.x; acc[nt][1] = bb.y; acc[nt][2] = bb.x; acc[nt][3] = bb.y;
-    uint32_t b0, bq;
-    load_b(W1, kLdK16, nt * 8, 0, b0, bq);
-    mma16816(acc[nt], ha[0], ha[1], ha[2], ha[3], b0, bq);
+    acc[nt + 1][0] = bc.x; acc[nt + 1][1] = bc.y; acc[nt + 1][2] = bc.x; acc[nt + 1][3] = bc.y;
+    uint32_t b00, b01, b10, b11;
+    load_b2(W1, kLdK16, nt * 8, 0, b00, b01, b10, b11);
+    mma16816(acc[nt], ha[0], ha[1], ha[2], ha[3], b00, b01);
+    mma16816(acc[nt + 1], ha[0], ha[1], ha[2], ha[3], b10, b11);
   }
   // ReLU, bf16: the A fragments of u1 (4 k-steps of 16)
   uint32_t ua[4][4];
@@ -168,14 +186,17 @@ __device__ __forceinline__ void flow_mlp(const FlowLayer& L, const unsigned char
   }
   // layer 2: u1 (16 x 64) W2^T -> 16 x 64
 #pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
+  for (int nt = 0; nt < 8; nt += 2) {
     const float2 bb = *reinterpret_cast<const float2*>(b2 + nt * 8 + 2 * t);
+    const float2 bc = *reinterpret_cast<const float2*>(b2 + nt * 8 + 8 + 2 * t);
     acc[nt][0] = bb.x; acc[nt][1] = bb.y; acc[nt][2] = bb.x; acc[nt][3] = bb.y;
+    acc[nt + 1][0] = bc.x; acc[nt + 1][1] = bc.y; acc[nt + 1][2] = bc.x; acc[nt + 1][3] = bc.y;
 #pragma unroll
     for (int ks = 0; ks < 4; ++ks) {
-      uint32_t b0, bq;
-      load_b(W2, kLdK64, nt * 8, ks * 16, b0, bq);
-      mma16816(acc[nt], ua[ks][0], ua[ks][1], ua[ks][2], ua[ks][3], b0, bq);
+      uint32_t b00, b01, b10, b11;
+      load_b2(W2, kLdK64, nt * 8, ks * 16, b00, b01, b10, b11);
+      mma16816(acc[nt], ua[ks][0], ua[ks][1], ua[ks][2], ua[ks][3], b00, b01);
+      mma16816(acc[nt + 1], ua[ks][0], ua[ks][1], ua[ks][2], ua[ks][3], b10, b11);
     }
   }
 #pragma unroll
@@ -186,16 +207,20 @@ __device__ __forceinline__ void flow_mlp(const FlowLayer& L, const unsigned char
     ua[ks][3] = pack_bf16(fmaxf(acc[2 * ks + 1][2], 0.0f), fmaxf(acc[2 * ks + 1][3], 0.0f));
   }
   // layer 3: u2 (16 x 64) W3^T -> 16 x no
+  // (W3 is staged with a multiple of 16 rows, zero past 2b, so the n-tiles go in pairs)
 #pragma unroll
-  for (int nt = 0; nt < NT3; ++nt) {
+  for (int nt = 0; nt < NT3; nt += 2) {
     if (nt * 8 < L.no) {
       const float2 bb = *reinterpret_cast<const float2*>(b3 + nt * 8 + 2 * t);
+      const float2 bc = *reinterpret_cast<const float2*>(b3 + nt * 8 + 8 + 2 * t);
       o[nt][0] = bb.x; o[nt][1] = bb.y; o[nt][2] = bb.x; o[nt][3] = bb.y;
+      o[nt + 1][0] = bc.x; o[nt + 1][1] = bc.y; o[nt + 1][2] = bc.x; o[nt + 1][3] = bc.y;
 #pragma unroll
       for (int ks = 0; ks < 4; ++ks) {
-        uint32_t b0, bq;
-        load_b(W3, kLdK64, nt * 8, ks * 16, b0, bq);
-        mma16816(o[nt], ua[ks][0], ua[ks][1], ua[ks][2], ua[ks][3], b0, bq);
+        uint32_t b00, b01, b10, b11;
+        load_b2(W3, kLdK64, nt * 8, ks * 16, b00, b01, b10, b11);
+        mma16816(o[nt], ua[ks][0], ua[ks][1], ua[ks][2], ua[ks][3], b00, b01);
+        mma16816(o[nt + 1], ua[ks][0], ua[ks][1], ua[ks][2], ua[ks][3], b10, b11);
       }
     }
   }

@@ -124,7 +124,11 @@ int flow_apply(int d, int direction, const float* d_params, const float* d_xin, 
                int64_t n, cudaStream_t s);
 int flow_eval(int integrand, int d, const double* d_params, int64_t nparams, const float* X, const float* logdet,
               float* values, int64_t n, cudaStream_t s);
-int flow_gather(const float* X, int d, int64_t stride, int64_t m, float* xs, cudaStream_t s);
+// training set of an iteration: every kFloorPeriod-th row a uniform point when lambda > 0
+constexpr int kFloorPeriod = 4;
+int64_t flow_train_rows(int64_t m, float lambda);
+int flow_gather(const float* X, int d, int64_t stride, int64_t m, const float* w, float lambda, uint64_t seed,
+                uint32_t iter, double* wsum, float* xs, float* ws, cudaStream_t s);
 int fill_args_axes(FillArgs& a, const int32_t* nstrat, int precision, int nprm);
 int derived_param_count(int integrand, int d, const double* host_params_or_null, int64_t np);
 

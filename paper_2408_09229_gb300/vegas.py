@@ -99,7 +99,7 @@ def _load():
         "vegas_batch_get": ([P, i32, i32, P, i64], i32),
         "vegas_flow_param_count": ([i32], i64),
         "vegas_set_flow": ([P, P, i64], i32),
-        "vegas_set_flow_training": ([P, i32, i32, i32, i32, ctypes.c_float, ctypes.c_float], i32),
+        "vegas_set_flow_training": ([P, i32, i32, i32, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float], i32),
         "vegas_get_flow": ([P, P, i64, P], i32),
         "vegas_flow_apply": ([i32, i32, P, P, P, P, i64, P], i32),
         "vegas_flow_grad_scratch_bytes": ([i32, i64], sz),
@@ -233,9 +233,12 @@ class Vegas:
         self._flow = p
         _check(lib.vegas_set_flow(self._h, p.ctypes.data_as(ctypes.c_void_p), p.size), "vegas_set_flow")
 
-    def set_flow_training(self, iterations, steps_per_iteration, samples, batch=4096, lr=1e-3, temper=1.0):
-        _check(lib.vegas_set_flow_training(self._h, iterations, steps_per_iteration, samples, batch, lr, temper),
-               "vegas_set_flow_training")
+    def set_flow_training(self, iterations, steps_per_iteration, samples, batch=4096, lr=1e-3, temper=1.0,
+                          floor=0.03):
+        """train the flow after each of the next `iterations` iterations (vegas_set_flow_training); floor is the
+        weight of the uniform points mixed into the training set, 0 for none"""
+        _check(lib.vegas_set_flow_training(self._h, iterations, steps_per_iteration, samples, batch, lr, temper,
+                                           floor), "vegas_set_flow_training")
 
     def get_flow(self):
         n = lib.vegas_flow_param_count(self.dim)
