@@ -235,6 +235,7 @@ __device__ __forceinline__ T integrand(const T (&x)[DMAX], int d, const T* __res
     for (int i = 0; i < DMAX / 2; ++i) xp[i] = pk2(x[2 * i], x[2 * i + 1]);
     const float4* mu = reinterpret_cast<const float4*>(p + 4);
     float acc = 0.0f;
+#pragma unroll 2
     for (int k = 0; k < K; ++k, mu += DMAX / 4) {
       uint64_t r2 = 0ull;  // (+0, +0)
 #pragma unroll
@@ -362,6 +363,20 @@ __device__ __forceinline__ uint4 philox_rk(uint4 c, const uint32_t* rk0, const u
   return c;
 }
 
+// Two Philox4x32-10 blocks in lockstep.  The rounds of one block form a
+// dependent chain; two independent chains interleaved halve its stalls.
+__device__ __forceinline__ void philox_rk_x2(uint4& c, uint4& e, const uint32_t* rk0, const uint32_t* rk1) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x, p1 = (uint64_t)0xCD9E8D57u * c.z;
+    const uint64_t q0 = (uint64_t)0xD2511F53u * e.x, q1 = (uint64_t)0xCD9E8D57u * e.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk0[round], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ rk1[round],
+                   (uint32_t)p0);
+    e = make_uint4((uint32_t)(q1 >> 32) ^ e.y ^ rk0[round], (uint32_t)q1, (uint32_t)(q0 >> 32) ^ e.w ^ rk1[round],
+                   (uint32_t)q0);
+  }
+}
+
 // Coordinates c_k of cube h (axis 0 fastest), by multiplication with the
 // magic reciprocals.  In the FP32 form they are kept as the high bits of a
 // float in [2^23, 2^24): 0x4B000000 | c_k << b_k, with b_k fraction bits.
@@ -399,6 +414,10 @@ __device__ __forceinline__ void make_point(const FillArgs& a, const uint32_t* __
   J = J0;
   uint4 r = make_uint4(0u, 0u, 0u, 0u);
   const uint32_t jlo = (uint32_t)j, jhi = (uint32_t)((uint64_t)j >> 32);
+  // FP32 with exactly 8 axes: both blocks of the point at once
+  constexpr bool kPair = sizeof(T) == 4 && EXACT && DMAX == 8;
+  uint4 ra = make_uint4(jlo, jhi, a.iter, a.pid << 16), rb = make_uint4(jlo, jhi, a.iter, (a.pid << 16) | 1u);
+  if constexpr (kPair) philox_rk_x2(ra, rb, rk0, rk1);
 #pragma unroll
   for (int k = 0; k < DMAX; ++k) {
     x[k] = T(0);
@@ -416,7 +435,8 @@ __device__ __forceinline__ void make_point(const FillArgs& a, const uint32_t* __
         i = i < G - 1 ? i : G - 1;
         dz = z - (double)i;  // exact
       } else {
-        if ((k & 3) == 0) r = philox_rk(make_uint4(jlo, jhi, a.iter, (a.pid << 16) | (uint32_t)(k >> 2)), rk0, rk1);
+        if constexpr (kPair) r = k < 4 ? ra : rb;
+        else if ((k & 3) == 0) r = philox_rk(make_uint4(jlo, jhi, a.iter, (a.pid << 16) | (uint32_t)(k >> 2)), rk0, rk1);
         const uint32_t w = (k & 3) == 0 ? r.x : (k & 3) == 1 ? r.y : (k & 3) == 2 ? r.z : r.w;
         const float big = __uint_as_float(cb[k] | (w >> (32 - a.fbits[k])));  // 2^23 + v
         const float z = fmaf(big, a.gzb32[k], a.gzn32[k]);                     // RN(v g 2^-b)
@@ -757,13 +777,14 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
       }
     }
   }
-  // ---- offsets and 1/n_h of the cubes the tile can meet ----
-  for (int c = tid; c <= kMaxCubesPerTile; c += kFillThreads) {
+  // ---- offsets and 1/n_h of the cubes the tile can meet: up to the next tile's first cube ----
+  const int ncand = min(kMaxCubesPerTile, (tile + 1 < a.ntiles ? a.tile_first[tile + 1] : a.NH - 1) - h0 + 1);
+  for (int c = tid; c <= ncand; c += kFillThreads) {
     const int64_t h = (int64_t)h0 + c;
     const int64_t o0 = h <= a.NH ? a.offsets[h] : INT64_MAX;
     const int64_t rel = o0 - j0;
     off_r[c] = rel < -1 ? -1 : (rel > kTile + 1 ? kTile + 1 : (int)rel);
-    if (c < kMaxCubesPerTile) {
+    if (c < ncand) {
       T inv = T(0);
       if (o0 < jend) {
         if constexpr (sizeof(T) == 8) inv = 1.0 / (double)(a.offsets[h + 1] - o0);
@@ -779,7 +800,7 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
   }
   __syncthreads();
   // every cube tells the threads whose first evaluation it holds
-  for (int c = tid; c < kMaxCubesPerTile; c += kFillThreads) {
+  for (int c = tid; c < ncand; c += kFillThreads) {
     const int r0 = max(off_r[c], 0), r1 = min(off_r[c + 1], len);
     if (r0 < r1) {
       for (int t = (r0 + kSamplesPerThread - 1) / kSamplesPerThread; t * kSamplesPerThread < r1; ++t) startc[t] = c;
