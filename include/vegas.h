@@ -389,9 +389,16 @@ enum vegas_flow_direction {
 VEGAS_API int64_t vegas_flow_param_count(int32_t dim);
 /* Apply the flow to n points d_x_in [n][dim] (device, FP32, in [0,1]) in the
  * given direction: d_x_out [n][dim] and d_logdet [n] (device).  d_x_out may
- * equal d_x_in.  Asynchronous on stream.  Errors: EINVAL, ECUDA. */
+ * equal d_x_in.  Asynchronous on stream.  The GEMMs run as tcgen05 MMAs
+ * (bf16 operands, FP32 accumulators in tensor memory); the biases enter the
+ * accumulation in FP32.  Errors: EINVAL, ECUDA. */
 VEGAS_API int vegas_flow_apply(int32_t dim, int32_t direction, const float *d_params, const float *d_x_in,
                                float *d_x_out, float *d_logdet, int64_t n, void *stream);
+/* Synchronise stream and report whether a bounded device wait of an earlier
+ * vegas_flow_apply ran out (VEGAS_ETIMEOUT; the points of the affected tiles
+ * are then not written) or not (VEGAS_OK); clears the report.
+ * Errors: ECUDA. */
+VEGAS_API int vegas_flow_check(void *stream);
 /* Training loss and gradient.  For samples d_x [n][dim] with weights
  * d_w [n] >= 0 of positive sum (|f| over the density that drew them, e.g.
  * |J f| of a VEGAS+ iteration), loss = - sum_i w_i log|det dF^-1/dx(x_i)| /

@@ -454,6 +454,7 @@ extern "C" int vegas_integrate(vegas_handle h, int integrand, const double* para
   out->nitn_run = nrun;
   out->neval_total = neval * (int64_t)nrun;
   if (flags & 2) return VEGAS_ECUDA;  // a cube crossing tiles was not reassembled: internal error
+  if (flow && (rc = vg::flow_tc_status(true)) != VEGAS_OK) return rc;
   return (flags & 1) ? VEGAS_ENONFINITE : VEGAS_OK;
 }
 

@@ -48,62 +48,7 @@ int flow_layout(int d, FlowArgs& fa) {
 
 namespace {
 
-constexpr int kFlowWarps = 8;
-
 __host__ __device__ inline int flow_zld(int d) { return d | 1; }  // odd row stride: fewer bank conflicts
-
-size_t flow_apply_smem(const FlowArgs& fa) {
-  return (size_t)fa.smem_weights + sizeof(float) * kFlowWarps * 16 * (flow_zld(fa.d) + 1);
-}
-
-// x_out = flow(x_in) in direction dir (+1 normalising, -1 sampling) and the
-// log-determinant of that direction; one warp per 16 rows, grid-stride
-template <int NT3>
-__global__ void __launch_bounds__(kFlowWarps * 32) flow_apply_kernel(const __grid_constant__ FlowArgs fa, int dir,
-                                                                     const float* __restrict__ xin,
-                                                                     float* __restrict__ xout,
-                                                                     float* __restrict__ logdet, int64_t n) {
-  extern __shared__ __align__(16) unsigned char sm[];
-  flow_stage_weights(fa, sm);
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int d = fa.d, zld = flow_zld(d);
-  float* z = reinterpret_cast<float*>(sm + fa.smem_weights) + warp * 16 * zld;
-  float* ldr = reinterpret_cast<float*>(sm + fa.smem_weights) + kFlowWarps * 16 * zld + warp * 16;
-  const int64_t nchunks = (n + 15) / 16;
-  for (int64_t c = (int64_t)blockIdx.x * kFlowWarps + warp; c < nchunks; c += (int64_t)gridDim.x * kFlowWarps) {
-    const int64_t r0 = c * 16;
-    const int rows = (int)min((int64_t)16, n - r0);
-    for (int i = lane; i < 16 * d; i += 32) {
-      const int r = i / d, k = i - r * d;
-      z[r * zld + k] = flow_logit(r < rows ? xin[(r0 + r) * d + k] : 0.5f);
-    }
-    __syncwarp();
-    if (lane < 16) {
-      float s = 0.0f;
-      for (int k = 0; k < d; ++k) s -= flow_log_sig_prime(z[lane * zld + k]);
-      ldr[lane] = s;
-    }
-    __syncwarp();
-    float a0, a1;
-    flow_rows<NT3>(fa, sm, z, zld, dir, a0, a1);
-    if ((lane & 3) == 0) {
-      ldr[lane >> 2] += a0;
-      ldr[(lane >> 2) + 8] += a1;
-    }
-    __syncwarp();
-    for (int i = lane; i < 16 * d; i += 32) {
-      const int r = i / d, k = i - r * d;
-      if (r < rows) xout[(r0 + r) * d + k] = flow_sigmoid(z[r * zld + k]);
-    }
-    if (lane < rows) {
-      float s = ldr[lane];
-      for (int k = 0; k < d; ++k) s += flow_log_sig_prime(z[lane * zld + k]);
-      logdet[r0 + lane] = s;
-    }
-    __syncwarp();
-  }
-}
 
 int num_sms_flow() {
   int dev = 0, n = 0;
@@ -112,33 +57,7 @@ int num_sms_flow() {
   return n;
 }
 
-template <int NT3>
-int launch_apply(const FlowArgs& fa, int dir, const float* xin, float* xout, float* logdet, int64_t n,
-                 cudaStream_t s) {
-  const size_t smem = flow_apply_smem(fa);
-  auto k = flow_apply_kernel<NT3>;
-  VG_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int occ = 0;
-  VG_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kFlowWarps * 32, smem));
-  if (occ < 1) return VEGAS_ECUDA;
-  const int64_t chunks = (n + 15) / 16;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)occ * num_sms_flow(),
-                                                                (chunks + kFlowWarps - 1) / kFlowWarps));
-  k<<<grid, kFlowWarps * 32, smem, s>>>(fa, dir, xin, xout, logdet, n);
-  return cuda_status(cudaGetLastError());
-}
-
 }  // namespace
-
-int flow_apply(int d, int direction, const float* d_params, const float* d_xin, float* d_xout, float* d_logdet,
-               int64_t n, cudaStream_t s) {
-  FlowArgs fa{};
-  if (flow_layout(d, fa) != VEGAS_OK) return VEGAS_EINVAL;
-  fa.params = d_params;
-  const int dir = direction == VEGAS_FLOW_NORMALISE ? 1 : -1;
-  return d <= 16 ? launch_apply<2>(fa, dir, d_xin, d_xout, d_logdet, n, s)
-                 : launch_apply<4>(fa, dir, d_xin, d_xout, d_logdet, n, s);
-}
 
 }  // namespace vg
 
@@ -156,6 +75,11 @@ extern "C" int vegas_flow_apply(int32_t dim, int32_t direction, const float* d_p
   if (direction != VEGAS_FLOW_NORMALISE && direction != VEGAS_FLOW_SAMPLE) return VEGAS_EINVAL;
   if (n == 0) return VEGAS_OK;
   return flow_apply(dim, direction, d_params, d_x_in, d_x_out, d_logdet, n, (cudaStream_t)stream);
+}
+
+extern "C" int vegas_flow_check(void* stream) {
+  VG_CHECK(cudaStreamSynchronize((cudaStream_t)stream));
+  return flow_tc_status(true);
 }
 
 // ===========================================================================

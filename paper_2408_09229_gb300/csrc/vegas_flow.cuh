@@ -14,12 +14,14 @@
 //   log-determinant is sum s plus the two wrap terms log sigmoid'(z).
 // MLP_l: a_l -> 64 -> 64 -> 2 b_l with ReLU; output row 2j is s_j, 2j+1 t_j.
 //
-// GEMMs run on the tensor cores with mma.sync m16n8k16 (bf16 operands, FP32
-// accumulation).  A warp owns 16 samples.  The accumulator fragment of one
-// layer is, after ReLU and conversion, the A fragment of the next, so the
-// hidden activations never leave registers in the forward direction.
-// Weights are bf16 in shared memory, rows padded so that the fragment loads
-// of a warp hit 32 distinct banks.
+// The batched transform (vegas_flow_apply) runs on tcgen05 with the
+// accumulators in tensor memory (vegas_flow_tc.cu).  The training pass, which
+// needs the transposed products of the backward direction as well, runs the
+// layer below with mma.sync m16n8k16 (bf16 operands, FP32 accumulation): a
+// warp owns 16 samples, and the accumulator fragment of one GEMM is, after
+// ReLU and conversion, the A fragment of the next, so the hidden activations
+// never leave registers.  Weights are bf16 in shared memory, rows padded so
+// that the fragment loads of a warp hit 32 distinct banks.
 #pragma once
 #include <cuda_bf16.h>
 #include <cstdint>
@@ -271,25 +273,6 @@ __device__ __forceinline__ void flow_layer(const FlowLayer& L, int l, const unsi
     }
   }
   __syncwarp();
-}
-
-// The whole flow on the warp's 16 rows: z holds logit(x) on entry and the
-// final z on exit; returns in lanes t == 0 the coupling part of the
-// log-determinant of rows g (r0) and g + 8 (r1).
-template <int NT3>
-__device__ __forceinline__ void flow_rows(const FlowArgs& fa, const unsigned char* sm, float* z, int zld, int dir,
-                                          float& r0, float& r1) {
-  float ld0 = 0.0f, ld1 = 0.0f;
-  for (int i = 0; i < kFlowLayers; ++i) {
-    const int l = dir > 0 ? i : kFlowLayers - 1 - i;
-    flow_layer<NT3>(fa.lay[l], l, sm, z, zld, dir, ld0, ld1);
-  }
-  ld0 += __shfl_xor_sync(0xffffffffu, ld0, 1);
-  ld0 += __shfl_xor_sync(0xffffffffu, ld0, 2);
-  ld1 += __shfl_xor_sync(0xffffffffu, ld1, 1);
-  ld1 += __shfl_xor_sync(0xffffffffu, ld1, 2);
-  r0 = ld0;
-  r1 = ld1;
 }
 
 int flow_layout(int d, FlowArgs& fa);

@@ -1,0 +1,365 @@
+// vegas_flow_tc.cu -- the coupling flow's batched transform (vegas_flow_apply)
+// on the fifth-generation tensor cores: tcgen05.mma with the accumulators in
+// tensor memory.  The flow is defined in vegas_flow.cuh.
+//
+// A CTA of kTcGroups warpgroups stays resident on one SM; each warpgroup
+// transforms its own tile of 128 points, so while one waits for its MMAs the
+// others run their element-wise work.  Thread t of a warpgroup owns point t of
+// the tile: it keeps the point's z in registers and reads row t of every
+// accumulator (tensor-memory lane t).  Per coupling layer:
+//   H  = [bf16(z[A]) | 1 1 1 | 0]           128 x K1   (shared memory)
+//   D  = H W1'^T                            128 x 64   (tensor memory)
+//   U  = [bf16(relu D) | 1 1 1 | 0]          128 x 80   (shared memory)
+//   D  = U W2'^T;  U = [bf16(relu D) | ...]
+//   D  = U W3'^T                            128 x N3
+// then s, t from D and the affine update of z[B].  The primed weights carry
+// the bias in three extra columns as a bf16 triple (hi, mid, lo) with
+// hi + mid + lo = b to 2^-24 relative, multiplied by the three ones-columns
+// of H and U: the bias enters the FP32 accumulation at full FP32 precision.
+// One thread of the warpgroup issues the MMAs and waits (bounded) on the
+// warpgroup's mbarrier; the others wait at the warpgroup's named barrier.
+#include <algorithm>
+
+#include "vegas_flow.cuh"
+#include "vegas_internal.h"
+#include "vegas_tc.cuh"
+
+namespace vg {
+
+namespace {
+
+constexpr int kTcGroups = 4;                   // warpgroups (tiles in flight) per CTA
+constexpr int kTcThreads = 128 * kTcGroups;
+constexpr int kTcK2 = kFlowHidden + 16;        // K of the second and third GEMMs: 64 + bias block
+constexpr int kTcColsPerGroup = 64;            // tensor-memory columns of one warpgroup's accumulator
+constexpr int kTcWaitPolls = 1 << 22;          // bound of every mbarrier wait
+
+// a module-wide status word: bit 2 is set when a bounded wait ran out
+__device__ int g_flow_tc_status;
+
+template <int DMAX>
+struct TcShape {
+  static constexpr int K1 = DMAX;   // K of the first GEMM: a <= DMAX/2 inputs + 3 bias columns, padded
+  static constexpr int N3 = DMAX;   // N of the third GEMM: 2 b <= DMAX outputs
+  static constexpr uint32_t W1 = 64 * K1 * 2, W2 = 64 * kTcK2 * 2, W3 = N3 * kTcK2 * 2;
+  static constexpr uint32_t layer = W1 + W2 + W3;
+  static constexpr uint32_t weights = kFlowLayers * layer;
+  static constexpr uint32_t H = 128 * K1 * 2, U = 128 * kTcK2 * 2;  // U doubles as the x staging area
+  static constexpr uint32_t group = H + U;
+  static constexpr uint32_t misc = weights + kTcGroups * group;
+  static constexpr uint32_t total = misc + 8 * kTcGroups + 4 * kTcGroups + 16;
+  static_assert(128 * (DMAX + 1) * 4 <= U, "staging fits in U");
+};
+
+__device__ __forceinline__ void bias3(float b, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(b);
+  const float r = b - __bfloat162float(h);
+  m = __float2bfloat16_rn(r);
+  l = __float2bfloat16_rn(r - __bfloat162float(m));
+}
+
+// weights of every layer in the core-matrix layout, biases in columns (k, k+1, k+2)
+template <int DMAX>
+__device__ void tc_stage_weights(const FlowArgs& fa, unsigned char* sm) {
+  using S = TcShape<DMAX>;
+  const float* P = fa.params;
+  for (int l = 0; l < kFlowLayers; ++l) {
+    const FlowLayer& L = fa.lay[l];
+    unsigned char* w1 = sm + l * S::layer;
+    unsigned char* w2 = w1 + S::W1;
+    unsigned char* w3 = w2 + S::W2;
+    for (int i = threadIdx.x; i < 64 * S::K1; i += kTcThreads) {
+      const int j = i / S::K1, c = i - j * S::K1;
+      __nv_bfloat16 v = __float2bfloat16_rn(0.0f), h, m, lo;
+      if (c < L.a) v = __float2bfloat16_rn(P[L.oW1 + j * L.a + c]);
+      else if (c < L.a + 3) {
+        bias3(P[L.ob1 + j], h, m, lo);
+        v = c == L.a ? h : (c == L.a + 1 ? m : lo);
+      }
+      *reinterpret_cast<__nv_bfloat16*>(w1 + tc_off(j, c, S::K1)) = v;
+    }
+    for (int i = threadIdx.x; i < 64 * kTcK2; i += kTcThreads) {
+      const int j = i / kTcK2, c = i - j * kTcK2;
+      __nv_bfloat16 v = __float2bfloat16_rn(0.0f), h, m, lo;
+      if (c < kFlowHidden) v = __float2bfloat16_rn(P[L.oW2 + j * kFlowHidden + c]);
+      else if (c < kFlowHidden + 3) {
+        bias3(P[L.ob2 + j], h, m, lo);
+        v = c == kFlowHidden ? h : (c == kFlowHidden + 1 ? m : lo);
+      }
+      *reinterpret_cast<__nv_bfloat16*>(w2 + tc_off(j, c, kTcK2)) = v;
+    }
+    for (int i = threadIdx.x; i < S::N3 * kTcK2; i += kTcThreads) {
+      const int j = i / kTcK2, c = i - j * kTcK2;
+      __nv_bfloat16 v = __float2bfloat16_rn(0.0f), h, m, lo;
+      if (j < 2 * L.b) {
+        if (c < kFlowHidden) v = __float2bfloat16_rn(P[L.oW3 + j * kFlowHidden + c]);
+        else if (c < kFlowHidden + 3) {
+          bias3(P[L.ob3 + j], h, m, lo);
+          v = c == kFlowHidden ? h : (c == kFlowHidden + 1 ? m : lo);
+        }
+      }
+      *reinterpret_cast<__nv_bfloat16*>(w3 + tc_off(j, c, kTcK2)) = v;
+    }
+  }
+}
+
+__device__ __forceinline__ void wg_bar(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+
+__device__ __forceinline__ void st_shared_v4(unsigned char* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(tc_smem_u32(p)), "r"(a), "r"(b), "r"(c), "r"(d)
+               : "memory");
+}
+
+__device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
+// row t of U from the 64 accumulator columns: ReLU, bf16
+__device__ __forceinline__ void tc_hidden_epilogue(uint32_t tacc, unsigned char* U, int t) {
+#pragma unroll
+  for (int cb = 0; cb < 64; cb += 32) {
+    float v[32];
+    tc_ld32(tacc + cb, v);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      st_shared_v4(U + tc_off(t, cb + 8 * q, kTcK2), bf16x2_relu(v[8 * q], v[8 * q + 1]),
+                   bf16x2_relu(v[8 * q + 2], v[8 * q + 3]), bf16x2_relu(v[8 * q + 4], v[8 * q + 5]),
+                   bf16x2_relu(v[8 * q + 6], v[8 * q + 7]));
+  }
+}
+
+// the MMAs of one GEMM, issued by one thread: D = A B^T over K / 16 k-steps
+__device__ __forceinline__ void tc_gemm(uint32_t tacc, const unsigned char* A, const unsigned char* B, int K,
+                                        uint32_t idesc) {
+  const uint32_t a0 = tc_smem_u32(A), b0 = tc_smem_u32(B), sbo = (uint32_t)K * 16;
+  for (int s = 0; s < K / 16; ++s)
+    tc_mma(tacc, tc_desc(a0 + 256 * s, kTcLbo, sbo), tc_desc(b0 + 256 * s, kTcLbo, sbo), idesc, s > 0);
+}
+
+struct TcGroup {
+  int id, t;             // warpgroup, thread in it
+  uint32_t tacc;         // its accumulator columns, lane base of this warp
+  uint64_t* mbar;
+  volatile int* abort;
+  uint32_t phase;
+};
+
+// issue (thread 0), wait (thread 0, bounded), then the whole warpgroup may
+// read the accumulator; false when the wait ran out
+__device__ __forceinline__ bool tc_run(TcGroup& G, const unsigned char* A, const unsigned char* B, int K,
+                                       uint32_t idesc) {
+  tc_fence_proxy();
+  tc_fence_before();
+  wg_bar(1 + G.id);
+  if (G.t == 0) {
+    tc_fence_after();
+    tc_gemm(G.tacc & 0xFFFFu, A, B, K, idesc);  // thread 0 is in lane quarter 0
+    tc_commit(G.mbar);
+    if (!mbar_wait(G.mbar, G.phase, kTcWaitPolls)) {
+      *G.abort = 1;
+      atomicOr(&g_flow_tc_status, 4);
+    }
+  }
+  G.phase ^= 1u;
+  wg_bar(1 + G.id);
+  tc_fence_after();
+  return *G.abort == 0;
+}
+
+// one coupling layer on the warpgroup's tile; PAR = l mod 2
+template <int DMAX, int PAR>
+__device__ __forceinline__ bool tc_layer(const FlowLayer& L, const unsigned char* wl, unsigned char* H,
+                                         unsigned char* U, TcGroup& G, int dir, float (&z)[DMAX], float& ld) {
+  using S = TcShape<DMAX>;
+  const int t = G.t;
+  // H row t: the conditioning axes 2c + PAR, then the three ones of the bias
+#pragma unroll
+  for (int q = 0; q < S::K1 / 8; ++q) {
+    float hv[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int c = 8 * q + e, k = 2 * c + PAR;
+      float v = 0.0f;
+      if (k < DMAX && c < L.a) v = z[k];
+      else if (c >= L.a && c < L.a + 3) v = 1.0f;
+      hv[e] = v;
+    }
+    st_shared_v4(H + tc_off(t, 8 * q, S::K1), bf16x2(hv[0], hv[1]), bf16x2(hv[2], hv[3]), bf16x2(hv[4], hv[5]),
+                 bf16x2(hv[6], hv[7]));
+  }
+  const unsigned char* w1 = wl;
+  const unsigned char* w2 = wl + S::W1;
+  const unsigned char* w3 = w2 + S::W2;
+  if (!tc_run(G, H, w1, S::K1, tc_idesc_bf16(128, 64))) return false;
+  tc_hidden_epilogue(G.tacc, U, t);
+  tc_fence_before();
+  if (!tc_run(G, U, w2, kTcK2, tc_idesc_bf16(128, 64))) return false;
+  tc_hidden_epilogue(G.tacc, U, t);
+  tc_fence_before();
+  if (!tc_run(G, U, w3, kTcK2, tc_idesc_bf16(128, S::N3))) return false;
+  float o[S::N3];
+  if constexpr (S::N3 == 16) {
+    tc_ld16(G.tacc, o);
+  } else {
+    tc_ld32(G.tacc, o);
+  }
+  tc_fence_before();
+  // pair m = (s_m, t_m) moves axis 2m + 1 - PAR
+#pragma unroll
+  for (int m = 0; m < DMAX / 2 + 1; ++m) {
+    const int k = 2 * m + 1 - PAR;
+    if (k < DMAX && 2 * m + 1 < S::N3 && m < L.b) {
+      const float s = flow_soft_clamp(o[2 * m]), tt = o[2 * m + 1];
+      if (dir > 0) {
+        z[k] = fmaf(z[k], __expf(s), tt);
+        ld += s;
+      } else {
+        z[k] = (z[k] - tt) * __expf(-s);
+        ld -= s;
+      }
+    }
+  }
+  return true;
+}
+
+template <int DMAX>
+__global__ void __launch_bounds__(kTcThreads, 1) flow_apply_tc_kernel(const __grid_constant__ FlowArgs fa, int dir,
+                                                                      const float* __restrict__ xin,
+                                                                      float* __restrict__ xout,
+                                                                      float* __restrict__ logdet, int64_t n) {
+  using S = TcShape<DMAX>;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int warp = threadIdx.x >> 5;
+  uint64_t* mbars = reinterpret_cast<uint64_t*>(sm + S::misc);
+  int* aborts = reinterpret_cast<int*>(sm + S::misc + 8 * kTcGroups);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::misc + 12 * kTcGroups);
+  tc_stage_weights<DMAX>(fa, sm);
+  if (warp == 0) tc_alloc(tslot, kTcColsPerGroup * kTcGroups);
+  if (threadIdx.x == 0) {
+    for (int g = 0; g < kTcGroups; ++g) {
+      mbar_init(mbars + g, 1);
+      aborts[g] = 0;
+    }
+    mbar_fence_init();
+  }
+  tc_fence_proxy();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+
+  TcGroup G;
+  G.id = threadIdx.x >> 7;
+  G.t = threadIdx.x & 127;
+  G.tacc = tbase + (uint32_t)(G.id * kTcColsPerGroup) + ((uint32_t)((warp & 3) * 32) << 16);
+  G.mbar = mbars + G.id;
+  G.abort = aborts + G.id;
+  G.phase = 0;
+  unsigned char* H = sm + S::weights + G.id * S::group;
+  unsigned char* U = H + S::H;
+  float* stg = reinterpret_cast<float*>(U);
+  const int d = fa.d, zld = d | 1, t = G.t;
+  const float inv_d = 1.0f / (float)d;
+  const int64_t ntiles = (n + 127) / 128;
+
+  for (int64_t tile = (int64_t)blockIdx.x * kTcGroups + G.id; tile < ntiles && !*G.abort;
+       tile += (int64_t)gridDim.x * kTcGroups) {
+    const int64_t r0 = tile * 128;
+    const int rows = (int)min((int64_t)128, n - r0);
+    // the tile's x, coalesced, into rows of stride zld (odd: conflict-free row reads)
+    for (int i = t; i < 128 * d; i += 128) {
+      const int r = (int)(((float)i + 0.5f) * inv_d), k = i - r * d;
+      stg[r * zld + k] = r < rows ? xin[r0 * d + i] : 0.5f;
+    }
+    wg_bar(1 + G.id);
+    float z[DMAX];
+    float ld = 0.0f;
+#pragma unroll
+    for (int k = 0; k < DMAX; ++k) {
+      z[k] = 0.0f;
+      if (k < d) {
+        z[k] = flow_logit(stg[t * zld + k]);
+        ld -= flow_log_sig_prime(z[k]);
+      }
+    }
+    wg_bar(1 + G.id);
+    // the bias block of U: ones in columns 64-66, zeros in 67-79
+    st_shared_v4(U + tc_off(t, kFlowHidden, kTcK2), 0x3F803F80u, 0x00003F80u, 0u, 0u);
+    st_shared_v4(U + tc_off(t, kFlowHidden + 8, kTcK2), 0u, 0u, 0u, 0u);
+    bool ok = true;
+    for (int i = 0; i < kFlowLayers && ok; ++i) {
+      const int l = dir > 0 ? i : kFlowLayers - 1 - i;
+      const unsigned char* wl = sm + l * S::layer;
+      ok = (l & 1) ? tc_layer<DMAX, 1>(fa.lay[l], wl, H, U, G, dir, z, ld)
+                   : tc_layer<DMAX, 0>(fa.lay[l], wl, H, U, G, dir, z, ld);
+    }
+    if (!ok) break;
+#pragma unroll
+    for (int k = 0; k < DMAX; ++k)
+      if (k < d) {
+        ld += flow_log_sig_prime(z[k]);
+        stg[t * zld + k] = flow_sigmoid(z[k]);
+      }
+    if (t < rows) logdet[r0 + t] = ld;
+    wg_bar(1 + G.id);
+    for (int i = t; i < rows * d; i += 128) {
+      const int r = (int)(((float)i + 0.5f) * inv_d), k = i - r * d;
+      xout[r0 * d + i] = stg[r * zld + k];
+    }
+    wg_bar(1 + G.id);
+  }
+  // a warpgroup that gave up waits once more for its MMAs before the columns are freed
+  if (G.t == 0 && *G.abort) mbar_wait(G.mbar, G.phase ^ 1u, kTcWaitPolls);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tc_dealloc(tbase, kTcColsPerGroup * kTcGroups);
+}
+
+int num_sms_tc() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return n;
+}
+
+template <int DMAX>
+int launch_apply_tc(const FlowArgs& fa, int dir, const float* xin, float* xout, float* logdet, int64_t n,
+                    cudaStream_t s) {
+  using S = TcShape<DMAX>;
+  auto k = flow_apply_tc_kernel<DMAX>;
+  VG_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::total));
+  const int64_t ntiles = (n + 127) / 128;
+  const int sms = num_sms_tc();
+  if (sms < 1) return VEGAS_ECUDA;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(sms, (ntiles + kTcGroups - 1) / kTcGroups));
+  k<<<grid, kTcThreads, S::total, s>>>(fa, dir, xin, xout, logdet, n);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+
+int flow_apply(int d, int direction, const float* d_params, const float* d_xin, float* d_xout, float* d_logdet,
+               int64_t n, cudaStream_t s) {
+  FlowArgs fa{};
+  if (flow_layout(d, fa) != VEGAS_OK) return VEGAS_EINVAL;
+  if (n == 0) return VEGAS_OK;
+  fa.params = d_params;
+  const int dir = direction == VEGAS_FLOW_NORMALISE ? 1 : -1;
+  return d <= 16 ? launch_apply_tc<16>(fa, dir, d_xin, d_xout, d_logdet, n, s)
+                 : launch_apply_tc<32>(fa, dir, d_xin, d_xout, d_logdet, n, s);
+}
+
+int flow_tc_status(bool reset) {
+  int v = 0;
+  VG_CHECK(cudaMemcpyFromSymbol(&v, g_flow_tc_status, sizeof(int)));
+  if (reset && v) {
+    const int zero = 0;
+    VG_CHECK(cudaMemcpyToSymbol(g_flow_tc_status, &zero, sizeof(int)));
+  }
+  return (v & 4) ? VEGAS_ETIMEOUT : VEGAS_OK;
+}
+
+}  // namespace vg

@@ -122,6 +122,8 @@ int dmax_for(int d);
 // learned proposal (vegas_flow.cu)
 int flow_apply(int d, int direction, const float* d_params, const float* d_xin, float* d_xout, float* d_logdet,
                int64_t n, cudaStream_t s);
+// VEGAS_ETIMEOUT when a bounded wait of the tensor-core transform ran out since the last reset
+int flow_tc_status(bool reset);
 int flow_eval(int integrand, int d, const double* d_params, int64_t nparams, const float* X, const float* logdet,
               float* values, int64_t n, cudaStream_t s);
 // training set of an iteration: every kFloorPeriod-th row a uniform point when lambda > 0

@@ -102,6 +102,7 @@ def _load():
         "vegas_set_flow_training": ([P, i32, i32, i32, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float], i32),
         "vegas_get_flow": ([P, P, i64, P], i32),
         "vegas_flow_apply": ([i32, i32, P, P, P, P, i64, P], i32),
+        "vegas_flow_check": ([P], i32),
         "vegas_flow_grad_scratch_bytes": ([i32, i64], sz),
         "vegas_flow_grad": ([i32, P, P, P, i64, P, P, P, sz, P], i32),
         "vegas_flow_adam": ([i64, P, P, P, P, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
@@ -404,6 +405,11 @@ def flow_apply(dim, direction, params, x_in, x_out, logdet, stream=None):
     """vegas_flow_apply: x_in / x_out [n][dim], logdet [n], params [flow_param_count(dim)]"""
     _check(lib.vegas_flow_apply(dim, direction, _ptr(params), _ptr(x_in), _ptr(x_out), _ptr(logdet),
                                 x_in.shape[0], _stream_ptr(stream)), "vegas_flow_apply")
+
+
+def flow_check(stream=None):
+    """vegas_flow_check: synchronise and raise if a bounded wait of an earlier flow_apply ran out"""
+    _check(lib.vegas_flow_check(_stream_ptr(stream)), "vegas_flow_check")
 
 
 def flow_grad_scratch_bytes(dim, n):
