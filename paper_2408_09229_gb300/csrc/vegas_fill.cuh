@@ -539,6 +539,7 @@ __device__ __forceinline__ float stream_point_eval(const FillArgs& a, const uint
     const uint4 r = philox_rk(make_uint4(jlo, jhi, a.iter, (a.pid << 16) | (uint32_t)g), rk0, rk1);
     uint32_t word = 0u, w16a = 0u, w16b = 0u;
     float den = 1.0f;
+    float xv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     uint32_t dig = 0u;
 #pragma unroll
     for (int gg = 0; gg < DMAX / 4; ++gg)
@@ -560,7 +561,7 @@ __device__ __forceinline__ float stream_point_eval(const FillArgs& a, const uint
         word |= (uint32_t)i << (8 * q);
         if (q < 2) w16a |= (uint32_t)i << (16 * q);
         else w16b |= (uint32_t)i << (16 * (q - 2));
-        if (xout) xout[k] = x;
+        xv[q] = x;
         if constexpr (ID == VEGAS_GAUSS_SUM) {
           const float4* m4 = reinterpret_cast<const float4*>(muT + k * KP);
 #pragma unroll
@@ -590,6 +591,15 @@ __device__ __forceinline__ float stream_point_eval(const FillArgs& a, const uint
         } else if constexpr (ID == VEGAS_MOROKOFF_CAFLISCH) {
           prod *= powf(x, s1);
         }
+      }
+    }
+    if (xout) {  // the point's four coordinates: one 16-byte store when rows are 16-byte aligned
+      if ((d & 3) == 0) {
+        *reinterpret_cast<float4*>(xout + 4 * g) = make_float4(xv[0], xv[1], xv[2], xv[3]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (4 * g + q < d) xout[4 * g + q] = xv[q];
       }
     }
     if (binw_col) {
@@ -865,9 +875,18 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
         T J;
         make_point<T, DMAX, EXACT>(a, rk0, rk1, cb, j0 + jl, tab, x, bin, J, st.J0);
         if constexpr (ID == kIntegrandPoints) {  // the points only, for an outside evaluation
+          float* xo = a.points_out + (j0 + jl) * d;
+          if ((d & 3) == 0) {  // 16-byte aligned rows
 #pragma unroll
-          for (int k = 0; k < DMAX; ++k)
-            if (k < d) a.points_out[(j0 + jl) * d + k] = (float)x[k];
+            for (int k = 0; k < DMAX; k += 4)
+              if (k < d)
+                *reinterpret_cast<float4*>(xo + k) =
+                    make_float4((float)x[k], (float)x[k + 1], (float)x[k + 2], (float)x[k + 3]);
+          } else {
+#pragma unroll
+            for (int k = 0; k < DMAX; ++k)
+              if (k < d) xo[k] = (float)x[k];
+          }
           continue;
         }
         T f;

@@ -2,12 +2,12 @@
 // on the fifth-generation tensor cores: tcgen05.mma with the accumulators in
 // tensor memory.  The flow is defined in vegas_flow.cuh.
 //
-// A CTA of kTcGroups warpgroups stays resident on one SM; each warpgroup
-// transforms its own tile of 128 points, so while one waits for its MMAs the
-// others run their element-wise work.  Thread t of a warpgroup owns point t of
+// A CTA of G warpgroups (6 up to 16 axes, 4 above) stays resident on one SM;
+// each warpgroup transforms its own tile of 128 points, so while one waits for
+// its MMAs the others run their element-wise work.  Thread t of a warpgroup owns point t of
 // the tile: it keeps the point's z in registers and reads row t of every
 // accumulator (tensor-memory lane t).  Per coupling layer:
-//   H  = [bf16(z[A]) | 1 1 1 | 0]           128 x K1   (shared memory)
+//   H  = [bf16(z[A]) | 1 1 1 | 0]           128 x K1   (the first K1 columns of U)
 //   D  = H W1'^T                            128 x 64   (tensor memory)
 //   U  = [bf16(relu D) | 1 1 1 | 0]          128 x 80   (shared memory)
 //   D  = U W2'^T;  U = [bf16(relu D) | ...]
@@ -16,8 +16,8 @@
 // the bias in three extra columns as a bf16 triple (hi, mid, lo) with
 // hi + mid + lo = b to 2^-24 relative, multiplied by the three ones-columns
 // of H and U: the bias enters the FP32 accumulation at full FP32 precision.
-// One thread of the warpgroup issues the MMAs and waits (bounded) on the
-// warpgroup's mbarrier; the others wait at the warpgroup's named barrier.
+// One thread of the warpgroup issues the MMAs; every thread waits (bounded)
+// on the warpgroup's mbarrier, which the MMAs' completion arrives on.
 #include <algorithm>
 
 #include "vegas_flow.cuh"
@@ -28,8 +28,6 @@ namespace vg {
 
 namespace {
 
-constexpr int kTcGroups = 4;                   // warpgroups (tiles in flight) per CTA
-constexpr int kTcThreads = 128 * kTcGroups;
 constexpr int kTcK2 = kFlowHidden + 16;        // K of the second and third GEMMs: 64 + bias block
 constexpr int kTcColsPerGroup = 64;            // tensor-memory columns of one warpgroup's accumulator
 constexpr int kTcWaitPolls = 1 << 22;          // bound of every mbarrier wait
@@ -39,16 +37,20 @@ __device__ int g_flow_tc_status;
 
 template <int DMAX>
 struct TcShape {
+  static constexpr int G = DMAX <= 16 ? 6 : 4;  // warpgroups a CTA (shared memory and registers)
+  static constexpr int threads = 128 * G;
+  static constexpr uint32_t tmem_cols = G * kTcColsPerGroup <= 256 ? 256 : 512;  // a power of two
   static constexpr int K1 = DMAX;   // K of the first GEMM: a <= DMAX/2 inputs + 3 bias columns, padded
   static constexpr int N3 = DMAX;   // N of the third GEMM: 2 b <= DMAX outputs
   static constexpr uint32_t W1 = 64 * K1 * 2, W2 = 64 * kTcK2 * 2, W3 = N3 * kTcK2 * 2;
   static constexpr uint32_t layer = W1 + W2 + W3;
   static constexpr uint32_t weights = kFlowLayers * layer;
-  static constexpr uint32_t H = 128 * K1 * 2, U = 128 * kTcK2 * 2;  // U doubles as the x staging area
-  static constexpr uint32_t group = H + U;
-  static constexpr uint32_t misc = weights + kTcGroups * group;
-  static constexpr uint32_t total = misc + 8 * kTcGroups + 4 * kTcGroups + 16;
+  static constexpr uint32_t U = 128 * kTcK2 * 2;  // activations; also H (first K1 columns) and the x staging
+  static constexpr uint32_t misc = weights + G * U;
+  static constexpr uint32_t total = misc + 8 * G + 4 * G + 16;
   static_assert(128 * (DMAX + 1) * 4 <= U, "staging fits in U");
+  static_assert(K1 <= kFlowHidden, "H fits in U's hidden columns");
+  static_assert(total <= 232448, "shared memory of one CTA");
 };
 
 __device__ __forceinline__ void bias3(float b, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
@@ -62,6 +64,7 @@ __device__ __forceinline__ void bias3(float b, __nv_bfloat16& h, __nv_bfloat16& 
 template <int DMAX>
 __device__ void tc_stage_weights(const FlowArgs& fa, unsigned char* sm) {
   using S = TcShape<DMAX>;
+  constexpr int kTcThreads = S::threads;
   const float* P = fa.params;
   for (int l = 0; l < kFlowLayers; ++l) {
     const FlowLayer& L = fa.lay[l];
@@ -116,62 +119,74 @@ __device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
   return d;
 }
 
-// row t of U from the 64 accumulator columns: ReLU, bf16
+// row t of U from the 64 accumulator columns: ReLU, bf16 (16 columns at a time: registers)
 __device__ __forceinline__ void tc_hidden_epilogue(uint32_t tacc, unsigned char* U, int t) {
 #pragma unroll
-  for (int cb = 0; cb < 64; cb += 32) {
-    float v[32];
-    tc_ld32(tacc + cb, v);
+  for (int cb = 0; cb < 64; cb += 16) {
+    float v[16];
+    tc_ld16(tacc + cb, v);
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < 2; ++q)
       st_shared_v4(U + tc_off(t, cb + 8 * q, kTcK2), bf16x2_relu(v[8 * q], v[8 * q + 1]),
                    bf16x2_relu(v[8 * q + 2], v[8 * q + 3]), bf16x2_relu(v[8 * q + 4], v[8 * q + 5]),
                    bf16x2_relu(v[8 * q + 6], v[8 * q + 7]));
   }
 }
 
-// the MMAs of one GEMM, issued by one thread: D = A B^T over K / 16 k-steps
-__device__ __forceinline__ void tc_gemm(uint32_t tacc, const unsigned char* A, const unsigned char* B, int K,
+// the MMAs of one GEMM, issued by one thread: D = A B^T over K / 16 k-steps;
+// A is a tile of KA columns (its row-group stride), B one of K columns
+__device__ __forceinline__ void tc_gemm(uint32_t tacc, const unsigned char* A, const unsigned char* B, int KA, int K,
                                         uint32_t idesc) {
-  const uint32_t a0 = tc_smem_u32(A), b0 = tc_smem_u32(B), sbo = (uint32_t)K * 16;
+  const uint32_t a0 = tc_smem_u32(A), b0 = tc_smem_u32(B);
   for (int s = 0; s < K / 16; ++s)
-    tc_mma(tacc, tc_desc(a0 + 256 * s, kTcLbo, sbo), tc_desc(b0 + 256 * s, kTcLbo, sbo), idesc, s > 0);
+    tc_mma(tacc, tc_desc(a0 + 256 * s, kTcLbo, (uint32_t)KA * 16), tc_desc(b0 + 256 * s, kTcLbo, (uint32_t)K * 16),
+           idesc, s > 0);
 }
 
 struct TcGroup {
   int id, t;             // warpgroup, thread in it
   uint32_t tacc;         // its accumulator columns, lane base of this warp
   uint64_t* mbar;
-  volatile int* abort;
   uint32_t phase;
+  bool failed;           // this thread's last wait ran out
 };
 
-// issue (thread 0), wait (thread 0, bounded), then the whole warpgroup may
-// read the accumulator; false when the wait ran out
-__device__ __forceinline__ bool tc_run(TcGroup& G, const unsigned char* A, const unsigned char* B, int K,
+// the warpgroup's barrier; true on every thread when any thread arrived with `bad`
+__device__ __forceinline__ bool wg_bar_any(int id, bool bad) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbarrier.red.or.pred q, %2, 128, p;\nselp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)bad), "r"(id)
+      : "memory");
+  return r != 0;
+}
+
+// H or U written: thread 0 issues the GEMM, every thread waits (bounded) for
+// its completion; false on every thread of the warpgroup once any wait ran out
+__device__ __forceinline__ bool tc_run(TcGroup& G, const unsigned char* A, const unsigned char* B, int KA, int K,
                                        uint32_t idesc) {
   tc_fence_proxy();
   tc_fence_before();
-  wg_bar(1 + G.id);
+  if (wg_bar_any(1 + G.id, G.failed)) return false;
   if (G.t == 0) {
     tc_fence_after();
-    tc_gemm(G.tacc & 0xFFFFu, A, B, K, idesc);  // thread 0 is in lane quarter 0
+    tc_gemm(G.tacc & 0xFFFFu, A, B, KA, K, idesc);  // thread 0 is in lane quarter 0
     tc_commit(G.mbar);
-    if (!mbar_wait(G.mbar, G.phase, kTcWaitPolls)) {
-      *G.abort = 1;
-      atomicOr(&g_flow_tc_status, 4);
-    }
+  }
+  if (!mbar_wait(G.mbar, G.phase, kTcWaitPolls)) {
+    G.failed = true;
+    atomicOr(&g_flow_tc_status, 4);
   }
   G.phase ^= 1u;
-  wg_bar(1 + G.id);
   tc_fence_after();
-  return *G.abort == 0;
+  return true;
 }
 
 // one coupling layer on the warpgroup's tile; PAR = l mod 2
 template <int DMAX, int PAR>
-__device__ __forceinline__ bool tc_layer(const FlowLayer& L, const unsigned char* wl, unsigned char* H,
-                                         unsigned char* U, TcGroup& G, int dir, float (&z)[DMAX], float& ld) {
+__device__ __forceinline__ bool tc_layer(const FlowLayer& L, const unsigned char* wl, unsigned char* U, TcGroup& G,
+                                         int dir, float (&z)[DMAX], float& ld) {
   using S = TcShape<DMAX>;
   const int t = G.t;
   // H row t: the conditioning axes 2c + PAR, then the three ones of the bias
@@ -186,19 +201,19 @@ __device__ __forceinline__ bool tc_layer(const FlowLayer& L, const unsigned char
       else if (c >= L.a && c < L.a + 3) v = 1.0f;
       hv[e] = v;
     }
-    st_shared_v4(H + tc_off(t, 8 * q, S::K1), bf16x2(hv[0], hv[1]), bf16x2(hv[2], hv[3]), bf16x2(hv[4], hv[5]),
+    st_shared_v4(U + tc_off(t, 8 * q, kTcK2), bf16x2(hv[0], hv[1]), bf16x2(hv[2], hv[3]), bf16x2(hv[4], hv[5]),
                  bf16x2(hv[6], hv[7]));
   }
   const unsigned char* w1 = wl;
   const unsigned char* w2 = wl + S::W1;
   const unsigned char* w3 = w2 + S::W2;
-  if (!tc_run(G, H, w1, S::K1, tc_idesc_bf16(128, 64))) return false;
+  if (!tc_run(G, U, w1, kTcK2, S::K1, tc_idesc_bf16(128, 64))) return false;
   tc_hidden_epilogue(G.tacc, U, t);
   tc_fence_before();
-  if (!tc_run(G, U, w2, kTcK2, tc_idesc_bf16(128, 64))) return false;
+  if (!tc_run(G, U, w2, kTcK2, kTcK2, tc_idesc_bf16(128, 64))) return false;
   tc_hidden_epilogue(G.tacc, U, t);
   tc_fence_before();
-  if (!tc_run(G, U, w3, kTcK2, tc_idesc_bf16(128, S::N3))) return false;
+  if (!tc_run(G, U, w3, kTcK2, kTcK2, tc_idesc_bf16(128, S::N3))) return false;
   float o[S::N3];
   if constexpr (S::N3 == 16) {
     tc_ld16(G.tacc, o);
@@ -225,23 +240,18 @@ __device__ __forceinline__ bool tc_layer(const FlowLayer& L, const unsigned char
 }
 
 template <int DMAX>
-__global__ void __launch_bounds__(kTcThreads, 1) flow_apply_tc_kernel(const __grid_constant__ FlowArgs fa, int dir,
-                                                                      const float* __restrict__ xin,
-                                                                      float* __restrict__ xout,
-                                                                      float* __restrict__ logdet, int64_t n) {
+__global__ void __launch_bounds__(TcShape<DMAX>::threads, 1)
+    flow_apply_tc_kernel(const __grid_constant__ FlowArgs fa, int dir, const float* __restrict__ xin,
+                         float* __restrict__ xout, float* __restrict__ logdet, int64_t n) {
   using S = TcShape<DMAX>;
   extern __shared__ __align__(1024) unsigned char sm[];
   const int warp = threadIdx.x >> 5;
   uint64_t* mbars = reinterpret_cast<uint64_t*>(sm + S::misc);
-  int* aborts = reinterpret_cast<int*>(sm + S::misc + 8 * kTcGroups);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::misc + 12 * kTcGroups);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::misc + 8 * S::G);
   tc_stage_weights<DMAX>(fa, sm);
-  if (warp == 0) tc_alloc(tslot, kTcColsPerGroup * kTcGroups);
+  if (warp == 0) tc_alloc(tslot, S::tmem_cols);
   if (threadIdx.x == 0) {
-    for (int g = 0; g < kTcGroups; ++g) {
-      mbar_init(mbars + g, 1);
-      aborts[g] = 0;
-    }
+    for (int g = 0; g < S::G; ++g) mbar_init(mbars + g, 1);
     mbar_fence_init();
   }
   tc_fence_proxy();
@@ -255,17 +265,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) flow_apply_tc_kernel(const __gr
   G.t = threadIdx.x & 127;
   G.tacc = tbase + (uint32_t)(G.id * kTcColsPerGroup) + ((uint32_t)((warp & 3) * 32) << 16);
   G.mbar = mbars + G.id;
-  G.abort = aborts + G.id;
   G.phase = 0;
-  unsigned char* H = sm + S::weights + G.id * S::group;
-  unsigned char* U = H + S::H;
+  G.failed = false;
+  unsigned char* U = sm + S::weights + G.id * S::U;
   float* stg = reinterpret_cast<float*>(U);
   const int d = fa.d, zld = d | 1, t = G.t;
   const float inv_d = 1.0f / (float)d;
   const int64_t ntiles = (n + 127) / 128;
 
-  for (int64_t tile = (int64_t)blockIdx.x * kTcGroups + G.id; tile < ntiles && !*G.abort;
-       tile += (int64_t)gridDim.x * kTcGroups) {
+  for (int64_t tile = (int64_t)blockIdx.x * S::G + G.id; tile < ntiles; tile += (int64_t)gridDim.x * S::G) {
     const int64_t r0 = tile * 128;
     const int rows = (int)min((int64_t)128, n - r0);
     // the tile's x, coalesced, into rows of stride zld (odd: conflict-free row reads)
@@ -292,10 +300,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) flow_apply_tc_kernel(const __gr
     for (int i = 0; i < kFlowLayers && ok; ++i) {
       const int l = dir > 0 ? i : kFlowLayers - 1 - i;
       const unsigned char* wl = sm + l * S::layer;
-      ok = (l & 1) ? tc_layer<DMAX, 1>(fa.lay[l], wl, H, U, G, dir, z, ld)
-                   : tc_layer<DMAX, 0>(fa.lay[l], wl, H, U, G, dir, z, ld);
+      ok = (l & 1) ? tc_layer<DMAX, 1>(fa.lay[l], wl, U, G, dir, z, ld)
+                   : tc_layer<DMAX, 0>(fa.lay[l], wl, U, G, dir, z, ld);
     }
-    if (!ok) break;
+    // the last wait's outcome, agreed by the whole warpgroup
+    if (!ok || wg_bar_any(1 + G.id, G.failed)) break;
 #pragma unroll
     for (int k = 0; k < DMAX; ++k)
       if (k < d) {
@@ -311,11 +320,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) flow_apply_tc_kernel(const __gr
     wg_bar(1 + G.id);
   }
   // a warpgroup that gave up waits once more for its MMAs before the columns are freed
-  if (G.t == 0 && *G.abort) mbar_wait(G.mbar, G.phase ^ 1u, kTcWaitPolls);
+  if (G.failed) mbar_wait(G.mbar, G.phase ^ 1u, kTcWaitPolls);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tc_dealloc(tbase, kTcColsPerGroup * kTcGroups);
+  if (warp == 0) tc_dealloc(tbase, S::tmem_cols);
 }
 
 int num_sms_tc() {
@@ -334,8 +343,8 @@ int launch_apply_tc(const FlowArgs& fa, int dir, const float* xin, float* xout, 
   const int64_t ntiles = (n + 127) / 128;
   const int sms = num_sms_tc();
   if (sms < 1) return VEGAS_ECUDA;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(sms, (ntiles + kTcGroups - 1) / kTcGroups));
-  k<<<grid, kTcThreads, S::total, s>>>(fa, dir, xin, xout, logdet, n);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(sms, (ntiles + S::G - 1) / S::G));
+  k<<<grid, S::threads, S::total, s>>>(fa, dir, xin, xout, logdet, n);
   return cuda_status(cudaGetLastError());
 }
 
