@@ -113,10 +113,15 @@ __device__ __forceinline__ float flow_log_sig_prime(float z) {
   const float az = fabsf(z);
   return -az - 2.0f * __logf(1.0f + __expf(-az));
 }
-__device__ __forceinline__ float flow_sigmoid(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
-// s = S tanh(o / S) = S (1 - 2 / (1 + e^(2 o / S))), with the hardware exp
+// sigmoid from e^-|z| <= 1: finite for every z
+__device__ __forceinline__ float flow_sigmoid(float z) {
+  const float e = __expf(-fabsf(z)), r = __frcp_rn(1.0f + e);
+  return z >= 0.0f ? r : e * r;
+}
+// s = S tanh(o / S) = sign(o) S (1 - 2 e / (1 + e)), e = e^(-2 |o| / S) <= 1: finite for every o
 __device__ __forceinline__ float flow_soft_clamp(float o) {
-  return kFlowSClamp - __fdividef(2.0f * kFlowSClamp, 1.0f + __expf(o * (2.0f / kFlowSClamp)));
+  const float e = __expf(fabsf(o) * (-2.0f / kFlowSClamp));
+  return copysignf(kFlowSClamp * __fdividef(1.0f - e, 1.0f + e), o);
 }
 
 // Stage every layer's weights in shared memory as bf16 (biases FP32); zero

@@ -276,10 +276,21 @@ __global__ void __launch_bounds__(TcShape<DMAX>::threads, 1)
   for (int64_t tile = (int64_t)blockIdx.x * S::G + G.id; tile < ntiles; tile += (int64_t)gridDim.x * S::G) {
     const int64_t r0 = tile * 128;
     const int rows = (int)min((int64_t)128, n - r0);
-    // the tile's x, coalesced, into rows of stride zld (odd: conflict-free row reads)
-    for (int i = t; i < 128 * d; i += 128) {
-      const int r = (int)(((float)i + 0.5f) * inv_d), k = i - r * d;
-      stg[r * zld + k] = r < rows ? xin[r0 * d + i] : 0.5f;
+    // the tile's x, coalesced, into rows of stride zld (odd: conflict-free row reads); all loads first
+    {
+      float xl[DMAX];
+#pragma unroll
+      for (int j = 0; j < DMAX; ++j) {
+        const int i = t + 128 * j;
+        xl[j] = (j < d && i < rows * d) ? xin[r0 * d + i] : 0.5f;
+      }
+#pragma unroll
+      for (int j = 0; j < DMAX; ++j)
+        if (j < d) {
+          const int i = t + 128 * j;
+          const int r = (int)(((float)i + 0.5f) * inv_d), k = i - r * d;
+          stg[r * zld + k] = xl[j];
+        }
     }
     wg_bar(1 + G.id);
     float z[DMAX];

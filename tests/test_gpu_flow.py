@@ -90,6 +90,22 @@ def test_apply_many_tiles_and_check(V):
     assert np.median(el) < 2e-4 and np.quantile(el, 0.9999) < 5e-2, (np.median(el), el.max())
 
 
+@pytest.mark.parametrize("direction", ["normalise", "sample"])
+def test_apply_extreme_inputs_stay_finite(V, direction):
+    """exact 0, denormal-sized and 1 - 2^-24 coordinates through a strongly scaled flow: the logit clamp,
+    the soft clamp and the sigmoid keep x in [0, 1] and the log-determinant finite"""
+    d = 12
+    th = W.flow_params(d, seed=13, out_scale=2.0)
+    rng = np.random.default_rng(14)
+    x = rng.uniform(0.0, 1.0, (4096, d)).astype(np.float32)
+    specials = np.array([0.0, 1e-30, 2.0 ** -24, 0.5, 1.0 - 2.0 ** -24], dtype=np.float32)
+    x[::7] = rng.choice(specials, size=x[::7].shape)
+    dirn = V.FLOW_NORMALISE if direction == "normalise" else V.FLOW_SAMPLE
+    gx, gl = gpu_apply(V, d, dirn, th, x)
+    assert np.isfinite(gx).all() and np.isfinite(gl).all()
+    assert gx.min() >= 0.0 and gx.max() <= 1.0
+
+
 def test_identity_flow_on_gpu(V):
     d = 7
     th = W.flow_params(d, seed=1, out_scale=0.0)
