@@ -115,7 +115,7 @@ __device__ __forceinline__ float flow_log_sig_prime(float z) {
 }
 // sigmoid from e^-|z| <= 1: finite for every z
 __device__ __forceinline__ float flow_sigmoid(float z) {
-  const float e = __expf(-fabsf(z)), r = __frcp_rn(1.0f + e);
+  const float e = __expf(-fabsf(z)), r = __fdividef(1.0f, 1.0f + e);  // 1 + e in [1, 2]
   return z >= 0.0f ? r : e * r;
 }
 // s = S tanh(o / S) = sign(o) S (1 - 2 e / (1 + e)), e = e^(-2 |o| / S) <= 1: finite for every o

@@ -137,10 +137,11 @@ __device__ __forceinline__ void tc_hidden_epilogue(uint32_t tacc, unsigned char*
 // A is a tile of KA columns (its row-group stride), B one of K columns
 __device__ __forceinline__ void tc_gemm(uint32_t tacc, const unsigned char* A, const unsigned char* B, int KA, int K,
                                         uint32_t idesc) {
-  const uint32_t a0 = tc_smem_u32(A), b0 = tc_smem_u32(B);
-  for (int s = 0; s < K / 16; ++s)
-    tc_mma(tacc, tc_desc(a0 + 256 * s, kTcLbo, (uint32_t)KA * 16), tc_desc(b0 + 256 * s, kTcLbo, (uint32_t)K * 16),
-           idesc, s > 0);
+  // a k-step moves both start addresses by 256 bytes: 16 in the descriptors' address field, which cannot
+  // carry out of its 14 bits (shared addresses stay below 2^18)
+  const uint64_t ad = tc_desc(tc_smem_u32(A), kTcLbo, (uint32_t)KA * 16);
+  const uint64_t bd = tc_desc(tc_smem_u32(B), kTcLbo, (uint32_t)K * 16);
+  for (int s = 0; s < K / 16; ++s) tc_mma(tacc, ad + 16u * s, bd + 16u * s, idesc, s > 0);
 }
 
 struct TcGroup {

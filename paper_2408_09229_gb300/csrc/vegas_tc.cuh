@@ -94,22 +94,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, int l
   return false;
 }
 
-// the same with a suspend-time hint: a poll sleeps until the phase completes
-// or about 1 ms passes, so a waiting warp issues no instructions meanwhile
-__device__ __forceinline__ bool mbar_wait_hint(uint64_t* mbar, uint32_t parity, int limit) {
-  const uint32_t a = tc_smem_u32(mbar);
-  for (int it = 0; it < limit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(a), "r"(parity), "r"(1000000u)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
 // 16 / 32 consecutive FP32 columns of this thread's row
 __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];

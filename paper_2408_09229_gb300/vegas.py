@@ -401,8 +401,19 @@ def flow_param_count(dim):
     return lib.vegas_flow_param_count(dim)
 
 
+def _f32_device(name, *tensors):
+    """the flow entry points take contiguous FP32 device buffers: refuse anything else before the call"""
+    for t in tensors:
+        if t is None:
+            continue
+        if not (getattr(t, "is_cuda", False) and str(t.dtype) == "torch.float32" and t.is_contiguous()):
+            raise TypeError(f"{name}: buffers must be contiguous float32 CUDA tensors, got "
+                            f"{getattr(t, 'dtype', type(t))} on {getattr(t, 'device', '?')}")
+
+
 def flow_apply(dim, direction, params, x_in, x_out, logdet, stream=None):
     """vegas_flow_apply: x_in / x_out [n][dim], logdet [n], params [flow_param_count(dim)]"""
+    _f32_device("flow_apply", params, x_in, x_out, logdet)
     _check(lib.vegas_flow_apply(dim, direction, _ptr(params), _ptr(x_in), _ptr(x_out), _ptr(logdet),
                                 x_in.shape[0], _stream_ptr(stream)), "vegas_flow_apply")
 
@@ -418,11 +429,13 @@ def flow_grad_scratch_bytes(dim, n):
 
 def flow_grad(dim, params, x, w, grad, loss, scratch, stream=None):
     """vegas_flow_grad: the weighted negative log-likelihood of samples x [n][dim] with weights w [n]"""
+    _f32_device("flow_grad", params, x, w, grad, loss)
     _check(lib.vegas_flow_grad(dim, _ptr(params), _ptr(x), _ptr(w), x.shape[0], _ptr(grad), _ptr(loss),
                                _ptr(scratch), scratch.numel(), _stream_ptr(stream)), "vegas_flow_grad")
 
 
 def flow_adam(params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _f32_device("flow_adam", params, grad, m, v)
     _check(lib.vegas_flow_adam(params.numel(), _ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(step), lr, beta1,
                                beta2, eps, _stream_ptr(stream)), "vegas_flow_adam")
 

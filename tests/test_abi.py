@@ -55,3 +55,19 @@ def test_product_path_has_no_oracle_reference():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "oracle_vegas" not in text, f
+
+
+def test_flow_binding_refuses_wrong_buffers():
+    """the flow entry points read raw FP32 device memory: the binding refuses host or FP64 tensors before the
+    call instead of passing their bytes on"""
+    torch = __import__("pytest").importorskip("torch")
+    from paper_2408_09229_gb300 import vegas as V
+    d, n = 4, 8
+    p = torch.zeros(V.flow_param_count(d), dtype=torch.float64)
+    x = torch.zeros((n, d), dtype=torch.float32)
+    ld = torch.zeros(n, dtype=torch.float32)
+    import pytest
+    with pytest.raises(TypeError):
+        V.flow_apply(d, V.FLOW_SAMPLE, p, x, x, ld)
+    with pytest.raises(TypeError):
+        V.flow_adam(x, x, x, x, 1)
