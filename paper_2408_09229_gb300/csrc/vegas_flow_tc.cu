@@ -19,6 +19,7 @@
 // One thread of the warpgroup issues the MMAs; every thread waits (bounded)
 // on the warpgroup's mbarrier, which the MMAs' completion arrives on.
 #include <algorithm>
+#include <type_traits>
 
 #include "vegas_flow.cuh"
 #include "vegas_internal.h"
@@ -35,20 +36,25 @@ constexpr int kTcWaitPolls = 1 << 22;          // bound of every mbarrier wait
 // a module-wide status word: bit 2 is set when a bounded wait ran out
 __device__ int g_flow_tc_status;
 
-template <int DMAX>
+// The shapes for d = D axes (every D in 2..32 is its own instantiation: the
+// column selections, the moved axes and the row arithmetic of the staging are
+// then compile-time).
+template <int D>
 struct TcShape {
-  static constexpr int G = DMAX <= 16 ? 6 : 4;  // warpgroups a CTA (shared memory and registers)
+  static constexpr int G = D <= 16 ? 6 : 4;  // warpgroups a CTA (shared memory and registers)
   static constexpr int threads = 128 * G;
   static constexpr uint32_t tmem_cols = G * kTcColsPerGroup <= 256 ? 256 : 512;  // a power of two
-  static constexpr int K1 = DMAX;   // K of the first GEMM: a <= DMAX/2 inputs + 3 bias columns, padded
-  static constexpr int N3 = DMAX;   // N of the third GEMM: 2 b <= DMAX outputs
+  static constexpr int A0 = (D + 1) / 2;                // conditioning axes of even layers (the larger a)
+  static constexpr int K1 = A0 + 3 <= 16 ? 16 : 32;     // K of the first GEMM: a inputs + 3 bias columns
+  static constexpr int N3 = 2 * A0 <= 16 ? 16 : 32;     // N of the third GEMM: 2 b outputs, padded
+  static constexpr int ZLD = D | 1;                     // staging row stride (odd: conflict-free)
   static constexpr uint32_t W1 = 64 * K1 * 2, W2 = 64 * kTcK2 * 2, W3 = N3 * kTcK2 * 2;
   static constexpr uint32_t layer = W1 + W2 + W3;
   static constexpr uint32_t weights = kFlowLayers * layer;
   static constexpr uint32_t U = 128 * kTcK2 * 2;  // activations; also H (first K1 columns) and the x staging
   static constexpr uint32_t misc = weights + G * U;
   static constexpr uint32_t total = misc + 8 * G + 4 * G + 16;
-  static_assert(128 * (DMAX + 1) * 4 <= U, "staging fits in U");
+  static_assert(128 * ZLD * 4 <= U, "staging fits in U");
   static_assert(K1 <= kFlowHidden, "H fits in U's hidden columns");
   static_assert(total <= 232448, "shared memory of one CTA");
 };
@@ -61,9 +67,9 @@ __device__ __forceinline__ void bias3(float b, __nv_bfloat16& h, __nv_bfloat16& 
 }
 
 // weights of every layer in the core-matrix layout, biases in columns (k, k+1, k+2)
-template <int DMAX>
+template <int D>
 __device__ void tc_stage_weights(const FlowArgs& fa, unsigned char* sm) {
-  using S = TcShape<DMAX>;
+  using S = TcShape<D>;
   constexpr int kTcThreads = S::threads;
   const float* P = fa.params;
   for (int l = 0; l < kFlowLayers; ++l) {
@@ -185,10 +191,11 @@ __device__ __forceinline__ bool tc_run(TcGroup& G, const unsigned char* A, const
 }
 
 // one coupling layer on the warpgroup's tile; PAR = l mod 2
-template <int DMAX, int PAR>
-__device__ __forceinline__ bool tc_layer(const FlowLayer& L, const unsigned char* wl, unsigned char* U, TcGroup& G,
-                                         int dir, float (&z)[DMAX], float& ld) {
-  using S = TcShape<DMAX>;
+template <int D, int PAR>
+__device__ __forceinline__ bool tc_layer(const unsigned char* wl, unsigned char* U, TcGroup& G, int dir,
+                                         float (&z)[D], float& ld) {
+  using S = TcShape<D>;
+  constexpr int a = PAR == 0 ? (D + 1) / 2 : D / 2, b = D - a;  // conditioning and moved axes
   const int t = G.t;
   // H row t: the conditioning axes 2c + PAR, then the three ones of the bias
 #pragma unroll
@@ -196,11 +203,8 @@ __device__ __forceinline__ bool tc_layer(const FlowLayer& L, const unsigned char
     float hv[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-      const int c = 8 * q + e, k = 2 * c + PAR;
-      float v = 0.0f;
-      if (k < DMAX && c < L.a) v = z[k];
-      else if (c >= L.a && c < L.a + 3) v = 1.0f;
-      hv[e] = v;
+      const int c = 8 * q + e;
+      hv[e] = c < a ? z[2 * c + PAR] : (c < a + 3 ? 1.0f : 0.0f);
     }
     st_shared_v4(U + tc_off(t, 8 * q, kTcK2), bf16x2(hv[0], hv[1]), bf16x2(hv[2], hv[3]), bf16x2(hv[4], hv[5]),
                  bf16x2(hv[6], hv[7]));
@@ -224,9 +228,9 @@ __device__ __forceinline__ bool tc_layer(const FlowLayer& L, const unsigned char
   tc_fence_before();
   // pair m = (s_m, t_m) moves axis 2m + 1 - PAR
 #pragma unroll
-  for (int m = 0; m < DMAX / 2 + 1; ++m) {
+  for (int m = 0; m < b; ++m) {
     const int k = 2 * m + 1 - PAR;
-    if (k < DMAX && 2 * m + 1 < S::N3 && m < L.b) {
+    {
       const float s = flow_soft_clamp(o[2 * m]), tt = o[2 * m + 1];
       if (dir > 0) {
         z[k] = fmaf(z[k], __expf(s), tt);
@@ -240,16 +244,16 @@ __device__ __forceinline__ bool tc_layer(const FlowLayer& L, const unsigned char
   return true;
 }
 
-template <int DMAX>
-__global__ void __launch_bounds__(TcShape<DMAX>::threads, 1)
+template <int D>
+__global__ void __launch_bounds__(TcShape<D>::threads, 1)
     flow_apply_tc_kernel(const __grid_constant__ FlowArgs fa, int dir, const float* __restrict__ xin,
                          float* __restrict__ xout, float* __restrict__ logdet, int64_t n) {
-  using S = TcShape<DMAX>;
+  using S = TcShape<D>;
   extern __shared__ __align__(1024) unsigned char sm[];
   const int warp = threadIdx.x >> 5;
   uint64_t* mbars = reinterpret_cast<uint64_t*>(sm + S::misc);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::misc + 8 * S::G);
-  tc_stage_weights<DMAX>(fa, sm);
+  tc_stage_weights<D>(fa, sm);
   if (warp == 0) tc_alloc(tslot, S::tmem_cols);
   if (threadIdx.x == 0) {
     for (int g = 0; g < S::G; ++g) mbar_init(mbars + g, 1);
@@ -270,8 +274,8 @@ __global__ void __launch_bounds__(TcShape<DMAX>::threads, 1)
   G.failed = false;
   unsigned char* U = sm + S::weights + G.id * S::U;
   float* stg = reinterpret_cast<float*>(U);
-  const int d = fa.d, zld = d | 1, t = G.t;
-  const float inv_d = 1.0f / (float)d;
+  constexpr int zld = S::ZLD;
+  const int t = G.t;
   const int64_t ntiles = (n + 127) / 128;
 
   for (int64_t tile = (int64_t)blockIdx.x * S::G + G.id; tile < ntiles; tile += (int64_t)gridDim.x * S::G) {
@@ -279,30 +283,25 @@ __global__ void __launch_bounds__(TcShape<DMAX>::threads, 1)
     const int rows = (int)min((int64_t)128, n - r0);
     // the tile's x, coalesced, into rows of stride zld (odd: conflict-free row reads); all loads first
     {
-      float xl[DMAX];
+      float xl[D];
 #pragma unroll
-      for (int j = 0; j < DMAX; ++j) {
+      for (int j = 0; j < D; ++j) {
         const int i = t + 128 * j;
-        xl[j] = (j < d && i < rows * d) ? xin[r0 * d + i] : 0.5f;
+        xl[j] = i < rows * D ? xin[r0 * D + i] : 0.5f;
       }
 #pragma unroll
-      for (int j = 0; j < DMAX; ++j)
-        if (j < d) {
-          const int i = t + 128 * j;
-          const int r = (int)(((float)i + 0.5f) * inv_d), k = i - r * d;
-          stg[r * zld + k] = xl[j];
-        }
+      for (int j = 0; j < D; ++j) {
+        const int i = t + 128 * j;
+        stg[(i / D) * zld + i % D] = xl[j];
+      }
     }
     wg_bar(1 + G.id);
-    float z[DMAX];
+    float z[D];
     float ld = 0.0f;
 #pragma unroll
-    for (int k = 0; k < DMAX; ++k) {
-      z[k] = 0.0f;
-      if (k < d) {
-        z[k] = flow_logit(stg[t * zld + k]);
-        ld -= flow_log_sig_prime(z[k]);
-      }
+    for (int k = 0; k < D; ++k) {
+      z[k] = flow_logit(stg[t * zld + k]);
+      ld -= flow_log_sig_prime(z[k]);
     }
     wg_bar(1 + G.id);
     // the bias block of U: ones in columns 64-66, zeros in 67-79
@@ -312,22 +311,21 @@ __global__ void __launch_bounds__(TcShape<DMAX>::threads, 1)
     for (int i = 0; i < kFlowLayers && ok; ++i) {
       const int l = dir > 0 ? i : kFlowLayers - 1 - i;
       const unsigned char* wl = sm + l * S::layer;
-      ok = (l & 1) ? tc_layer<DMAX, 1>(fa.lay[l], wl, U, G, dir, z, ld)
-                   : tc_layer<DMAX, 0>(fa.lay[l], wl, U, G, dir, z, ld);
+      ok = (l & 1) ? tc_layer<D, 1>(wl, U, G, dir, z, ld) : tc_layer<D, 0>(wl, U, G, dir, z, ld);
     }
     // the last wait's outcome, agreed by the whole warpgroup
     if (!ok || wg_bar_any(1 + G.id, G.failed)) break;
 #pragma unroll
-    for (int k = 0; k < DMAX; ++k)
-      if (k < d) {
-        ld += flow_log_sig_prime(z[k]);
-        stg[t * zld + k] = flow_sigmoid(z[k]);
-      }
+    for (int k = 0; k < D; ++k) {
+      ld += flow_log_sig_prime(z[k]);
+      stg[t * zld + k] = flow_sigmoid(z[k]);
+    }
     if (t < rows) logdet[r0 + t] = ld;
     wg_bar(1 + G.id);
-    for (int i = t; i < rows * d; i += 128) {
-      const int r = (int)(((float)i + 0.5f) * inv_d), k = i - r * d;
-      xout[r0 * d + i] = stg[r * zld + k];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const int i = t + 128 * j;
+      if (i < rows * D) xout[r0 * D + i] = stg[(i / D) * zld + i % D];
     }
     wg_bar(1 + G.id);
   }
@@ -339,6 +337,16 @@ __global__ void __launch_bounds__(TcShape<DMAX>::threads, 1)
   if (warp == 0) tc_dealloc(tbase, S::tmem_cols);
 }
 
+// f(std::integral_constant<int, d>) for d in 2..32
+template <int D = 2, typename F>
+int dispatch_d(int d, F&& f) {
+  if constexpr (D > kFlowMaxDim) {
+    return VEGAS_EINVAL;
+  } else {
+    return d == D ? f(std::integral_constant<int, D>{}) : dispatch_d<D + 1>(d, f);
+  }
+}
+
 int num_sms_tc() {
   int dev = 0, n = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -346,11 +354,11 @@ int num_sms_tc() {
   return n;
 }
 
-template <int DMAX>
+template <int D>
 int launch_apply_tc(const FlowArgs& fa, int dir, const float* xin, float* xout, float* logdet, int64_t n,
                     cudaStream_t s) {
-  using S = TcShape<DMAX>;
-  auto k = flow_apply_tc_kernel<DMAX>;
+  using S = TcShape<D>;
+  auto k = flow_apply_tc_kernel<D>;
   VG_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::total));
   const int64_t ntiles = (n + 127) / 128;
   const int sms = num_sms_tc();
@@ -369,8 +377,7 @@ int flow_apply(int d, int direction, const float* d_params, const float* d_xin, 
   if (n == 0) return VEGAS_OK;
   fa.params = d_params;
   const int dir = direction == VEGAS_FLOW_NORMALISE ? 1 : -1;
-  return d <= 16 ? launch_apply_tc<16>(fa, dir, d_xin, d_xout, d_logdet, n, s)
-                 : launch_apply_tc<32>(fa, dir, d_xin, d_xout, d_logdet, n, s);
+  return dispatch_d(d, [&](auto D) { return launch_apply_tc<decltype(D)::value>(fa, dir, d_xin, d_xout, d_logdet, n, s); });
 }
 
 int flow_tc_status(bool reset) {
