@@ -787,21 +787,13 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
       }
     }
   }
-  // ---- offsets and 1/n_h of the cubes the tile can meet: up to the next tile's first cube ----
+  // ---- offsets of the cubes the tile can meet (up to the next tile's first cube), relative to the tile
+  // and clamped to +-2^30: one global load a cube; n_h is the difference of neighbours ----
+  constexpr int kRelCap = 1 << 30;
   const int ncand = min(kMaxCubesPerTile, (tile + 1 < a.ntiles ? a.tile_first[tile + 1] : a.NH - 1) - h0 + 1);
   for (int c = tid; c <= ncand; c += kFillThreads) {
-    const int64_t h = (int64_t)h0 + c;
-    const int64_t o0 = h <= a.NH ? a.offsets[h] : INT64_MAX;
-    const int64_t rel = o0 - j0;
-    off_r[c] = rel < -1 ? -1 : (rel > kTile + 1 ? kTile + 1 : (int)rel);
-    if (c < ncand) {
-      T inv = T(0);
-      if (o0 < jend) {
-        if constexpr (sizeof(T) == 8) inv = 1.0 / (double)(a.offsets[h + 1] - o0);
-        else inv = __fdividef(1.0f, (float)(a.offsets[h + 1] - o0));
-      }
-      invn[c] = inv;
-    }
+    const int64_t rel = a.offsets[(int64_t)h0 + c] - j0;  // h0 + c <= NH
+    off_r[c] = rel < -kRelCap ? -kRelCap : (rel > kRelCap ? kRelCap : (int)rel);
   }
   if (tid == 0) {
     misc[0] = 0;
@@ -809,13 +801,22 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
     a.carries[2 * tile + 1] = Carry{-1, 0, 0.0, 0.0};
   }
   __syncthreads();
-  // every cube tells the threads whose first evaluation it holds
+  // 1/n_h of every cube the tile meets; every cube tells the threads whose first evaluation it holds
   for (int c = tid; c < ncand; c += kFillThreads) {
-    const int r0 = max(off_r[c], 0), r1 = min(off_r[c + 1], len);
+    const int o0 = off_r[c], o1 = off_r[c + 1];
+    const int r0 = max(o0, 0), r1 = min(o1, len);
+    T inv = T(0);
     if (r0 < r1) {
+      // a cube longer than 2^30 (clamped ends) takes its count from the global offsets
+      const int64_t n = (o0 > -kRelCap && o1 < kRelCap)
+                            ? (int64_t)(o1 - o0)
+                            : a.offsets[(int64_t)h0 + c + 1] - a.offsets[(int64_t)h0 + c];
+      if constexpr (sizeof(T) == 8) inv = 1.0 / (double)n;
+      else inv = __fdividef(1.0f, (float)n);
       for (int t = (r0 + kSamplesPerThread - 1) / kSamplesPerThread; t * kSamplesPerThread < r1; ++t) startc[t] = c;
       if (r1 == len) misc[1] = c + 1;  // cubes met by the tile
     }
+    invn[c] = inv;
   }
   __syncthreads();
 
