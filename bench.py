@@ -42,7 +42,7 @@ WORKLOAD = ("plain VEGAS+ d=8, ridge of 5 Gaussians (s=0.05) on the diagonal, Ng
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one launch of the dominant kernel on this workload, from one ncu capture of
 # that kernel (dram__bytes_read.sum + dram__bytes_write.sum): the per-cube offsets and weights
-FILL_TRAFFIC_BYTES = (346.30 + 147.53) * 1e6
+FILL_TRAFFIC_BYTES = (346.41 + 147.93) * 1e6
 
 
 def fp32_ops_per_eval(d=D, K=K_PEAKS):

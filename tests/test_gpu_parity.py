@@ -463,3 +463,19 @@ def test_probe_pipes(V):
     r = V.probe_pipes()
     assert np.all(r > 0)
     assert r[0] > 16  # FP32 FMA per SM per clock
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_one_cube_longer_than_2_30(V, precision):
+    """a single hypercube (nstrat = 1) holding 1.2e9 evaluations: every tile lies inside it, its offsets are more
+    than 2^30 from most tiles, so the fill takes n_h from the global offsets and reassembles the cube from the
+    carries of all 1.17 million tiles; the estimate agrees with the closed form"""
+    d, neval = 2, 1_200_000_000
+    p = W.ridge(d, 3, 0.1)
+    prec = V.FP32 if precision == "fp32" else V.FP64
+    v = V.Vegas(d, 50, 1, 0.5, 0.75, precision=prec)
+    r = v.integrate(W.GAUSS_SUM, p, neval, 2, seed=3)
+    exact = W.exact(W.GAUSS_SUM, d, p)
+    assert r["status"] == 0 and r["nitn_run"] == 2
+    assert abs(r["estimate"] - exact) < 5 * r["sigma"], (r["estimate"], r["sigma"], exact)
+    assert 0 < r["sigma"] < 1e-4 * exact
