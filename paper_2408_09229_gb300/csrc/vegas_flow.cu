@@ -84,9 +84,10 @@ extern "C" int vegas_flow_check(void* stream) {
 
 // ===========================================================================
 // Training: loss = - sum_i w_i log|det dN/dx(x_i)| / sum_i w_i and its
-// gradient.  A CTA of 4 warps takes 64 samples (2 warps and 32 samples above
-// 16 axes, for shared memory): the forward pass in the
-// normalising direction keeps z before every layer; the backward pass
+// gradient.  A CTA of 2 warps takes 32 samples, so a minibatch of 4096
+// spreads over 128 CTAs; the bf16 weights, natural and transposed, are built
+// once a call (flow_image_kernel) and copied by every CTA.  The forward pass in
+// the normalising direction keeps z before every layer; the backward pass
 // recomputes each layer's conditioner and runs its six GEMMs on the tensor
 // cores (bf16 operands, FP32 accumulation):
 //   dW3 = GO^T U2,  gU2 = GO W3,  dW2 = GA2^T U1,  gU1 = GA2 W2,
@@ -98,10 +99,11 @@ extern "C" int vegas_flow_check(void* stream) {
 namespace vg {
 namespace {
 
-// W warps a CTA, 16 W samples; W = 4 up to 16 axes, 2 above (shared memory)
+// W warps a CTA, 16 W samples.  W = 2: a minibatch of 4096 samples then spreads over 128 CTAs (with W = 4,
+// 64 CTAs left most SMs idle), and above 16 axes shared memory allows no more.
 __host__ __device__ constexpr int grad_rows(int W) { return 16 * W; }
 __host__ __device__ constexpr int grad_ldr(int W) { return 16 * W + 8; }  // sample-major tiles: 20 or 36 words
-inline int grad_warps(int d) { return d <= 16 ? 4 : 2; }
+inline int grad_warps(int) { return 2; }
 
 struct GradLayout {
   int wnat;               // natural weights of all layers (flow_stage_weights)
@@ -114,6 +116,9 @@ struct GradLayout {
   int red;                // [W] f32
   int total;
   int ldo;                // leading dimension of GO (no padded to 16 or 32, + 8)
+  // the weight image in global memory: the staged natural weights (smem_weights bytes), then per layer
+  // the transposed block W1T, W2T, W3T exactly as laid out in shared memory from w1t on (img_tsz bytes)
+  int img_t, img_tsz, img_total;
 };
 
 GradLayout grad_layout(const FlowArgs& fa, int W) {
@@ -148,7 +153,55 @@ GradLayout grad_layout(const FlowArgs& fa, int W) {
   G.bias = take(sizeof(float) * (64 + 64 + 32));
   G.red = take(sizeof(float) * W);
   G.total = (int)o;
+  G.img_t = (int)al16((size_t)fa.smem_weights);
+  G.img_tsz = G.zs - G.w1t;
+  G.img_total = G.img_t + kFlowLayers * G.img_tsz;
   return G;
+}
+
+// The weight image of one gradient call: blockIdx.y = layer; the CTAs of a layer share its elements.
+__global__ void flow_image_kernel(const __grid_constant__ FlowArgs fa, GradLayout G, unsigned char* __restrict__ img) {
+  const int l = blockIdx.y;
+  const FlowLayer& L = fa.lay[l];
+  const float* P = fa.params;
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x, step = gridDim.x * blockDim.x;
+  __nv_bfloat16* W1 = reinterpret_cast<__nv_bfloat16*>(img + L.sW1);
+  __nv_bfloat16* W2 = reinterpret_cast<__nv_bfloat16*>(img + L.sW2);
+  __nv_bfloat16* W3 = reinterpret_cast<__nv_bfloat16*>(img + L.sW3);
+  float* b1 = reinterpret_cast<float*>(img + L.sb1);
+  float* b2 = reinterpret_cast<float*>(img + L.sb2);
+  float* b3 = reinterpret_cast<float*>(img + L.sb3);
+  unsigned char* T = img + G.img_t + (size_t)l * G.img_tsz;
+  __nv_bfloat16* W1T = reinterpret_cast<__nv_bfloat16*>(T);
+  __nv_bfloat16* W2T = reinterpret_cast<__nv_bfloat16*>(T + (G.w2t - G.w1t));
+  __nv_bfloat16* W3T = reinterpret_cast<__nv_bfloat16*>(T + (G.w3t - G.w1t));
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+  // natural layout (as flow_stage_weights): rows padded, zero padding; the transposes beside them
+  for (int i = i0; i < kFlowHidden * kLdK16; i += step) {
+    const int r = i / kLdK16, c = i - r * kLdK16;
+    const __nv_bfloat16 v = c < L.a ? __float2bfloat16_rn(P[L.oW1 + r * L.a + c]) : zero;
+    W1[i] = v;
+    if (c < 16) W1T[c * kLdK64 + r] = v;  // W1T [16][64 + pad]: column c of W1
+  }
+  for (int i = i0; i < kFlowHidden * kLdK64; i += step) {
+    const int r = i / kLdK64, c = i - r * kLdK64;
+    const __nv_bfloat16 v = c < kFlowHidden ? __float2bfloat16_rn(P[L.oW2 + r * kFlowHidden + c]) : zero;
+    W2[i] = v;
+    if (c < kFlowHidden) W2T[c * kLdK64 + r] = v;
+  }
+  for (int i = i0; i < L.no * kLdK64; i += step) {
+    const int r = i / kLdK64, c = i - r * kLdK64;
+    W3[i] = (r < 2 * L.b && c < kFlowHidden) ? __float2bfloat16_rn(P[L.oW3 + r * kFlowHidden + c]) : zero;
+  }
+  for (int i = i0; i < kFlowHidden * G.ldo; i += step) {  // W3T [64][ldo]: zero past 2 b
+    const int c = i / G.ldo, o = i - c * G.ldo;
+    W3T[i] = o < 2 * L.b ? __float2bfloat16_rn(P[L.oW3 + o * kFlowHidden + c]) : zero;
+  }
+  for (int i = i0; i < kFlowHidden; i += step) {
+    b1[i] = P[L.ob1 + i];
+    b2[i] = P[L.ob2 + i];
+  }
+  for (int i = i0; i < L.no; i += step) b3[i] = i < 2 * L.b ? P[L.ob3 + i] : 0.0f;
 }
 
 template <typename T>
@@ -188,11 +241,19 @@ __device__ __forceinline__ float sum_over_g(float v) {
 
 __device__ __forceinline__ void st_bf16(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 
+// 16-byte copy of `bytes` (a multiple of 16) from global to shared memory by the CTA
+__device__ __forceinline__ void copy16(unsigned char* dst, const unsigned char* __restrict__ src, int bytes) {
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+  uint4* d4 = reinterpret_cast<uint4*>(dst);
+  for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) d4[i] = s4[i];
+}
+
 template <int W>
 __global__ void __launch_bounds__(W * 32) flow_grad_kernel(const __grid_constant__ FlowArgs fa,
                                                                    GradLayout G, const float* __restrict__ x,
                                                                    const float* __restrict__ w,
                                                                    const double* __restrict__ wsum, int64_t n,
+                                                                   const unsigned char* __restrict__ img,
                                                                    float* __restrict__ gpart,
                                                                    float* __restrict__ lpart) {
   extern __shared__ __align__(16) unsigned char sm[];
@@ -202,7 +263,7 @@ __global__ void __launch_bounds__(W * 32) flow_grad_kernel(const __grid_constant
   const int64_t r0 = (int64_t)blockIdx.x * R;
   const int rows = (int)min((int64_t)R, n - r0);
   unsigned char* wsm = sm + G.wnat;
-  flow_stage_weights(fa, wsm);
+  copy16(wsm, img, fa.smem_weights);  // the staged weights, built once for all CTAs (flow_image_kernel)
   float* zs = at<float>(sm, G.zs);
   float* gz = at<float>(sm, G.gz);
   float* wn = at<float>(sm, G.wn);
@@ -289,19 +350,8 @@ __global__ void __launch_bounds__(W * 32) flow_grad_kernel(const __grid_constant
     const float* b2 = reinterpret_cast<const float*>(wsm + L.sb2);
     const float* b3 = reinterpret_cast<const float*>(wsm + L.sb3);
     const int kpad = G.ldo - 8;
-    // transposed weights of this layer; H and its transpose; zero the padding of GO / GOT
-    for (int i = tid; i < 16 * 64; i += blockDim.x) {
-      const int c = i / 64, j = i - c * 64;
-      W1T[c * kLdK64 + j] = W1[j * kLdK16 + c];
-    }
-    for (int i = tid; i < 64 * 64; i += blockDim.x) {
-      const int c = i / 64, j = i - c * 64;
-      W2T[c * kLdK64 + j] = W2[j * kLdK64 + c];
-    }
-    for (int i = tid; i < 64 * kpad; i += blockDim.x) {
-      const int c = i / kpad, o = i - c * kpad;
-      W3T[c * G.ldo + o] = o < L.no ? W3[o * kLdK64 + c] : __float2bfloat16_rn(0.0f);
-    }
+    // transposed weights of this layer (from the image); H and its transpose; zero the padding of GO / GOT
+    copy16(sm + G.w1t, img + G.img_t + (size_t)l * G.img_tsz, G.img_tsz);
     for (int i = tid; i < R * 16; i += blockDim.x) {
       const int r = i / 16, c = i - r * 16;
       const __nv_bfloat16 v = __float2bfloat16_rn(c < L.a ? zi[r * zld + 2 * c + par] : 0.0f);
@@ -517,18 +567,19 @@ __global__ void flow_adam_kernel(int64_t np, float* __restrict__ theta, const fl
 }
 
 struct GradScratch {
-  size_t wsum, lpart, gpart, total;
+  size_t wsum, lpart, gpart, img, total;
   int nblk;
 };
-
 GradScratch grad_scratch(const FlowArgs& fa, int64_t n) {
   GradScratch S{};
-  const int R = grad_rows(grad_warps(fa.d));
+  const int W = grad_warps(fa.d);
+  const int R = grad_rows(W);
   S.nblk = (int)((n + R - 1) / R);
   size_t o = 0;
   S.wsum = o; o = al16(o + sizeof(double));
   S.lpart = o; o = al16(o + sizeof(float) * S.nblk);
   S.gpart = o; o = al16(o + sizeof(float) * (size_t)S.nblk * fa.nparams);
+  S.img = o; o = al16(o + (size_t)grad_layout(fa, W).img_total);
   S.total = o;
   return S;
 }
@@ -559,15 +610,14 @@ extern "C" int vegas_flow_grad(int32_t dim, const float* d_params, const float* 
   double* wsum = (double*)(sc + S.wsum);
   float* lpart = (float*)(sc + S.lpart);
   float* gpart = (float*)(sc + S.gpart);
+  unsigned char* img = sc + S.img;
   flow_wsum_kernel<<<1, 1024, 0, s>>>(d_w, n, wsum);
   VG_CHECK(cudaGetLastError());
-  if (W == 4) {
-    VG_CHECK(cudaFuncSetAttribute(flow_grad_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, G.total));
-    flow_grad_kernel<4><<<S.nblk, 4 * 32, G.total, s>>>(fa, G, d_x, d_w, wsum, n, gpart, lpart);
-  } else {
-    VG_CHECK(cudaFuncSetAttribute(flow_grad_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, G.total));
-    flow_grad_kernel<2><<<S.nblk, 2 * 32, G.total, s>>>(fa, G, d_x, d_w, wsum, n, gpart, lpart);
-  }
+  flow_image_kernel<<<dim3(4, kFlowLayers), 256, 0, s>>>(fa, G, img);
+  VG_CHECK(cudaGetLastError());
+  static_assert(grad_rows(2) == 32, "two-warp CTAs");
+  VG_CHECK(cudaFuncSetAttribute(flow_grad_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, G.total));
+  flow_grad_kernel<2><<<S.nblk, 2 * 32, G.total, s>>>(fa, G, d_x, d_w, wsum, n, img, gpart, lpart);
   VG_CHECK(cudaGetLastError());
   flow_reduce_kernel<<<(fa.nparams + 255) / 256, 256, 0, s>>>(gpart, lpart, S.nblk, fa.nparams, d_grad, d_loss);
   return cuda_status(cudaGetLastError());
