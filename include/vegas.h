@@ -399,6 +399,13 @@ VEGAS_API int vegas_flow_apply(int32_t dim, int32_t direction, const float *d_pa
  * are then not written) or not (VEGAS_OK); clears the report.
  * Errors: ECUDA. */
 VEGAS_API int vegas_flow_check(void *stream);
+/* Self-test of that bounded wait, as the transform uses it: one CTA waits
+ * `polls` polls (1 <= polls <= 2^24) on an mbarrier.  arrive = 0: nothing
+ * arrives, the wait runs out and the call returns VEGAS_ETIMEOUT (the report
+ * is cleared); arrive != 0: a thread arrives first, the call returns VEGAS_OK.
+ * Synchronises stream.  Nothing faults or hangs either way.
+ * Errors: EINVAL, ECUDA. */
+VEGAS_API int vegas_flow_wait_selftest(int32_t polls, int32_t arrive, void *stream);
 /* Training loss and gradient.  For samples d_x [n][dim] with weights
  * d_w [n] >= 0 of positive sum (|f| over the density that drew them, e.g.
  * |J f| of a VEGAS+ iteration), loss = - sum_i w_i log|det dF^-1/dx(x_i)| /

@@ -82,6 +82,13 @@ extern "C" int vegas_flow_check(void* stream) {
   return flow_tc_status(true);
 }
 
+extern "C" int vegas_flow_wait_selftest(int32_t polls, int32_t arrive, void* stream) {
+  if (polls < 1 || polls > (1 << 24)) return VEGAS_EINVAL;
+  const int rc = flow_tc_wait_selftest(polls, arrive != 0, (cudaStream_t)stream);
+  if (rc != VEGAS_OK) return rc;
+  return vegas_flow_check(stream);
+}
+
 // ===========================================================================
 // Training: loss = - sum_i w_i log|det dN/dx(x_i)| / sum_i w_i and its
 // gradient.  A CTA of 2 warps takes 32 samples, so a minibatch of 4096

@@ -380,6 +380,28 @@ int flow_apply(int d, int direction, const float* d_params, const float* d_xin, 
   return dispatch_d(d, [&](auto D) { return launch_apply_tc<decltype(D)::value>(fa, dir, d_xin, d_xout, d_logdet, n, s); });
 }
 
+// The bounded wait on its own: an mbarrier of one expected arrival, waited
+// on for `polls` polls.  With arrive = 0 nothing arrives, the wait runs out
+// and the status word records it, as a stalled MMA would; with arrive = 1 one
+// thread arrives first and the wait completes.
+__global__ void tc_wait_selftest_kernel(int polls, int arrive) {
+  __shared__ uint64_t mbar;
+  if (threadIdx.x == 0) {
+    mbar_init(&mbar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (arrive && threadIdx.x == 0)
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(tc_smem_u32(&mbar))
+                 : "memory");
+  if (!mbar_wait(&mbar, 0, polls)) atomicOr(&g_flow_tc_status, 4);
+}
+
+int flow_tc_wait_selftest(int polls, int arrive, cudaStream_t s) {
+  tc_wait_selftest_kernel<<<1, 32, 0, s>>>(polls, arrive);
+  return cuda_status(cudaGetLastError());
+}
+
 int flow_tc_status(bool reset) {
   int v = 0;
   VG_CHECK(cudaMemcpyFromSymbol(&v, g_flow_tc_status, sizeof(int)));

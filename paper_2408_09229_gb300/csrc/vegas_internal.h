@@ -124,6 +124,7 @@ int flow_apply(int d, int direction, const float* d_params, const float* d_xin, 
                int64_t n, cudaStream_t s);
 // VEGAS_ETIMEOUT when a bounded wait of the tensor-core transform ran out since the last reset
 int flow_tc_status(bool reset);
+int flow_tc_wait_selftest(int polls, int arrive, cudaStream_t s);
 int flow_eval(int integrand, int d, const double* d_params, int64_t nparams, const float* X, const float* logdet,
               float* values, int64_t n, cudaStream_t s);
 // training set of an iteration: every kFloorPeriod-th row a uniform point when lambda > 0

@@ -103,6 +103,7 @@ def _load():
         "vegas_get_flow": ([P, P, i64, P], i32),
         "vegas_flow_apply": ([i32, i32, P, P, P, P, i64, P], i32),
         "vegas_flow_check": ([P], i32),
+        "vegas_flow_wait_selftest": ([i32, i32, P], i32),
         "vegas_flow_grad_scratch_bytes": ([i32, i64], sz),
         "vegas_flow_grad": ([i32, P, P, P, i64, P, P, P, sz, P], i32),
         "vegas_flow_adam": ([i64, P, P, P, P, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
@@ -421,6 +422,11 @@ def flow_apply(dim, direction, params, x_in, x_out, logdet, stream=None):
 def flow_check(stream=None):
     """vegas_flow_check: synchronise and raise if a bounded wait of an earlier flow_apply ran out"""
     _check(lib.vegas_flow_check(_stream_ptr(stream)), "vegas_flow_check")
+
+
+def flow_wait_selftest(polls, arrive, stream=None):
+    """vegas_flow_wait_selftest: the status code (ETIMEOUT when nothing arrived within `polls` polls)"""
+    return lib.vegas_flow_wait_selftest(int(polls), int(arrive), _stream_ptr(stream))
 
 
 def flow_grad_scratch_bytes(dim, n):

@@ -106,6 +106,22 @@ def test_apply_extreme_inputs_stay_finite(V, direction):
     assert gx.min() >= 0.0 and gx.max() <= 1.0
 
 
+def test_bounded_wait_reports_timeout(V):
+    """failure detection without a fault: an mbarrier that nothing arrives on runs out its poll budget and the
+    host reads VEGAS_ETIMEOUT; the report is cleared, the context stays usable, and a wait that is satisfied
+    returns OK"""
+    V.flow_check()
+    assert V.flow_wait_selftest(1000, 0) == V.ETIMEOUT
+    V.flow_check()  # cleared: no error
+    assert V.flow_wait_selftest(1000, 1) == V.OK
+    assert V.flow_wait_selftest(0, 1) == V.EINVAL
+    x = torch.rand((300, 6), device="cuda")
+    xo, ld = torch.empty_like(x), torch.empty(300, device="cuda")
+    V.flow_apply(6, V.FLOW_SAMPLE, dev(W.flow_params(6, seed=1, out_scale=0.0)), x, xo, ld)
+    V.flow_check()
+    assert torch.allclose(xo, x, atol=1e-6)
+
+
 def test_identity_flow_on_gpu(V):
     d = 7
     th = W.flow_params(d, seed=1, out_scale=0.0)
