@@ -2,9 +2,10 @@
 // on the fifth-generation tensor cores: tcgen05.mma with the accumulators in
 // tensor memory.  The flow is defined in vegas_flow.cuh.
 //
-// A CTA of G warpgroups (6 up to 16 axes, 4 above) stays resident on one SM;
-// each warpgroup transforms its own tile of 128 points, so while one waits for
-// its MMAs the others run their element-wise work.  Thread t of a warpgroup owns point t of
+// Above 16 axes a CTA of 4 warpgroups stays resident on one SM; each
+// warpgroup transforms its own tile of 128 points, so while one waits for its
+// MMAs the others run their element-wise work.  Up to 16 axes the activation
+// tiles are smaller and more warpgroups fit (flow_apply_u64_kernel, below).  Thread t of a warpgroup owns point t of
 // the tile: it keeps the point's z in registers and reads row t of every
 // accumulator (tensor-memory lane t).  Per coupling layer:
 //   H  = [bf16(z[A]) | 1 1 1 | 0]           128 x K1   (the first K1 columns of U)
@@ -32,6 +33,7 @@ namespace {
 constexpr int kTcK2 = kFlowHidden + 16;        // K of the second and third GEMMs: 64 + bias block
 constexpr int kTcColsPerGroup = 64;            // tensor-memory columns of one warpgroup's accumulator
 constexpr int kTcWaitPolls = 1 << 22;          // bound of every mbarrier wait
+constexpr int kU64Groups = 8;                  // warpgroups a CTA up to 16 axes (8 measured fastest: 7 and 6 slower)
 
 // a module-wide status word: bit 2 is set when a bounded wait ran out
 __device__ int g_flow_tc_status;
@@ -41,7 +43,7 @@ __device__ int g_flow_tc_status;
 // then compile-time).
 template <int D>
 struct TcShape {
-  static constexpr int G = D <= 16 ? 6 : 4;  // warpgroups a CTA (shared memory and registers)
+  static constexpr int G = 4;  // warpgroups a CTA (shared memory): this kernel serves 17..32 axes
   static constexpr int threads = 128 * G;
   static constexpr uint32_t tmem_cols = G * kTcColsPerGroup <= 256 ? 256 : 512;  // a power of two
   static constexpr int A0 = (D + 1) / 2;                // conditioning axes of even layers (the larger a)
@@ -70,7 +72,7 @@ __device__ __forceinline__ void bias3(float b, __nv_bfloat16& h, __nv_bfloat16& 
 template <int D>
 __device__ void tc_stage_weights(const FlowArgs& fa, unsigned char* sm) {
   using S = TcShape<D>;
-  constexpr int kTcThreads = S::threads;
+  const int kTcThreads = blockDim.x;
   const float* P = fa.params;
   for (int l = 0; l < kFlowLayers; ++l) {
     const FlowLayer& L = fa.lay[l];
@@ -125,15 +127,15 @@ __device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
   return d;
 }
 
-// row t of U from the 64 accumulator columns: ReLU, bf16 (16 columns at a time: registers)
-__device__ __forceinline__ void tc_hidden_epilogue(uint32_t tacc, unsigned char* U, int t) {
+// row t of U (ku columns) from the 64 accumulator columns: ReLU, bf16 (16 columns at a time: registers)
+__device__ __forceinline__ void tc_hidden_epilogue(uint32_t tacc, unsigned char* U, int t, int ku = kTcK2) {
 #pragma unroll
   for (int cb = 0; cb < 64; cb += 16) {
     float v[16];
     tc_ld16(tacc + cb, v);
 #pragma unroll
     for (int q = 0; q < 2; ++q)
-      st_shared_v4(U + tc_off(t, cb + 8 * q, kTcK2), bf16x2_relu(v[8 * q], v[8 * q + 1]),
+      st_shared_v4(U + tc_off(t, cb + 8 * q, ku), bf16x2_relu(v[8 * q], v[8 * q + 1]),
                    bf16x2_relu(v[8 * q + 2], v[8 * q + 3]), bf16x2_relu(v[8 * q + 4], v[8 * q + 5]),
                    bf16x2_relu(v[8 * q + 6], v[8 * q + 7]));
   }
@@ -337,6 +339,197 @@ __global__ void __launch_bounds__(TcShape<D>::threads, 1)
   if (warp == 0) tc_dealloc(tbase, S::tmem_cols);
 }
 
+// ---------------------------------------------------------------------------
+// Up to 16 axes: more tiles in flight.  A tile's activations U are 128 x 64
+// (16 KB) instead of 128 x 80: the bias k-step of the second and third GEMMs
+// takes its A operand from one shared 128 x 16 tile of ones (columns 0-2 one,
+// the rest zero) against the bias columns 64-79 of the weights.  The shared
+// memory this frees holds more warpgroups, each on its own tile.
+// ---------------------------------------------------------------------------
+constexpr int kU64 = kFlowHidden;  // columns of U
+
+template <int D>
+struct U64Shape {
+  using S = TcShape<D>;  // the staged weights are the same
+  static_assert(D <= 16 && S::K1 == 16 && S::N3 == 16, "up to 16 axes");
+  static constexpr int G = kU64Groups;
+  static constexpr int threads = 128 * G;
+  static constexpr uint32_t tmem_cols = G * kTcColsPerGroup <= 256 ? 256 : 512;
+  static constexpr uint32_t ONES = 128 * 16 * 2, U = 128 * kU64 * 2;
+  static constexpr uint32_t ones_off = S::weights, u_off = S::weights + ONES;
+  static constexpr uint32_t misc = u_off + G * U;
+  static constexpr uint32_t total = misc + 8 * G + 16;
+  static_assert(128 * S::ZLD * 4 <= U, "staging fits in U");
+  static_assert(total <= 232448, "shared memory of one CTA");
+  static_assert(G * kTcColsPerGroup <= 512, "tensor memory");
+};
+
+// the MMAs of one GEMM, issued by one thread: nks k-steps from U, then (bias) one from the ones tile
+__device__ __forceinline__ void u64_gemm(uint32_t tcol, const unsigned char* U, const unsigned char* ones,
+                                         const unsigned char* B, int kb, int nks, bool bias, uint32_t idesc) {
+  const uint64_t ad = tc_desc(tc_smem_u32(U), kTcLbo, (uint32_t)kU64 * 16);
+  const uint64_t bd = tc_desc(tc_smem_u32(B), kTcLbo, (uint32_t)kb * 16);
+  for (int s = 0; s < nks; ++s) tc_mma(tcol, ad + 16u * s, bd + 16u * s, idesc, s > 0);
+  if (bias) tc_mma(tcol, tc_desc(tc_smem_u32(ones), kTcLbo, 16 * 16), bd + 16u * nks, idesc, 1u);
+}
+
+// operands written: vote barrier, thread 0 issues and commits, every thread waits (bounded);
+// false on every thread of the warpgroup once a wait ran out
+__device__ __forceinline__ bool u64_run(TcGroup& G, const unsigned char* U, const unsigned char* ones,
+                                        const unsigned char* B, int kb, int nks, bool bias, uint32_t idesc) {
+  tc_fence_proxy();
+  tc_fence_before();
+  if (wg_bar_any(1 + G.id, G.failed)) return false;
+  if (G.t == 0) {
+    tc_fence_after();
+    u64_gemm(G.tacc & 0xFFFFu, U, ones, B, kb, nks, bias, idesc);
+    tc_commit(G.mbar);
+  }
+  if (!mbar_wait(G.mbar, G.phase, kTcWaitPolls)) {
+    G.failed = true;
+    atomicOr(&g_flow_tc_status, 4);
+  }
+  G.phase ^= 1u;
+  tc_fence_after();
+  return true;
+}
+
+template <int D, int PAR>
+__device__ __forceinline__ bool u64_layer(const unsigned char* wl, const unsigned char* ones, unsigned char* U,
+                                          TcGroup& G, int dir, float (&z)[D], float& ld) {
+  using T = TcShape<D>;
+  constexpr int a = PAR == 0 ? (D + 1) / 2 : D / 2, b = D - a;
+  const int t = G.t;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {  // H: the first 16 columns of U
+    float hv[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int c = 8 * q + e;
+      hv[e] = c < a ? z[2 * c + PAR] : (c < a + 3 ? 1.0f : 0.0f);
+    }
+    st_shared_v4(U + tc_off(t, 8 * q, kU64), bf16x2(hv[0], hv[1]), bf16x2(hv[2], hv[3]), bf16x2(hv[4], hv[5]),
+                 bf16x2(hv[6], hv[7]));
+  }
+  const unsigned char* w1 = wl;
+  const unsigned char* w2 = wl + T::W1;
+  const unsigned char* w3 = w2 + T::W2;
+  if (!u64_run(G, U, ones, w1, 16, 1, false, tc_idesc_bf16(128, 64))) return false;
+  tc_hidden_epilogue(G.tacc, U, t, kU64);
+  tc_fence_before();
+  if (!u64_run(G, U, ones, w2, kTcK2, 4, true, tc_idesc_bf16(128, 64))) return false;
+  tc_hidden_epilogue(G.tacc, U, t, kU64);
+  tc_fence_before();
+  if (!u64_run(G, U, ones, w3, kTcK2, 4, true, tc_idesc_bf16(128, 16))) return false;
+  float o[16];
+  tc_ld16(G.tacc, o);
+  tc_fence_before();
+#pragma unroll
+  for (int m = 0; m < b; ++m) {
+    const int k = 2 * m + 1 - PAR;
+    const float s = flow_soft_clamp(o[2 * m]), tt = o[2 * m + 1];
+    if (dir > 0) {
+      z[k] = fmaf(z[k], __expf(s), tt);
+      ld += s;
+    } else {
+      z[k] = (z[k] - tt) * __expf(-s);
+      ld -= s;
+    }
+  }
+  return true;
+}
+
+template <int D>
+__global__ void __launch_bounds__(U64Shape<D>::threads, 1)
+    flow_apply_u64_kernel(const __grid_constant__ FlowArgs fa, int dir, const float* __restrict__ xin,
+                          float* __restrict__ xout, float* __restrict__ logdet, int64_t n) {
+  using P = U64Shape<D>;
+  constexpr int zld = D | 1;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int warp = threadIdx.x >> 5;
+  uint64_t* mbars = reinterpret_cast<uint64_t*>(sm + P::misc);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + P::misc + 8 * P::G);
+  unsigned char* ones = sm + P::ones_off;
+  tc_stage_weights<D>(fa, sm);
+  for (int i = threadIdx.x; i < 128 * 16; i += blockDim.x) {
+    const int r = i >> 4, c = i & 15;
+    *reinterpret_cast<__nv_bfloat16*>(ones + tc_off(r, c, 16)) = __float2bfloat16_rn(c < 3 ? 1.0f : 0.0f);
+  }
+  if (warp == 0) tc_alloc(tslot, P::tmem_cols);
+  if (threadIdx.x == 0) {
+    for (int g = 0; g < P::G; ++g) mbar_init(mbars + g, 1);
+    mbar_fence_init();
+  }
+  tc_fence_proxy();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+  TcGroup G;
+  G.id = threadIdx.x >> 7;
+  G.t = threadIdx.x & 127;
+  G.tacc = tbase + (uint32_t)(G.id * kTcColsPerGroup) + ((uint32_t)((warp & 3) * 32) << 16);
+  G.mbar = mbars + G.id;
+  G.phase = 0;
+  G.failed = false;
+  unsigned char* U = sm + P::u_off + G.id * P::U;
+  float* stg = reinterpret_cast<float*>(U);
+  const int t = G.t;
+  const int64_t ntiles = (n + 127) / 128;
+  for (int64_t tile = (int64_t)blockIdx.x * P::G + G.id; tile < ntiles; tile += (int64_t)gridDim.x * P::G) {
+    const int64_t r0 = tile * 128;
+    const int rows = (int)min((int64_t)128, n - r0);
+    {  // the tile's x, coalesced, into rows of stride zld (odd: conflict-free row reads); all loads first
+      float xl[D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const int i = t + 128 * j;
+        xl[j] = i < rows * D ? xin[r0 * D + i] : 0.5f;
+      }
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const int i = t + 128 * j;
+        stg[(i / D) * zld + i % D] = xl[j];
+      }
+    }
+    wg_bar(1 + G.id);
+    float z[D];
+    float ld = 0.0f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      z[k] = flow_logit(stg[t * zld + k]);
+      ld -= flow_log_sig_prime(z[k]);
+    }
+    wg_bar(1 + G.id);
+    bool ok = true;
+    for (int i = 0; i < kFlowLayers && ok; ++i) {
+      const int l = dir > 0 ? i : kFlowLayers - 1 - i;
+      const unsigned char* wl = sm + l * TcShape<D>::layer;
+      ok = (l & 1) ? u64_layer<D, 1>(wl, ones, U, G, dir, z, ld) : u64_layer<D, 0>(wl, ones, U, G, dir, z, ld);
+    }
+    if (!ok || wg_bar_any(1 + G.id, G.failed)) break;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      ld += flow_log_sig_prime(z[k]);
+      stg[t * zld + k] = flow_sigmoid(z[k]);
+    }
+    if (t < rows) logdet[r0 + t] = ld;
+    wg_bar(1 + G.id);
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const int i = t + 128 * j;
+      if (i < rows * D) xout[r0 * D + i] = stg[(i / D) * zld + i % D];
+    }
+    wg_bar(1 + G.id);
+  }
+  // a warpgroup that gave up waits once more for its MMAs before the columns are freed
+  if (G.failed) mbar_wait(G.mbar, G.phase ^ 1u, kTcWaitPolls);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tc_dealloc(tbase, P::tmem_cols);
+}
+
 // f(std::integral_constant<int, d>) for d in 2..32
 template <int D = 2, typename F>
 int dispatch_d(int d, F&& f) {
@@ -357,15 +550,27 @@ int num_sms_tc() {
 template <int D>
 int launch_apply_tc(const FlowArgs& fa, int dir, const float* xin, float* xout, float* logdet, int64_t n,
                     cudaStream_t s) {
-  using S = TcShape<D>;
-  auto k = flow_apply_tc_kernel<D>;
-  VG_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::total));
-  const int64_t ntiles = (n + 127) / 128;
-  const int sms = num_sms_tc();
-  if (sms < 1) return VEGAS_ECUDA;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(sms, (ntiles + S::G - 1) / S::G));
-  k<<<grid, S::threads, S::total, s>>>(fa, dir, xin, xout, logdet, n);
-  return cuda_status(cudaGetLastError());
+  if constexpr (D <= 16) {
+    using P = U64Shape<D>;
+    auto k = flow_apply_u64_kernel<D>;
+    VG_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::total));
+    const int64_t ntiles = (n + 127) / 128;
+    const int sms = num_sms_tc();
+    if (sms < 1) return VEGAS_ECUDA;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(sms, (ntiles + P::G - 1) / P::G));
+    k<<<grid, P::threads, P::total, s>>>(fa, dir, xin, xout, logdet, n);
+    return cuda_status(cudaGetLastError());
+  } else {
+    using S = TcShape<D>;
+    auto k = flow_apply_tc_kernel<D>;
+    VG_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::total));
+    const int64_t ntiles = (n + 127) / 128;
+    const int sms = num_sms_tc();
+    if (sms < 1) return VEGAS_ECUDA;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(sms, (ntiles + S::G - 1) / S::G));
+    k<<<grid, S::threads, S::total, s>>>(fa, dir, xin, xout, logdet, n);
+    return cuda_status(cudaGetLastError());
+  }
 }
 
 }  // namespace
