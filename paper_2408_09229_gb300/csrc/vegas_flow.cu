@@ -663,8 +663,20 @@ __global__ void __launch_bounds__(256) flow_eval_kernel(const float* __restrict_
   const int K = ID == VEGAS_GAUSS_SUM ? (int)prm[2] : 0;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
     float x[DMAX];
+    if ((d & 3) == 0) {  // 16-byte aligned rows: four coordinates a load
 #pragma unroll
-    for (int k = 0; k < DMAX; ++k) x[k] = k < d ? X[j * d + k] : 0.0f;
+      for (int k = 0; k < DMAX; k += 4) {
+        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (k < d) v = *reinterpret_cast<const float4*>(X + j * d + k);
+        x[k] = v.x;
+        x[k + 1] = v.y;
+        x[k + 2] = v.z;
+        x[k + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < DMAX; ++k) x[k] = k < d ? X[j * d + k] : 0.0f;
+    }
     const float f = integrand<ID, float, DMAX>(x, d, prm, np_derived, s0, s1, K);
     values[j] = f * __expf(logdet[j]);
   }

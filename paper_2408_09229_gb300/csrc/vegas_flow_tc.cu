@@ -2,23 +2,27 @@
 // on the fifth-generation tensor cores: tcgen05.mma with the accumulators in
 // tensor memory.  The flow is defined in vegas_flow.cuh.
 //
-// Above 16 axes a CTA of 4 warpgroups stays resident on one SM; each
-// warpgroup transforms its own tile of 128 points, so while one waits for its
-// MMAs the others run their element-wise work.  Up to 16 axes the activation
-// tiles are smaller and more warpgroups fit (flow_apply_u64_kernel, below).  Thread t of a warpgroup owns point t of
-// the tile: it keeps the point's z in registers and reads row t of every
-// accumulator (tensor-memory lane t).  Per coupling layer:
-//   H  = [bf16(z[A]) | 1 1 1 | 0]           128 x K1   (the first K1 columns of U)
-//   D  = H W1'^T                            128 x 64   (tensor memory)
-//   U  = [bf16(relu D) | 1 1 1 | 0]          128 x 80   (shared memory)
-//   D  = U W2'^T;  U = [bf16(relu D) | ...]
-//   D  = U W3'^T                            128 x N3
-// then s, t from D and the affine update of z[B].  The primed weights carry
-// the bias in three extra columns as a bf16 triple (hi, mid, lo) with
-// hi + mid + lo = b to 2^-24 relative, multiplied by the three ones-columns
-// of H and U: the bias enters the FP32 accumulation at full FP32 precision.
-// One thread of the warpgroup issues the MMAs; every thread waits (bounded)
-// on the warpgroup's mbarrier, which the MMAs' completion arrives on.
+// A persistent CTA on each SM holds the six layers' weights in shared memory
+// and runs several warpgroups, each transforming its own tile of 128 points,
+// so that while one waits for its MMAs the others run their element-wise
+// work: 8 warpgroups up to 16 axes (flow_apply_u64_kernel), 4 above
+// (flow_apply_tc_kernel).  Thread t of a warpgroup owns point t of the tile:
+// it keeps the point's z in registers and reads row t of every accumulator
+// (tensor-memory lane t).  Per coupling layer:
+//   H  = [bf16(z[A]) | 1 1 1 | 0]     128 x K1   (the first K1 columns of U)
+//   D  = H W1'^T                      128 x 64   (tensor memory)
+//   U  = bf16(relu D)                 128 x 64   (shared memory)
+//   D  = [U | ONES] W2'^T;  U = bf16(relu D)
+//   D  = [U | ONES] W3'^T             128 x N3
+// then s, t from D and the affine update of z[B].  ONES is a 128 x 16 block
+// whose first three columns are one: above 16 axes it is the last 16 columns
+// of each tile's U (128 x 80), up to 16 axes one shared tile that the bias
+// k-step's descriptor points at.  The primed weights carry the bias in three
+// extra columns as a bf16 triple (hi, mid, lo) with hi + mid + lo = b to
+// 2^-24 relative, multiplied by those ones: the bias enters the FP32
+// accumulation at full FP32 precision.  One thread of the warpgroup issues
+// the MMAs; every thread waits (bounded) on the warpgroup's mbarrier, which
+// the MMAs' completion arrives on.
 #include <algorithm>
 #include <type_traits>
 
@@ -33,7 +37,7 @@ namespace {
 constexpr int kTcK2 = kFlowHidden + 16;        // K of the second and third GEMMs: 64 + bias block
 constexpr int kTcColsPerGroup = 64;            // tensor-memory columns of one warpgroup's accumulator
 constexpr int kTcWaitPolls = 1 << 22;          // bound of every mbarrier wait
-constexpr int kU64Groups = 8;                  // warpgroups a CTA up to 16 axes (8 measured fastest: 7 and 6 slower)
+constexpr int kU64Groups = 8;                  // warpgroups a CTA up to 16 axes (measured: 8 beats 7 and 6)
 
 // a module-wide status word: bit 2 is set when a bounded wait ran out
 __device__ int g_flow_tc_status;
