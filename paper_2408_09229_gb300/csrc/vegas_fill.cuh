@@ -6,9 +6,10 @@
 // consecutive indices; a persistent grid walks the tiles round-robin.  A tile
 // meets at most kMaxCubesPerTile hypercubes because n_h >= 2.  It stages their
 // offsets, relative to the tile start, in shared memory.  Each thread takes
-// kSamplesPerThread consecutive evaluations.  A thread binary-searches the
-// cube of its first evaluation and steps forward from there; no
-// evaluation-to-cube array is ever built.
+// kSamplesPerThread consecutive evaluations.  Every cube writes its index
+// into a start-cube table for the threads whose first evaluation it holds; a
+// thread starts there and steps forward.  No evaluation-to-cube array is ever
+// built.
 //
 // Accumulation without global atomics (the paper's atomicAdd of Sec. 3.3.3):
 //  * cube weights: every J f goes to a shared array.  The cubes that lie inside
@@ -17,9 +18,10 @@
 //    edge leaves a Carry record, and a fix-up kernel merges the records
 //    (Chan's pairwise formula) in tile order.
 //  * map weights: a per-CTA histogram.  The FP64 form adds with shared FP64
-//    atomics.  Shared FP32 atomic adds become compare-and-swap loops, and the
-//    32 lanes of a warp share a stratum on the high axes, so they collide on
-//    a handful of bins.  The FP32 form therefore adds in two phases per tile:
+//    atomics.  The 32 lanes of a warp share a stratum on the high axes, so
+//    their adds collide on a handful of bins, and shared floating-point
+//    atomics measured slower than integer ones.  The FP32 form therefore adds
+//    in two phases per tile:
 //    the tile's largest weight fixes a power-of-two scale, the weights go in
 //    as 32-bit fixed-point integers through native shared integer atomics,
 //    and every tile's totals are folded into float-float accumulators.
@@ -644,7 +646,7 @@ struct FillShared {
   uint32_t* binw;     // two-phase: intervals of an evaluation, 4 or 2 per word
   float* wv_s;        // two-phase: map weight of every evaluation
   T* prm;
-  int* off_r;         // cube offsets relative to the tile, clamped
+  int* off_r;         // cube offsets relative to the tile, clamped to +-2^30
   T* invn;
   T* vals;
   int* longlist;
