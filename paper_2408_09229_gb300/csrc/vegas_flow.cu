@@ -113,7 +113,7 @@ __host__ __device__ constexpr int grad_ldr(int W) { return 16 * W + 8; }  // sam
 inline int grad_warps(int) { return 2; }
 
 struct GradLayout {
-  int wnat;               // natural weights of all layers (flow_stage_weights)
+  int wnat;               // natural weights of all layers (the layout of flow_layout, built by flow_image_kernel)
   int w1t, w2t, w3t;      // transposed weights of the current layer
   int zs;                 // z before each layer [L][R][zld] f32, then z after the last
   int gz;                 // [R][zld] f32
@@ -183,7 +183,7 @@ __global__ void flow_image_kernel(const __grid_constant__ FlowArgs fa, GradLayou
   __nv_bfloat16* W2T = reinterpret_cast<__nv_bfloat16*>(T + (G.w2t - G.w1t));
   __nv_bfloat16* W3T = reinterpret_cast<__nv_bfloat16*>(T + (G.w3t - G.w1t));
   const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
-  // natural layout (as flow_stage_weights): rows padded, zero padding; the transposes beside them
+  // natural layout (offsets sW1.. of flow_layout): rows padded, zero padding; the transposes beside them
   for (int i = i0; i < kFlowHidden * kLdK16; i += step) {
     const int r = i / kLdK16, c = i - r * kLdK16;
     const __nv_bfloat16 v = c < L.a ? __float2bfloat16_rn(P[L.oW1 + r * L.a + c]) : zero;

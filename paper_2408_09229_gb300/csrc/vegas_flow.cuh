@@ -124,38 +124,6 @@ __device__ __forceinline__ float flow_soft_clamp(float o) {
   return copysignf(kFlowSClamp * __fdividef(1.0f - e, 1.0f + e), o);
 }
 
-// Stage every layer's weights in shared memory as bf16 (biases FP32); zero
-// padding rows and columns.  Called by the whole CTA.
-__device__ inline void flow_stage_weights(const FlowArgs& fa, unsigned char* sm) {
-  for (int l = 0; l < kFlowLayers; ++l) {
-    const FlowLayer& L = fa.lay[l];
-    const float* P = fa.params;
-    __nv_bfloat16* W1 = reinterpret_cast<__nv_bfloat16*>(sm + L.sW1);
-    __nv_bfloat16* W2 = reinterpret_cast<__nv_bfloat16*>(sm + L.sW2);
-    __nv_bfloat16* W3 = reinterpret_cast<__nv_bfloat16*>(sm + L.sW3);
-    float* b1 = reinterpret_cast<float*>(sm + L.sb1);
-    float* b2 = reinterpret_cast<float*>(sm + L.sb2);
-    float* b3 = reinterpret_cast<float*>(sm + L.sb3);
-    for (int i = threadIdx.x; i < kFlowHidden * kLdK16; i += blockDim.x) {
-      const int r = i / kLdK16, c = i - r * kLdK16;
-      W1[i] = __float2bfloat16_rn(c < L.a ? P[L.oW1 + r * L.a + c] : 0.0f);
-    }
-    for (int i = threadIdx.x; i < kFlowHidden * kLdK64; i += blockDim.x) {
-      const int r = i / kLdK64, c = i - r * kLdK64;
-      W2[i] = __float2bfloat16_rn(c < kFlowHidden ? P[L.oW2 + r * kFlowHidden + c] : 0.0f);
-    }
-    for (int i = threadIdx.x; i < L.no * kLdK64; i += blockDim.x) {
-      const int r = i / kLdK64, c = i - r * kLdK64;
-      W3[i] = __float2bfloat16_rn((r < 2 * L.b && c < kFlowHidden) ? P[L.oW3 + r * kFlowHidden + c] : 0.0f);
-    }
-    for (int i = threadIdx.x; i < kFlowHidden; i += blockDim.x) {
-      b1[i] = P[L.ob1 + i];
-      b2[i] = P[L.ob2 + i];
-    }
-    for (int i = threadIdx.x; i < L.no; i += blockDim.x) b3[i] = i < 2 * L.b ? P[L.ob3 + i] : 0.0f;
-  }
-}
-
 // The conditioner of layer L on the warp's 16 rows: from the A fragments of
 // h (one k-step: a <= 16), the output fragments o[nt][4] for nt < no/8.
 // u1 and u2 stay in registers.
