@@ -71,6 +71,24 @@ def test_apply_matches_oracle(V, d):
         assert np.abs(ox - x).max() > 0.02
 
 
+@pytest.mark.parametrize("d", [3, 16, 17])
+@pytest.mark.parametrize("n", [1, 127, 128, 129])
+def test_apply_small_and_ragged_sizes(V, d, n):
+    """a single point, one short of a tile, exactly one tile and one over, on both tensor-core kernels (up to 16
+    axes and above); rows past n are never written"""
+    th = W.flow_params(d, seed=20 + d, out_scale=0.05)
+    x = np.random.default_rng(n).uniform(0.01, 0.99, (n, d)).astype(np.float32)
+    xi = dev(x)
+    xo = torch.full((n + 5, d), -3.0, dtype=torch.float32, device="cuda")
+    ld = torch.full((n + 5,), -3.0, dtype=torch.float32, device="cuda")
+    V.flow_apply(d, V.FLOW_SAMPLE, dev(th), xi, xo[:n], ld[:n])
+    V.flow_check()
+    ox, ol = F.sample(th, x.astype(np.float64), d, bf16_path=True)
+    got = xo.cpu().numpy()
+    assert np.abs(got[:n] - ox).max() < 5e-3 and np.abs(ld.cpu().numpy()[:n] - ol).max() < 5e-2
+    assert (got[n:] == -3.0).all() and (ld.cpu().numpy()[n:] == -3.0).all()
+
+
 def test_apply_many_tiles_and_check(V):
     """more tiles than the resident warpgroups: every warpgroup loops over several tiles; in place; the
     bounded waits all completed"""
