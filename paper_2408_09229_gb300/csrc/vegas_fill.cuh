@@ -398,6 +398,25 @@ __device__ __forceinline__ void decode_cube(const FillArgs& a, uint32_t h, uint3
   }
 }
 
+// Coordinates of cube h + 1 from those of cube h, in the encoding of
+// decode_cube: one added to axis 0 and carried upwards (an odometer).  A
+// thread's consecutive evaluations stay in a cube or move to the next one,
+// so after one full decode a step costs an add and a compare; the carry into
+// axis k is taken once in s_0 ... s_{k-1} steps.
+template <typename T, int DMAX, bool EXACT>
+__device__ __forceinline__ void next_cube(const FillArgs& a, uint32_t (&cb)[DMAX]) {
+#pragma unroll
+  for (int k = 0; k < DMAX; ++k) {
+    if (EXACT || k < a.d) {
+      const uint32_t one = sizeof(T) == 8 ? 1u : (1u << a.fbits[k]);
+      const uint32_t zero = sizeof(T) == 8 ? 0u : 0x4B000000u;
+      cb[k] += one;
+      if (cb[k] < zero + a.nstrat[k] * one) return;
+      cb[k] = zero;
+    }
+  }
+}
+
 // Point of evaluation j in the cube with coordinates cb: Philox words, the
 // position z = (c + u) N_g / s_k, interval i = min(floor z, N_g - 1), the
 // point x = e_i + (z - i) dx_i and the Jacobian J = prod N_g dx_i.
@@ -862,16 +881,15 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
     }
   } else if (jl0 < len) {
     int c = startc[tid];
-    int c_decoded = -1;
     uint32_t cb[DMAX];
+    decode_cube<T, DMAX, EXACT>(a, (uint32_t)(h0 + c), cb);
 #pragma unroll 1
     for (int s = 0; s < kSamplesPerThread; ++s) {
       const int jl = jl0 + s;
       if (jl < len) {
-        while (off_r[c + 1] <= jl) ++c;
-        if (c != c_decoded) {  // consecutive evaluations often share a cube
-          decode_cube<T, DMAX, EXACT>(a, (uint32_t)(h0 + c), cb);
-          c_decoded = c;
+        while (off_r[c + 1] <= jl) {
+          ++c;
+          next_cube<T, DMAX, EXACT>(a, cb);
         }
         T x[DMAX];
         int bin[DMAX];
@@ -912,10 +930,12 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
 #pragma unroll
             for (int w = 0; w < (DMAX + 3) / 4; ++w) {
               if (4 * w < d) {
-                uint32_t word = 0u;
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                  if (4 * w + q < DMAX) word |= (uint32_t)bin[4 * w + q] << (8 * q);
+                // intervals below 256: byte 0 of each, four to a word
+                const uint32_t b0 = (uint32_t)bin[4 * w];
+                const uint32_t b1 = 4 * w + 1 < DMAX ? (uint32_t)bin[4 * w + 1] : 0u;
+                const uint32_t b2 = 4 * w + 2 < DMAX ? (uint32_t)bin[4 * w + 2] : 0u;
+                const uint32_t b3 = 4 * w + 3 < DMAX ? (uint32_t)bin[4 * w + 3] : 0u;
+                const uint32_t word = __byte_perm(__byte_perm(b0, b1, 0x0040u), __byte_perm(b2, b3, 0x0040u), 0x5410u);
                 binw[w * kTile + tix(jl)] = word;
               }
             }
