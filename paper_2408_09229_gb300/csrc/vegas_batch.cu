@@ -707,6 +707,7 @@ extern "C" int vegas_batch_create(const vegas_problem* problems, int32_t nproble
     a.sm_wv = layout.sm_wv;
     a.sm_params = layout.sm_params;
     a.sm_off = layout.sm_off;
+    a.sm_raw = layout.sm_raw;
     a.sm_invn = layout.sm_invn;
     a.sm_vals = layout.sm_vals;
     a.sm_long = layout.sm_long;

@@ -652,6 +652,16 @@ __device__ __forceinline__ float stream_point_eval(const FillArgs& a, const uint
   }
 }
 
+// Asynchronous 8-byte global -> shared copies (cp.async, no registers held):
+// the single-integral fill loads the next tile's cube offsets while it
+// computes the current one.
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Shared-memory views of the fill and the per-thread running state; one tile
 // of evaluations is processed by fill_tile, which both the single-integral and
 // the batched kernels call.
@@ -666,6 +676,7 @@ struct FillShared {
   float* wv_s;        // two-phase: map weight of every evaluation
   T* prm;
   int* off_r;         // cube offsets relative to the tile, clamped to +-2^30
+  int64_t* raw_off;   // prefetched global offsets of the cubes a tile can meet (single-integral fill)
   T* invn;
   T* vals;
   int* longlist;
@@ -687,6 +698,7 @@ __device__ __forceinline__ FillShared<T> fill_shared(unsigned char* smem, const 
   S.wv_s = (float*)(smem + a.sm_wv);
   S.prm = (T*)(smem + a.sm_params);
   S.off_r = (int*)(smem + a.sm_off);
+  S.raw_off = (int64_t*)(smem + a.sm_raw);
   S.invn = (T*)(smem + a.sm_invn);
   S.vals = (T*)(smem + a.sm_vals);
   S.longlist = (int*)(smem + a.sm_long);
@@ -763,10 +775,11 @@ __device__ __forceinline__ void fill_prologue(const FillArgs& a, const FillShare
 // rk1: the Philox round keys (kernel parameters, so that they are
 // constant-bank operands).  STREAM: the streamed point path (FP32, DMAX >= 16,
 // two-phase histogram, s_k <= 256).
-template <int ID, typename T, int DMAX, bool EXACT, bool STREAM = false>
+template <int ID, typename T, int DMAX, bool EXACT, bool STREAM = false, bool PREFETCH = false>
 __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __restrict__ rk0,
                                           const uint32_t* __restrict__ rk1, const FillShared<T>& S,
-                                          FillState<T>& st, int tile, T ps0, T ps1, int pK, double* hist_g) {
+                                          FillState<T>& st, int tile, T ps0, T ps1, int pK, double* hist_g,
+                                          int next_tile = 0) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int d = EXACT ? DMAX : a.d, G = a.G, dG = d * a.G;
   const bool two_phase = a.hist_mode == kHistTwoPhase;
@@ -794,8 +807,23 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
   float& inv_scale = st.inv_scale;
   const int64_t j0 = (int64_t)tile * kTile;
   const int len = (int)min((int64_t)kTile, a.neval - j0);
-  const int h0 = a.tile_first[tile];
-  const int64_t jend = j0 + len;
+  constexpr int kRelCap = 1 << 30;
+  // first cube of the tile and the number of cubes it can meet (up to the
+  // next tile's first cube); with PREFETCH the previous tile left them, and
+  // the cubes' global offsets, in shared memory
+  int h0, ncand;
+  int nh0 = 0, nend = 0;
+  if constexpr (PREFETCH) {
+    h0 = misc[2];
+    ncand = misc[3];
+    if (next_tile < a.ntiles) {  // bounds of the next tile, needed once this tile's prologue is done
+      nh0 = a.tile_first[next_tile];
+      nend = next_tile + 1 < a.ntiles ? a.tile_first[next_tile + 1] : a.NH - 1;
+    }
+  } else {
+    h0 = a.tile_first[tile];
+    ncand = min(kMaxCubesPerTile, (tile + 1 < a.ntiles ? a.tile_first[tile + 1] : a.NH - 1) - h0 + 1);
+  }
 
   // ---- fold the previous tile's fixed-point histogram ----
   if (two_phase && inv_scale > 0.0f) {
@@ -809,9 +837,49 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
     }
   }
   // ---- offsets of the cubes the tile can meet (up to the next tile's first cube), relative to the tile
-  // and clamped to +-2^30: one global load a cube; n_h is the difference of neighbours ----
-  constexpr int kRelCap = 1 << 30;
-  const int ncand = min(kMaxCubesPerTile, (tile + 1 < a.ntiles ? a.tile_first[tile + 1] : a.NH - 1) - h0 + 1);
+  // and clamped to +-2^30; n_h is the difference of neighbours ----
+  if constexpr (PREFETCH) {
+    // one pass over the prefetched offsets: relative offsets, 1/n_h and the
+    // start-cube entries of the threads whose first evaluation a cube holds
+    const int64_t* raw = S.raw_off;
+    for (int c = tid; c <= ncand; c += kFillThreads) {
+      const int64_t g0 = raw[c], rel0 = g0 - j0;
+      const int o0 = rel0 < -kRelCap ? -kRelCap : (rel0 > kRelCap ? kRelCap : (int)rel0);
+      off_r[c] = o0;
+      if (c < ncand) {
+        const int64_t g1 = raw[c + 1], rel1 = g1 - j0;
+        const int o1 = rel1 < -kRelCap ? -kRelCap : (rel1 > kRelCap ? kRelCap : (int)rel1);
+        const int r0 = max(o0, 0), r1 = min(o1, len);
+        T inv = T(0);
+        if (r0 < r1) {
+          const int64_t n = (o0 > -kRelCap && o1 < kRelCap) ? (int64_t)(o1 - o0) : g1 - g0;
+          if constexpr (sizeof(T) == 8) inv = 1.0 / (double)n;
+          else inv = __fdividef(1.0f, (float)n);
+          for (int t = (r0 + kSamplesPerThread - 1) / kSamplesPerThread; t * kSamplesPerThread < r1; ++t)
+            startc[t] = c;
+          if (r1 == len) misc[1] = c + 1;  // cubes met by the tile
+        }
+        invn[c] = inv;
+      }
+    }
+    if (tid == 0) {
+      misc[0] = 0;
+      a.carries[2 * tile] = Carry{-1, 0, 0.0, 0.0};
+      a.carries[2 * tile + 1] = Carry{-1, 0, 0.0, 0.0};
+    }
+    __syncthreads();
+    // the offsets of the next tile go to the same buffer, read by now, while
+    // this tile computes; they are complete before the barrier after phase A
+    if (next_tile < a.ntiles) {
+      const int nc = min(kMaxCubesPerTile, nend - nh0 + 1);
+      for (int c = tid; c <= nc; c += kFillThreads) cp_async8(S.raw_off + c, a.offsets + (int64_t)nh0 + c);
+      cp_async_commit();
+      if (tid == 0) {
+        misc[2] = nh0;
+        misc[3] = nc;
+      }
+    }
+  } else {
   for (int c = tid; c <= ncand; c += kFillThreads) {
     const int64_t rel = a.offsets[(int64_t)h0 + c] - j0;  // h0 + c <= NH
     off_r[c] = rel < -kRelCap ? -kRelCap : (rel > kRelCap ? kRelCap : (int)rel);
@@ -840,6 +908,7 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
     invn[c] = inv;
   }
   __syncthreads();
+  }
 
   // ---- phase A: point, map, integrand, J f; map weights ----
   const int jl0 = tid * kSamplesPerThread;
@@ -965,6 +1034,7 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
     for (int o = 16; o > 0; o >>= 1) my_max = fmaxf(my_max, __shfl_xor_sync(0xffffffffu, my_max, o));
     if (lane == 0) wmax[warp] = my_max;
   }
+  if constexpr (PREFETCH) cp_async_wait_all();
   __syncthreads();
   if constexpr (ID == kIntegrandPoints) return;
 
@@ -1047,11 +1117,13 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
     }
   };
 
+  bool had_long = false;
   for (int c = tid; c < ncub; c += kFillThreads) {
     const int r0 = max(off_r[c], 0), r1 = min(off_r[c + 1], len);
     const int L = r1 - r0;
     if (L > kLongSegment) {
       longlist[atomicAdd(&misc[0], 1)] = c;
+      had_long = true;
       continue;
     }
     // one pass over the segment, shifted by its first value: mean = v0 + s/L,
@@ -1074,7 +1146,14 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
       finish(c, L, ff_add(ff{v0, 0.0f}, sl), fmaxf(fmaf(-sd, sl, qd), 0.0f));
     }
   }
-  __syncthreads();
+  // the long segments, if the tile has any, one warp each; without them the
+  // single-integral fill ends the tile at this barrier
+  if constexpr (PREFETCH) {
+    if (!__syncthreads_or(had_long)) return;
+  } else {
+    (void)had_long;
+    __syncthreads();
+  }
   const int nlong = misc[0];
   for (int e = warp; e < nlong; e += kFillThreads / 32) {
     const int c = longlist[e];
@@ -1190,6 +1269,17 @@ __global__ void __launch_bounds__(kFillThreads, (sizeof(T) == 4 && (DMAX <= 8 ||
   double* hist_g = a.hist_part + (size_t)blockIdx.x * dG;
   fill_prologue<T>(a, S, d, table_in_smem);
   prep_params<ID, T, DMAX>(a.params_raw, a.np_raw, d, S.prm);
+  if (blockIdx.x < a.ntiles) {  // the first tile's cube offsets; later tiles' come during the tile before
+    const int t = blockIdx.x, fh0 = a.tile_first[t];
+    const int nc = min(kMaxCubesPerTile, (t + 1 < a.ntiles ? a.tile_first[t + 1] : a.NH - 1) - fh0 + 1);
+    for (int c = tid; c <= nc; c += kFillThreads) cp_async8(S.raw_off + c, a.offsets + (int64_t)fh0 + c);
+    cp_async_commit();
+    if (tid == 0) {
+      S.misc[2] = fh0;
+      S.misc[3] = nc;
+    }
+    cp_async_wait_all();
+  }
   __syncthreads();
   const T ps0 = S.prm[0], ps1 = S.prm[1];
   const int pK = (ID == VEGAS_GAUSS_SUM) ? (int)S.prm[2] : 0;
@@ -1199,7 +1289,8 @@ __global__ void __launch_bounds__(kFillThreads, (sizeof(T) == 4 && (DMAX <= 8 ||
     st.J0 = ldexpf(1.0f, -st.vexp);
   }
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x)
-    fill_tile<ID, T, DMAX, EXACT, STREAM>(a, a.rk0, a.rk1, S, st, tile, ps0, ps1, pK, hist_g);
+    fill_tile<ID, T, DMAX, EXACT, STREAM, true>(a, a.rk0, a.rk1, S, st, tile, ps0, ps1, pK, hist_g,
+                                                 tile + gridDim.x);
   if constexpr (ID == kIntegrandPoints) return;
 
   // ---- epilogue: CTA partial sums, max weight, flags, histogram ----

@@ -88,6 +88,7 @@ void magic_div(uint32_t s, uint32_t& m, uint32_t& shift) {
 int smem_layout(FillArgs& a, size_t tsz, int nprm, bool fp32) {
   const int dG = a.d * a.G;
   const size_t base = align_up(nprm * tsz) + align_up(sizeof(int) * (kMaxCubesPerTile + 1)) +
+                      align_up(sizeof(int64_t) * (kMaxCubesPerTile + 1)) +
                       align_up(tsz * kMaxCubesPerTile) + align_up(tsz * kTile) +
                       align_up(sizeof(int) * kMaxCubesPerTile) + align_up(sizeof(int) * kFillThreads) +
                       align_up(64 + 8 * 32);
@@ -137,6 +138,7 @@ int smem_layout(FillArgs& a, size_t tsz, int nprm, bool fp32) {
   }
   a.sm_params = (int)off; off += align_up(nprm * tsz);
   a.sm_off = (int)off;    off += align_up(sizeof(int) * (kMaxCubesPerTile + 1));
+  a.sm_raw = (int)off;    off += align_up(sizeof(int64_t) * (kMaxCubesPerTile + 1));
   a.sm_invn = (int)off;   off += align_up(tsz * kMaxCubesPerTile);
   a.sm_vals = (int)off;   off += align_up(tsz * kTile);
   a.sm_long = (int)off;   off += align_up(sizeof(int) * kMaxCubesPerTile);

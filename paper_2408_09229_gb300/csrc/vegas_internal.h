@@ -79,7 +79,7 @@ struct FillArgs {
   uint32_t fbits[kMaxDim];  // b_k = 23 - ceil(log2 s_k): fraction bits of an FP32 coordinate
   uint32_t rk0[10], rk1[10];  // Philox round keys
   // shared-memory byte offsets of the regions
-  int sm_table, sm_hist, sm_hacc, sm_bins, sm_wv, sm_params, sm_off, sm_invn, sm_vals, sm_long, sm_start, sm_misc,
+  int sm_table, sm_hist, sm_hacc, sm_bins, sm_wv, sm_params, sm_off, sm_raw, sm_invn, sm_vals, sm_long, sm_start, sm_misc,
       sm_total;
 };
 
