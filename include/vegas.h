@@ -88,14 +88,22 @@ enum vegas_precision {
                      cube, FP64 across cubes, map refinement and combination in FP64 */
 };
 
+/* ---- how the iterations are combined (Sec. 2.1.3) ------------------------ */
+enum vegas_weighting {
+  VEGAS_WEIGHT_AUTO = 0,             /* handle default: LAGGED with a learned proposal, else INVERSE_VARIANCE */
+  VEGAS_WEIGHT_INVERSE_VARIANCE = 1, /* Eqs. (8)-(9): weight 1/sigma_t^2                                      */
+  VEGAS_WEIGHT_LAGGED = 2            /* weight 1/sigma_{t-1}^2 (own sigma for t = 0 or sigma_{t-1} = 0);
+                                        sigma^2 = sum w_t^2 sigma_t^2 / (sum w_t)^2                            */
+};
+
 /* ======================================================================== */
 /* Level 1: handle                                                          */
 /* ======================================================================== */
 typedef struct vegas_s *vegas_handle;
 
 typedef struct {
-  double estimate;      /* Eq. (8): inverse-variance weighted mean of the used iterations   */
-  double sigma;         /* Eq. (9)                                                          */
+  double estimate;      /* Eq. (8): weighted mean of the used iterations (vegas_set_weighting) */
+  double sigma;         /* Eq. (9), or its form for lagged weights                             */
   double chi2_dof;      /* sum_t (I_t - I)^2 / sigma_t^2 / (n_used - 1); 0 for one iteration */
   int64_t neval_total;  /* evaluations made by this call                                    */
   int32_t nitn_run;     /* iterations run (fewer than asked when the rtol target was met)   */
@@ -125,6 +133,15 @@ VEGAS_API int vegas_set_nstrat_axes(vegas_handle h, const int32_t *nstrat, int d
 VEGAS_API int vegas_set_skip(vegas_handle h, int skip);
 /* VEGAS_FP64 (default) or VEGAS_FP32. */
 VEGAS_API int vegas_set_precision(vegas_handle h, int precision);
+/* How vegas_integrate combines the iterations (enum vegas_weighting; default
+ * VEGAS_WEIGHT_AUTO).  Not in the paper, which uses Eq. (8) throughout.  Eq. (8)
+ * weights iteration t by its own 1/sigma_t^2, which is biased when I_t and
+ * sigma_t are correlated: under the learned proposal the weight J f / q is
+ * heavy-tailed, an iteration that misses the tail is low in both, and the
+ * weighted mean leans low by many sigma over hundreds of iterations.  LAGGED
+ * takes the weight from the previous iteration's independent samples, so it
+ * does not depend on I_t.  Errors: EINVAL. */
+VEGAS_API int vegas_set_weighting(vegas_handle h, int weighting);
 /* Run on this cudaStream_t.  NULL restores the handle's own stream. */
 VEGAS_API int vegas_set_stream(vegas_handle h, void *stream);
 /* Stop an integrate call early once sigma/|estimate| <= rtol (0 disables the
@@ -261,6 +278,13 @@ VEGAS_API int vegas_refine(int32_t dim, int32_t nbins, double alpha, const doubl
  * Errors: EINVAL, ECUDA. */
 VEGAS_API int vegas_combine(const double *d_it_est, const double *d_it_sigma, int32_t n, int32_t skip, double *d_out,
                   void *stream);
+/* vegas_combine with a choice of weights: VEGAS_WEIGHT_INVERSE_VARIANCE is
+ * Eqs. (8)-(9), VEGAS_WEIGHT_LAGGED weights iteration t by 1/sigma_{t-1}^2 (see
+ * enum vegas_weighting; not in the paper).  The chi2/dof is the same for both.
+ * Same buffers and layout as vegas_combine.  Errors: EINVAL (also for
+ * VEGAS_WEIGHT_AUTO), ECUDA. */
+VEGAS_API int vegas_combine_weighted(const double *d_it_est, const double *d_it_sigma, int32_t n, int32_t skip,
+                           int32_t weighting, double *d_out, void *stream);
 
 /* ======================================================================== */
 /* Level 3: a batch of independent integrals                                */

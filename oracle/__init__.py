@@ -50,6 +50,7 @@ def lib():
         L.orc_refine_axis.argtypes = [i32, f64, P, P, P]
         L.orc_refine_axis.restype = i32
         L.orc_combine.argtypes = [P, P, i32, i32, P]
+        L.orc_combine_lagged.argtypes = [P, P, i32, i32, P]
         L.orc_ncubes.argtypes = [ctypes.POINTER(_Config)]
         L.orc_ncubes.restype = i64
         L.orc_default_nstrat.argtypes = [i64, i32]
@@ -126,11 +127,12 @@ def refine_axis(w, edges, alpha):
     return out, bool(unchanged)
 
 
-def combine(it_est, it_sig, skip=0):
+def combine(it_est, it_sig, skip=0, lagged=False):
+    """Eqs. (8)-(9) (R9), or with lagged=True the weights of the previous iteration (R20)"""
     I = np.ascontiguousarray(it_est, dtype=np.float64)
     S = np.ascontiguousarray(it_sig, dtype=np.float64)
     out = np.zeros(4)
-    lib().orc_combine(_ptr(I), _ptr(S), I.size, skip, _ptr(out))
+    (lib().orc_combine_lagged if lagged else lib().orc_combine)(_ptr(I), _ptr(S), I.size, skip, _ptr(out))
     return {"estimate": out[0], "sigma": out[1], "chi2_dof": out[2], "n_used": int(out[3])}
 
 

@@ -349,6 +349,38 @@ void orc_combine(const double *I, const double *sig, int n, int skip, double out
   out[3] = used;
 }
 
+void orc_combine_lagged(const double *I, const double *sig, int n, int skip, double out[4]) {
+  if (skip < 0) skip = 0;
+  int used = n - skip;
+  if (used <= 0) {
+    orc_combine(I, sig, n, skip, out);
+    return;
+  }
+  for (int t = skip; t < n; ++t)
+    if (sig[t] == 0.0) { /* exact iterations: the same rule as Eq. (8)'s */
+      orc_combine(I, sig, n, skip, out);
+      return;
+    }
+  double wsum = 0.0, wisum = 0.0, w2var = 0.0;
+  for (int t = skip; t < n; ++t) {
+    double s = (t > 0 && sig[t - 1] > 0.0) ? sig[t - 1] : sig[t]; /* the previous iteration's sigma */
+    double w = 1.0 / (s * s);
+    wsum += w;
+    wisum += w * I[t];
+    w2var += w * w * sig[t] * sig[t]; /* variance of a mean with weights fixed apart from I_t */
+  }
+  double est = wisum / wsum;
+  double chi2 = 0.0;
+  for (int t = skip; t < n; ++t) {
+    double dv = I[t] - est;
+    chi2 += dv * dv / (sig[t] * sig[t]);
+  }
+  out[0] = est;
+  out[1] = sqrt(w2var) / wsum;
+  out[2] = used > 1 ? chi2 / (used - 1) : 0.0;
+  out[3] = used;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Configuration helpers                                                     */
 /* ------------------------------------------------------------------------ */

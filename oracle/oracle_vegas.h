@@ -81,6 +81,12 @@ int orc_refine_axis(int nbins, double alpha, const double *w, const double *e_in
 /* Sec. 2.1.3 Eqs. (8)-(9), reading R9: out = {estimate, sigma, chi2/dof, n_used} */
 void orc_combine(const double *it_est, const double *it_sig, int n, int skip, double out[4]);
 
+/* Lagged weights, reading R20 (not in the paper): iteration t is weighted by
+ * 1/sigma_{t-1}^2 (its own sigma_t for t = 0 or sigma_{t-1} = 0); estimate
+ * sum w_t I_t / sum w_t, sigma sqrt(sum w_t^2 sigma_t^2) / sum w_t, chi2/dof
+ * and the sigma_t = 0 rule as in orc_combine. */
+void orc_combine_lagged(const double *it_est, const double *it_sig, int n, int skip, double out[4]);
+
 /* configuration of one integral */
 typedef struct {
   int dim;              /* d */

@@ -20,7 +20,7 @@ struct vegas_s {
   int dim = 0, nbins = 0, nstrat_scalar = 0;
   double alpha = 0.5, beta = 0.75;
   std::vector<int32_t> nstrat_axes;  // empty: use nstrat_scalar / automatic
-  int skip = 0, precision = VEGAS_FP64;
+  int skip = 0, precision = VEGAS_FP64, weighting = VEGAS_WEIGHT_AUTO;
   double rtol = 0.0;
   cudaStream_t own_stream = nullptr, user_stream = nullptr;
   bool has_user_stream = false;
@@ -244,6 +244,12 @@ extern "C" int vegas_set_nstrat_axes(vegas_handle h, const int32_t* nstrat, int 
   return VEGAS_OK;
 }
 
+extern "C" int vegas_set_weighting(vegas_handle h, int weighting) {
+  if (!h || weighting < VEGAS_WEIGHT_AUTO || weighting > VEGAS_WEIGHT_LAGGED) return VEGAS_EINVAL;
+  h->weighting = weighting;
+  return VEGAS_OK;
+}
+
 extern "C" int vegas_set_skip(vegas_handle h, int skip) {
   if (!h || skip < 0) return VEGAS_EINVAL;
   h->skip = skip;
@@ -401,7 +407,8 @@ extern "C" int vegas_integrate(vegas_handle h, int integrand, const double* para
     rc = vegas_refine(d, G, h->alpha, h->d_bins, h->d_edges[h->cur], h->d_edges[1 - h->cur], s);
     if (rc != VEGAS_OK) return rc;
     h->cur = 1 - h->cur;
-    rc = vg::launch_record_combine(h->d_result, it, h->d_it_est, h->d_it_sig, h->skip, h->d_out, s);
+    const bool lagged = h->weighting == VEGAS_WEIGHT_LAGGED || (h->weighting == VEGAS_WEIGHT_AUTO && flow);
+    rc = vg::launch_record_combine(h->d_result, it, h->d_it_est, h->d_it_sig, h->skip, h->d_out, lagged, s);
     if (rc != VEGAS_OK) return rc;
     if (train) {
       // Adam steps on the weighted samples of this iteration (x = F(x'), weight |J f| / n_h), with uniform

@@ -116,7 +116,7 @@ int allocate_impl(const float* d_ell, int64_t ncubes, int64_t neval, int uniform
 // device address of the fill's max-ell key inside its scratch area
 const int* fill_ellmax_key(const vegas_geometry* g, int64_t neval, const void* d_scratch);
 int launch_record_combine(const double* d_result, int t, double* d_est, double* d_sig, int skip, double* d_out,
-                          cudaStream_t s);
+                          bool lagged, cudaStream_t s);
 
 int dmax_for(int d);
 // learned proposal (vegas_flow.cu)

@@ -113,8 +113,17 @@ __device__ __forceinline__ void refine_axis_body(int G, double alpha, const doub
 }
 
 // Eqs. (8)-(9) over iterations t >= skip; iterations with sigma_t = 0 give
-// their mean exactly with sigma 0.  out = {estimate, sigma, chi2/dof, n_used}
-__device__ __forceinline__ void combine_dev(const double* est, const double* sig, int n, int skip, double* out) {
+// their mean exactly with sigma 0.  out = {estimate, sigma, chi2/dof, n_used}.
+// lagged: iteration t is weighted by 1/sigma_{t-1}^2, the variance estimate of
+// the iteration before it (its own for t = 0 or when sigma_{t-1} = 0).  Those
+// samples are independent of iteration t's, so the weight carries no
+// information about I_t and the weighted mean stays unbiased when I_t and
+// sigma_t are correlated (heavy-tailed weights: a run that misses the tail is
+// low in both).  The variance of a mean with such weights is
+// sum w_t^2 sigma_t^2 / (sum w_t)^2; with equal sigma both forms reduce to the
+// plain mean and sigma / sqrt(n).
+__device__ __forceinline__ void combine_dev(const double* est, const double* sig, int n, int skip, double* out,
+                                            bool lagged = false) {
   if (skip < 0) skip = 0;
   const int used = n - skip;
   if (used <= 0) {
@@ -140,11 +149,13 @@ __device__ __forceinline__ void combine_dev(const double* est, const double* sig
     out[3] = used;
     return;
   }
-  double wsum = 0.0, wisum = 0.0;
+  double wsum = 0.0, wisum = 0.0, w2var = 0.0;
   for (int t = skip; t < n; ++t) {
-    const double w = 1.0 / (sig[t] * sig[t]);
+    const double sw = (lagged && t > 0 && sig[t - 1] > 0.0) ? sig[t - 1] : sig[t];
+    const double w = 1.0 / (sw * sw);
     wsum += w;
     wisum += w * est[t];
+    w2var += w * w * sig[t] * sig[t];
   }
   const double mean = wisum / wsum;
   double chi2 = 0.0;
@@ -153,7 +164,7 @@ __device__ __forceinline__ void combine_dev(const double* est, const double* sig
     chi2 += dv * dv / (sig[t] * sig[t]);
   }
   out[0] = mean;
-  out[1] = sqrt(1.0 / wsum);
+  out[1] = lagged ? sqrt(w2var) / wsum : sqrt(1.0 / wsum);
   out[2] = used > 1 ? chi2 / (used - 1) : 0.0;
   out[3] = used;
 }

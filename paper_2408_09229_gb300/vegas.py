@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(HERE, "libvegas_gb300.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ESTATE, ENOSPACE = 0, -1, -2, -3, -4, -5, -6, -7
 FP64, FP32 = 0, 1
+WEIGHT_AUTO, WEIGHT_INVERSE_VARIANCE, WEIGHT_LAGGED = 0, 1, 2
 
 
 class VegasError(RuntimeError):
@@ -67,6 +68,7 @@ def _load():
         "vegas_destroy": ([P], i32),
         "vegas_set_nstrat_axes": ([P, P, i32], i32),
         "vegas_set_skip": ([P, i32], i32),
+        "vegas_set_weighting": ([P, i32], i32),
         "vegas_set_precision": ([P, i32], i32),
         "vegas_set_stream": ([P, P], i32),
         "vegas_set_rtol": ([P, f64], i32),
@@ -85,6 +87,7 @@ def _load():
                         P, P, sz, P], i32),
         "vegas_refine": ([i32, i32, f64, P, P, P, P], i32),
         "vegas_combine": ([P, P, i32, i32, P, P], i32),
+        "vegas_combine_weighted": ([P, P, i32, i32, i32, P, P], i32),
         "vegas_probe_pipes": ([P], i32),
         "vegas_batch_create": ([ctypes.POINTER(Problem), i32, i32, f64, f64, u64, ctypes.POINTER(P)], i32),
         "vegas_batch_destroy": ([P], i32),
@@ -175,6 +178,10 @@ class Vegas:
 
     def set_skip(self, skip):
         _check(lib.vegas_set_skip(self._h, skip), "vegas_set_skip")
+
+    def set_weighting(self, weighting):
+        """WEIGHT_AUTO (lagged with a flow, else Eq. (8)), WEIGHT_INVERSE_VARIANCE or WEIGHT_LAGGED"""
+        _check(lib.vegas_set_weighting(self._h, weighting), "vegas_set_weighting")
 
     def set_rtol(self, rtol):
         _check(lib.vegas_set_rtol(self._h, rtol), "vegas_set_rtol")
@@ -390,6 +397,11 @@ def refine(dim, nbins, alpha, bins, edges_in, edges_out, stream=None):
 def combine(it_est, it_sig, skip, out, stream=None):
     _check(lib.vegas_combine(_ptr(it_est), _ptr(it_sig), it_est.numel(), int(skip), _ptr(out), _stream_ptr(stream)),
            "vegas_combine")
+
+
+def combine_weighted(it_est, it_sig, skip, weighting, out, stream=None):
+    _check(lib.vegas_combine_weighted(_ptr(it_est), _ptr(it_sig), it_est.numel(), int(skip), int(weighting), _ptr(out),
+                                      _stream_ptr(stream)), "vegas_combine_weighted")
 
 
 # ---------------------------------------------------------------------------

@@ -272,6 +272,25 @@ def test_random_flow_keeps_the_estimate_unbiased(V, name, iid, d, params):
     assert abs(r["estimate"] - exact) < 5 * r["sigma"], (r["estimate"], r["sigma"], exact)
 
 
+def test_flow_handle_combines_with_lagged_weights(V, orc):
+    """with a flow the handle's default combination weights iteration t by 1/sigma_{t-1}^2 (R20); the
+    setter restores Eq. (8), and plain VEGAS+ keeps Eq. (8) by default"""
+    d = 4
+    p = W.ridge(4, 3, 0.1)
+    v = V.Vegas(d, 50, 0, 0.5, 0.75, precision=V.FP32)
+    v.set_flow(W.flow_params(d, seed=5, out_scale=0.05))
+    r = v.integrate(W.GAUSS_SUM, p, 100_000, 6, seed=2)
+    want = orc.combine(r["it_est"], r["it_sig"], 0, lagged=True)
+    assert r["estimate"] == pytest.approx(want["estimate"], rel=1e-13)
+    assert r["sigma"] == pytest.approx(want["sigma"], rel=1e-13)
+    assert r["chi2_dof"] == pytest.approx(want["chi2_dof"], rel=1e-11)
+    v.set_weighting(V.WEIGHT_INVERSE_VARIANCE)
+    r = v.integrate(W.GAUSS_SUM, p, 100_000, 4, seed=3)
+    assert r["estimate"] == pytest.approx(orc.combine(r["it_est"], r["it_sig"], 0)["estimate"], rel=1e-13)
+    q = V.Vegas(d, 50, 0, 0.5, 0.75, precision=V.FP32).integrate(W.GAUSS_SUM, p, 100_000, 4, seed=3)
+    assert q["estimate"] == pytest.approx(orc.combine(q["it_est"], q["it_sig"], 0)["estimate"], rel=1e-13)
+
+
 def test_online_training_in_the_loop(V):
     """training between iterations lowers the flow's loss; the trained proposal integrates the ridge with a
     lower variance per iteration than plain VEGAS+ and an estimate within 5 sigma.  (Trained on its own

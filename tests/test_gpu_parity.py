@@ -310,6 +310,32 @@ def test_combine_matches_oracle(V, orc):
         assert got[3] == want["n_used"]
 
 
+def test_combine_weighted_matches_oracle(V, orc):
+    rng = np.random.default_rng(4)
+    cases = [(1, 0), (5, 0), (10, 3), (4, 4), (7, 2)]
+    for n, skip in cases:
+        I = rng.normal(1, 0.1, n)
+        S = rng.uniform(0.01, 0.2, n)
+        if n == 7:
+            S[1] = 0.0  # a zero sigma before the used range lends no weight
+        for mode, lagged in ((V.WEIGHT_INVERSE_VARIANCE, False), (V.WEIGHT_LAGGED, True)):
+            out = torch.zeros(4, dtype=torch.float64, device="cuda")
+            V.combine_weighted(dev(I, torch.float64), dev(S, torch.float64), skip, mode, out)
+            got = out.cpu().numpy()
+            want = orc.combine(I, S, skip, lagged=lagged)
+            if want["n_used"] == 0:
+                assert got[3] == 0 and np.isnan(got[0])
+                continue
+            assert got[0] == pytest.approx(want["estimate"], rel=1e-14)
+            assert got[1] == pytest.approx(want["sigma"], rel=1e-14)
+            assert got[2] == pytest.approx(want["chi2_dof"], rel=1e-12, abs=1e-15)
+            assert got[3] == want["n_used"]
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    one = dev(np.ones(2), torch.float64)
+    with pytest.raises(V.VegasError):
+        V.combine_weighted(one, one, 0, V.WEIGHT_AUTO, out)
+
+
 # ---------------------------------------------------------------------------
 # whole iterations through the handle
 # ---------------------------------------------------------------------------

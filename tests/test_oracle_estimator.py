@@ -12,7 +12,10 @@ Eqs. (2)-(9), Algorithms 1 and 2 of the paper).
 * splitting the samples into two ranges and merging the cube statistics
   reproduces the single-range fill (the sharding of Sec. 3.4);
 * the paper's own ablation (Sec. 4.6): adaptive stratification (beta > 0)
-  lowers the error of a peaked integrand against beta = 0.
+  lowers the error of a peaked integrand against beta = 0;
+* lagged weights (R20) on inputs worked out by hand, and their point: on
+  iterations whose sigma_t is correlated with I_t (lognormal draws, mean known
+  in closed form) Eq. (8) is biased low and the lagged mean is not.
 """
 import math
 
@@ -50,6 +53,45 @@ def test_combination_by_hand(orc):
     assert c["estimate"] == 5.0 and c["sigma"] == 0.5 and c["chi2_dof"] == 0.0
     c = orc.combine([2.0, 2.0, 7.0], [0.0, 0.0, 1.0])
     assert c["estimate"] == 2.0 and c["sigma"] == 0.0
+
+
+def test_lagged_combination_by_hand(orc):
+    # weights 1 (own sigma at t = 0), 1/sigma_0^2 = 1, 1/sigma_1^2 = 1/4: estimate 4 / 2.25 = 16/9;
+    # sigma = sqrt(1 + 4 + 1/16) / 2.25 = 1; chi2 = (49/81 + (4/81)/4 + 400/81) / 2 = 25/9
+    c = orc.combine([1.0, 2.0, 4.0], [1.0, 2.0, 1.0], lagged=True)
+    assert c["estimate"] == pytest.approx(16 / 9, rel=1e-15) and c["sigma"] == pytest.approx(1.0, rel=1e-15)
+    assert c["chi2_dof"] == pytest.approx(25 / 9, rel=1e-15) and c["n_used"] == 3
+    # a skipped iteration still lends its sigma: weights 1 and 1/4, estimate 3 / 1.25, sigma sqrt(4 + 1/16) / 1.25
+    c = orc.combine([1.0, 2.0, 4.0], [1.0, 2.0, 1.0], skip=1, lagged=True)
+    assert c["estimate"] == pytest.approx(2.4, rel=1e-15)
+    assert c["sigma"] == pytest.approx(math.sqrt(4.0625) / 1.25, rel=1e-15) and c["n_used"] == 2
+    # equal sigma: the plain mean and sigma / sqrt(n), as Eq. (8)
+    c = orc.combine([1.0, 2.0, 3.0, 6.0], [0.5] * 4, lagged=True)
+    assert c["estimate"] == 3.0 and c["sigma"] == 0.25
+    # a zero sigma before the used range: that iteration weighs with its own sigma
+    c = orc.combine([2.0, 3.0, 5.0], [0.0, 1.0, 2.0], skip=1, lagged=True)
+    assert c["estimate"] == 4.0 and c["sigma"] == pytest.approx(math.sqrt(5.0) / 2.0, rel=1e-15)
+    # exact iterations in the used range: the same rule as Eq. (8)
+    c = orc.combine([2.0, 2.0, 7.0], [0.0, 0.0, 1.0], lagged=True)
+    assert c["estimate"] == 2.0 and c["sigma"] == 0.0
+
+
+def test_lagged_weights_unbiased_where_eq8_is_not(orc):
+    # each iteration averages m lognormal draws: I_t and its sigma_t are strongly correlated (a run that misses
+    # the tail is low in both), the integral E[x] = exp(mu + s^2 / 2) is known
+    rng = np.random.default_rng(20)
+    mu, s, m, n, R = 0.0, 1.5, 20, 50, 400
+    true = math.exp(mu + s * s / 2)
+    inv, lag = [], []
+    for _ in range(R):
+        x = rng.lognormal(mu, s, size=(n, m))
+        I, S = x.mean(1), x.std(1, ddof=1) / math.sqrt(m)
+        inv.append(orc.combine(I, S)["estimate"])
+        lag.append(orc.combine(I, S, lagged=True)["estimate"])
+    inv, lag = np.array(inv), np.array(lag)
+    se = lambda a: a.std(ddof=1) / math.sqrt(R)
+    assert abs(lag.mean() - true) < 4 * se(lag)
+    assert (true - inv.mean()) > 20 * se(inv)
 
 
 CASES = [
