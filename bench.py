@@ -43,6 +43,9 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one launch of the dominant kernel on this workload, from one ncu capture of
 # that kernel (dram__bytes_read.sum + dram__bytes_write.sum): the per-cube offsets and weights
 FILL_TRAFFIC_BYTES = (346.28 + 146.85) * 1e6
+# the same capture: issue slots busy and warp instructions x 32 per evaluation (1.843e9 x 32 / 1e8)
+FILL_ISSUE_ACTIVE = 0.681
+FILL_INSTR_PER_EVAL = 590
 
 
 def fp32_ops_per_eval(d=D, K=K_PEAKS):
@@ -509,6 +512,8 @@ def run_ours(args, rank, world):
         "roofline": {"bound": "alu", "kernel": "fill_kernel<GAUSS_SUM, float, 8, exact>", "achieved": achieved,
                      "peak": peak, "unit": "Tops/s (FP32-pipe operations, FMA = 1)", "frac": achieved / peak,
                      "traffic": FILL_TRAFFIC_BYTES,
+                     "issue": {"slots_busy": FILL_ISSUE_ACTIVE, "instructions_per_eval": FILL_INSTR_PER_EVAL,
+                               "source": "ncu capture of this kernel (profiles/fill_kernel_ridge8_fp32.md)"},
                      "ops_per_eval": ops, "fill_ms": fill_mean32 * 1e3,
                      "peak_basis": "FP32 FMA pipe: 128 lanes x %d SMs x 2070 MHz (max SM clock)" % sms,
                      "probe_ops_per_sm_clk": {"ffma": rates[0], "dfma": rates[1], "mufu_ex2": rates[2],

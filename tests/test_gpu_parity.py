@@ -445,6 +445,36 @@ def test_full_size_ridge8_sampled_cubes(V, orc):
     assert g["est"] == pytest.approx(np.mean(g["mean"]), rel=1e-12)
 
 
+def test_full_size_ridge8_fp32_sampled_cubes(V, orc):
+    """the bench's form at its size: FP32 evaluation, d = 8, 1e8 evaluations, 9^8 cubes; sampled cubes
+    against the oracle on the same FP32 points (R3), one by one"""
+    d, G, neval = 8, 50, 100_000_000
+    p = W.ridge8_params()
+    cfg = orc.Config(d, G, 9, 0.5, 0.75, points_f32=True)
+    nh = cfg.ncubes
+    rng = np.random.default_rng(6)
+    edges = random_edges(rng, d, G)
+    ell = (rng.standard_normal(nh, dtype=np.float32) * 3).astype(np.float32)
+    ell[-10:] = 40.0  # heavy cubes at the end of the range: they span many tiles
+    off = orc.allocate(ell, nh, neval, 0.75)
+    g = gpu_fill(V, cfg, V.FP32, W.GAUSS_SUM, p, neval, 3, 9, edges, off)
+    assert g["flags"] == 0
+    n = np.diff(off)
+    crossing = np.nonzero((off[:-1] // TILE) != ((off[1:] - 1) // TILE))[0]
+    centre = np.argmax(g["mean"])  # a cube on the ridge
+    picks = np.concatenate([np.arange(nh - 10, nh), rng.choice(nh, 24, replace=False), rng.choice(crossing, 16),
+                            [0, centre]])
+    top = float(np.max(g["mean"]))
+    for h in picks:
+        m, q = orc.cube_stats(cfg, W.GAUSS_SUM, p, 3, 9, edges, h, off[h], n[h])
+        # per evaluation the FP32 form errs by about ten float ulps (map FMA, ex2.approx at an argument up to
+        # ~100, the product J); the cube sums are compensated, so the error of the mean stays at that level
+        assert abs(g["mean"][h] - m) <= 5e-5 * abs(m) + 1e-6 * top, (h, g["mean"][h], m)
+        # M2 = sum (v - mean)^2: value errors delta ~ 1e-6 |m| move it by about 2 sum |v - mean| delta
+        assert abs(g["m2"][h] - q) <= 2e-3 * q + 2e-6 * n[h] * m * m + 1e-6 * top * top, (h, g["m2"][h], q)
+    assert g["est"] == pytest.approx(np.mean(g["mean"]), rel=1e-9)
+
+
 def test_checkpoint_resume(V):
     p = W.ridge4_params()
     a = V.Vegas(4, 50, 0, 0.5, 0.75)
