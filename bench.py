@@ -48,6 +48,16 @@ FILL_ISSUE_ACTIVE = 0.681
 FILL_INSTR_PER_EVAL = 590
 
 
+def measured_hbm_gbs():
+    """HBM copy bandwidth measured on the GB300s (MEASURED_PEAKS.json at the repository root), else the
+    fallback figure of one earlier GB300 measurement"""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
 def fp32_ops_per_eval(d=D, K=K_PEAKS):
     """FP32 FMA-pipe operations the method needs per evaluation of the d-dimensional
     ridge in the FP32 form, counted from the algorithm:
@@ -480,8 +490,10 @@ def run_ours(args, rank, world):
     evals = NEVAL * args.steps * world
     value = evals / t_dev32
     rates = V.probe_pipes()
+    atom_rate = V.probe_shared_atomics()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     ops = fp32_ops_per_eval()
+    hbm = measured_hbm_gbs()
     achieved = ops * NEVAL / fill_mean32 / 1e12
     peak = FP32_LANES_PER_SM * sms * 2070e6 / 1e12
     # per steady iteration: allocation 3 (q sums, their scan, offsets; the max of the weights comes from
@@ -517,7 +529,17 @@ def run_ours(args, rank, world):
                      "ops_per_eval": ops, "fill_ms": fill_mean32 * 1e3,
                      "peak_basis": "FP32 FMA pipe: 128 lanes x %d SMs x 2070 MHz (max SM clock)" % sms,
                      "probe_ops_per_sm_clk": {"ffma": rates[0], "dfma": rates[1], "mufu_ex2": rates[2],
-                                              "imad_hi": rates[3]}},
+                                              "imad_hi": rates[3], "shared_atomic_add": atom_rate},
+                     # the accumulation's own bounds: d shared 32-bit atomic adds per evaluation into the
+                     # fixed-point histogram against the probe's rate, and the kernel's DRAM traffic
+                     "accumulation": {
+                         "shared_atomics_per_eval": D,
+                         "achieved_per_sm_clk": D * NEVAL / (fill_mean32 * 2070e6 * sms),
+                         "peak_per_sm_clk": atom_rate,
+                         "frac": D * NEVAL / (fill_mean32 * 2070e6 * sms) / atom_rate,
+                         "dram_gbs": FILL_TRAFFIC_BYTES / fill_mean32 / 1e9,
+                         "dram_frac": FILL_TRAFFIC_BYTES / fill_mean32 / 1e9 / hbm[0],
+                         "dram_peak_gbs": hbm[0], "dram_peak_basis": hbm[1]}},
         "clocks": clocks,
         "gpu_launches": launches_per_it * args.steps,
         "timing_check": {"outer_event_ms": outer32, "sum_iteration_ms": float(np.sum(it32))},

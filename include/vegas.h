@@ -484,6 +484,14 @@ VEGAS_API int vegas_get_flow(vegas_handle h, float *params, int64_t nparams, flo
  * with the device clock counter.  Used to state the roofline of the fill
  * kernel.  Errors: ECUDA. */
 VEGAS_API int vegas_probe_pipes(double rates[4]);
+/* Measured rate of 32-bit integer atomic adds to shared memory with every lane
+ * of a warp on its own bank: lane operations per SM per clock on the current
+ * device.  It is the denominator of the accumulation's roofline; the paper
+ * accumulates with global atomicAdd instead (Sec. 3.3.3), this library with
+ * the fixed-point shared histogram of the fill.  Same method as
+ * vegas_probe_pipes (four blocks per SM, median block, SM cycle counter).
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+VEGAS_API int vegas_probe_shared_atomics(double *rate);
 
 #ifdef __cplusplus
 }

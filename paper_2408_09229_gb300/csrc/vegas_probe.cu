@@ -1,5 +1,6 @@
 // vegas_probe.cu -- issue-rate probes of the arithmetic pipes the fill kernel
-// uses (FP32 FMA, FP64 FMA, MUFU ex2, 32-bit multiply-high).  Each thread runs
+// uses (FP32 FMA, FP64 FMA, MUFU ex2, 32-bit multiply-high) and of the shared
+// memory integer atomics its map-weight histogram accumulates with.  Each thread runs
 // eight independent dependent chains; every block times itself with the SM
 // cycle counter.  The rate is operations per SM per clock, taken from the
 // median block with four blocks resident per SM.  These rates, times the SM
@@ -48,11 +49,36 @@ __global__ void __launch_bounds__(kProbeThreads) probe_kernel(float seedf, doubl
   if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
+// 32-bit integer atomic adds to shared memory, every lane of a warp on its own
+// bank (the fill's fixed-point histogram when its intervals do not collide);
+// the return value is unused, as in the fill
+__global__ void __launch_bounds__(kProbeThreads) probe_atomics_kernel(double* sink, long long* cycles) {
+  __shared__ uint32_t hs[kChains * kProbeThreads];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) hs[c * kProbeThreads + threadIdx.x] = 0u;
+  __syncthreads();
+  const long long t0 = clock64();
+#pragma unroll 4
+  for (int it = 0; it < kProbeIters; ++it) {
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) atomicAdd(&hs[c * kProbeThreads + threadIdx.x], (uint32_t)it | 1u);
+  }
+  __syncthreads();
+  const long long t1 = clock64();
+  uint32_t acc = 0u;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) acc += hs[c * kProbeThreads + threadIdx.x];
+  if (acc == 12345u) sink[0] = (double)acc;  // keeps the adds alive
+  if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
 template <int KIND>
 int run_probe(int sms, double* d_sink, long long* d_cyc, double& rate) {
   const int blocks = 4 * sms;
-  probe_kernel<KIND><<<blocks, kProbeThreads>>>(1.0f, d_sink, d_cyc);  // warm-up
-  probe_kernel<KIND><<<blocks, kProbeThreads>>>(1.0f, d_sink, d_cyc);
+  for (int rep = 0; rep < 2; ++rep) {  // warm-up, then the timed launch
+    if constexpr (KIND == 4) probe_atomics_kernel<<<blocks, kProbeThreads>>>(d_sink, d_cyc);
+    else probe_kernel<KIND><<<blocks, kProbeThreads>>>(1.0f, d_sink, d_cyc);
+  }
   VG_CHECK(cudaGetLastError());
   VG_CHECK(cudaDeviceSynchronize());
   std::vector<long long> cyc(blocks);
@@ -66,6 +92,32 @@ int run_probe(int sms, double* d_sink, long long* d_cyc, double& rate) {
 
 }  // namespace
 }  // namespace vg
+
+namespace {
+// one probe of kind KIND on the current device, with its own small buffers
+template <int KIND>
+int probe_one(double& rate) {
+  int dev = 0, sms = 0;
+  VG_CHECK(cudaGetDevice(&dev));
+  VG_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  double* d_sink = nullptr;
+  long long* d_cyc = nullptr;
+  if (cudaMalloc(&d_sink, sizeof(double)) != cudaSuccess) return VEGAS_ENOMEM;
+  if (cudaMalloc(&d_cyc, sizeof(long long) * 4 * sms) != cudaSuccess) {
+    cudaFree(d_sink);
+    return VEGAS_ENOMEM;
+  }
+  const int rc = vg::run_probe<KIND>(sms, d_sink, d_cyc, rate);
+  cudaFree(d_sink);
+  cudaFree(d_cyc);
+  return rc;
+}
+}  // namespace
+
+extern "C" int vegas_probe_shared_atomics(double* rate) {
+  if (!rate) return VEGAS_EINVAL;
+  return probe_one<4>(*rate);
+}
 
 extern "C" int vegas_probe_pipes(double rates[4]) {
   if (!rates) return VEGAS_EINVAL;

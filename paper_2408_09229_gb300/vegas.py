@@ -89,6 +89,7 @@ def _load():
         "vegas_combine": ([P, P, i32, i32, P, P], i32),
         "vegas_combine_weighted": ([P, P, i32, i32, i32, P, P], i32),
         "vegas_probe_pipes": ([P], i32),
+        "vegas_probe_shared_atomics": ([P], i32),
         "vegas_batch_create": ([ctypes.POINTER(Problem), i32, i32, f64, f64, u64, ctypes.POINTER(P)], i32),
         "vegas_batch_destroy": ([P], i32),
         "vegas_batch_set_stream": ([P, P], i32),
@@ -463,3 +464,10 @@ def probe_pipes():
     r = np.zeros(4)
     _check(lib.vegas_probe_pipes(r.ctypes.data_as(ctypes.c_void_p)), "vegas_probe_pipes")
     return r
+
+
+def probe_shared_atomics():
+    """shared-memory 32-bit atomic adds per SM per clock, lanes on distinct banks"""
+    r = ctypes.c_double()
+    _check(lib.vegas_probe_shared_atomics(ctypes.byref(r)), "vegas_probe_shared_atomics")
+    return r.value

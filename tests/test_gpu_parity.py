@@ -521,6 +521,11 @@ def test_probe_pipes(V):
     assert r[0] > 16  # FP32 FMA per SM per clock
 
 
+def test_probe_shared_atomics(V):
+    r = V.probe_shared_atomics()
+    assert 2.0 < r < 1024.0, r  # 32-bit shared atomic adds per SM per clock
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_one_cube_longer_than_2_30(V, precision):
     """a single hypercube (nstrat = 1) holding 1.2e9 evaluations: every tile lies inside it, its offsets are more
