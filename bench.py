@@ -547,6 +547,7 @@ def run_ours(args, rank, world):
     if rank == 0:
         try:
             line["cpu_baseline"] = cpu_baseline()
+            line["cpu_baseline_all_cores"] = cpu_baseline_all_cores()
         except Exception as e:  # the oracle build needs gcc; report instead of failing the bench
             line["cpu_baseline"] = {"error": str(e)[:200]}
         print(json.dumps(line))
@@ -563,6 +564,54 @@ def cpu_baseline(neval=10_000_000, nitn=2):
     return {"value": neval * nitn / dt, "unit": "evals/s", "cores": 1, "kind": "oracle",
             "sample": f"{nitn} iterations x {neval:.0e} evals of the same integrand, d, Ng, alpha, beta; "
                       f"{int(cfg.nstrat[0])}^8 cubes (auto strata for that size); {dt:.1f} s"}
+
+
+def oracle_iterations_threaded(neval, nitn, threads):
+    """The oracle's iterations with the fill on all host cores: each iteration splits the evaluation range into
+    `threads` contiguous parts, runs the oracle's range fill on each in its own thread (ctypes releases the GIL
+    for the C call), merges the partial cube statistics in range order with Chan's update and sums the map
+    weights; then the oracle's cube finish, map refinement and allocation, as one oracle iteration does.
+    Returns the per-iteration estimates."""
+    import concurrent.futures as cf
+    import oracle
+    from paper_2408_09229_gb300 import workloads as W
+    cfg = oracle.Config(D, NBINS, oracle.default_nstrat(neval, D), ALPHA, BETA)
+    params = W.ridge8_params()
+    edges = cfg.uniform_edges()
+    off = oracle.allocate(None, cfg.ncubes, neval, BETA)
+    est = []
+    bounds = [neval * r // threads for r in range(threads + 1)]
+    with cf.ThreadPoolExecutor(threads) as ex:
+        for t in range(nitn):
+            parts = list(ex.map(lambda r: oracle.fill_range(cfg, W.GAUSS_SUM, params, neval, t, SEED, edges, off,
+                                                              bounds[r], bounds[r + 1]), range(threads)))
+            n, mu, q, bins = parts[0][0].astype(np.float64), parts[0][1], parts[0][2], parts[0][3].copy()
+            for n2, mu2, q2, b2 in parts[1:]:
+                n2 = n2.astype(np.float64)
+                nt = n + n2
+                delta = mu2 - mu
+                with np.errstate(invalid="ignore", divide="ignore"):
+                    f = np.where(nt > 0, n2 / np.where(nt > 0, nt, 1.0), 0.0)
+                mu = mu + delta * f
+                q = q + q2 + delta * delta * n * f
+                n = nt
+                bins += b2
+            I, _, ell = oracle.finish_cubes(cfg, off, mu, q)
+            est.append(I)
+            edges = np.stack([oracle.refine_axis(bins[k], edges[k], ALPHA)[0] for k in range(D)])
+            off = oracle.allocate(ell, cfg.ncubes, neval, BETA)
+    return cfg, est
+
+
+def cpu_baseline_all_cores(neval=10_000_000, nitn=4):
+    """the oracle's iterations with the fill split over every host core (see oracle_iterations_threaded)"""
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    cfg, _ = oracle_iterations_threaded(neval, nitn, threads)
+    dt = time.perf_counter() - t0
+    return {"value": neval * nitn / dt, "unit": "evals/s", "cores": threads, "kind": "oracle",
+            "sample": f"{nitn} iterations x {neval:.0e} evals, the fill's evaluation range split over {threads} "
+                      f"threads; {int(cfg.nstrat[0])}^8 cubes; {dt:.1f} s"}
 
 
 def run_reference(args, rank, world):
