@@ -1,7 +1,7 @@
 // vegas_map.cu -- adjustWeights + updateMap and combineIterationsResults of
 // Algorithm 1 in cuVegas (Sec. 2.1.1 map refinement with damping alpha;
 // Sec. 2.1.3, Eqs. (8)-(9)).  Both are small: one CTA per axis for the map
-// and one thread for the combination.
+// and one CTA for the combination.
 #include <cmath>
 
 #include "vegas_device.cuh"
@@ -17,21 +17,26 @@ __global__ void __launch_bounds__(256) refine_kernel(int G, double alpha, const 
   refine_axis_body(G, alpha, bins + (size_t)k * G, e_in + (size_t)k * (G + 1), e_out + (size_t)k * (G + 1), sh);
 }
 
-__global__ void combine_kernel(const double* est, const double* sig, int n, int skip, double* out, bool lagged) {
-  combine_dev(est, sig, n, skip, out, lagged);
+__global__ void __launch_bounds__(kCombineThreads) combine_kernel(const double* est, const double* sig, int n,
+                                                                   int skip, double* out, bool lagged) {
+  combine_block(est, sig, n, skip, out, lagged);
 }
 
 // handle path: store (I_t, sigma_t) of iteration t from the fill's (I, var), then combine
-__global__ void record_combine_kernel(const double* result, int t, double* est, double* sig, int skip, double* out,
-                                      bool lagged) {
-  est[t] = result[0];
-  sig[t] = sqrt(result[1]);
-  combine_dev(est, sig, t + 1, skip, out, lagged);
+__global__ void __launch_bounds__(kCombineThreads) record_combine_kernel(const double* result, int t, double* est,
+                                                                         double* sig, int skip, double* out,
+                                                                         bool lagged) {
+  if (threadIdx.x == 0) {
+    est[t] = result[0];
+    sig[t] = sqrt(result[1]);
+  }
+  __syncthreads();
+  combine_block(est, sig, t + 1, skip, out, lagged);
 }
 
 int launch_record_combine(const double* d_result, int t, double* d_est, double* d_sig, int skip, double* d_out,
                           bool lagged, cudaStream_t s) {
-  record_combine_kernel<<<1, 1, 0, s>>>(d_result, t, d_est, d_sig, skip, d_out, lagged);
+  record_combine_kernel<<<1, kCombineThreads, 0, s>>>(d_result, t, d_est, d_sig, skip, d_out, lagged);
   return cuda_status(cudaGetLastError());
 }
 
@@ -54,7 +59,7 @@ extern "C" int vegas_refine(int32_t dim, int32_t nbins, double alpha, const doub
 extern "C" int vegas_combine(const double* d_it_est, const double* d_it_sigma, int32_t n, int32_t skip, double* d_out,
                              void* stream) {
   if (n < 1 || skip < 0 || !d_it_est || !d_it_sigma || !d_out) return VEGAS_EINVAL;
-  combine_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(d_it_est, d_it_sigma, n, skip, d_out, false);
+  combine_kernel<<<1, kCombineThreads, 0, (cudaStream_t)stream>>>(d_it_est, d_it_sigma, n, skip, d_out, false);
   return cuda_status(cudaGetLastError());
 }
 
@@ -63,7 +68,7 @@ extern "C" int vegas_combine_weighted(const double* d_it_est, const double* d_it
   if (n < 1 || skip < 0 || !d_it_est || !d_it_sigma || !d_out ||
       (weighting != VEGAS_WEIGHT_INVERSE_VARIANCE && weighting != VEGAS_WEIGHT_LAGGED))
     return VEGAS_EINVAL;
-  combine_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(d_it_est, d_it_sigma, n, skip, d_out,
-                                                     weighting == VEGAS_WEIGHT_LAGGED);
+  combine_kernel<<<1, kCombineThreads, 0, (cudaStream_t)stream>>>(d_it_est, d_it_sigma, n, skip, d_out,
+                                                                   weighting == VEGAS_WEIGHT_LAGGED);
   return cuda_status(cudaGetLastError());
 }

@@ -169,4 +169,84 @@ __device__ __forceinline__ void combine_dev(const double* est, const double* sig
   out[3] = used;
 }
 
+// combine_dev over one block of kCombineThreads threads, for the handle, which
+// combines after every iteration: iteration t is summed by thread
+// (t - skip) mod kCombineThreads and the partial sums meet in a fixed tree, so
+// the result is deterministic and a call costs O(n / kCombineThreads) instead
+// of O(n) on one thread (a 6000-iteration run spent most of its time there).
+constexpr int kCombineThreads = 256;
+
+__device__ __forceinline__ double combine_tree_sum(double v, double* buf) {
+  const int tid = threadIdx.x;
+  buf[tid] = v;
+  __syncthreads();
+#pragma unroll 1
+  for (int s = kCombineThreads / 2; s > 0; s >>= 1) {
+    if (tid < s) buf[tid] += buf[tid + s];
+    __syncthreads();
+  }
+  const double r = buf[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ void combine_block(const double* est, const double* sig, int n, int skip, double* out,
+                                              bool lagged) {
+  __shared__ double buf[kCombineThreads];
+  const int tid = threadIdx.x;
+  if (skip < 0) skip = 0;
+  const int used = n - skip;
+  if (used <= 0) {
+    if (tid == 0) {
+      out[0] = out[1] = out[2] = nan("");
+      out[3] = 0.0;
+    }
+    return;
+  }
+  double nz = 0.0, zs = 0.0, ws = 0.0, wi = 0.0, w2 = 0.0;
+  for (int t = skip + tid; t < n; t += kCombineThreads) {
+    if (sig[t] == 0.0) {
+      nz += 1.0;
+      zs += est[t];
+      continue;
+    }
+    const double sw = (lagged && t > 0 && sig[t - 1] > 0.0) ? sig[t - 1] : sig[t];
+    const double w = 1.0 / (sw * sw);
+    ws += w;
+    wi += w * est[t];
+    w2 += w * w * sig[t] * sig[t];
+  }
+  const double nzero = combine_tree_sum(nz, buf);
+  if (nzero > 0.0) {  // exact iterations: their mean, sigma 0
+    const double mean = combine_tree_sum(zs, buf) / nzero;
+    int bad = 0;
+    for (int t = skip + tid; t < n; t += kCombineThreads)
+      if (sig[t] == 0.0 && est[t] != mean) bad = 1;
+    const int any_bad = __syncthreads_or(bad);
+    if (tid == 0) {
+      out[0] = mean;
+      out[1] = 0.0;
+      out[2] = any_bad ? INFINITY : 0.0;
+      out[3] = used;
+    }
+    return;
+  }
+  const double wsum = combine_tree_sum(ws, buf);
+  const double wisum = combine_tree_sum(wi, buf);
+  const double w2var = combine_tree_sum(w2, buf);
+  const double mean = wisum / wsum;
+  double c2 = 0.0;
+  for (int t = skip + tid; t < n; t += kCombineThreads) {
+    const double dv = est[t] - mean;
+    c2 += dv * dv / (sig[t] * sig[t]);
+  }
+  const double chi2 = combine_tree_sum(c2, buf);
+  if (tid == 0) {
+    out[0] = mean;
+    out[1] = lagged ? sqrt(w2var) / wsum : sqrt(1.0 / wsum);
+    out[2] = used > 1 ? chi2 / (used - 1) : 0.0;
+    out[3] = used;
+  }
+}
+
 }  // namespace vg
