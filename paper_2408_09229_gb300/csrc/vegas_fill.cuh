@@ -400,9 +400,10 @@ __device__ __forceinline__ void decode_cube(const FillArgs& a, uint32_t h, uint3
 
 // Coordinates of cube h + 1 from those of cube h, in the encoding of
 // decode_cube: one added to axis 0 and carried upwards (an odometer).  A
-// thread's consecutive evaluations stay in a cube or move to the next one,
-// so after one full decode a step costs an add and a compare; the carry into
-// axis k is taken once in s_0 ... s_{k-1} steps.
+// thread's consecutive evaluations stay in a cube or move forward by whole
+// cubes (one when every cube holds at least two evaluations, as the
+// allocation guarantees), so after one full decode a step costs an add and a
+// compare; the carry into axis k is taken once in s_0 ... s_{k-1} steps.
 template <typename T, int DMAX, bool EXACT>
 __device__ __forceinline__ void next_cube(const FillArgs& a, uint32_t (&cb)[DMAX]) {
 #pragma unroll
@@ -681,7 +682,8 @@ struct FillShared {
   T* vals;
   int* longlist;
   int* startc;        // cube of every thread's first evaluation
-  int* misc;          // [0] long count, [1] cubes in tile
+  int* misc;          // [0] long count, [1] cubes in tile; single-integral fill: [2] first cube and [3] cubes
+                     // that the next tile can meet, whose offsets are being prefetched
   float* wmax;        // [8] per-warp max of the map weight
   double* red;
 };
