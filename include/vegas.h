@@ -468,7 +468,9 @@ VEGAS_API int vegas_flow_adam(int64_t nparams, float *d_params, const float *d_g
  * including regions that the flow's own samples no longer reach.  0 turns it
  * off (the training set is the samples alone).  vegas_get_flow copies the current
  * parameters (nparams = the count, or params NULL) and the last training loss.
- * The checkpoint of vegas_get_state does not include the flow.
+ * The checkpoint of vegas_get_state does not include the flow.  With a flow
+ * on, the default weighting (VEGAS_WEIGHT_AUTO, vegas_set_weighting) combines
+ * the iterations with lagged weights.
  * Errors: EINVAL, ENOMEM, ECUDA. */
 VEGAS_API int vegas_set_flow(vegas_handle h, const float *params, int64_t nparams);
 VEGAS_API int vegas_set_flow_training(vegas_handle h, int32_t iterations, int32_t steps_per_iteration,
