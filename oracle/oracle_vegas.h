@@ -6,7 +6,7 @@
  * load or execute this code: only tests/, __graft_entry__.smoke() and the
  * CPU-baseline / reference leg of bench.py use it.  It shares no code, header,
  * table or constant generator with the CUDA library; the two are written
- * separately from the paper and from the same readings of it (R1..R12 below).
+ * separately from the paper and from the same readings of it (numbered below).
  *
  * Every routine states the passage of the paper it follows:
  *   Sec. 2.1.1  adaptive importance sampling, Eqs. (2)-(4): the separable map,
@@ -20,8 +20,8 @@
  *   Algorithm 2 vegasFill: per evaluation, cube -> point -> Jacobian ->
  *               integrand -> map weights and cube weights.
  *   Table 3     the paper's test integrands.
- * Where the paper is silent the oracle takes readings numbered R1..R12; each
- * use below states its reading.
+ * Where the paper is silent the oracle takes numbered readings (R1..R20, the
+ * same list the kernels follow); each use below states its reading.
  *
  * Parity pins: every function here is pinned by tests/test_oracle_*.py against
  * closed forms, brute force, invariants or published known-answer values; see

@@ -131,3 +131,18 @@ def test_brute_force_rational_shares(orc):
             if h < nh:
                 acc += q[h]
         assert list(off) == want
+
+
+def test_default_strata_rule(orc):
+    """R10: the automatic strata per axis are the largest s with s^d <= N_eval / 2 (about two evaluations per
+    cube); checked by exact integer powers, and at the workloads' own sizes"""
+    for neval in (2, 3, 7, 100, 1000, 99_999, 100_000, 1_000_000, 10_000_000, 100_000_000, 400_000_000):
+        for d in (1, 2, 3, 4, 8, 12, 30):
+            s = orc.default_nstrat(neval, d)
+            assert s >= 1
+            assert s ** d <= max(neval // 2, 1) or s == 1
+            assert (s + 1) ** d > neval // 2
+    assert orc.default_nstrat(100_000, 4) == 14      # 14^4 = 38,416 cubes, 2.6 evaluations each
+    assert orc.default_nstrat(100_000_000, 8) == 9   # 9^8 = 43,046,721 cubes
+    cfg = orc.Config(3, 10, [2, 3, 5], 0.5, 0.75)
+    assert cfg.ncubes == 30
