@@ -1,0 +1,94 @@
+// Host-only check of the fill's shared-memory layout (no CUDA call is made):
+// for many (d, N_g, precision, parameter count) the regions that the fill
+// kernels index lie in order, 16-byte aligned, without overlap and inside the
+// dynamic shared memory total; the streamed path's layout without the map
+// table is checked the same way.  Prints "ok <cases>" or the first failure.
+#include "../../paper_2408_09229_gb300/csrc/vegas_fill_host.cu"
+
+#include <cstdio>
+#include <vector>
+
+using namespace vg;
+
+// The launchers and occupancy queries live in the other translation units of
+// the library; this check never launches, so they are stubs here.
+namespace vg {
+int launch_fill_f64(int, int, FillArgs&, int, cudaStream_t) { return VEGAS_ECUDA; }
+int launch_fill_f32(int, int, FillArgs&, int, cudaStream_t) { return VEGAS_ECUDA; }
+int launch_fill_f64_exact(int, int, FillArgs&, int, cudaStream_t) { return VEGAS_ECUDA; }
+int launch_fill_f32_exact(int, int, FillArgs&, int, cudaStream_t) { return VEGAS_ECUDA; }
+int launch_fill_f32_stream(int, int, FillArgs&, int, cudaStream_t) { return VEGAS_ECUDA; }
+int fill_occupancy_f64(int, int, int) { return 0; }
+int fill_occupancy_f32(int, int, int) { return 0; }
+int fill_occupancy_f64_exact(int, int, int) { return 0; }
+int fill_occupancy_f32_exact(int, int, int) { return 0; }
+int fill_occupancy_f32_stream(int, int, int) { return 0; }
+}  // namespace vg
+
+static int check(const FillArgs& a, int d, int G, size_t tsz, int nprm, const char* what) {
+  const size_t dG = (size_t)d * G;
+  const bool two = a.hist_mode == kHistTwoPhase;
+  const int per_word = 32 >> a.bin_shift;
+  struct R {
+    const char* name;
+    int off;
+    size_t size;
+  } r[] = {
+      {"table", a.sm_table, a.table_smem ? dG * 4 * tsz : 0},
+      {"hist", a.sm_hist, two ? dG * 4 : (a.hist_mode == kHistShared ? dG * tsz : 0)},
+      {"hacc", a.sm_hacc, two ? dG * (a.acc32 ? 4 : 8) : 0},
+      {"bins", a.sm_bins, two ? (size_t)kTile * 4 * ((d + per_word - 1) / per_word) : 0},
+      {"wv", a.sm_wv, two ? (size_t)kTile * 4 : 0},
+      {"params", a.sm_params, (size_t)nprm * tsz},
+      {"off", a.sm_off, sizeof(int) * (kMaxCubesPerTile + 1)},
+      {"raw", a.sm_raw, sizeof(int64_t) * (kMaxCubesPerTile + 1)},
+      {"invn", a.sm_invn, tsz * kMaxCubesPerTile},
+      {"vals", a.sm_vals, tsz * kTile},
+      {"long", a.sm_long, sizeof(int) * kMaxCubesPerTile},
+      {"start", a.sm_start, sizeof(int) * kFillThreads},
+      {"misc", a.sm_misc, 64 + 8 * 32},
+  };
+  const int n = sizeof(r) / sizeof(r[0]);
+  for (int i = 0; i < n; ++i) {
+    const size_t end = (size_t)r[i].off + r[i].size;
+    const size_t next = i + 1 < n ? (size_t)r[i + 1].off : (size_t)a.sm_total;
+    if (r[i].off % 16 != 0 || end > next) {
+      std::printf("FAIL %s d=%d G=%d tsz=%zu nprm=%d: %s at %d size %zu, next at %zu\n", what, d, G, tsz, nprm,
+                  r[i].name, r[i].off, r[i].size, next);
+      return 1;
+    }
+  }
+  if (a.sm_total > 227 * 1024) {
+    std::printf("FAIL %s d=%d G=%d: total %d above 227 KB\n", what, d, G, a.sm_total);
+    return 1;
+  }
+  return 0;
+}
+
+int main() {
+  const int dims[] = {1, 2, 3, 4, 5, 8, 9, 12, 16, 17, 30, 32};
+  const int bins[] = {2, 16, 50, 256, 257, 1024, 4096};
+  const int nprms[] = {0, 3, 64, 4 + 8 * 32};
+  int cases = 0;
+  for (int d : dims)
+    for (int G : bins)
+      for (int prec = 0; prec < 2; ++prec)
+        for (int nprm : nprms) {
+          FillArgs a{};
+          a.d = d;
+          a.G = G;
+          std::vector<int32_t> ns(d, 2);
+          if (fill_args_axes(a, ns.data(), prec == 0 ? VEGAS_FP64 : VEGAS_FP32, nprm) != VEGAS_OK) continue;
+          const size_t tsz = prec == 0 ? sizeof(double) : sizeof(float);
+          if (check(a, d, G, tsz, nprm, "layout")) return 1;
+          ++cases;
+          if (prec == 1 && a.table_smem) {  // the streamed path's alternative without the map table
+            FillArgs b = a;
+            smem_layout(b, sizeof(float), nprm, true, false);
+            if (b.table_smem || check(b, d, G, tsz, nprm, "no-table layout")) return 1;
+            ++cases;
+          }
+        }
+  std::printf("ok %d\n", cases);
+  return 0;
+}
