@@ -111,7 +111,37 @@ typedef struct {
   double *it_est;       /* caller-owned host array of it_cap entries, or NULL: I_t          */
   double *it_sigma;     /* caller-owned host array of it_cap entries, or NULL: sigma_t      */
   int32_t it_cap;
+  int32_t flags;        /* VEGAS_RESULT_* bits (below)                                      */
+  int32_t nitn_judge;   /* iterations of the other form run beside these for the judge of
+                           the learned proposal (vegas_set_flow_judge); their evaluations
+                           are in neval_total, their estimates are not in the result        */
+  int32_t pad;
+  double judge_ratio;   /* at the judge's decision: median over its window of
+                           sigma_t^2 x iteration time of plain VEGAS+ divided by that of
+                           the learned proposal (above 1: the learned proposal reaches a
+                           given error sooner); 0 when no decision was made               */
 } vegas_result;
+
+/* vegas_result.flags */
+#define VEGAS_RESULT_CHI2_HIGH 1 /* chi2/dof above the bound of vegas_set_chi2_bound: the combined
+                                    iterations disagree beyond their sigmas (Sec. 2.1.3), so the
+                                    estimate and sigma should not be trusted                      */
+#define VEGAS_RESULT_FLOW_OFF 2  /* the judge turned the learned proposal off; the result is the
+                                    plain VEGAS+ iterations run beside it                        */
+#define VEGAS_RESULT_FLOW_KEPT 4 /* the judge compared the two and kept the learned proposal      */
+
+/* Device memory hooks (not in the paper, which allocates with cudaMalloc).
+ * alloc returns `bytes` of device memory of the handle's device, aligned to at
+ * least 256 bytes, or NULL when it cannot; the library then returns
+ * VEGAS_ENOMEM from the call that asked and keeps its state as before the call.
+ * free returns a pointer that alloc gave, with the same byte count.  `stream`
+ * is the cudaStream_t (as void*) of the handle or batch: the library frees a
+ * buffer only after synchronising that stream, and reads or writes a buffer
+ * only on that stream, so a stream-ordered pool (for example a framework's
+ * caching allocator) may hand the memory back at once.  ctx is passed
+ * through unchanged. */
+typedef void *(*vegas_alloc_fn)(void *ctx, size_t bytes, void *stream);
+typedef void (*vegas_free_fn)(void *ctx, void *ptr, size_t bytes, void *stream);
 
 /* Create a handle for dimension dim, N_g = nbins intervals per axis, nstrat
  * strata per axis (nstrat <= 0: chosen at each integrate call as the largest s
@@ -150,6 +180,24 @@ VEGAS_API int vegas_set_stream(vegas_handle h, void *stream);
 VEGAS_API int vegas_set_rtol(vegas_handle h, double rtol);
 /* Back to the uniform map and uniform allocation; iteration counter to 0. */
 VEGAS_API int vegas_reset_map(vegas_handle h);
+/* Route every device allocation of the handle through alloc / free (both
+ * non-NULL), or back to cudaMalloc / cudaFree (both NULL).  Ownership: the
+ * handle still owns its buffers and the adapted map; the hook only supplies
+ * and takes back their memory.  The call moves the buffers the handle holds
+ * into memory of the new allocator (the map, the stratification, the learned
+ * proposal's parameters and Adam state are kept) and gives the old memory back
+ * to the allocator that supplied it; set the hook before the first integrate
+ * call to avoid copying the per-cube buffers.  Pinned host memory for results
+ * stays with the CUDA runtime.  On failure the handle keeps its old allocator
+ * and buffers.  Errors: EINVAL (only one of alloc, free given), ENOMEM, ECUDA. */
+VEGAS_API int vegas_set_allocator(vegas_handle h, vegas_alloc_fn alloc, vegas_free_fn free, void *ctx);
+/* chi2/dof above which vegas_integrate sets VEGAS_RESULT_CHI2_HIGH (Sec. 2.1.3:
+ * chi2/dof near 1 means the iterations agree within their sigmas).  bound <= 0
+ * (the default) takes the 0.999 quantile of chi2_nu / nu with nu = n_used - 1,
+ * by the Wilson-Hilferty cube-root normal approximation:
+ * (1 - 2/(9 nu) + 3.0902 sqrt(2/(9 nu)))^3, e.g. 11.1 at nu = 1, 3.1 at nu = 9,
+ * 1.4 at nu = 100.  One used iteration never raises the flag.  Errors: EINVAL. */
+VEGAS_API int vegas_set_chi2_bound(vegas_handle h, double bound);
 
 /* Run nitn iterations of Algorithm 1 on integrand family `integrand` with the
  * host array params[nparams] (layout in enum vegas_integrand).  Each iteration
@@ -326,6 +374,9 @@ typedef struct {
   int32_t converged;                /* 1: sigma <= rtol |estimate| was reached            */
   int32_t status;                   /* VEGAS_OK, VEGAS_ENONFINITE, or VEGAS_ECUDA when a
                                        cube split across tiles was not reassembled        */
+  int32_t flags;                    /* VEGAS_RESULT_CHI2_HIGH when chi2/dof is above the
+                                       bound of vegas_batch_set_chi2_bound                */
+  int32_t pad;
 } vegas_problem_result;
 
 /* Create a batch of nproblems integrals on the current CUDA device, with
@@ -336,7 +387,22 @@ typedef struct {
  * range; nothing is allocated), ENOMEM, ECUDA. */
 VEGAS_API int vegas_batch_create(const vegas_problem *problems, int32_t nproblems, int32_t nbins, double alpha,
                                  double beta, uint64_t seed, vegas_batch *out);
+/* vegas_batch_create with device memory from alloc / free (both non-NULL;
+ * both NULL is vegas_batch_create).  Every device buffer of the batch (one
+ * arena for all integrals and the iteration records, which grow with the
+ * iterations run) comes from alloc and goes back through free when the batch
+ * no longer needs it, under the rules given at vegas_alloc_fn.  The batch owns
+ * the buffers until then.  A NULL from alloc at create returns ENOMEM with
+ * nothing leaked; at vegas_batch_integrate it returns ENOMEM with the batch
+ * unchanged.  Pinned host memory for results stays with the CUDA runtime.
+ * Errors: as vegas_batch_create, and EINVAL when only one hook is given. */
+VEGAS_API int vegas_batch_create_ex(const vegas_problem *problems, int32_t nproblems, int32_t nbins, double alpha,
+                                    double beta, uint64_t seed, vegas_alloc_fn alloc, vegas_free_fn free, void *ctx,
+                                    vegas_batch *out);
 VEGAS_API int vegas_batch_destroy(vegas_batch b);
+/* chi2/dof above which a result gets VEGAS_RESULT_CHI2_HIGH; bound <= 0 (the
+ * default) is the 0.999 quantile rule of vegas_set_chi2_bound.  Errors: EINVAL. */
+VEGAS_API int vegas_batch_set_chi2_bound(vegas_batch b, double bound);
 /* Stream of later calls (NULL: the legacy default stream).  The graph is
  * captured on a stream of the batch's own and launched on this one. */
 VEGAS_API int vegas_batch_set_stream(vegas_batch b, void *stream);
@@ -476,6 +542,29 @@ VEGAS_API int vegas_set_flow(vegas_handle h, const float *params, int64_t nparam
 VEGAS_API int vegas_set_flow_training(vegas_handle h, int32_t iterations, int32_t steps_per_iteration,
                                       int32_t samples, int32_t batch, float lr, float temper, float floor);
 VEGAS_API int vegas_get_flow(vegas_handle h, float *params, int64_t nparams, float *last_loss);
+/* Plain VEGAS+ as the fallback and the judge of the learned proposal (not in
+ * the paper, which has no learned component; the yardstick is its estimator,
+ * Eq. (6) of Sec. 2.1.2).  window > 0 turns the judge on; it applies from the
+ * next vegas_integrate call with a flow set and carries over between calls.
+ * Beside every iteration of the learned proposal the handle then runs one
+ * plain VEGAS+ iteration (FP32 form) with its own map and stratification,
+ * drawing with Philox problem id 1 so that its points are independent of the
+ * learned proposal's.  After the flow's training iterations, the handle records
+ * for each form sigma_t^2 times the iteration's device time (CUDA events; no
+ * training step runs in these iterations): the product is the variance of the
+ * estimate per unit of device time, lower for the form that reaches a given
+ * error sooner.  Once `window` such pairs exist, and at least 5 + window pairs
+ * in all (so that the plain map has adapted), the form with the lower median
+ * product over the last `window` pairs is kept: if plain VEGAS+ wins (a tie or
+ * NaN counts for it), the learned proposal stops, the handle continues with
+ * the plain form's map, stratification and iterations, and the result combines
+ * the plain iterations (VEGAS_RESULT_FLOW_OFF); otherwise the plain form stops
+ * and the result is the learned proposal's (VEGAS_RESULT_FLOW_KEPT).  Before
+ * the decision, an rtol target (vegas_set_rtol) that either form reaches ends
+ * the call with that form's result and decides the same way.  vegas_set_flow,
+ * vegas_reset_map and vegas_set_state start the judge over.  window = 0 (the
+ * default) turns it off.  Errors: EINVAL (window < 0 or > 1024). */
+VEGAS_API int vegas_set_flow_judge(vegas_handle h, int32_t window);
 
 /* ======================================================================== */
 /* Measurement support                                                      */
@@ -494,6 +583,13 @@ VEGAS_API int vegas_probe_pipes(double rates[4]);
  * vegas_probe_pipes (four blocks per SM, median block, SM cycle counter).
  * Errors: EINVAL, ENOMEM, ECUDA. */
 VEGAS_API int vegas_probe_shared_atomics(double *rate);
+/* Measured throughput of the FP64 exp() that the FP64 form's Gaussian
+ * integrand calls once per peak and evaluation (Table 3's Gaussian and Ridge;
+ * the ridge workloads): exp calls per SM per clock on the current device, same
+ * method as vegas_probe_pipes.  With the FP64 FMA rate it states the FP64 fill's
+ * roofline: the time the FP64 pipe needs for the evaluation's FP64 operations
+ * and exponentials against the kernel's measured time.  Errors: ENOMEM, ECUDA. */
+VEGAS_API int vegas_probe_exp64(double *rate);
 
 #ifdef __cplusplus
 }

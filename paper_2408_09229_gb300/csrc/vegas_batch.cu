@@ -302,6 +302,14 @@ __global__ void batch_set_records_kernel(BatchProblem* prob, int P, double* est,
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
+// 0.999 quantile of chi2_nu / nu (Wilson-Hilferty), the default bound of VEGAS_RESULT_CHI2_HIGH
+double chi2_dof_quantile_999_batch(int nu) {
+  const double z = 3.090232306167813;
+  const double a = 2.0 / (9.0 * nu);
+  const double c = 1.0 - a + z * std::sqrt(a);
+  return c * c * c;
+}
+
 int num_sms_now() {
   int dev = 0, n = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -358,6 +366,12 @@ struct vegas_batch_s {
   double* d_it = nullptr;  // [2][P][it_cap]
   int it_cap = 0;
   int rec_bound = 0;  // upper bound of any integral's recorded iterations
+  double chi2_bound = 0.0;  // <= 0: the 0.999 quantile of chi2_nu / nu
+  // device memory hooks (NULL: cudaMalloc / cudaFree) and the sizes they were asked for
+  vegas_alloc_fn al_alloc = nullptr;
+  vegas_free_fn al_free = nullptr;
+  void* al_ctx = nullptr;
+  size_t arena_bytes = 0, it_bytes = 0;
   uint32_t* h_running = nullptr;  // pinned
   double* h_out = nullptr;        // pinned [P][4]
   BatchCtl* h_ctl = nullptr;      // pinned [P]
@@ -385,10 +399,28 @@ struct DevGuard {
   }
 };
 
+void* batch_alloc(vegas_batch_s* b, size_t bytes) {
+  void* p = nullptr;
+  if (b->al_alloc) {
+    p = b->al_alloc(b->al_ctx, bytes, (void*)b->stream());
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  return p;
+}
+
+// the caller has synchronised the batch's stream (cudaFree also synchronises)
+void batch_free(vegas_batch_s* b, void* p, size_t bytes) {
+  if (!p) return;
+  if (b->al_free) b->al_free(b->al_ctx, p, bytes, (void*)b->stream());
+  else cudaFree(p);
+}
+
 void release(vegas_batch_s* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
-  if (b->arena) cudaFree(b->arena);
-  if (b->d_it) cudaFree(b->d_it);
+  batch_free(b, b->arena, b->arena_bytes);
+  batch_free(b, b->d_it, b->it_bytes);
   if (b->h_running) cudaFreeHost(b->h_running);
   if (b->h_out) cudaFreeHost(b->h_out);
   if (b->h_ctl) cudaFreeHost(b->h_ctl);
@@ -403,8 +435,9 @@ void release(vegas_batch_s* b) {
 int ensure_records(vegas_batch_s* b, int need) {
   if (need <= b->it_cap) return VEGAS_OK;
   const int cap = std::max(need, std::max(16, 2 * b->it_cap));
-  double* nd = nullptr;
-  if (cudaMalloc((void**)&nd, sizeof(double) * 2 * (size_t)b->P * cap) != cudaSuccess) return VEGAS_ENOMEM;
+  const size_t nbytes = sizeof(double) * 2 * (size_t)b->P * cap;
+  double* nd = (double*)batch_alloc(b, nbytes);
+  if (!nd) return VEGAS_ENOMEM;
   cudaStream_t s = b->stream();
   if (b->d_it && b->it_cap > 0) {
     for (int half = 0; half < 2; ++half)
@@ -415,8 +448,9 @@ int ensure_records(vegas_batch_s* b, int need) {
   batch_set_records_kernel<<<(b->P + 127) / 128, 128, 0, s>>>(b->L.prob, b->P, nd, nd + (size_t)b->P * cap, cap);
   VG_CHECK(cudaGetLastError());
   VG_CHECK(cudaStreamSynchronize(s));
-  if (b->d_it) cudaFree(b->d_it);
+  batch_free(b, b->d_it, b->it_bytes);
   b->d_it = nd;
+  b->it_bytes = nbytes;
   b->it_cap = cap;
   b->graph_dirty = true;
   return VEGAS_OK;
@@ -533,6 +567,13 @@ int reset_batch(vegas_batch_s* b) {
 
 extern "C" int vegas_batch_create(const vegas_problem* problems, int32_t nproblems, int32_t nbins, double alpha,
                                   double beta, uint64_t seed, vegas_batch* out) {
+  return vegas_batch_create_ex(problems, nproblems, nbins, alpha, beta, seed, nullptr, nullptr, nullptr, out);
+}
+
+extern "C" int vegas_batch_create_ex(const vegas_problem* problems, int32_t nproblems, int32_t nbins, double alpha,
+                                     double beta, uint64_t seed, vegas_alloc_fn alloc, vegas_free_fn free_fn,
+                                     void* ctx, vegas_batch* out) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return VEGAS_EINVAL;
   if (!out || !problems || nproblems < 1 || nproblems > kBatchMaxProblems) return VEGAS_EINVAL;
   if (nbins < 2 || nbins > 256 || !(alpha >= 0.0) || !(beta >= 0.0 && beta <= 1.0)) return VEGAS_EINVAL;
   *out = nullptr;
@@ -593,6 +634,9 @@ extern "C" int vegas_batch_create(const vegas_problem* problems, int32_t nproble
   b->alpha = alpha;
   b->beta = beta;
   b->seed = seed;
+  b->al_alloc = alloc;
+  b->al_free = free_fn;
+  b->al_ctx = ctx;
   b->hp = std::move(hp);
   b->tiles_total = tiles;
   b->blocks_total = blocks;
@@ -635,10 +679,9 @@ extern "C" int vegas_batch_create(const vegas_problem* problems, int32_t nproble
   for (int p = 0; p < P; ++p) o_tf[p] = take(sizeof(int32_t) * (size_t)b->hp[p].ntiles);
   for (int p = 0; p < P; ++p) o_car[p] = take(sizeof(Carry) * 2 * (size_t)b->hp[p].ntiles);
   for (int p = 0; p < P; ++p) o_bsum[p] = take(sizeof(uint64_t) * (size_t)(b->hp[p].nblocks + 1));
-  if (cudaMalloc((void**)&b->arena, off) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(VEGAS_ENOMEM);
-  }
+  b->arena = (unsigned char*)batch_alloc(b, off);
+  if (!b->arena) return fail(VEGAS_ENOMEM);
+  b->arena_bytes = off;
   unsigned char* A = b->arena;
   BatchLaunch& L = b->L;
   L.P = P;
@@ -755,6 +798,12 @@ extern "C" int vegas_batch_set_stream(vegas_batch b, void* stream) {
   return VEGAS_OK;
 }
 
+extern "C" int vegas_batch_set_chi2_bound(vegas_batch b, double bound) {
+  if (!b || std::isnan(bound)) return VEGAS_EINVAL;
+  b->chi2_bound = bound > 0.0 ? bound : 0.0;
+  return VEGAS_OK;
+}
+
 extern "C" int vegas_batch_set_skip(vegas_batch b, int32_t skip) {
   if (!b || skip < 0) return VEGAS_EINVAL;
   b->skip = skip;
@@ -780,6 +829,7 @@ extern "C" int vegas_batch_integrate(vegas_batch b, int32_t nitn, double rtol, v
                                      int32_t* nitn_run, float* ms) {
   if (!b || nitn < 1 || !(rtol >= 0.0)) return VEGAS_EINVAL;
   DevGuard g(b->device);
+  clear_stale_error();
   int nrun = 0;
   int rc = run_iterations(b, nitn, rtol, &nrun, ms);
   if (rc != VEGAS_OK) return rc;
@@ -800,6 +850,12 @@ extern "C" int vegas_batch_integrate(vegas_batch b, int32_t nitn, double rtol, v
       r.converged = b->h_ctl[p].converged;
       const int f = b->h_flags[p];
       r.status = (f & 6) ? VEGAS_ECUDA : (f & 1) ? VEGAS_ENONFINITE : VEGAS_OK;
+      r.flags = 0;
+      r.pad = 0;
+      if (r.n_used >= 2) {
+        const double bound = b->chi2_bound > 0.0 ? b->chi2_bound : chi2_dof_quantile_999_batch(r.n_used - 1);
+        if (!(r.chi2_dof <= bound)) r.flags |= VEGAS_RESULT_CHI2_HIGH;
+      }
     }
   }
   return VEGAS_OK;

@@ -137,11 +137,21 @@ int derived_param_count(int integrand, int d, const double* host_params_or_null,
 
 // status helpers
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? VEGAS_OK : VEGAS_ECUDA; }
+// At the start of a call that launches kernels: an error that an earlier, unrelated runtime call left in the
+// last-error slot (a failed stream capture, the caller's own failed call) is not this call's.  A sticky error
+// (a device fault) stays: the call's own runtime calls report it.
+inline void clear_stale_error() { cudaGetLastError(); }
 
 }  // namespace vg
 
+// A failed runtime call also leaves its error in the runtime's last-error slot;
+// clear it, so that the launch check of a later call (cudaGetLastError) does
+// not report this error a second time.
 #define VG_CHECK(call)                                  \
   do {                                                  \
     cudaError_t _e = (call);                            \
-    if (_e != cudaSuccess) return VEGAS_ECUDA;          \
+    if (_e != cudaSuccess) {                            \
+      cudaGetLastError();                               \
+      return VEGAS_ECUDA;                               \
+    }                                                   \
   } while (0)

@@ -1,5 +1,6 @@
 // vegas_probe.cu -- issue-rate probes of the arithmetic pipes the fill kernel
-// uses (FP32 FMA, FP64 FMA, MUFU ex2, 32-bit multiply-high) and of the shared
+// uses (FP32 FMA, FP64 FMA, MUFU ex2, 32-bit multiply-high, the FP64 exp() of
+// the FP64 form's Gaussian integrand) and of the shared
 // memory integer atomics its map-weight histogram accumulates with.  Each thread runs
 // eight independent dependent chains; every block times itself with the SM
 // cycle counter.  The rate is operations per SM per clock, taken from the
@@ -37,6 +38,7 @@ __global__ void __launch_bounds__(kProbeThreads) probe_kernel(float seedf, doubl
       if constexpr (KIND == 0) f[c] = fmaf(f[c], 0.999999f, 1e-7f);
       else if constexpr (KIND == 1) g[c] = fma(g[c], 0.999999, 1e-7);
       else if constexpr (KIND == 2) asm volatile("ex2.approx.ftz.f32 %0, %0;" : "+f"(f[c]));
+      else if constexpr (KIND == 5) g[c] = exp(-g[c]);  // converges to 0.567..., stays in range
       else u[c] = __umulhi(u[c], 0x9E3779B9u) + c;
     }
   }
@@ -113,6 +115,11 @@ int probe_one(double& rate) {
   return rc;
 }
 }  // namespace
+
+extern "C" int vegas_probe_exp64(double* rate) {
+  if (!rate) return VEGAS_EINVAL;
+  return probe_one<5>(*rate);
+}
 
 extern "C" int vegas_probe_shared_atomics(double* rate) {
   if (!rate) return VEGAS_EINVAL;

@@ -23,6 +23,11 @@ LIB_PATH = os.path.join(HERE, "libvegas_gb300.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ESTATE, ENOSPACE = 0, -1, -2, -3, -4, -5, -6, -7
 FP64, FP32 = 0, 1
+RESULT_CHI2_HIGH, RESULT_FLOW_OFF, RESULT_FLOW_KEPT = 1, 2, 4
+
+# device memory hooks (vegas_alloc_fn, vegas_free_fn)
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 WEIGHT_AUTO, WEIGHT_INVERSE_VARIANCE, WEIGHT_LAGGED = 0, 1, 2
 
 
@@ -36,7 +41,8 @@ class Result(ctypes.Structure):
     _fields_ = [("estimate", ctypes.c_double), ("sigma", ctypes.c_double), ("chi2_dof", ctypes.c_double),
                 ("neval_total", ctypes.c_int64), ("nitn_run", ctypes.c_int32), ("n_used", ctypes.c_int32),
                 ("it_est", ctypes.POINTER(ctypes.c_double)), ("it_sigma", ctypes.POINTER(ctypes.c_double)),
-                ("it_cap", ctypes.c_int32)]
+                ("it_cap", ctypes.c_int32), ("flags", ctypes.c_int32), ("nitn_judge", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("judge_ratio", ctypes.c_double)]
 
 
 class Problem(ctypes.Structure):
@@ -48,7 +54,7 @@ class Problem(ctypes.Structure):
 class ProblemResult(ctypes.Structure):
     _fields_ = [("estimate", ctypes.c_double), ("sigma", ctypes.c_double), ("chi2_dof", ctypes.c_double),
                 ("n_used", ctypes.c_int32), ("nitn_run", ctypes.c_int32), ("converged", ctypes.c_int32),
-                ("status", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("flags", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class Geometry(ctypes.Structure):
@@ -73,6 +79,9 @@ def _load():
         "vegas_set_stream": ([P, P], i32),
         "vegas_set_rtol": ([P, f64], i32),
         "vegas_reset_map": ([P], i32),
+        "vegas_set_allocator": ([P, ALLOC_FN, FREE_FN, P], i32),
+        "vegas_set_chi2_bound": ([P, f64], i32),
+        "vegas_set_flow_judge": ([P, i32], i32),
         "vegas_integrate": ([P, i32, P, i64, i64, i32, u64, ctypes.POINTER(Result)], i32),
         "vegas_get_timings": ([P, P, P, i32, ctypes.POINTER(i32)], i32),
         "vegas_get_state": ([P, P, ctypes.POINTER(sz)], i32),
@@ -90,8 +99,12 @@ def _load():
         "vegas_combine_weighted": ([P, P, i32, i32, i32, P, P], i32),
         "vegas_probe_pipes": ([P], i32),
         "vegas_probe_shared_atomics": ([P], i32),
+        "vegas_probe_exp64": ([P], i32),
         "vegas_batch_create": ([ctypes.POINTER(Problem), i32, i32, f64, f64, u64, ctypes.POINTER(P)], i32),
+        "vegas_batch_create_ex": ([ctypes.POINTER(Problem), i32, i32, f64, f64, u64, ALLOC_FN, FREE_FN, P,
+                                   ctypes.POINTER(P)], i32),
         "vegas_batch_destroy": ([P], i32),
+        "vegas_batch_set_chi2_bound": ([P, f64], i32),
         "vegas_batch_set_stream": ([P, P], i32),
         "vegas_batch_set_skip": ([P, i32], i32),
         "vegas_batch_set_launch": ([P, i32, i32, i32], i32),
@@ -135,6 +148,37 @@ def _check(status, where):
 def _ptr(t):
     """device pointer of a torch tensor (or None)"""
     return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def hooks(alloc, free):
+    """ctypes function pointers for the device memory hooks: alloc(nbytes, stream) -> device address or 0,
+    free(address, nbytes, stream).  Keep the returned pair alive while a handle or batch uses it."""
+    if alloc is None and free is None:
+        return ALLOC_FN(), FREE_FN()
+
+    def _alloc(ctx, nbytes, stream):
+        try:
+            return int(alloc(int(nbytes), stream or 0)) or None
+        except Exception:
+            return None
+
+    def _free(ctx, ptr, nbytes, stream):
+        free(int(ptr), int(nbytes), stream or 0)
+
+    return ALLOC_FN(_alloc), FREE_FN(_free)
+
+
+def torch_hooks():
+    """(alloc, free) through torch's CUDA caching allocator on the current device"""
+    import torch
+
+    def alloc(nbytes, stream):
+        return torch.cuda.caching_allocator_alloc(nbytes, stream=stream)
+
+    def free(ptr, nbytes, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return alloc, free
 
 
 def _stream_ptr(stream):
@@ -197,6 +241,21 @@ class Vegas:
     def reset_map(self):
         _check(lib.vegas_reset_map(self._h), "vegas_reset_map")
 
+    def set_allocator(self, alloc=None, free=None):
+        """vegas_set_allocator: alloc(nbytes, stream) -> device address (0 when it cannot), free(address, nbytes,
+        stream); both None returns to cudaMalloc / cudaFree"""
+        fa, ff = hooks(alloc, free)
+        _check(lib.vegas_set_allocator(self._h, fa, ff, None), "vegas_set_allocator")
+        self._hooks = (fa, ff)
+
+    def set_chi2_bound(self, bound):
+        _check(lib.vegas_set_chi2_bound(self._h, float(bound)), "vegas_set_chi2_bound")
+
+    def set_flow_judge(self, window):
+        """vegas_set_flow_judge: plain VEGAS+ beside the learned proposal until a decision over `window`
+        iterations after training; 0 turns it off"""
+        _check(lib.vegas_set_flow_judge(self._h, int(window)), "vegas_set_flow_judge")
+
     def integrate(self, integrand, params, neval, nitn, seed=0, check=True):
         p = np.ascontiguousarray(params, dtype=np.float64) if len(params) else np.zeros(0)
         it_est = np.zeros(nitn)
@@ -212,7 +271,7 @@ class Vegas:
         n = r.nitn_run
         return {"estimate": r.estimate, "sigma": r.sigma, "chi2_dof": r.chi2_dof, "n_used": r.n_used,
                 "nitn_run": n, "neval_total": r.neval_total, "it_est": it_est[:n], "it_sig": it_sig[:n],
-                "status": st}
+                "status": st, "flags": r.flags, "nitn_judge": r.nitn_judge, "judge_ratio": r.judge_ratio}
 
     def timings(self, cap=4096):
         it = np.zeros(cap, dtype=np.float32)
@@ -229,6 +288,19 @@ class Vegas:
         buf = ctypes.create_string_buffer(size.value)
         _check(lib.vegas_get_state(self._h, buf, ctypes.byref(size)), "vegas_get_state")
         return buf.raw[:size.value]
+
+    def state_arrays(self):
+        """the checkpoint's contents as arrays: edges [dim][nbins+1], the stratification weights ell (float32
+        [ncubes], or None before the first iteration), the strata and the iteration counter"""
+        blob = self.get_state()
+        ell_valid = int(np.frombuffer(blob, np.int32, 1, 20)[0])
+        ncubes, iteration = (int(x) for x in np.frombuffer(blob, np.int64, 2, 24))
+        nstrat = np.frombuffer(blob, np.int32, self.dim, 40).copy()
+        head = 40 + 4 * 32
+        ne = self.dim * (self.nbins + 1)
+        edges = np.frombuffer(blob, np.float64, ne, head).reshape(self.dim, self.nbins + 1).copy()
+        ell = np.frombuffer(blob, np.float32, ncubes, head + 8 * ne).copy() if ell_valid else None
+        return {"edges": edges, "ell": ell, "nstrat": nstrat if ell_valid else None, "iteration": iteration}
 
     def set_state(self, blob):
         buf = ctypes.create_string_buffer(blob, len(blob))
@@ -275,7 +347,8 @@ class Batch:
     problems: a list of dicts with keys dim, integrand, params, neval and
     optionally nstrat (0: automatic)."""
 
-    def __init__(self, problems, nbins=50, alpha=0.5, beta=0.75, seed=0, skip=0, stream=None):
+    def __init__(self, problems, nbins=50, alpha=0.5, beta=0.75, seed=0, skip=0, stream=None, alloc=None,
+                 free=None):
         n = len(problems)
         arr = (Problem * n)()
         self._params = []
@@ -285,7 +358,9 @@ class Batch:
             arr[i] = Problem(int(q["dim"]), int(q["integrand"]), prm.ctypes.data if prm.size else None, prm.size,
                              int(q["neval"]), int(q.get("nstrat", 0)), 0)
         h = ctypes.c_void_p()
-        _check(lib.vegas_batch_create(arr, n, nbins, alpha, beta, int(seed), ctypes.byref(h)), "vegas_batch_create")
+        self._hooks = hooks(alloc, free)
+        _check(lib.vegas_batch_create_ex(arr, n, nbins, alpha, beta, int(seed), self._hooks[0], self._hooks[1], None,
+                                         ctypes.byref(h)), "vegas_batch_create_ex")
         self._h = h
         self.n, self.nbins = n, nbins
         self.dims = [int(q["dim"]) for q in problems]
@@ -304,6 +379,9 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+    def set_chi2_bound(self, bound):
+        _check(lib.vegas_batch_set_chi2_bound(self._h, float(bound)), "vegas_batch_set_chi2_bound")
 
     def set_launch(self, variant, ctas_per_sm=0, chunk_tiles=4):
         _check(lib.vegas_batch_set_launch(self._h, variant, ctas_per_sm, chunk_tiles), "vegas_batch_set_launch")
@@ -325,7 +403,8 @@ class Batch:
         _check(lib.vegas_batch_integrate(self._h, int(nitn), float(rtol), res, ctypes.byref(nrun), ctypes.byref(ms)),
                "vegas_batch_integrate")
         out = [{"estimate": r.estimate, "sigma": r.sigma, "chi2_dof": r.chi2_dof, "n_used": r.n_used,
-                "nitn_run": r.nitn_run, "converged": bool(r.converged), "status": r.status} for r in res]
+                "nitn_run": r.nitn_run, "converged": bool(r.converged), "status": r.status, "flags": r.flags}
+               for r in res]
         return out, nrun.value, ms.value
 
     def info(self, p):
@@ -464,6 +543,13 @@ def probe_pipes():
     r = np.zeros(4)
     _check(lib.vegas_probe_pipes(r.ctypes.data_as(ctypes.c_void_p)), "vegas_probe_pipes")
     return r
+
+
+def probe_exp64():
+    """FP64 exp() calls per SM per clock (vegas_probe_exp64)"""
+    r = ctypes.c_double()
+    _check(lib.vegas_probe_exp64(ctypes.byref(r)), "vegas_probe_exp64")
+    return r.value
 
 
 def probe_shared_atomics():
