@@ -93,6 +93,42 @@ __global__ void __launch_bounds__(1024) batch_plan_kernel(const __grid_constant_
   }
 }
 
+// the tile prefix of each fill group: block g sums the tiles of the running integrals of group g (the other
+// integrals count 0, so a search in the prefix skips them), 4 integrals a thread (P <= 4096); zeroes the group's
+// work counter
+__global__ void __launch_bounds__(1024) batch_group_plan_kernel(const __grid_constant__ BatchLaunch L) {
+  __shared__ int64_t wt[32];
+  const int g = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  int32_t* pre = L.grp_tile + (size_t)g * (L.P + 1);
+  int64_t nt[4], st = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int p = 4 * tid + i;
+    const bool on = p < L.P && L.ctl[p].active && L.prob[p].group == g;
+    nt[i] = on ? L.prob[p].a.ntiles : 0;
+    st += nt[i];
+  }
+  int64_t xt = st;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t yt = __shfl_up_sync(0xffffffffu, xt, o);
+    if (lane >= o) xt += yt;
+  }
+  if (lane == 31) wt[w] = xt;
+  __syncthreads();
+  int64_t bt = xt - st;
+  for (int k = 0; k < w; ++k) bt += wt[k];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int p = 4 * tid + i;
+    if (p < L.P) pre[p] = (int32_t)bt;
+    if (p == L.P - 1) pre[L.P] = (int32_t)(bt + nt[i]);
+    bt += nt[i];
+  }
+  if (tid == 0) L.counter[2 + g] = 0u;
+}
+
 __global__ void __launch_bounds__(kAllocThreads) batch_bsum_kernel(const __grid_constant__ BatchLaunch L) {
   const int64_t blk = blockIdx.x;
   if (blk >= L.act_blk[L.P]) return;
@@ -302,6 +338,8 @@ __global__ void batch_set_records_kernel(BatchProblem* prob, int P, double* est,
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
+constexpr int kGroupDmax[3] = {4, 8, 16};
+
 // 0.999 quantile of chi2_nu / nu (Wilson-Hilferty), the default bound of VEGAS_RESULT_CHI2_HIGH
 double chi2_dof_quantile_999_batch(int nu) {
   const double z = 3.090232306167813;
@@ -338,6 +376,27 @@ int default_nstrat_batch(int64_t neval, int d) {
 }
 
 }  // namespace
+// the fill of group g: family g / 3, width kGroupDmax[g % 3]
+int launch_batch_fill(int variant, int group, const BatchLaunch& L, int grid, int smem, cudaStream_t s) {
+  if (variant < 0 || variant >= kBatchVariants || group < 0 || group >= kBatchGroups) return VEGAS_EINVAL;
+  const int dmax = kGroupDmax[group % 3];
+  switch (group / 3) {
+    case 0: return launch_batch_fill_gauss(variant, dmax, group, L, grid, smem, s);
+    case 1: return launch_batch_fill_peak(variant, dmax, group, L, grid, smem, s);
+    default: return launch_batch_fill_osc(variant, dmax, group, L, grid, smem, s);
+  }
+}
+
+int batch_fill_occupancy(int variant, int group, int smem) {
+  if (variant < 0 || variant >= kBatchVariants || group < 0 || group >= kBatchGroups) return 0;
+  const int dmax = kGroupDmax[group % 3];
+  switch (group / 3) {
+    case 0: return batch_fill_occupancy_gauss(variant, dmax, smem);
+    case 1: return batch_fill_occupancy_peak(variant, dmax, smem);
+    default: return batch_fill_occupancy_osc(variant, dmax, smem);
+  }
+}
+
 }  // namespace vg
 
 using namespace vg;
@@ -377,7 +436,9 @@ struct vegas_batch_s {
   BatchCtl* h_ctl = nullptr;      // pinned [P]
   int* h_flags = nullptr;         // pinned [P]
   // launch shape and graph
-  int variant = 0, ctas_per_sm = 0, chunk = 4, fill_grid = 1;
+  int variant = 0, ctas_per_sm = 0, chunk = 4;
+  int fill_grid[kBatchGroups] = {};        // 0: no integral of the group
+  int64_t group_tiles[kBatchGroups] = {};  // tiles of each fill group (all integrals)
   cudaGraphExec_t exec = nullptr;
   bool graph_dirty = true;
   double graph_rtol = -1.0;
@@ -462,6 +523,8 @@ int enqueue_iteration(vegas_batch_s* b, const BatchLaunch& L, cudaStream_t s) {
   VG_CHECK(cudaMemsetAsync(b->d_bins, 0, sizeof(double) * b->bins_total, s));
   batch_plan_kernel<<<1, 1024, 0, s>>>(L);
   VG_CHECK(cudaGetLastError());
+  batch_group_plan_kernel<<<kBatchGroups, 1024, 0, s>>>(L);
+  VG_CHECK(cudaGetLastError());
   const unsigned nb = (unsigned)std::max<int64_t>(1, b->blocks_total);
   batch_bsum_kernel<<<nb, kAllocThreads, 0, s>>>(L);
   VG_CHECK(cudaGetLastError());
@@ -472,8 +535,11 @@ int enqueue_iteration(vegas_batch_s* b, const BatchLaunch& L, cudaStream_t s) {
   const unsigned ntb = (unsigned)((b->tiles_total + 255) / 256);
   batch_tile_first_kernel<<<ntb, 256, 0, s>>>(L);
   VG_CHECK(cudaGetLastError());
-  int rc = launch_batch_fill(b->variant, L, b->fill_grid, b->smem, s);
-  if (rc != VEGAS_OK) return rc;
+  for (int g = 0; g < kBatchGroups; ++g) {
+    if (b->fill_grid[g] <= 0) continue;  // no integral of this group
+    const int rc = launch_batch_fill(b->variant, g, L, b->fill_grid[g], b->smem, s);
+    if (rc != VEGAS_OK) return rc;
+  }
   batch_carry_scan_kernel<<<ntb, kCarryBlock, 0, s>>>(L);
   VG_CHECK(cudaGetLastError());
   batch_fixup_kernel<<<ntb, 256, 0, s>>>(L);
@@ -500,11 +566,16 @@ int capture(vegas_batch_s* b, double rtol) {
   L.rtol = rtol;
   L.skip = b->skip;
   L.chunk_tiles = b->chunk;
-  // the fill's grid: resident CTAs per SM (sets the kernel's shared-memory attribute) times SMs
-  const int occ = batch_fill_occupancy(b->variant, b->smem);
-  if (occ <= 0) return VEGAS_ECUDA;
-  const int per_sm = b->ctas_per_sm > 0 ? std::min(b->ctas_per_sm, occ) : occ;
-  b->fill_grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * b->sms, b->tiles_total));
+  // each group's fill grid: resident CTAs per SM (sets the kernel's shared-memory attribute) times SMs, at most
+  // the group's tiles; 0 for a group with no integral
+  for (int g = 0; g < kBatchGroups; ++g) {
+    b->fill_grid[g] = 0;
+    if (b->group_tiles[g] == 0) continue;
+    const int occ = batch_fill_occupancy(b->variant, g, b->smem);
+    if (occ <= 0) return VEGAS_ECUDA;
+    const int per_sm = b->ctas_per_sm > 0 ? std::min(b->ctas_per_sm, occ) : occ;
+    b->fill_grid[g] = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * b->sms, b->group_tiles[g]));
+  }
   cudaGraph_t g = nullptr;
   VG_CHECK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
   const int rc = enqueue_iteration(b, L, b->cap_stream);
@@ -664,7 +735,8 @@ extern "C" int vegas_batch_create_ex(const vegas_problem* problems, int32_t npro
   };
   const size_t o_prob = take(sizeof(BatchProblem) * P), o_ctl = take(sizeof(BatchCtl) * P),
                o_act_tile = take(sizeof(int32_t) * (P + 1)), o_act_blk = take(sizeof(int64_t) * (P + 1)),
-               o_counter = take(sizeof(uint32_t) * 2), o_acc = take(sizeof(double) * 2 * P),
+               o_grp_tile = take(sizeof(int32_t) * kBatchGroups * (P + 1)),
+               o_counter = take(sizeof(uint32_t) * (2 + kBatchGroups)), o_acc = take(sizeof(double) * 2 * P),
                o_key = take(sizeof(int) * P), o_flags = take(sizeof(int) * P), o_out = take(sizeof(double) * 4 * P),
                o_vexp = take(sizeof(int) * P);
   std::vector<size_t> o_edges(P), o_bins(P), o_params(P), o_offsets(P), o_ell(P), o_tf(P), o_car(P), o_bsum(P);
@@ -694,6 +766,7 @@ extern "C" int vegas_batch_create_ex(const vegas_problem* problems, int32_t npro
   L.ctl = (BatchCtl*)(A + o_ctl);
   L.act_tile = (int32_t*)(A + o_act_tile);
   L.act_blk = (int64_t*)(A + o_act_blk);
+  L.grp_tile = (int32_t*)(A + o_grp_tile);
   L.counter = (uint32_t*)(A + o_counter);
   L.acc = (double*)(A + o_acc);
   L.key = (int*)(A + o_key);
@@ -761,6 +834,8 @@ extern "C" int vegas_batch_create_ex(const vegas_problem* problems, int32_t npro
     q.bsum = (uint64_t*)(A + o_bsum[p]);
     q.nblocks = h.nblocks;
     q.dmax = h.dmax;
+    q.group = batch_group(h.iid, h.dmax);
+    b->group_tiles[q.group] += h.ntiles;
     if (!h.params.empty() &&
         cudaMemcpy(A + o_params[p], h.params.data(), sizeof(double) * h.params.size(), cudaMemcpyHostToDevice) !=
             cudaSuccess)
@@ -869,7 +944,9 @@ extern "C" int vegas_batch_tune(vegas_batch b, int32_t* variant, int32_t* ctas_p
   float best = INFINITY;
   int bv = b->variant, bc = b->ctas_per_sm, bk = b->chunk;
   for (int v = 0; v < kBatchVariants; ++v) {
-    const int occ = batch_fill_occupancy(v, b->smem);
+    int occ = 0;  // the most resident CTAs of any present group's kernel (capture clamps each group to its own)
+    for (int g = 0; g < kBatchGroups; ++g)
+      if (b->group_tiles[g] > 0) occ = std::max(occ, batch_fill_occupancy(v, g, b->smem));
     for (int c = 1; c <= occ; ++c) {
       for (int k : chunks) {
         int rc = vegas_batch_set_launch(b, v, c, k);

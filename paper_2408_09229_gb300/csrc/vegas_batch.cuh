@@ -20,6 +20,14 @@ constexpr int kBatchMaxDim = 16;
 // batched fill variants: minimum resident CTAs per SM of the launch bound
 constexpr int kBatchVariants = 2;
 constexpr int kBatchMinBlocks[kBatchVariants] = {4, 2};
+// The fill runs one persistent kernel per group of integrals with the same family and width (3 families x
+// widths 4, 8, 16): each kernel holds one instance of the fill's tile code, so its registers are those of that
+// instance alone (one kernel over every group spilled to local memory at 64 registers).
+constexpr int kBatchGroups = 9;
+__host__ __device__ inline int batch_group(int iid, int dmax) {
+  const int fam = iid == VEGAS_GAUSS_SUM ? 0 : iid == VEGAS_PRODUCT_PEAK ? 1 : 2;
+  return fam * 3 + (dmax == 4 ? 0 : dmax == 8 ? 1 : 2);
+}
 
 // per-integral data that only the batched driver uses
 struct BatchProblem {
@@ -30,7 +38,7 @@ struct BatchProblem {
   double* it_est;   // [cap] I_t of every recorded iteration
   double* it_sig;   // [cap] sigma_t
   int dmax;         // 4, 8 or 16: the fill instantiation
-  int pad;
+  int group;        // batch_group(family, dmax): the fill kernel that runs it
 };
 
 // batch-wide state, in device memory
@@ -49,8 +57,10 @@ struct BatchLaunch {
   BatchProblem* prob;    // [P]
   BatchCtl* ctl;         // [P]
   int32_t* act_tile;     // [P+1] prefix of the tiles of running integrals
+  int32_t* grp_tile;     // [kBatchGroups][P+1] the same prefix restricted to each fill group
   int64_t* act_blk;      // [P+1] prefix of their allocation blocks
-  uint32_t* counter;     // [2] fill work counter, running integrals after the iteration
+  uint32_t* counter;     // [2 + kBatchGroups] running integrals after the iteration at [1]; fill work
+                         // counter of group g at [2 + g]
   double* acc;           // [P][2] sum of cube means, sum of cube variances
   int* key;              // [P] order-preserving key of the largest ell
   int* flags;            // [P] 1: non-finite value, 2: a split cube was not reassembled
@@ -71,7 +81,14 @@ __device__ __forceinline__ int batch_find(const I* __restrict__ pre, int P, I i)
   return lo;
 }
 
-int launch_batch_fill(int variant, const BatchLaunch& L, int grid, int smem, cudaStream_t s);
-int batch_fill_occupancy(int variant, int smem);
+// the fill of group g (batch_group) in register-budget variant v; one definition per family file
+int launch_batch_fill(int variant, int group, const BatchLaunch& L, int grid, int smem, cudaStream_t s);
+int batch_fill_occupancy(int variant, int group, int smem);
+int launch_batch_fill_gauss(int variant, int dmax, int group, const BatchLaunch& L, int grid, int smem, cudaStream_t s);
+int launch_batch_fill_peak(int variant, int dmax, int group, const BatchLaunch& L, int grid, int smem, cudaStream_t s);
+int launch_batch_fill_osc(int variant, int dmax, int group, const BatchLaunch& L, int grid, int smem, cudaStream_t s);
+int batch_fill_occupancy_gauss(int variant, int dmax, int smem);
+int batch_fill_occupancy_peak(int variant, int dmax, int smem);
+int batch_fill_occupancy_osc(int variant, int dmax, int smem);
 
 }  // namespace vg

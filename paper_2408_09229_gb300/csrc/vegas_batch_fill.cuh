@@ -2,8 +2,11 @@
 // the tiles of every running integral of a batch (Algorithm 2 of cuVegas per
 // integral; the batch shares the launch).
 //
-// The CTAs take chunks of chunk_tiles consecutive tiles of the batch's work
-// list from a global counter, so integrals of different cost balance out.
+// The integrals fall into groups of one family and width; each group has its
+// own persistent kernel (one instance of the tile code: the registers of that
+// instance alone).  The CTAs take chunks of chunk_tiles consecutive tiles of
+// the group's work list from the group's counter, so integrals of different
+// cost balance out.
 // A CTA keeps one integral's state in shared memory: its FillArgs, its map
 // table, its derived parameters and its map-weight histogram.  When the next
 // tile belongs to another integral the CTA flushes that state (the
@@ -21,24 +24,6 @@
 
 namespace vg {
 
-// derived parameters of the integral in sa, for its family and width
-__device__ __forceinline__ void batch_prep(const FillArgs& sa, int dmax, float* prm) {
-  const int d = sa.d;
-#define VG_PREP(ID, DM) prep_params<ID, float, DM>(sa.params_raw, sa.np_raw, d, prm)
-  switch (sa.iid * 4 + (dmax == 4 ? 0 : dmax == 8 ? 1 : 2)) {
-    case VEGAS_GAUSS_SUM * 4 + 0: VG_PREP(VEGAS_GAUSS_SUM, 4); break;
-    case VEGAS_GAUSS_SUM * 4 + 1: VG_PREP(VEGAS_GAUSS_SUM, 8); break;
-    case VEGAS_GAUSS_SUM * 4 + 2: VG_PREP(VEGAS_GAUSS_SUM, 16); break;
-    case VEGAS_PRODUCT_PEAK * 4 + 0: VG_PREP(VEGAS_PRODUCT_PEAK, 4); break;
-    case VEGAS_PRODUCT_PEAK * 4 + 1: VG_PREP(VEGAS_PRODUCT_PEAK, 8); break;
-    case VEGAS_PRODUCT_PEAK * 4 + 2: VG_PREP(VEGAS_PRODUCT_PEAK, 16); break;
-    case VEGAS_OSCILLATORY * 4 + 0: VG_PREP(VEGAS_OSCILLATORY, 4); break;
-    case VEGAS_OSCILLATORY * 4 + 1: VG_PREP(VEGAS_OSCILLATORY, 8); break;
-    default: VG_PREP(VEGAS_OSCILLATORY, 16); break;
-  }
-#undef VG_PREP
-}
-
 template <int ID, int DMAX>
 __device__ __forceinline__ void batch_tile_one(const FillArgs& sa, const BatchLaunch& L, unsigned char* smem,
                                                FillState<float>& st, int tile) {
@@ -48,21 +33,6 @@ __device__ __forceinline__ void batch_tile_one(const FillArgs& sa, const BatchLa
   const int pK = (ID == VEGAS_GAUSS_SUM) ? (int)S.prm[2] : 0;
   // 16-axis integrals take the streamed point path (64 registers, no spills)
   fill_tile<ID, float, DMAX, false, (DMAX >= 16)>(sa, L.rk0, L.rk1, S, st, tile, ps0, ps1, pK, nullptr);
-}
-
-__device__ __forceinline__ void batch_tile(const FillArgs& sa, int dmax, const BatchLaunch& L, unsigned char* smem,
-                                           FillState<float>& st, int tile) {
-  switch (sa.iid * 4 + (dmax == 4 ? 0 : dmax == 8 ? 1 : 2)) {
-    case VEGAS_GAUSS_SUM * 4 + 0: batch_tile_one<VEGAS_GAUSS_SUM, 4>(sa, L, smem, st, tile); break;
-    case VEGAS_GAUSS_SUM * 4 + 1: batch_tile_one<VEGAS_GAUSS_SUM, 8>(sa, L, smem, st, tile); break;
-    case VEGAS_GAUSS_SUM * 4 + 2: batch_tile_one<VEGAS_GAUSS_SUM, 16>(sa, L, smem, st, tile); break;
-    case VEGAS_PRODUCT_PEAK * 4 + 0: batch_tile_one<VEGAS_PRODUCT_PEAK, 4>(sa, L, smem, st, tile); break;
-    case VEGAS_PRODUCT_PEAK * 4 + 1: batch_tile_one<VEGAS_PRODUCT_PEAK, 8>(sa, L, smem, st, tile); break;
-    case VEGAS_PRODUCT_PEAK * 4 + 2: batch_tile_one<VEGAS_PRODUCT_PEAK, 16>(sa, L, smem, st, tile); break;
-    case VEGAS_OSCILLATORY * 4 + 0: batch_tile_one<VEGAS_OSCILLATORY, 4>(sa, L, smem, st, tile); break;
-    case VEGAS_OSCILLATORY * 4 + 1: batch_tile_one<VEGAS_OSCILLATORY, 8>(sa, L, smem, st, tile); break;
-    default: batch_tile_one<VEGAS_OSCILLATORY, 16>(sa, L, smem, st, tile); break;
-  }
 }
 
 // the CTA's share of integral p: iteration sums, largest ell, flags and the
@@ -98,24 +68,27 @@ __device__ __forceinline__ void batch_flush(const BatchLaunch& L, int p, const F
   __syncthreads();
 }
 
-template <int MINB>
-__global__ void __launch_bounds__(kFillThreads, MINB) batch_fill_kernel(const __grid_constant__ BatchLaunch L) {
+// The fill of one group (one family ID at width DMAX): persistent CTAs over the group's tiles.
+template <int MINB, int ID, int DMAX>
+__global__ void __launch_bounds__(kFillThreads, MINB) batch_fill_kernel(const __grid_constant__ BatchLaunch L,
+                                                                        int group) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(16) FillArgs sa;
   __shared__ int s_chunk;
   const int tid = threadIdx.x;
-  const int total = L.act_tile[L.P];
-  int cur = -1, dmax = 4;
+  const int32_t* pre = L.grp_tile + (size_t)group * (L.P + 1);
+  const int total = pre[L.P];
+  int cur = -1;
   FillState<float> st;
   for (;;) {
-    if (tid == 0) s_chunk = (int)atomicAdd(L.counter, 1u);
+    if (tid == 0) s_chunk = (int)atomicAdd(L.counter + 2 + group, 1u);
     __syncthreads();
     const int64_t t0 = (int64_t)s_chunk * L.chunk_tiles;
     __syncthreads();  // s_chunk is rewritten only after every thread has read it
     if (t0 >= total) break;
     const int t1 = (int)min((int64_t)total, t0 + L.chunk_tiles);
     for (int gt = (int)t0; gt < t1; ++gt) {
-      const int p = batch_find(L.act_tile, L.P, gt);
+      const int p = batch_find(pre, L.P, gt);
       if (p != cur) {
         if (cur >= 0) batch_flush(L, cur, sa, smem, st);
         // load integral p: arguments, map table, derived parameters, zeroed histogram
@@ -123,11 +96,10 @@ __global__ void __launch_bounds__(kFillThreads, MINB) batch_fill_kernel(const __
         uint32_t* dst = reinterpret_cast<uint32_t*>(&sa);
         for (int i = tid; i < (int)(sizeof(FillArgs) / 4); i += kFillThreads) dst[i] = src[i];
         __syncthreads();
-        dmax = L.prob[p].dmax;
         {
           const FillShared<float> S = fill_shared<float>(smem, sa, true);
           fill_prologue<float>(sa, S, sa.d, true);
-          batch_prep(sa, dmax, S.prm);
+          prep_params<ID, float, DMAX>(sa.params_raw, sa.np_raw, sa.d, S.prm);
         }
         st = FillState<float>{};
         st.vexp = sa.vexp ? *sa.vexp : 0;
@@ -135,27 +107,53 @@ __global__ void __launch_bounds__(kFillThreads, MINB) batch_fill_kernel(const __
         cur = p;
         __syncthreads();
       }
-      batch_tile(sa, dmax, L, smem, st, gt - L.act_tile[p]);
+      batch_tile_one<ID, DMAX>(sa, L, smem, st, gt - pre[p]);
     }
   }
   if (cur >= 0) batch_flush(L, cur, sa, smem, st);
 }
 
-template <int MINB>
-int launch_batch_fill_variant(const BatchLaunch& L, int grid, int smem, cudaStream_t s) {
-  auto k = batch_fill_kernel<MINB>;
+template <int MINB, int ID, int DMAX>
+int launch_batch_fill_kernel(const BatchLaunch& L, int group, int grid, int smem, cudaStream_t s) {
+  auto k = batch_fill_kernel<MINB, ID, DMAX>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return VEGAS_ECUDA;
-  k<<<grid, kFillThreads, smem, s>>>(L);
+  k<<<grid, kFillThreads, smem, s>>>(L, group);
   return cuda_status(cudaGetLastError());
 }
 
-template <int MINB>
-int batch_fill_occupancy_variant(int smem) {
-  auto k = batch_fill_kernel<MINB>;
+template <int MINB, int ID, int DMAX>
+int batch_fill_kernel_occupancy(int smem) {
+  auto k = batch_fill_kernel<MINB, ID, DMAX>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kFillThreads, smem) != cudaSuccess) return 0;
   return n;
+}
+
+// the launcher and occupancy query of family ID, for the variant's register budget and the width
+template <int ID>
+int launch_batch_fill_family(int variant, int dmax, int group, const BatchLaunch& L, int grid, int smem,
+                             cudaStream_t s) {
+  // variant 0: 64 registers up to 8 axes; the 16-axis streamed path spills below 128 (2 CTAs an SM) in the
+  // persistent kernel, so both variants give it 128.  Variant 1: 128 registers at every width.
+  if (variant == 0) {
+    if (dmax == 4) return launch_batch_fill_kernel<4, ID, 4>(L, group, grid, smem, s);
+    if (dmax == 8) return launch_batch_fill_kernel<4, ID, 8>(L, group, grid, smem, s);
+  }
+  if (dmax == 4) return launch_batch_fill_kernel<2, ID, 4>(L, group, grid, smem, s);
+  if (dmax == 8) return launch_batch_fill_kernel<2, ID, 8>(L, group, grid, smem, s);
+  return launch_batch_fill_kernel<2, ID, 16>(L, group, grid, smem, s);
+}
+
+template <int ID>
+int batch_fill_family_occupancy(int variant, int dmax, int smem) {
+  if (variant == 0) {
+    if (dmax == 4) return batch_fill_kernel_occupancy<4, ID, 4>(smem);
+    if (dmax == 8) return batch_fill_kernel_occupancy<4, ID, 8>(smem);
+  }
+  if (dmax == 4) return batch_fill_kernel_occupancy<2, ID, 4>(smem);
+  if (dmax == 8) return batch_fill_kernel_occupancy<2, ID, 8>(smem);
+  return batch_fill_kernel_occupancy<2, ID, 16>(smem);
 }
 
 }  // namespace vg

@@ -1,7 +1,8 @@
 // vegas_device.cuh -- device helpers of the GB300 VEGAS+ kernels.
 //
 // Philox4x32-10 point draws, the reproducible FP32 log2/exp2 of the allocation
-// weights, float-float accumulation, and the integrand families.
+// weights, float-float accumulation, the integrand families and the FP64 exp
+// of the FP64 form's Gaussian integrand.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -238,6 +239,69 @@ __device__ __forceinline__ T integrand(const T (&x)[DMAX], int d, const T* __res
     }
     return r;
   }
+}
+
+// ---------------------------------------------------------------------------
+// e^x in FP64 by Tang's table-driven method (P. T. P. Tang, "Table-driven
+// implementation of the exponential function in IEEE floating-point
+// arithmetic", ACM TOMS 15(2), 1989) with 64 table entries:
+//   x = n ln2/64 + r, n = rint(64 x / ln2), |r| <= ln2/128 (+ rounding),
+//   e^x = 2^(n >> 6) 2^((n & 63)/64) e^r,
+// e^r - 1 by its Taylor polynomial to degree 5, whose truncation is below
+// r^6/720 < 4e-17 relative.  n comes from one fused multiply-add against
+// 1.5 2^52 (its low word); r from a two-part ln2/64 whose first part has 36
+// significant bits, so n ln2_hi/64 and x - n ln2_hi/64 are exact for |x| < 2^10.
+// The result is within about one ulp of e^x.  Ten FP64 operations; the rest
+// (table index, exponent) is integer work.  Below x = -745.2 the result is 0
+// (e^x is below half the smallest subnormal); from -745.2 to -707.6 the scale
+// takes one more multiply, which rounds to the subnormal result; above 707.6
+// and for NaN the library exp() runs.
+__device__ const double kExp2Table64[64] = {
+    // 2^(j/64), j = 0..63, each rounded to the nearest double (from a 60-digit decimal evaluation)
+    0x1.0000000000000p+0, 0x1.02c9a3e778061p+0, 0x1.059b0d3158574p+0, 0x1.0874518759bc8p+0,
+    0x1.0b5586cf9890fp+0, 0x1.0e3ec32d3d1a2p+0, 0x1.11301d0125b51p+0, 0x1.1429aaea92de0p+0,
+    0x1.172b83c7d517bp+0, 0x1.1a35beb6fcb75p+0, 0x1.1d4873168b9aap+0, 0x1.2063b88628cd6p+0,
+    0x1.2387a6e756238p+0, 0x1.26b4565e27cddp+0, 0x1.29e9df51fdee1p+0, 0x1.2d285a6e4030bp+0,
+    0x1.306fe0a31b715p+0, 0x1.33c08b26416ffp+0, 0x1.371a7373aa9cbp+0, 0x1.3a7db34e59ff7p+0,
+    0x1.3dea64c123422p+0, 0x1.4160a21f72e2ap+0, 0x1.44e086061892dp+0, 0x1.486a2b5c13cd0p+0,
+    0x1.4bfdad5362a27p+0, 0x1.4f9b2769d2ca7p+0, 0x1.5342b569d4f82p+0, 0x1.56f4736b527dap+0,
+    0x1.5ab07dd485429p+0, 0x1.5e76f15ad2148p+0, 0x1.6247eb03a5585p+0, 0x1.6623882552225p+0,
+    0x1.6a09e667f3bcdp+0, 0x1.6dfb23c651a2fp+0, 0x1.71f75e8ec5f74p+0, 0x1.75feb564267c9p+0,
+    0x1.7a11473eb0187p+0, 0x1.7e2f336cf4e62p+0, 0x1.82589994cce13p+0, 0x1.868d99b4492edp+0,
+    0x1.8ace5422aa0dbp+0, 0x1.8f1ae99157736p+0, 0x1.93737b0cdc5e5p+0, 0x1.97d829fde4e50p+0,
+    0x1.9c49182a3f090p+0, 0x1.a0c667b5de565p+0, 0x1.a5503b23e255dp+0, 0x1.a9e6b5579fdbfp+0,
+    0x1.ae89f995ad3adp+0, 0x1.b33a2b84f15fbp+0, 0x1.b7f76f2fb5e47p+0, 0x1.bcc1e904bc1d2p+0,
+    0x1.c199bdd85529cp+0, 0x1.c67f12e57d14bp+0, 0x1.cb720dcef9069p+0, 0x1.d072d4a07897cp+0,
+    0x1.d5818dcfba487p+0, 0x1.da9e603db3285p+0, 0x1.dfc97337b9b5fp+0, 0x1.e502ee78b3ff6p+0,
+    0x1.ea4afa2a490dap+0, 0x1.efa1bee615a27p+0, 0x1.f50765b6e4540p+0, 0x1.fa7c1819e90d8p+0};
+
+__device__ __forceinline__ double exp_table64(double x) {
+  constexpr double kInvL = 0x1.71547652b82fep+6;  // 64 / ln2
+  constexpr double kL1 = 0x1.62e42fefa0000p-7;    // ln2 / 64, first 36 bits
+  constexpr double kL2 = 0x1.cf79abc9e3b3ap-46;   // ln2 / 64 - kL1
+  constexpr double kShift = 0x1.8p52;
+  const double t = fma(x, kInvL, kShift);
+  const int n = __double2loint(t);  // the low word of 1.5 2^52 + n is n
+  const double nd = t - kShift;
+  double r = fma(-nd, kL1, x);
+  r = fma(-nd, kL2, r);
+  const double r2 = r * r;
+  double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+  q = fma(q, r, 1.0 / 6.0);
+  q = fma(q, r, 0.5);
+  const double p = fma(q, r2, r);  // e^r - 1
+  const double T = __ldg(&kExp2Table64[n & 63]);
+  const double y = fma(T, p, T);  // in [1, 2)
+  const int m = n >> 6;
+  // |x| < 707.6: 2^m (|m| <= 1021) is a normal scale; add it to the exponent field
+  if ((__double2hiint(x) & 0x7FFFFFFF) >= 0x40861CCC) {  // |x| >= 707.6, or NaN
+    if (x < -745.2) return 0.0;
+    if (!(x < 0.0)) return exp(x);  // NaN, or above the normal range
+    // -745.2 <= x <= -707.6: m in [-1076, -1021].  y 2^(m + 64) is normal (an exponent add); the exact scale
+    // 2^-64 then rounds once, to the subnormal result
+    return __hiloint2double(__double2hiint(y) + ((m + 64) << 20), __double2loint(y)) * 0x1p-64;
+  }
+  return __hiloint2double(__double2hiint(y) + (m << 20), __double2loint(y));
 }
 
 }  // namespace vg

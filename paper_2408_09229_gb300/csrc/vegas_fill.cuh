@@ -263,7 +263,7 @@ __device__ __forceinline__ T integrand(const T (&x)[DMAX], int d, const T* __res
         const T dx = x[j] - m[j];  // padded axes hold x = mu = 0
         r2 = fma(dx, dx, r2);
       }
-      if constexpr (sizeof(T) == 8) acc += exp(r2 * s1);
+      if constexpr (sizeof(T) == 8) acc += exp_table64(r2 * s1);
       else acc += ex2_approx(r2 * s1);
     }
     return s0 * acc;
@@ -451,8 +451,15 @@ __device__ __forceinline__ void make_point(const FillArgs& a, const uint32_t* __
         if ((k & 1) == 0) r = philox_rk(make_uint4(jlo, jhi, a.iter, (a.pid << 16) | (uint32_t)(k >> 1)), rk0, rk1);
         const uint32_t whi = (k & 1) ? r.z : r.x, wlo = (k & 1) ? r.w : r.y;
         const uint64_t bits = (((uint64_t)whi << 32) | wlo) >> 11;
-        const double u = __dmul_rn(__ull2double_rn(bits), 0x1p-53);
-        const double z = __dmul_rn(__dadd_rn((double)cb[k], u), a.gz64[k]);
+        double z;
+        if (cb[k] < 2048u) {
+          // c + u = (c 2^53 + bits) 2^-53 with the integer exact in 64 bits: one conversion rounds it as RN(c + u)
+          // does, and the power-of-two scale rides in the multiplier, so z = RN(RN(c + u) N_g / s) unchanged
+          z = __dmul_rn(__ull2double_rn(((uint64_t)cb[k] << 53) | bits), a.gz64s[k]);
+        } else {
+          const double u = __dmul_rn(__ull2double_rn(bits), 0x1p-53);
+          z = __dmul_rn(__dadd_rn((double)cb[k], u), a.gz64[k]);
+        }
         i = (int)z;  // z >= 0: truncation is floor
         i = i < G - 1 ? i : G - 1;
         dz = z - (double)i;  // exact
@@ -1261,7 +1268,7 @@ __device__ __forceinline__ Carry carry_suffix(Carry rec, bool joins) {
 // form with d <= 8 asks for 4 resident CTAs (at most 64 registers): measured
 // 7 % faster than 3 CTAs with more registers.  Wider or FP64 forms would spill.
 template <int ID, typename T, int DMAX, bool EXACT, bool STREAM = false>
-__global__ void __launch_bounds__(kFillThreads, (sizeof(T) == 4 && (DMAX <= 8 || STREAM)) ? 4 : 1)
+__global__ void __launch_bounds__(kFillThreads, (sizeof(T) == 4 && (DMAX <= 8 || STREAM)) ? 4 : (sizeof(T) == 8 && EXACT) ? 2 : 1)
     fill_kernel(const __grid_constant__ FillArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, lane = tid & 31;

@@ -160,6 +160,7 @@ int fill_args_axes(FillArgs& a, const int32_t* nstrat, int precision, int nprm) 
     magic_div(a.nstrat[k], a.magic[k], a.shift[k]);
     // z = (c + u) * N_g / s_k: the scale rounded once, in each precision
     a.gz64[k] = (double)G / (double)nstrat[k];
+    a.gz64s[k] = std::ldexp(a.gz64[k], -53);
     uint32_t l = 0;
     while ((1u << l) < (uint32_t)nstrat[k]) ++l;
     a.fbits[k] = 23u - l;

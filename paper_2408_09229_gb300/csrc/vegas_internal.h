@@ -74,6 +74,7 @@ struct FillArgs {
   float train_power;
   uint32_t nstrat[kMaxDim], magic[kMaxDim], shift[kMaxDim];
   double gz64[kMaxDim];     // N_g / s_k, rounded in FP64
+  double gz64s[kMaxDim];    // gz64 2^-53 (exact): the point's z from the 64-bit integer c 2^53 + (53 random bits)
   float gzb32[kMaxDim];     // RN32(N_g / s_k) 2^-b_k
   float gzn32[kMaxDim];     // -2^23 RN32(N_g / s_k) 2^-b_k
   uint32_t fbits[kMaxDim];  // b_k = 23 - ceil(log2 s_k): fraction bits of an FP32 coordinate

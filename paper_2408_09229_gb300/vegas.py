@@ -100,6 +100,7 @@ def _load():
         "vegas_probe_pipes": ([P], i32),
         "vegas_probe_shared_atomics": ([P], i32),
         "vegas_probe_exp64": ([P], i32),
+        "vegas_exp64_eval": ([P, P, i64, i32, P], i32),
         "vegas_batch_create": ([ctypes.POINTER(Problem), i32, i32, f64, f64, u64, ctypes.POINTER(P)], i32),
         "vegas_batch_create_ex": ([ctypes.POINTER(Problem), i32, i32, f64, f64, u64, ALLOC_FN, FREE_FN, P,
                                    ctypes.POINTER(P)], i32),
@@ -550,6 +551,11 @@ def probe_exp64():
     r = ctypes.c_double()
     _check(lib.vegas_probe_exp64(ctypes.byref(r)), "vegas_probe_exp64")
     return r.value
+
+
+def exp64_eval(x, y, which=0, stream=None):
+    """vegas_exp64_eval on float64 CUDA tensors: which 0 the FP64 form's exponential, 1 the library exp()"""
+    _check(lib.vegas_exp64_eval(_ptr(x), _ptr(y), x.numel(), int(which), _stream_ptr(stream)), "vegas_exp64_eval")
 
 
 def probe_shared_atomics():

@@ -6,6 +6,9 @@
   the per-cube partial statistics and merge them in rank order, and sum the
   map weights.  The merged result equals the single-process fill.
 * The benchmark's replica timing: the job time is the maximum over ranks.
+* Failure detection on the host: a rank that leaves between steps makes the
+  other rank's next collective end with an error within the process group's
+  timeout (no device is involved).
 """
 import os
 
@@ -75,3 +78,40 @@ def test_sharded_fill_equals_single_fill(tmp_path, orc):
     assert np.allclose(got["m2"], m2, rtol=1e-9, atol=1e-12 * m2.max())
     assert np.allclose(got["bins"], bins.ravel(), rtol=1e-13)
     assert float(got["tmax"]) == 2.0
+
+
+def _leaver(rank, world, port, out_path):
+    """rank 1 leaves between steps (after the first step's collective, with nothing in flight); rank 0 learns of
+    it on the host: its next collective ends with an error within the process group's short timeout instead of
+    waiting forever"""
+    import datetime
+    import time
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=3))
+    t = torch.ones(4)
+    dist.all_reduce(t)  # step 1: both ranks
+    if rank == 1:
+        os._exit(0)  # leaves without a goodbye
+    t0 = time.perf_counter()
+    err = ""
+    try:
+        dist.all_reduce(t)  # step 2: the peer is gone
+    except Exception as e:  # gloo reports a closed connection or a timeout
+        err = type(e).__name__ + ": " + str(e)[:200]
+    np.savez(out_path, err=np.array(err), dt=time.perf_counter() - t0, first=t.numpy())
+
+
+def test_rank_that_leaves_is_detected_on_the_host(tmp_path):
+    out = str(tmp_path / "leave.npz")
+    port = 29700 + os.getpid() % 1000
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_leaver, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    assert all(p.exitcode == 0 for p in procs), [p.exitcode for p in procs]
+    got = np.load(out)
+    assert str(got["err"]), "the collective with a departed rank returned without an error"
+    assert float(got["dt"]) < 60.0
+    assert np.all(got["first"] == 2.0)

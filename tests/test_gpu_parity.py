@@ -544,6 +544,36 @@ def test_probe_exp64(V):
     assert 0.0 < r < V.probe_pipes()[1], r
 
 
+def test_exp64_against_library_and_correct_rounding(V):
+    """the FP64 form's table-driven exponential (Tang's method, 64 entries) against the CUDA library's exp()
+    and against Python's exp (correctly rounded within 1 ulp), on random arguments over the whole range and at
+    the edges of its branches: within 2 ulp of the library, 1 ulp of the host value, exact 0 below -745.2"""
+    rng = np.random.default_rng(11)
+    xs = np.concatenate([rng.uniform(-750.0, 709.0, 200_000), rng.uniform(-2.0, 2.0, 200_000),
+                         -rng.exponential(20.0, 100_000), rng.uniform(-745.2, -707.6, 20_000),
+                         [0.0, -0.0, 1e-300, -1e-300, 1.0, -1.0, -707.59, -707.6, -707.61, -708.0, -745.1, -745.2,
+                          -745.3, -800.0, -1e10, 700.0, 707.5, 708.5, 709.7, -math.log(2) / 128,
+                          math.log(2) / 128, np.nextafter(-745.2, 0.0)]])
+    x = dev(xs, torch.float64)
+    yt, yl = torch.empty_like(x), torch.empty_like(x)
+    V.exp64_eval(x, yt, 0)
+    V.exp64_eval(x, yl, 1)
+    torch.cuda.synchronize()
+    yt, yl = yt.cpu().numpy(), yl.cpu().numpy()
+    host = np.array([math.exp(v) for v in xs])
+
+    def ulps(a, b):
+        a, b = np.asarray(a), np.asarray(b)
+        return np.abs(a.view(np.int64) - b.view(np.int64))
+
+    normal = (host > 2.2250738585072014e-308) & np.isfinite(host)
+    assert ulps(yt[normal], yl[normal]).max() <= 2
+    assert ulps(yt[normal], host[normal]).max() <= 1
+    assert np.all(yt[xs < -745.2] == 0.0)
+    sub = (~normal) & (xs >= -745.2)
+    assert np.all(np.abs(yt[sub] - host[sub]) <= 5e-324)
+
+
 def test_probe_shared_atomics(V):
     r = V.probe_shared_atomics()
     assert 2.0 < r < 1024.0, r  # 32-bit shared atomic adds per SM per clock
