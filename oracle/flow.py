@@ -42,7 +42,8 @@ Definitions (the same in the CUDA path):
 bf16=True rounds what the CUDA path stores as bf16 (the weight matrices,
 the conditioner input h and the hidden activations u1, u2; not the biases)
 to bf16, round to nearest even, from their FP32 values; the arithmetic stays
-FP64.
+FP64.  grad(..., bf16_grad=True) also rounds the backward operands that the
+tensor-core gradient stores as bf16 (see grad).
 """
 import numpy as np
 
@@ -163,9 +164,13 @@ def loss(theta, x, w, d, bf16_path=False):
     return -float(np.dot(w, logdet) / w.sum())
 
 
-def grad(theta, x, w, d, bf16_path=False):
-    """(loss, d loss / d theta) by backpropagation through N"""
+def grad(theta, x, w, d, bf16_path=False, bf16_grad=False):
+    """(loss, d loss / d theta) by backpropagation through N.  bf16_grad=True also rounds to bf16 what the
+    tensor-core gradient stores as bf16 operands: the gradient of the coupling outputs (s, t) and of the two
+    hidden pre-activations after the ReLU mask; the weight and bias gradients are then sums over those rounded
+    values"""
     theta = np.asarray(theta, dtype=np.float64)
+    gq = bf16 if bf16_grad else _ident
     w = np.asarray(w, dtype=np.float64)
     wn = w / w.sum()
     xp, logdet, z, caches = normalise(theta, x, d, bf16_path, keep=True)
@@ -183,14 +188,15 @@ def grad(theta, x, w, d, bf16_path=False):
         go = np.empty((x.shape[0], 2 * len(B)))
         go[:, 0::2] = gs * (1.0 - (s / S_CLAMP) ** 2)
         go[:, 1::2] = gt
+        go = gq(go)
         gl[l]["W3"][...] = go.T @ u2
         gl[l]["b3"][...] = go.sum(axis=0)
         gu2 = go @ W3
-        ga2 = gu2 * (a2 > 0.0)
+        ga2 = gq(gu2 * (a2 > 0.0))
         gl[l]["W2"][...] = ga2.T @ u1
         gl[l]["b2"][...] = ga2.sum(axis=0)
         gu1 = ga2 @ W2
-        ga1 = gu1 * (a1 > 0.0)
+        ga1 = gq(gu1 * (a1 > 0.0))
         gl[l]["W1"][...] = ga1.T @ hq
         gl[l]["b1"][...] = ga1.sum(axis=0)
         gh = ga1 @ W1

@@ -741,6 +741,7 @@ extern "C" int vegas_integrate(vegas_handle h, int integrand, const double* para
   out->flags = flags;
   if (dflags & 2) return VEGAS_ECUDA;  // a cube crossing tiles was not reassembled: internal error
   if (flow && (rc = vg::flow_tc_status(true)) != VEGAS_OK) return rc;
+  if (flow && (rc = vg::flow_grad_tc_status(true)) != VEGAS_OK) return rc;
   return (dflags & 1) ? VEGAS_ENONFINITE : VEGAS_OK;
 }
 

@@ -79,7 +79,8 @@ extern "C" int vegas_flow_apply(int32_t dim, int32_t direction, const float* d_p
 
 extern "C" int vegas_flow_check(void* stream) {
   VG_CHECK(cudaStreamSynchronize((cudaStream_t)stream));
-  return flow_tc_status(true);
+  const int a = flow_tc_status(true), b = flow_grad_tc_status(true);
+  return a != VEGAS_OK ? a : b;
 }
 
 extern "C" int vegas_flow_wait_selftest(int32_t polls, int32_t arrive, void* stream) {
@@ -620,6 +621,13 @@ extern "C" int vegas_flow_grad(int32_t dim, const float* d_params, const float* 
   unsigned char* img = sc + S.img;
   flow_wsum_kernel<<<1, 1024, 0, s>>>(d_w, n, wsum);
   VG_CHECK(cudaGetLastError());
+  if (dim <= kFlowGradTcMaxDim) {  // tcgen05: one CTA per 128 samples
+    const int rc = flow_grad_tc(fa, d_x, d_w, wsum, n, gpart, lpart, s);
+    if (rc != VEGAS_OK) return rc;
+    const int nblk = (int)((n + 127) / 128);
+    flow_reduce_kernel<<<(fa.nparams + 255) / 256, 256, 0, s>>>(gpart, lpart, nblk, fa.nparams, d_grad, d_loss);
+    return cuda_status(cudaGetLastError());
+  }
   flow_image_kernel<<<dim3(4, kFlowLayers), 256, 0, s>>>(fa, G, img);
   VG_CHECK(cudaGetLastError());
   static_assert(grad_rows(2) == 32, "two-warp CTAs");

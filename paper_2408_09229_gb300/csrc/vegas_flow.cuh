@@ -15,9 +15,9 @@
 // MLP_l: a_l -> 64 -> 64 -> 2 b_l with ReLU; output row 2j is s_j, 2j+1 t_j.
 //
 // The batched transform (vegas_flow_apply) runs on tcgen05 with the
-// accumulators in tensor memory (vegas_flow_tc.cu).  The training pass, which
-// needs the transposed products of the backward direction as well, runs the
-// layer below with mma.sync m16n8k16 (bf16 operands, FP32 accumulation): a
+// accumulators in tensor memory (vegas_flow_tc.cu), and so does the training
+// gradient up to 16 axes (vegas_flow_grad_tc.cu).  Wider flows train with the
+// layer below on mma.sync m16n8k16 (bf16 operands, FP32 accumulation): a
 // warp owns 16 samples, and the accumulator fragment of one GEMM is, after
 // ReLU and conversion, the A fragment of the next, so the hidden activations
 // never leave registers.  Weights are bf16 in shared memory, rows padded so
@@ -35,6 +35,12 @@ constexpr int kFlowHidden = 64;
 constexpr float kFlowSClamp = 2.0f;
 constexpr float kFlowZClamp = 20.0f;
 constexpr int kFlowMaxDim = 32;
+constexpr int kFlowGradTcMaxDim = 16;  // the training gradient runs on tcgen05 up to this many axes
+
+struct FlowArgs;
+// the tensor-core training gradient (vegas_flow_grad_tc.cu): per 128 samples one partial gradient and loss
+int flow_grad_tc(const FlowArgs& fa, const float* x, const float* w, const double* wsum, int64_t n, float* gpart,
+                 float* lpart, cudaStream_t s);
 // shared-memory leading dimensions (bf16 elements): 12, 36 and 20 words
 constexpr int kLdK16 = 24, kLdK64 = 72, kLdK32 = 40;
 

@@ -126,6 +126,8 @@ int flow_apply(int d, int direction, const float* d_params, const float* d_xin, 
 // VEGAS_ETIMEOUT when a bounded wait of the tensor-core transform ran out since the last reset
 int flow_tc_status(bool reset);
 int flow_tc_wait_selftest(int polls, int arrive, cudaStream_t s);
+// the same report for the tensor-core training gradient (vegas_flow_grad_tc.cu)
+int flow_grad_tc_status(bool reset);
 int flow_eval(int integrand, int d, const double* d_params, int64_t nparams, const float* X, const float* logdet,
               float* values, int64_t n, cudaStream_t s);
 // training set of an iteration: every kFloorPeriod-th row a uniform point when lambda > 0

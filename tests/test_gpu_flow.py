@@ -178,6 +178,44 @@ def test_change_of_variables_on_gpu(V, d):
     assert abs(float(f.mean()) - one ** d) < 5 * float(f.std()) / math.sqrt(n)
 
 
+def _gpu_grad(V, d, th, x, w):
+    n = x.shape[0]
+    grad = torch.zeros(th.size, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    scratch = torch.empty(V.flow_grad_scratch_bytes(d, n), dtype=torch.uint8, device="cuda")
+    V.flow_grad(d, dev(th), dev(x), dev(w), grad, loss, scratch)
+    V.flow_check()
+    return float(loss[0]), grad.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("d,n", [(2, 128), (4, 1), (5, 1000), (8, 4096), (12, 777), (12, 4096), (16, 300)])
+def test_tensor_core_gradient_matches_oracle_elementwise(V, d, n):
+    """the tcgen05 gradient (up to 16 axes) against the oracle rounding the same operands to bf16 (weights,
+    conditioner input, hidden activations, and the backward pass's gradients of (s, t) and of the hidden
+    pre-activations), element by element.  The bound: FP32 accumulation over at most 128 samples per tile and
+    the partials of the tiles (~1e-5 of the sum of magnitudes), plus rare bf16 rounding decisions that fall the
+    other way on the two sides (one operand of one sample moves by 2^-8 relative), plus the z before each
+    layer, which the GPU recomputes by inverting the layer: |g - g_oracle| <= 2e-3 max|block| + 1e-2 |g_oracle|"""
+    th = W.flow_params(d, seed=11 + d, out_scale=0.05)
+    rng = np.random.default_rng(d + n)
+    x = rng.uniform(0.02, 0.98, (n, d)).astype(np.float32).astype(np.float64)
+    w = rng.exponential(1.0, n).astype(np.float32).astype(np.float64)
+    lg, gg = _gpu_grad(V, d, th, x, w)
+    L, g = F.grad(th, x, w, d, bf16_path=True, bf16_grad=True)
+    assert lg == pytest.approx(L, rel=1e-4, abs=1e-4)
+    off = 0
+    worst = 0.0
+    for l in range(F.LAYERS):
+        for name, shape in F.layer_sizes(d, l):
+            k = int(np.prod(shape))
+            a, b = gg[off:off + k], g[off:off + k]
+            bound = 2e-3 * np.abs(b).max() + 1e-2 * np.abs(b) + 1e-9
+            worst = max(worst, float((np.abs(a - b) / bound).max()))
+            assert np.all(np.abs(a - b) <= bound), (l, name, np.abs(a - b).max(), np.abs(b).max())
+            off += k
+    print(f"d={d} n={n}: worst error / bound = {worst:.3f}")
+
+
 @pytest.mark.parametrize("d,n", [(5, 1000), (12, 777), (30, 333)])
 def test_gradient_matches_oracle(V, d, n):
     th = W.flow_params(d, seed=11 + d, out_scale=0.05)
