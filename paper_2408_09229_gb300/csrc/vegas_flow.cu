@@ -575,7 +575,7 @@ __global__ void flow_adam_kernel(int64_t np, float* __restrict__ theta, const fl
 }
 
 struct GradScratch {
-  size_t wsum, lpart, gpart, img, total;
+  size_t wsum, lpart, gpart, img, img_tc, total;
   int nblk;
 };
 GradScratch grad_scratch(const FlowArgs& fa, int64_t n) {
@@ -588,6 +588,7 @@ GradScratch grad_scratch(const FlowArgs& fa, int64_t n) {
   S.lpart = o; o = al16(o + sizeof(float) * S.nblk);
   S.gpart = o; o = al16(o + sizeof(float) * (size_t)S.nblk * fa.nparams);
   S.img = o; o = al16(o + (size_t)grad_layout(fa, W).img_total);
+  S.img_tc = o; o = al16(o + flow_grad_tc_image_bytes(fa.d));
   S.total = o;
   return S;
 }
@@ -622,7 +623,7 @@ extern "C" int vegas_flow_grad(int32_t dim, const float* d_params, const float* 
   flow_wsum_kernel<<<1, 1024, 0, s>>>(d_w, n, wsum);
   VG_CHECK(cudaGetLastError());
   if (dim <= kFlowGradTcMaxDim) {  // tcgen05: one CTA per 128 samples
-    const int rc = flow_grad_tc(fa, d_x, d_w, wsum, n, gpart, lpart, s);
+    const int rc = flow_grad_tc(fa, sc + S.img_tc, d_x, d_w, wsum, n, gpart, lpart, s);
     if (rc != VEGAS_OK) return rc;
     const int nblk = (int)((n + 127) / 128);
     flow_reduce_kernel<<<(fa.nparams + 255) / 256, 256, 0, s>>>(gpart, lpart, nblk, fa.nparams, d_grad, d_loss);

@@ -38,9 +38,11 @@ constexpr int kFlowMaxDim = 32;
 constexpr int kFlowGradTcMaxDim = 16;  // the training gradient runs on tcgen05 up to this many axes
 
 struct FlowArgs;
-// the tensor-core training gradient (vegas_flow_grad_tc.cu): per 128 samples one partial gradient and loss
-int flow_grad_tc(const FlowArgs& fa, const float* x, const float* w, const double* wsum, int64_t n, float* gpart,
-                 float* lpart, cudaStream_t s);
+// the tensor-core training gradient (vegas_flow_grad_tc.cu): per 128 samples one partial gradient and loss, from
+// a bf16 weight image of flow_grad_tc_image_bytes(d) bytes that it builds in img
+int flow_grad_tc(const FlowArgs& fa, unsigned char* img, const float* x, const float* w, const double* wsum,
+                 int64_t n, float* gpart, float* lpart, cudaStream_t s);
+size_t flow_grad_tc_image_bytes(int d);
 // shared-memory leading dimensions (bf16 elements): 12, 36 and 20 words
 constexpr int kLdK16 = 24, kLdK64 = 72, kLdK32 = 40;
 

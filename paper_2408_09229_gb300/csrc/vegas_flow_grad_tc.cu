@@ -58,6 +58,10 @@ struct GradTcShape {
   static constexpr uint32_t gat_off = p1_off + P, got_off = gat_off + GAT, ht_off = got_off + GOT;
   static constexpr uint32_t u1t_off = ht_off + HT, u2t_off = u1t_off + UT;
   static constexpr uint32_t misc = u2t_off + UT;  // mbarrier, tensor-memory slot, warp sums
+  // the bf16 weight image in global memory, built once a call: the natural weights of every layer exactly as they
+  // sit in shared memory, then each layer's transposed block (W3T, W2T, W1T, as at w3t_off)
+  static constexpr uint32_t WTL = W3T + W2T + W1T;
+  static constexpr uint32_t image = S::weights + kFlowLayers * WTL;
   static constexpr uint32_t total = misc + 64;
   static constexpr uint32_t kM128 = 128 * 128 * 2;  // the bytes an M = 128 A operand of K = 128 spans
   static_assert(gat_off + kM128 <= misc && got_off + kM128 <= misc, "padded A reads stay in the activations");
@@ -170,28 +174,94 @@ __device__ __forceinline__ void grad_store_rows(uint32_t taccB, int nrows, int n
   }
 }
 
-// The current layer's transposed weights, from the FP32 parameters
+// The weight image: element i of layer blockIdx.y's natural (tc_stage_weights' layout) and transposed blocks,
+// bf16 from the FP32 parameters, grid-stride over the layer's elements
 template <int D>
-__device__ void grad_stage_transposed(const FlowLayer& L, const float* __restrict__ P, unsigned char* sm) {
+__global__ void flow_grad_image_kernel(const __grid_constant__ FlowArgs fa, unsigned char* __restrict__ img) {
+  using S = TcShape<D>;
   using Q = GradTcShape<D>;
-  const int t = threadIdx.x;
-  unsigned char* w3t = sm + Q::w3t_off;
-  unsigned char* w2t = sm + Q::w2t_off;
-  unsigned char* w1t = sm + Q::w1t_off;
-  // the loops run along the rows of the FP32 matrices, so that a warp's loads are consecutive
-  for (int i = t; i < 64 * Q::N3; i += 128) {
-    const int o = i >> 6, h = i & 63;  // element (h, o) of W3T is W3[o][h]
-    st_bf16_at(w3t, tc_off(h, o, Q::N3), o < 2 * L.b ? P[L.oW3 + o * kFlowHidden + h] : 0.0f);
-  }
-  for (int i = t; i < 64 * 64; i += 128) {
-    const int c = i >> 6, r = i & 63;  // element (r, c) of W2T is W2[c][r]
-    st_bf16_at(w2t, tc_off(r, c, 64), P[L.oW2 + c * kFlowHidden + r]);
-  }
-  for (int i = t; i < 64 * Q::K1; i += 128) {
-    const int h = i / Q::K1, c = i - h * Q::K1;  // element (c, h) of W1T is W1[h][c]
-    st_bf16_at(w1t, tc_off(c, h, 64), c < L.a ? P[L.oW1 + h * L.a + c] : 0.0f);
+  const int l = blockIdx.y;
+  const FlowLayer& L = fa.lay[l];
+  const float* P = fa.params;
+  unsigned char* w1 = img + l * S::layer;
+  unsigned char* w2 = w1 + S::W1;
+  unsigned char* w3 = w2 + S::W2;
+  unsigned char* wt = img + S::weights + (size_t)l * Q::WTL;
+  unsigned char* w3t = wt;
+  unsigned char* w2t = wt + Q::W3T;
+  unsigned char* w1t = w2t + Q::W2T;
+  const int n1 = 64 * S::K1, n2 = 64 * kTcK2, n3 = S::N3 * kTcK2, n4 = 64 * S::N3, n5 = 64 * 64, n6 = S::K1 * 64;
+  const int total = n1 + n2 + n3 + n4 + n5 + n6;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    int e = i;
+    __nv_bfloat16 h, m, lo;
+    if (e < n1) {  // W1' [64][K1]: W1, then the bias triple
+      const int j = e / S::K1, c = e - j * S::K1;
+      float v = 0.0f;
+      if (c < L.a) v = P[L.oW1 + j * L.a + c];
+      __nv_bfloat16 b = __float2bfloat16_rn(v);
+      if (c >= L.a && c < L.a + 3) {
+        bias3(P[L.ob1 + j], h, m, lo);
+        b = c == L.a ? h : (c == L.a + 1 ? m : lo);
+      }
+      *reinterpret_cast<__nv_bfloat16*>(w1 + tc_off(j, c, S::K1)) = b;
+      continue;
+    }
+    e -= n1;
+    if (e < n2) {  // W2' [64][80]
+      const int j = e / kTcK2, c = e - j * kTcK2;
+      __nv_bfloat16 b = __float2bfloat16_rn(c < kFlowHidden ? P[L.oW2 + j * kFlowHidden + c] : 0.0f);
+      if (c >= kFlowHidden && c < kFlowHidden + 3) {
+        bias3(P[L.ob2 + j], h, m, lo);
+        b = c == kFlowHidden ? h : (c == kFlowHidden + 1 ? m : lo);
+      }
+      *reinterpret_cast<__nv_bfloat16*>(w2 + tc_off(j, c, kTcK2)) = b;
+      continue;
+    }
+    e -= n2;
+    if (e < n3) {  // W3' [N3][80]
+      const int j = e / kTcK2, c = e - j * kTcK2;
+      __nv_bfloat16 b = __float2bfloat16_rn(0.0f);
+      if (j < 2 * L.b) {
+        if (c < kFlowHidden) b = __float2bfloat16_rn(P[L.oW3 + j * kFlowHidden + c]);
+        else if (c < kFlowHidden + 3) {
+          bias3(P[L.ob3 + j], h, m, lo);
+          b = c == kFlowHidden ? h : (c == kFlowHidden + 1 ? m : lo);
+        }
+      }
+      *reinterpret_cast<__nv_bfloat16*>(w3 + tc_off(j, c, kTcK2)) = b;
+      continue;
+    }
+    e -= n3;
+    if (e < n4) {  // W3T [64][N3]: element (hh, o) is W3[o][hh]; the loop runs along the rows of W3
+      const int o = e >> 6, hh = e & 63;
+      *reinterpret_cast<__nv_bfloat16*>(w3t + tc_off(hh, o, S::N3)) =
+          __float2bfloat16_rn(o < 2 * L.b ? P[L.oW3 + o * kFlowHidden + hh] : 0.0f);
+      continue;
+    }
+    e -= n4;
+    if (e < n5) {  // W2T [64][64]: element (r, c) is W2[c][r]
+      const int c = e >> 6, r = e & 63;
+      *reinterpret_cast<__nv_bfloat16*>(w2t + tc_off(r, c, 64)) = __float2bfloat16_rn(P[L.oW2 + c * kFlowHidden + r]);
+      continue;
+    }
+    e -= n5;
+    {  // W1T [K1][64]: element (c, hh) is W1[hh][c]
+      const int hh = e / S::K1, c = e - hh * S::K1;
+      *reinterpret_cast<__nv_bfloat16*>(w1t + tc_off(c, hh, 64)) =
+          __float2bfloat16_rn(c < L.a ? P[L.oW1 + hh * L.a + c] : 0.0f);
+    }
   }
 }
+
+// 16-byte asynchronous copies of `bytes` (a multiple of 16) from global to shared memory by the CTA; completed
+// by cp_async_wait_all and a barrier
+__device__ __forceinline__ void copy_async(unsigned char* dst, const unsigned char* __restrict__ src, uint32_t bytes) {
+  for (uint32_t o = threadIdx.x * 16u; o < bytes; o += blockDim.x * 16u)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc_smem_u32(dst + o)), "l"(src + o) : "memory");
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void copy_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // H row t into the natural tile (first K1 columns) and, with `transposed`, column t of H^T
 template <int D, int PAR>
@@ -262,7 +332,7 @@ __device__ __forceinline__ bool grad_forward_layer(const unsigned char* wl, unsi
 // The backward pass through layer l: on entry z is the output of the layer and gz = dL/dz there; on exit z is
 // its input and gz = dL/dz before the layer.  The layer's weight gradients go to gp.
 template <int D, int PAR>
-__device__ __forceinline__ bool grad_backward_layer(const FlowLayer& L, const float* __restrict__ P,
+__device__ __forceinline__ bool grad_backward_layer(const FlowLayer& L, const unsigned char* __restrict__ wt_img,
                                                     const unsigned char* wl, unsigned char* sm, TcGroup& G,
                                                     float (&z)[D], float (&gz)[D], float wn, float* __restrict__ gp) {
   using S = TcShape<D>;
@@ -275,7 +345,10 @@ __device__ __forceinline__ bool grad_backward_layer(const FlowLayer& L, const fl
   unsigned char* GOT = sm + Q::got_off;
   const uint32_t tcolA = G.tacc & 0xFFFFu, tcolB = tcolA + 64;
   const uint32_t taccB = G.tacc + 64;
-  grad_stage_transposed<D>(L, P, sm);
+  // the layer's transposed weights: asynchronous copies, complete before the first MMA that reads them (the
+  // conditioner's barriers come after the wait)
+  copy_async(sm + Q::w3t_off, wt_img, Q::WTL);
+  copy_async_wait();
   float o[S::N3];
   uint64_t m1 = 0, m2 = 0;
   if (!grad_conditioner<D, PAR>(wl, sm, G, z, true, o, m1, m2)) return false;
@@ -346,9 +419,9 @@ __device__ __forceinline__ bool grad_backward_layer(const FlowLayer& L, const fl
 
 template <int D>
 __global__ void __launch_bounds__(128, 1)
-    flow_grad_tc_kernel(const __grid_constant__ FlowArgs fa, const float* __restrict__ x, const float* __restrict__ w,
-                        const double* __restrict__ wsum, int64_t n, float* __restrict__ gpart,
-                        float* __restrict__ lpart) {
+    flow_grad_tc_kernel(const __grid_constant__ FlowArgs fa, const unsigned char* __restrict__ img,
+                        const float* __restrict__ x, const float* __restrict__ w, const double* __restrict__ wsum,
+                        int64_t n, float* __restrict__ gpart, float* __restrict__ lpart) {
   using S = TcShape<D>;
   using Q = GradTcShape<D>;
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -356,7 +429,7 @@ __global__ void __launch_bounds__(128, 1)
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + Q::misc);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + Q::misc + 8);
   float* red = reinterpret_cast<float*>(sm + Q::misc + 16);
-  tc_stage_weights<D>(fa, sm);
+  copy_async(sm, img, S::weights);  // the natural weights of every layer
   // the constant parts of the activations: ones blocks of the natural tiles (columns 64..79: 1 1 1 0 ...) and
   // of the transposed ones (rows 64..79)
   for (unsigned char* Pn : {sm + Q::p0_off, sm + Q::p1_off}) {
@@ -373,6 +446,7 @@ __global__ void __launch_bounds__(128, 1)
     mbar_init(mbar, 1);
     mbar_fence_init();
   }
+  copy_async_wait();
   tc_fence_proxy();
   tc_fence_before();
   __syncthreads();
@@ -401,7 +475,7 @@ __global__ void __launch_bounds__(128, 1)
     ld -= flow_log_sig_prime(z[k]);
   }
   bool ok = true;
-#pragma unroll
+#pragma unroll 1
   for (int l = 0; l < kFlowLayers; ++l) {
     if (!ok) break;
     const unsigned char* wl = sm + l * S::layer;
@@ -419,12 +493,13 @@ __global__ void __launch_bounds__(128, 1)
     if (lane == 0) red[warp] = part;
   }
   float* gp = gpart + (size_t)blockIdx.x * fa.nparams;
-#pragma unroll
+#pragma unroll 1
   for (int l = kFlowLayers - 1; l >= 0; --l) {
     if (!ok) break;
     const unsigned char* wl = sm + l * S::layer;
-    ok = (l & 1) ? grad_backward_layer<D, 1>(fa.lay[l], fa.params, wl, sm, G, z, gz, wn, gp)
-                 : grad_backward_layer<D, 0>(fa.lay[l], fa.params, wl, sm, G, z, gz, wn, gp);
+    const unsigned char* wt = img + S::weights + (size_t)l * Q::WTL;
+    ok = (l & 1) ? grad_backward_layer<D, 1>(fa.lay[l], wt, wl, sm, G, z, gz, wn, gp)
+                 : grad_backward_layer<D, 0>(fa.lay[l], wt, wl, sm, G, z, gz, wn, gp);
   }
   // a warpgroup that gave up waits once more for its MMAs before the columns are freed
   if (G.failed) mbar_wait(G.mbar, G.phase ^ 1u, kTcWaitPolls);
@@ -436,13 +511,15 @@ __global__ void __launch_bounds__(128, 1)
 }
 
 template <int D>
-int launch_grad_tc(const FlowArgs& fa, const float* x, const float* w, const double* wsum, int64_t n, float* gpart,
-                   float* lpart, cudaStream_t s) {
+int launch_grad_tc(const FlowArgs& fa, unsigned char* img, const float* x, const float* w, const double* wsum,
+                   int64_t n, float* gpart, float* lpart, cudaStream_t s) {
   using Q = GradTcShape<D>;
+  flow_grad_image_kernel<D><<<dim3(8, kFlowLayers), 256, 0, s>>>(fa, img);
+  VG_CHECK(cudaGetLastError());
   auto k = flow_grad_tc_kernel<D>;
   VG_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Q::total));
   const int64_t nblk = (n + 127) / 128;
-  k<<<(unsigned)nblk, 128, Q::total, s>>>(fa, x, w, wsum, n, gpart, lpart);
+  k<<<(unsigned)nblk, 128, Q::total, s>>>(fa, img, x, w, wsum, n, gpart, lpart);
   return cuda_status(cudaGetLastError());
 }
 
@@ -460,12 +537,18 @@ int dispatch_grad_d(int d, F&& f) {
 
 }  // namespace
 
-// the tensor-core gradient: one CTA (128 threads) per 128 samples; gpart [ceil(n/128)][nparams], lpart likewise
-int flow_grad_tc(const FlowArgs& fa, const float* x, const float* w, const double* wsum, int64_t n, float* gpart,
-                 float* lpart, cudaStream_t s) {
+// the tensor-core gradient: the weight image (flow_grad_tc_image_bytes(d) bytes, 16-byte aligned), then one CTA
+// (128 threads) per 128 samples; gpart [ceil(n/128)][nparams], lpart likewise
+int flow_grad_tc(const FlowArgs& fa, unsigned char* img, const float* x, const float* w, const double* wsum,
+                 int64_t n, float* gpart, float* lpart, cudaStream_t s) {
   return dispatch_grad_d(fa.d, [&](auto D) {
-    return launch_grad_tc<decltype(D)::value>(fa, x, w, wsum, n, gpart, lpart, s);
+    return launch_grad_tc<decltype(D)::value>(fa, img, x, w, wsum, n, gpart, lpart, s);
   });
+}
+
+size_t flow_grad_tc_image_bytes(int d) {
+  if (d < 2 || d > kFlowGradTcMaxDim) return 0;
+  return dispatch_grad_d(d, [&](auto D) { return (int)GradTcShape<decltype(D)::value>::image; });
 }
 
 int flow_grad_tc_status(bool reset) {
