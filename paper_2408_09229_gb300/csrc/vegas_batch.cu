@@ -924,7 +924,7 @@ extern "C" int vegas_batch_integrate(vegas_batch b, int32_t nitn, double rtol, v
       r.nitn_run = b->h_ctl[p].nrec;
       r.converged = b->h_ctl[p].converged;
       const int f = b->h_flags[p];
-      r.status = (f & 6) ? VEGAS_ECUDA : (f & 1) ? VEGAS_ENONFINITE : VEGAS_OK;
+      r.status = (f & 14) ? VEGAS_ECUDA : (f & 1) ? VEGAS_ENONFINITE : VEGAS_OK;
       r.flags = 0;
       r.pad = 0;
       if (r.n_used >= 2) {

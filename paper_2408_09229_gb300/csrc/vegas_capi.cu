@@ -739,7 +739,8 @@ extern "C" int vegas_integrate(vegas_handle h, int integrand, const double* para
     if (!(out->chi2_dof <= bound)) flags |= VEGAS_RESULT_CHI2_HIGH;
   }
   out->flags = flags;
-  if (dflags & 2) return VEGAS_ECUDA;  // a cube crossing tiles was not reassembled: internal error
+  // a cube crossing tiles was not reassembled, or (bounds-checking builds) an index check failed: internal error
+  if (dflags & (2 | 8)) return VEGAS_ECUDA;
   if (flow && (rc = vg::flow_tc_status(true)) != VEGAS_OK) return rc;
   if (flow && (rc = vg::flow_grad_tc_status(true)) != VEGAS_OK) return rc;
   return (dflags & 1) ? VEGAS_ENONFINITE : VEGAS_OK;

@@ -304,4 +304,22 @@ __device__ __forceinline__ double exp_table64(double x) {
   return __hiloint2double(__double2hiint(y) + (m << 20), __double2loint(y));
 }
 
+// ---------------------------------------------------------------------------
+// Bounds-checking builds (nvcc -DVEGAS_BOUNDS_CHECK; build_lib.build(check=True)), the substitute for a memory
+// sanitizer: every index that the fill derives from data (an interval from a point, a cube from the offsets, a
+// slot of the tile's shared arrays, a histogram bin) goes through VG_IDX.  An index outside [0, n) sets bit 3 and
+// the site number (bits 8-15) in the caller's device flag word and is replaced by 0, so that no access leaves its
+// array; the handle then reports VEGAS_ECUDA.  Ordinary builds compile VG_IDX to the index itself.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long checked_index(long long i, long long n, int* flags, int site) {
+  if (i >= 0 && i < n) return i;
+  if (flags) atomicOr(flags, 8 | (site << 8));
+  return 0;
+}
+#ifdef VEGAS_BOUNDS_CHECK
+#define VG_IDX(i, n, flags, site) (vg::checked_index((long long)(i), (long long)(n), (flags), (site)))
+#else
+#define VG_IDX(i, n, flags, site) (i)
+#endif
+
 }  // namespace vg

@@ -473,7 +473,7 @@ __device__ __forceinline__ void make_point(const FillArgs& a, const uint32_t* __
         i = i < G - 1 ? i : G - 1;
         dz = z - (float)i;  // exact
       }
-      const TabEntry<T> te = tab[k * G + i];
+      const TabEntry<T> te = tab[VG_IDX(k * G + i, a.d * G, a.flags, 1)];
       x[k] = fma(dz, te.dx, te.e);
       J = J * te.jk;
       bin[k] = i;
@@ -584,7 +584,7 @@ __device__ __forceinline__ float stream_point_eval(const FillArgs& a, const uint
         int i = (int)z;
         i = i < G - 1 ? i : G - 1;
         const float dz = z - (float)i;
-        const TabEntry<float> te = tab[k * G + i];
+        const TabEntry<float> te = tab[VG_IDX(k * G + i, a.d * G, a.flags, 2)];
         const float x = fmaf(dz, te.dx, te.e);
         J = J * te.jk;
         word |= (uint32_t)i << (8 * q);
@@ -865,7 +865,7 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
           if constexpr (sizeof(T) == 8) inv = 1.0 / (double)n;
           else inv = __fdividef(1.0f, (float)n);
           for (int t = (r0 + kSamplesPerThread - 1) / kSamplesPerThread; t * kSamplesPerThread < r1; ++t)
-            startc[t] = c;
+            startc[VG_IDX(t, kFillThreads, a.flags, 20)] = c;
           if (r1 == len) misc[1] = c + 1;  // cubes met by the tile
         }
         invn[c] = inv;
@@ -911,7 +911,8 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
                             : a.offsets[(int64_t)h0 + c + 1] - a.offsets[(int64_t)h0 + c];
       if constexpr (sizeof(T) == 8) inv = 1.0 / (double)n;
       else inv = __fdividef(1.0f, (float)n);
-      for (int t = (r0 + kSamplesPerThread - 1) / kSamplesPerThread; t * kSamplesPerThread < r1; ++t) startc[t] = c;
+      for (int t = (r0 + kSamplesPerThread - 1) / kSamplesPerThread; t * kSamplesPerThread < r1; ++t)
+        startc[VG_IDX(t, kFillThreads, a.flags, 21)] = c;
       if (r1 == len) misc[1] = c + 1;  // cubes met by the tile
     }
     invn[c] = inv;
@@ -932,7 +933,7 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
       for (int s = 0; s < kSamplesPerThread; ++s) {
         const int jl = jl0 + s;
         if (jl < len) {
-          while (off_r[c + 1] <= jl) ++c;
+          while (off_r[VG_IDX(c + 1, kMaxCubesPerTile + 1, a.flags, 3)] <= jl) ++c;
           if (c != c_decoded) {
             decode_packed<DMAX>(a, (uint32_t)(h0 + c), cw);
             c_decoded = c;
@@ -945,13 +946,13 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
           if constexpr (ID == kIntegrandTabulated) f = a.values[j0 + jl];
           if (!isfinite(f)) bad = true;
           const float v = J * f;
-          vals[jl] = v;
+          vals[VG_IDX(jl, kTile, a.flags, 4)] = v;
           if constexpr (ID == kIntegrandTabulated) {
             const int64_t j = j0 + jl;
             if (a.train_w && j % a.train_stride == 0)
               a.train_w[j / a.train_stride] = powf(fabsf(v) * (float)invn[c], a.train_power);
           }
-          const float wv = v * v * (float)invn[c];
+          const float wv = v * v * (float)invn[VG_IDX(c, kMaxCubesPerTile, a.flags, 5)];
           wv_s[tix(jl)] = wv;
           my_max = fmaxf(my_max, wv);
         }
@@ -965,7 +966,7 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
     for (int s = 0; s < kSamplesPerThread; ++s) {
       const int jl = jl0 + s;
       if (jl < len) {
-        while (off_r[c + 1] <= jl) {
+        while (off_r[VG_IDX(c + 1, kMaxCubesPerTile + 1, a.flags, 6)] <= jl) {
           ++c;
           next_cube<T, DMAX, EXACT>(a, cb);
         }
@@ -993,14 +994,14 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
         else f = integrand<ID, T, DMAX>(x, d, prm, a.np_derived, ps0, ps1, pK);
         if (!isfinite(f)) bad = true;
         const T v = J * f;
-        vals[jl] = v;
+        vals[VG_IDX(jl, kTile, a.flags, 7)] = v;
         if constexpr (ID == kIntegrandTabulated) {
           // training weights (|J f| / n_h)^p of every train_stride-th evaluation
           const int64_t j = j0 + jl;
           if (a.train_w && j % a.train_stride == 0)
             a.train_w[j / a.train_stride] = powf(fabsf((float)v) * (float)invn[c], a.train_power);
         }
-        const T wv = v * v * invn[c];
+        const T wv = v * v * invn[VG_IDX(c, kMaxCubesPerTile, a.flags, 8)];
         if (two_phase) {
           wv_s[tix(jl)] = (float)wv;
           my_max = fmaxf(my_max, (float)wv);
@@ -1031,8 +1032,8 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
 #pragma unroll
           for (int k = 0; k < DMAX; ++k) {
             if (k < d) {
-              if (a.hist_mode == kHistShared) atomicAdd(hist_s + k * G + bin[k], wv);
-              else atomicAdd(hist_g + k * G + bin[k], (double)wv);
+              if (a.hist_mode == kHistShared) atomicAdd(hist_s + VG_IDX(k * G + bin[k], dG, a.flags, 9), wv);
+              else atomicAdd(hist_g + VG_IDX(k * G + bin[k], dG, a.flags, 10), (double)wv);
             }
           }
         }
@@ -1074,14 +1075,15 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
                   const int kk = 4 * w;
 #pragma unroll
                   for (int b = 0; b < 4; ++b)
-                    if (kk + b < d) atomicAdd(hist_u + (kk + b) * G + ((word >> (8 * b)) & 255u), q);
+                    if (kk + b < d)
+                      atomicAdd(hist_u + VG_IDX((kk + b) * G + ((word >> (8 * b)) & 255u), dG, a.flags, 11), q);
                 }
               } else {
                 for (int w = 0; w < nw; ++w) {
                   const uint32_t word = binw[w * kTile + tix(jl)];
                   const int kk = 2 * w;
-                  atomicAdd(hist_u + kk * G + (word & 0xFFFFu), q);
-                  if (kk + 1 < d) atomicAdd(hist_u + (kk + 1) * G + (word >> 16), q);
+                  atomicAdd(hist_u + VG_IDX(kk * G + (word & 0xFFFFu), dG, a.flags, 12), q);
+                  if (kk + 1 < d) atomicAdd(hist_u + VG_IDX((kk + 1) * G + (word >> 16), dG, a.flags, 13), q);
                 }
               }
             }
@@ -1102,7 +1104,7 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
     const bool before = r0 < 0, after = r1 > len;
     const int h = h0 + c;
     if (before || after) {
-      a.carries[2 * tile + (before ? 0 : 1)] = Carry{h, L, to_double(mean), (double)m2};
+      a.carries[VG_IDX(2 * tile + (before ? 0 : 1), 2 * a.ntiles, a.flags, 14)] = Carry{h, L, to_double(mean), (double)m2};
       return;
     }
     const int n = r1 - r0;
@@ -1118,11 +1120,11 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
       acc_v.add(__fdividef(m2, nf * (nf - 1.0f)));
       ell = a.half_beta * (log2_fast(__fdividef(m2, nf - 1.0f)) + (float)(2 * st.vexp));
     }
-    a.ell[h] = ell;
+    a.ell[VG_IDX(h, a.NH, a.flags, 15)] = ell;
     lmax = fmaxf(lmax, ell);
     if (a.cube_mean) {
-      a.cube_mean[h] = ldexp(to_double(mean), st.vexp);
-      a.cube_m2[h] = ldexp((double)m2, 2 * st.vexp);
+      a.cube_mean[VG_IDX(h, a.NH, a.flags, 16)] = ldexp(to_double(mean), st.vexp);
+      a.cube_m2[VG_IDX(h, a.NH, a.flags, 17)] = ldexp((double)m2, 2 * st.vexp);
     }
   };
 
@@ -1138,10 +1140,10 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
     // one pass over the segment, shifted by its first value: mean = v0 + s/L,
     // M2 = q - s^2/L with s, q the sums of (v - v0) and (v - v0)^2; the shift
     // keeps q within (L + 1) M2, so the cancellation costs a few ulps
-    const T v0 = vals[r0];
+    const T v0 = vals[VG_IDX(r0, kTile, a.flags, 18)];
     T sd = T(0), qd = T(0);
     for (int r = r0 + 1; r < r1; ++r) {
-      const T dv = vals[r] - v0;
+      const T dv = vals[VG_IDX(r, kTile, a.flags, 19)] - v0;
       sd += dv;
       qd = fma(dv, dv, qd);
     }

@@ -19,7 +19,8 @@ from .workloads import (GAUSS_SUM, PRODUCT_PEAK, OSCILLATORY, SIN_EXP, LINEAR, C
                         ROOS_ARNOLD, MOROKOFF_CAFLISCH, MAP_DENSITY)
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libvegas_gb300.so")
+# VEGAS_GB300_LIB selects another build of the library, e.g. the bounds-checking libvegas_gb300_check.so
+LIB_PATH = os.environ.get("VEGAS_GB300_LIB") or os.path.join(HERE, "libvegas_gb300.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ESTATE, ENOSPACE = 0, -1, -2, -3, -4, -5, -6, -7
 FP64, FP32 = 0, 1
