@@ -46,7 +46,7 @@ FP32_LANES_PER_SM = 128
 # that kernel (dram__bytes_read.sum + dram__bytes_write.sum): the per-cube offsets and weights
 FILL_TRAFFIC_BYTES = (346.28 + 146.85) * 1e6
 # the same for the FP64 form's fill kernel (profiles/fill_kernel_ridge8_fp64.md)
-FILL64_TRAFFIC_BYTES = (351.2 + 148.7) * 1e6
+FILL64_TRAFFIC_BYTES = (353.19 + 148.66) * 1e6
 # the same capture: issue slots busy and warp instructions x 32 per evaluation (1.843e9 x 32 / 1e8)
 FILL_ISSUE_ACTIVE = 0.681
 FILL_INSTR_PER_EVAL = 590
@@ -441,6 +441,29 @@ def run_ours(args, rank, world):
                               "iteration_ms": [float(x) for x in it_ms], "fill_ms": [float(x) for x in fill_ms],
                               "estimate": r["estimate"], "sigma": r["sigma"]}))
         return
+    if args.profile_grad:
+        # the learned proposal's training gradient alone: 4096 seeded samples in the d-cube, exponential weights,
+        # a seeded flow; 3 warm-up calls, then 200 timed ones (CUDA events)
+        d, n = args.profile_grad, 4096
+        th = torch.as_tensor(W.flow_params(d, seed=0, out_scale=0.05), dtype=torch.float32).cuda()
+        gen = torch.Generator("cuda").manual_seed(0)
+        x = torch.rand((n, d), device="cuda", generator=gen)
+        wts = torch.rand(n, device="cuda", generator=gen)
+        grad, loss = torch.empty_like(th), torch.empty(1, device="cuda")
+        sc = torch.empty(V.flow_grad_scratch_bytes(d, n), dtype=torch.uint8, device="cuda")
+        for _ in range(3):
+            V.flow_grad(d, th, x, wts, grad, loss, sc)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(200):
+            V.flow_grad(d, th, x, wts, grad, loss, sc)
+        e1.record()
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"profile": "flow gradient", "dim": d, "samples": n,
+                              "ms_per_gradient": e0.elapsed_time(e1) / 200}))
+        return
     if args.profile_batch:
         probs = W.batch_problems(args.profile_batch, seed=0, neval_range=(1e5, args.batch_max_neval))
         b = V.Batch(probs, NBINS, ALPHA, BETA, seed=SEED, stream=stream)
@@ -785,6 +808,8 @@ def main():
                     help="profiling run of the d = 30 workload (FP32 form) at NEVAL evaluations per iteration")
     ap.add_argument("--profile-flow", action="store_true",
                     help="profiling run of the learned proposal: d = 12 ridge, 1e7 evaluations, a fixed flow")
+    ap.add_argument("--profile-grad", type=int, default=0, metavar="D",
+                    help="profiling run of the learned proposal's training gradient in D dimensions (4096 samples)")
     ap.add_argument("--profile-batch", type=int, default=0, metavar="N",
                     help="profiling run of the batched form on the first N integrals of the batched workload")
     ap.add_argument("--batch-max-neval", type=float, default=1e8,
