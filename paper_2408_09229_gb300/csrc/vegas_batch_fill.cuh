@@ -134,11 +134,11 @@ int batch_fill_kernel_occupancy(int smem) {
 template <int ID>
 int launch_batch_fill_family(int variant, int dmax, int group, const BatchLaunch& L, int grid, int smem,
                              cudaStream_t s) {
-  // variant 0: 64 registers up to 8 axes; the 16-axis streamed path spills below 128 (2 CTAs an SM) in the
-  // persistent kernel, so both variants give it 128.  Variant 1: 128 registers at every width.
+  // variant 0: the fewest registers without local-memory spills in the persistent kernel: 64 at 4 axes (4 CTAs
+  // an SM), 80 at 8 (3 CTAs), 128 for the 16-axis streamed path (2 CTAs).  Variant 1: 128 at every width.
   if (variant == 0) {
     if (dmax == 4) return launch_batch_fill_kernel<4, ID, 4>(L, group, grid, smem, s);
-    if (dmax == 8) return launch_batch_fill_kernel<4, ID, 8>(L, group, grid, smem, s);
+    if (dmax == 8) return launch_batch_fill_kernel<3, ID, 8>(L, group, grid, smem, s);
   }
   if (dmax == 4) return launch_batch_fill_kernel<2, ID, 4>(L, group, grid, smem, s);
   if (dmax == 8) return launch_batch_fill_kernel<2, ID, 8>(L, group, grid, smem, s);
@@ -149,7 +149,7 @@ template <int ID>
 int batch_fill_family_occupancy(int variant, int dmax, int smem) {
   if (variant == 0) {
     if (dmax == 4) return batch_fill_kernel_occupancy<4, ID, 4>(smem);
-    if (dmax == 8) return batch_fill_kernel_occupancy<4, ID, 8>(smem);
+    if (dmax == 8) return batch_fill_kernel_occupancy<3, ID, 8>(smem);
   }
   if (dmax == 4) return batch_fill_kernel_occupancy<2, ID, 4>(smem);
   if (dmax == 8) return batch_fill_kernel_occupancy<2, ID, 8>(smem);
