@@ -129,6 +129,10 @@ typedef struct {
 #define VEGAS_RESULT_FLOW_OFF 2  /* the judge turned the learned proposal off; the result is the
                                     plain VEGAS+ iterations run beside it                        */
 #define VEGAS_RESULT_FLOW_KEPT 4 /* the judge compared the two and kept the learned proposal      */
+#define VEGAS_RESULT_FP32_FLOOR 8 /* FP32 form: sigma is below 2^-20 |estimate|, the relative rounding
+                                     bias the FP32 evaluation can carry (a few FP32 ulps of each value);
+                                     the error of the estimate is then max(sigma, 2^-20 |estimate|),
+                                     which is also what the rtol stop compares                        */
 
 /* Device memory hooks (not in the paper, which allocates with cudaMalloc).
  * alloc returns `bytes` of device memory of the handle's device, aligned to at
@@ -176,7 +180,8 @@ VEGAS_API int vegas_set_weighting(vegas_handle h, int weighting);
 VEGAS_API int vegas_set_stream(vegas_handle h, void *stream);
 /* Stop an integrate call early once sigma/|estimate| <= rtol (0 disables the
  * check, which is the default).  The check reads the result to the host after
- * every iteration. */
+ * every iteration.  In the FP32 form sigma counts as at least 2^-20 |estimate|
+ * (VEGAS_RESULT_FP32_FLOOR). */
 VEGAS_API int vegas_set_rtol(vegas_handle h, double rtol);
 /* Back to the uniform map and uniform allocation; iteration counter to 0. */
 VEGAS_API int vegas_reset_map(vegas_handle h);
@@ -269,9 +274,11 @@ VEGAS_API int vegas_allocate(const float *d_ell, int64_t ncubes, int64_t neval, 
  * library holds that array until the process exits.
  *   - Limit: ncubes <= VEGAS_ALLOCATE_STATIC_MAX_CUBES; larger sizes return
  *     VEGAS_ENOSPACE before anything runs.
- *   - Set-up: the first call on a device looks up the array's device address
- *     with that device current.  Make that first call before any stream
- *     capture on the device.
+ *   - Set-up: each call made outside stream capture looks up the array's
+ *     device address with the device current (after cudaDeviceReset the next
+ *     such call finds the new context's array).  A call on a capturing stream
+ *     uses the address that the last call outside capture found, so make the
+ *     first call on a device before any stream capture on it.
  *   - Sharing: every call on a device shares the one array, which keeps the
  *     contents of the last call.  Each call re-initialises what it reads, so
  *     sequential calls are independent.  Calls that overlap on the GPU
@@ -375,7 +382,10 @@ typedef struct {
   int32_t status;                   /* VEGAS_OK, VEGAS_ENONFINITE, or VEGAS_ECUDA when a
                                        cube split across tiles was not reassembled        */
   int32_t flags;                    /* VEGAS_RESULT_CHI2_HIGH when chi2/dof is above the
-                                       bound of vegas_batch_set_chi2_bound                */
+                                       bound of vegas_batch_set_chi2_bound;
+                                       VEGAS_RESULT_FP32_FLOOR when sigma is below the FP32
+                                       evaluation's rounding floor (the batch's rtol test
+                                       uses the floor too)                                */
   int32_t pad;
 } vegas_problem_result;
 

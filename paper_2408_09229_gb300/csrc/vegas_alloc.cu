@@ -120,15 +120,25 @@ void* g_static_scratch[kMaxDevices] = {};
 
 // Device address of g_allocate_scratch on the current device.  In host code
 // the array's name is only a host-side stand-in, so the address comes from
-// cudaGetSymbolAddress, once per device, with that device current.
-int static_scratch(void** out) {
+// cudaGetSymbolAddress with that device current.  The lookup runs on every call
+// made outside stream capture, so that a call after cudaDeviceReset sees the
+// array of the new context; a call on a capturing stream uses the address that
+// the last call outside capture found on the device.
+int static_scratch(cudaStream_t s, void** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return VEGAS_ECUDA;
   if (dev < 0 || dev >= kMaxDevices) return VEGAS_EINVAL;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const cudaError_t qe = cudaStreamIsCapturing(s, &cs);
+  if (qe != cudaSuccess) (void)cudaGetLastError();  // e.g. the legacy stream while another stream captures
+  const bool capturing = qe != cudaSuccess || cs != cudaStreamCaptureStatusNone;
   std::lock_guard<std::mutex> lock(g_static_mutex);
-  if (!g_static_scratch[dev]) {
+  if (!capturing || !g_static_scratch[dev]) {
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_allocate_scratch) != cudaSuccess || !p) return VEGAS_ECUDA;
+    if (cudaGetSymbolAddress(&p, g_allocate_scratch) != cudaSuccess || !p) {
+      (void)cudaGetLastError();
+      return VEGAS_ECUDA;
+    }
     g_static_scratch[dev] = p;
   }
   *out = g_static_scratch[dev];
@@ -144,7 +154,7 @@ extern "C" int vegas_allocate_static(const float* d_ell, int64_t ncubes, int64_t
   if (ncubes > VEGAS_ALLOCATE_STATIC_MAX_CUBES) return VEGAS_ENOSPACE;
   if (!d_offsets || (!uniform && !d_ell)) return VEGAS_EINVAL;
   void* base = nullptr;
-  const int rc = static_scratch(&base);
+  const int rc = static_scratch((cudaStream_t)stream, &base);
   if (rc != VEGAS_OK) return rc;
   const AllocScratch L = alloc_layout(ncubes);
   if (L.total > kStaticScratchBytes) return VEGAS_ENOSPACE;

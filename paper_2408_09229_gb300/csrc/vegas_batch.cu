@@ -292,7 +292,8 @@ __global__ void batch_finish_kernel(const __grid_constant__ BatchLaunch L, doubl
   c.nrec = t + 1;
   c.uniform = beta == 0.0 ? 1 : 0;
   q.a.iter += 1u;
-  if (L.rtol > 0.0 && t + 1 > L.skip && out[1] <= L.rtol * fabs(out[0])) {
+  // the FP32 evaluation's sigma counts as at least its rounding floor (kFp32SigmaFloor)
+  if (L.rtol > 0.0 && t + 1 > L.skip && fmax(out[1], kFp32SigmaFloor * fabs(out[0])) <= L.rtol * fabs(out[0])) {
     c.active = 0;
     c.converged = 1;
   }
@@ -931,6 +932,7 @@ extern "C" int vegas_batch_integrate(vegas_batch b, int32_t nitn, double rtol, v
         const double bound = b->chi2_bound > 0.0 ? b->chi2_bound : chi2_dof_quantile_999_batch(r.n_used - 1);
         if (!(r.chi2_dof <= bound)) r.flags |= VEGAS_RESULT_CHI2_HIGH;
       }
+      if (r.sigma < kFp32SigmaFloor * std::fabs(r.estimate)) r.flags |= VEGAS_RESULT_FP32_FLOOR;  // FP32 only
     }
   }
   return VEGAS_OK;

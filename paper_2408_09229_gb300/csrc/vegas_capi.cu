@@ -697,8 +697,10 @@ extern "C" int vegas_integrate(vegas_handle h, int integrand, const double* para
       if (paired)
         VG_CHECK(cudaMemcpyAsync(h->h_out + 4, h->arm[1].d_out, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
       VG_CHECK(cudaStreamSynchronize(s));
-      const double r0 = h->h_out[1] / std::fabs(h->h_out[0]);
-      const double r1 = paired ? h->h_out[5] / std::fabs(h->h_out[4]) : INFINITY;
+      // the FP32 form's sigma counts as at least its rounding floor
+      const double fl = h->precision == VEGAS_FP32 ? vg::kFp32SigmaFloor : 0.0;
+      const double r0 = std::max(h->h_out[1] / std::fabs(h->h_out[0]), fl);
+      const double r1 = paired ? std::max(h->h_out[5] / std::fabs(h->h_out[4]), fl) : INFINITY;
       if (r0 <= h->rtol || r1 <= h->rtol) {
         if (paired) {  // the first form to reach the target is the result
           if (r1 < r0) {
@@ -738,6 +740,8 @@ extern "C" int vegas_integrate(vegas_handle h, int integrand, const double* para
     const double bound = h->chi2_bound > 0.0 ? h->chi2_bound : chi2_dof_quantile_999(out->n_used - 1);
     if (!(out->chi2_dof <= bound)) flags |= VEGAS_RESULT_CHI2_HIGH;
   }
+  if (h->precision == VEGAS_FP32 && out->sigma < vg::kFp32SigmaFloor * std::fabs(out->estimate))
+    flags |= VEGAS_RESULT_FP32_FLOOR;
   out->flags = flags;
   // a cube crossing tiles was not reassembled, or (bounds-checking builds) an index check failed: internal error
   if (dflags & (2 | 8)) return VEGAS_ECUDA;

@@ -19,9 +19,10 @@
 //    (Chan's pairwise formula) in tile order.
 //  * map weights: a per-CTA histogram.  The FP64 form adds with shared FP64
 //    atomics.  The 32 lanes of a warp share a stratum on the high axes, so
-//    their adds collide on a handful of bins, and shared floating-point
-//    atomics measured slower than integer ones.  The FP32 form therefore adds
-//    in two phases per tile:
+//    their adds collide on a handful of bins; the FP64 histogram is therefore
+//    kept in up to 8 copies, lane l adding into copy l mod copies.  Shared
+//    floating-point atomics measured slower than integer ones, so the FP32
+//    form adds in two phases per tile:
 //    the tile's largest weight fixes a power-of-two scale, the weights go in
 //    as 32-bit fixed-point integers through native shared integer atomics,
 //    and every tile's totals are folded into float-float accumulators.
@@ -771,7 +772,7 @@ __device__ __forceinline__ void fill_prologue(const FillArgs& a, const FillShare
     }
   }
   if (a.hist_mode == kHistShared)
-    for (int b = tid; b < dG; b += kFillThreads) S.hist_s[b] = T(0);
+    for (int b = tid; b < (dG << a.hist_rep_log2); b += kFillThreads) S.hist_s[b] = T(0);
   if (a.hist_mode == kHistTwoPhase)
     for (int b = tid; b < dG; b += kFillThreads) {
       S.hist_u[b] = 0u;
@@ -1032,7 +1033,10 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
 #pragma unroll
           for (int k = 0; k < DMAX; ++k) {
             if (k < d) {
-              if (a.hist_mode == kHistShared) atomicAdd(hist_s + VG_IDX(k * G + bin[k], dG, a.flags, 9), wv);
+              if (a.hist_mode == kHistShared)
+                atomicAdd(hist_s + VG_IDX(((k * G + bin[k]) << a.hist_rep_log2) + (lane & ((1 << a.hist_rep_log2) - 1)),
+                                          dG << a.hist_rep_log2, a.flags, 9),
+                          wv);
               else atomicAdd(hist_g + VG_IDX(k * G + bin[k], dG, a.flags, 10), (double)wv);
             }
           }
@@ -1316,7 +1320,11 @@ __global__ void __launch_bounds__(kFillThreads, (sizeof(T) == 4 && (DMAX <= 8 ||
   if (lane == 0) atomicMax(a.ellmax_key, float_key(lmax));
   if (__syncthreads_or(st.bad) && tid == 0) atomicOr(a.flags, 1);
   if (a.hist_mode == kHistShared)
-    for (int b = tid; b < dG; b += kFillThreads) hist_g[b] = (double)S.hist_s[b];
+    for (int b = tid; b < dG; b += kFillThreads) {
+      double t = 0.0;
+      for (int c = 0; c < (1 << a.hist_rep_log2); ++c) t += (double)S.hist_s[(b << a.hist_rep_log2) + c];
+      hist_g[b] = t;
+    }
   if (a.hist_mode == kHistTwoPhase) {
     for (int b = tid; b < dG; b += kFillThreads) {
       const float pend = st.inv_scale > 0.0f ? __fmul_rn((float)S.hist_u[b], st.inv_scale) : 0.0f;

@@ -119,6 +119,15 @@ int smem_layout(FillArgs& a, size_t tsz, int nprm, bool fp32, bool table_ok = tr
   } else if (base + shared_hist <= budget) {
     a.hist_mode = kHistShared;
     hist = shared_hist;
+    // FP64 atomic adds into shared memory are slow when lanes of a warp hit one address, and they do on the
+    // slow axes, where a warp's evaluations share the cube coordinate: up to 8 copies of the histogram (at
+    // most 32 KB), lane l adding into copy l mod copies, summed in copy order at the end of the CTA
+    a.hist_rep_log2 = 0;
+    if (!fp32)
+      while (a.hist_rep_log2 < 3 && ((size_t)dG * tsz << (a.hist_rep_log2 + 1)) <= 32 * 1024 &&
+             base + align_up((size_t)dG * tsz << (a.hist_rep_log2 + 1)) <= budget)
+        ++a.hist_rep_log2;
+    hist = align_up((size_t)dG * tsz << a.hist_rep_log2);
   } else {
     a.hist_mode = kHistGlobal;
     hist = 0;
@@ -133,7 +142,7 @@ int smem_layout(FillArgs& a, size_t tsz, int nprm, bool fp32, bool table_ok = tr
     a.sm_bins = (int)off; off += align_up(bin_words);
     a.sm_wv = (int)off;   off += align_up(sizeof(float) * kTile);
   } else {
-    off += a.hist_mode == kHistShared ? shared_hist : 0;
+    off += a.hist_mode == kHistShared ? hist : 0;
     a.sm_hacc = a.sm_bins = a.sm_wv = (int)off;
   }
   a.sm_params = (int)off; off += align_up(nprm * tsz);

@@ -25,6 +25,11 @@ constexpr int kMaxDerivedParams = 8192;
 constexpr int kAllocThreads = 256;
 constexpr int kAllocItems = 16;  // cubes per thread in the allocation scan
 constexpr int64_t kMaxEval = (int64_t(1) << 31) - 1;
+// The FP32 form's evaluation-rounding floor, relative to |I|: the estimate carries a rounding bias of a few FP32
+// ulps of each value (map fused multiply-add, ex2 within 2 ulp, the integrand's sums), measured up to 1.1e-6 on
+// single-iteration 2-d results and 1.3e-7 at full size.  A stated sigma below 2^-20 |I| (16 ulps) is not a
+// statistical error the result can be trusted to: the rtol test uses max(sigma, floor |I|) and the result is flagged.
+constexpr double kFp32SigmaFloor = 0x1p-20;
 // internal integrand identifiers of the fill (not in the public enumeration):
 // tabulated values f_j = values[j] by evaluation index, and a points-only
 // pass that writes the evaluation points and nothing else
@@ -50,6 +55,7 @@ struct FillArgs {
   int hist_mode;   // kHistShared, kHistGlobal or kHistTwoPhase
   int bin_shift;   // two-phase: log2 of the bits of a packed interval index (3: 8 bits, N_g <= 256; 4: 16 bits)
   int acc32;       // two-phase: 1 when the CTA histogram accumulates in FP32 (large d * N_g), 0 for float-float
+  int hist_rep_log2;  // shared FP64 histogram: log2 of its copies; lane l adds into copy l mod 2^hist_rep_log2
   int np_derived;
   int iid;  // integrand family (the batched fill dispatches on it per tile)
   const double* edges;     // [d][G+1] FP64

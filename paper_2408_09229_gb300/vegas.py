@@ -24,7 +24,7 @@ LIB_PATH = os.environ.get("VEGAS_GB300_LIB") or os.path.join(HERE, "libvegas_gb3
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ESTATE, ENOSPACE = 0, -1, -2, -3, -4, -5, -6, -7
 FP64, FP32 = 0, 1
-RESULT_CHI2_HIGH, RESULT_FLOW_OFF, RESULT_FLOW_KEPT = 1, 2, 4
+RESULT_CHI2_HIGH, RESULT_FLOW_OFF, RESULT_FLOW_KEPT, RESULT_FP32_FLOOR = 1, 2, 4, 8
 
 # device memory hooks (vegas_alloc_fn, vegas_free_fn)
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)

@@ -47,7 +47,8 @@ CHILD = textwrap.dedent("""
     run("fp32 ridge d8", 8, W.GAUSS_SUM, W.ridge8_params(), 2_000_000, 3, V.FP32)
     run("fp64 d5 general path", 5, W.OSCILLATORY, W.oscillatory(5, 1), 300_007, 3, V.FP64)
     run("fp32 d12 streamed", 12, W.GAUSS_SUM, W.ridge(12, 3, 0.1), 1_000_000, 3, V.FP32)
-    run("fp32 d30 streamed", 30, W.GAUSS_SUM, W.two_diagonal_ridge(30, 0.1), 2_000_000, 3, V.FP32,
+    # 2^20 cubes: at least 2^21 evaluations (two a cube)
+    run("fp32 d30 streamed", 30, W.GAUSS_SUM, W.two_diagonal_ridge(30, 0.1), 3_000_000, 3, V.FP32,
         nstrat_axes=[2] * 20 + [1] * 10)
     run("fp32 N_g 1024", 4, W.LINEAR, [], 500_000, 3, V.FP32, nbins=1024)
     run("fp64 one long cube", 2, W.GAUSS_SUM, W.ridge(2, 3, 0.1), 50_000, 2, V.FP64, nstrat_axes=[1, 1])

@@ -175,6 +175,24 @@ def test_chi2_flag(V):
     assert not r["flags"] & V.RESULT_CHI2_HIGH
 
 
+def test_fp32_rounding_floor(V):
+    """the FP32 form: a sigma below 2^-20 |I| is flagged and the rtol stop counts the floor; FP64 is not floored.
+    The linear integrand x_0 + x_1 (I = 1) on 1e6 cubes of 2 evaluations has sigma_t about 3e-7 an iteration
+    (cube variance 2 (1e-3)^2 / 12), about 1.2e-7 over six, well under the floor 2^-20 = 9.5e-7"""
+    v = V.Vegas(2, 50, 0, 0.5, 0.75, precision=V.FP32, rtol=1e-7)
+    r = v.integrate(W.LINEAR, [], 2_000_000, 6, seed=0)
+    assert r["nitn_run"] == 6  # 1e-7 is below the floor: never reached
+    assert r["sigma"] < 2.0 ** -20 * abs(r["estimate"])
+    assert r["flags"] & V.RESULT_FP32_FLOOR
+    assert abs(r["estimate"] - 1.0) < 3.0 * max(r["sigma"], 2.0 ** -20)
+    w = V.Vegas(2, 50, 0, 0.5, 0.75, precision=V.FP64, rtol=1e-7)
+    q = w.integrate(W.LINEAR, [], 2_000_000, 6, seed=0)
+    assert not q["flags"] & V.RESULT_FP32_FLOOR
+    u = V.Vegas(4, 50, 0, 0.5, 0.75, precision=V.FP32)
+    q = u.integrate(W.GAUSS_SUM, W.ridge4_params(), 100_000, 3, seed=0)
+    assert not q["flags"] & V.RESULT_FP32_FLOOR  # sigma/I ~ 1e-3
+
+
 def test_batch_chi2_flag(V):
     probs = [dict(dim=12, integrand=W.GAUSS_SUM, params=W.ridge(12, 4, 0.03), neval=10_000_000, exact=1.0),
              dict(dim=4, integrand=W.GAUSS_SUM, params=W.ridge4_params(), neval=100_000, exact=1.0)]
