@@ -11,9 +11,9 @@ namespace vg {
 constexpr int kMaxDim = 32;
 constexpr int kMaxBins = 4096;
 constexpr int kFillThreads = 256;
-constexpr int kSamplesPerThread = 4;
+constexpr int kSamplesPerThread = 8;
 constexpr int kTile = kFillThreads * kSamplesPerThread;  // evaluations per tile
-constexpr int kTileLog2 = 10;                            // kTile = 2^kTileLog2
+constexpr int kTileLog2 = 11;                            // kTile = 2^kTileLog2
 static_assert(kTile == (1 << kTileLog2), "tile size is a power of two");
 // how the fill accumulates the map weights
 constexpr int kHistShared = 0;    // shared-memory histogram of the evaluation type, atomic adds
@@ -80,7 +80,6 @@ struct FillArgs {
   float train_power;
   uint32_t nstrat[kMaxDim], magic[kMaxDim], shift[kMaxDim];
   double gz64[kMaxDim];     // N_g / s_k, rounded in FP64
-  double gz64s[kMaxDim];    // gz64 2^-53 (exact): the point's z from the 64-bit integer c 2^53 + (53 random bits)
   float gzb32[kMaxDim];     // RN32(N_g / s_k) 2^-b_k
   float gzn32[kMaxDim];     // -2^23 RN32(N_g / s_k) 2^-b_k
   uint32_t fbits[kMaxDim];  // b_k = 23 - ceil(log2 s_k): fraction bits of an FP32 coordinate

@@ -20,7 +20,7 @@ problem_id = p.  Checked here, through the C ABI:
     batch's map weights to 1e-13;
   * the combination over iterations, the rtol stop, a non-finite integral
     that stops alone, launch shapes that agree, and argument errors.
-Sizes span several 1024-evaluation tiles with ragged last tiles, and the
+Sizes span several 2048-evaluation tiles with ragged last tiles, and the
 batch mixes dimensions (widths 4, 8 and 16 of the fill) and the three
 families.
 """

@@ -11,7 +11,7 @@ below, each derived from the arithmetic of the two sides:
     4 float ulps (the FP64 form evaluates them with the reproducible log2).
   FP32 path against the oracle on the same FP32 points: I_t 2e-5 relative,
     sigma_t^2 2e-3 relative, cube means 5e-4 relative of the largest mean.
-Inputs are seeded and synthetic; sizes span several tiles (1024 evaluations)
+Inputs are seeded and synthetic; sizes span several tiles (2048 evaluations)
 and a ragged last tile, plus the full 1e8-evaluation, 43-million-cube
 configuration checked on sampled cubes.
 """
@@ -26,7 +26,7 @@ torch = pytest.importorskip("torch")
 
 from paper_2408_09229_gb300 import workloads as W  # noqa: E402
 
-TILE = 1024
+TILE = 2048  # evaluations per tile of the fill kernel
 
 
 @pytest.fixture(scope="module")
