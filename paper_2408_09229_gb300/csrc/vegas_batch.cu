@@ -695,7 +695,7 @@ extern "C" int vegas_batch_create_ex(const vegas_problem* problems, int32_t npro
     std::vector<int32_t> ones(maxd, 1);
     layout.d = maxd;
     layout.G = G;
-    if (fill_args_axes(layout, ones.data(), VEGAS_FP32, nprm_max) != VEGAS_OK) return VEGAS_EINVAL;
+    if (fill_args_axes(layout, ones.data(), VEGAS_FP32, nprm_max, false) != VEGAS_OK) return VEGAS_EINVAL;
     if (!layout.table_smem || layout.hist_mode != kHistTwoPhase) return VEGAS_EINVAL;
   }
 
@@ -814,7 +814,7 @@ extern "C" int vegas_batch_create_ex(const vegas_problem* problems, int32_t npro
     a.vexp = (const int*)(A + o_vexp) + p;
     vexp[p] = value_exponent(h.iid, h.d, h.params.data(), (int)h.params.size());
     std::vector<int32_t> ns(h.d, h.nstrat);
-    if (fill_args_axes(a, ns.data(), VEGAS_FP32, nprm_max) != VEGAS_OK) return fail(VEGAS_EINVAL);
+    if (fill_args_axes(a, ns.data(), VEGAS_FP32, nprm_max, false) != VEGAS_OK) return fail(VEGAS_EINVAL);
     a.table_smem = layout.table_smem;
     a.hist_mode = layout.hist_mode;
     a.sm_table = layout.sm_table;

@@ -1141,10 +1141,12 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
     float ell;
     acc_i.add(mean);
     if constexpr (sizeof(T) == 8) {
-      acc_v.add(m2 / ((double)n * (double)(n - 1)));
+      // sigma_h^2 = M2 / (n - 1) divided exactly (it decides the counts); sigma_h^2 / n with the tile's 1/n
+      const double var = m2 / (double)(n - 1);
+      acc_v.add(var * invn[c]);
       // the FP64 form keeps the reproducible log2, so that the counts of a
       // free-running FP64 run follow the CPU reference bit for bit
-      ell = __fmul_rn(a.half_beta, log2r(m2 / (double)(n - 1)));
+      ell = __fmul_rn(a.half_beta, log2r(var));
     } else {
       const float nf = (float)n;
       acc_v.add(__fdividef(m2, nf * (nf - 1.0f)));
@@ -1163,7 +1165,7 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
     const int r0 = max(off_r[c], 0), r1 = min(off_r[c + 1], len);
     const int L = r1 - r0;
     if (L > kLongSegment) {
-      longlist[atomicAdd(&misc[0], 1)] = c;
+      longlist[VG_IDX(atomicAdd(&misc[0], 1), kMaxLongPerTile, a.flags, 22)] = c;
       had_long = true;
       continue;
     }
@@ -1178,7 +1180,8 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
       qd = fma(dv, dv, qd);
     }
     if constexpr (sizeof(T) == 8) {
-      const double sl = sd / (double)L;
+      // a cube inside the tile has L = n_h: its 1/n_h is the tile's
+      const double sl = (off_r[c] >= 0 && off_r[c + 1] <= len) ? sd * invn[c] : sd / (double)L;
       finish(c, L, v0 + sl, fmax(fma(-sd, sl, qd), 0.0));
     } else {
       const float sl = __fdividef(sd, (float)L);

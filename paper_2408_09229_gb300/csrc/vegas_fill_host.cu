@@ -85,12 +85,14 @@ void magic_div(uint32_t s, uint32_t& m, uint32_t& shift) {
 // type.  When the histogram does not fit, a per-CTA global histogram takes
 // FP64 atomic adds.  The map table goes to shared memory when it also fits;
 // otherwise the kernel reads it from global memory.
-int smem_layout(FillArgs& a, size_t tsz, int nprm, bool fp32, bool table_ok = true) {
+int smem_layout(FillArgs& a, size_t tsz, int nprm, bool fp32, bool table_ok = true, bool prefetch = true) {
   const int dG = a.d * a.G;
+  // the buffer of the next tile's global offsets, filled by cp.async during a tile (single-integral fill)
+  const size_t raw = prefetch ? align_up(sizeof(int64_t) * (kMaxCubesPerTile + 1)) : 0;
   const size_t base = align_up(nprm * tsz) + align_up(sizeof(int) * (kMaxCubesPerTile + 1)) +
-                      align_up(sizeof(int64_t) * (kMaxCubesPerTile + 1)) +
+                      raw +
                       align_up(tsz * kMaxCubesPerTile) + align_up(tsz * kTile) +
-                      align_up(sizeof(int) * kMaxCubesPerTile) + align_up(sizeof(int) * kFillThreads) +
+                      align_up(sizeof(int) * kMaxLongPerTile) + align_up(sizeof(int) * kFillThreads) +
                       align_up(64 + 8 * 32);
   const size_t budget = 160 * 1024;
   const size_t table = align_up((size_t)dG * 4 * tsz);
@@ -148,10 +150,10 @@ int smem_layout(FillArgs& a, size_t tsz, int nprm, bool fp32, bool table_ok = tr
   }
   a.sm_params = (int)off; off += align_up(nprm * tsz);
   a.sm_off = (int)off;    off += align_up(sizeof(int) * (kMaxCubesPerTile + 1));
-  a.sm_raw = (int)off;    off += align_up(sizeof(int64_t) * (kMaxCubesPerTile + 1));
+  a.sm_raw = (int)off;    off += raw;
   a.sm_invn = (int)off;   off += align_up(tsz * kMaxCubesPerTile);
   a.sm_vals = (int)off;   off += align_up(tsz * kTile);
-  a.sm_long = (int)off;   off += align_up(sizeof(int) * kMaxCubesPerTile);
+  a.sm_long = (int)off;   off += align_up(sizeof(int) * kMaxLongPerTile);
   a.sm_start = (int)off;  off += align_up(sizeof(int) * kFillThreads);
   a.sm_misc = (int)off;   off += align_up(64 + 8 * 32);
   a.sm_total = (int)off;
@@ -163,7 +165,7 @@ int smem_layout(FillArgs& a, size_t tsz, int nprm, bool fp32, bool table_ok = tr
 // Per-axis constants (magic reciprocals, z scales, FP32 fraction bits), the
 // Philox round keys and the shared-memory layout of a.  a.d, a.G, a.key0 and
 // a.key1 must be set.
-int fill_args_axes(FillArgs& a, const int32_t* nstrat, int precision, int nprm) {
+int fill_args_axes(FillArgs& a, const int32_t* nstrat, int precision, int nprm, bool prefetch) {
   const int G = a.G;
   for (int k = 0; k < a.d; ++k) {
     a.nstrat[k] = (uint32_t)nstrat[k];
@@ -183,7 +185,7 @@ int fill_args_axes(FillArgs& a, const int32_t* nstrat, int precision, int nprm) 
     a.rk1[r] = a.key1 + (uint32_t)r * 0xBB67AE85u;
   }
   const size_t tsz = precision == VEGAS_FP64 ? sizeof(double) : sizeof(float);
-  return smem_layout(a, tsz, nprm, precision == VEGAS_FP32);
+  return smem_layout(a, tsz, nprm, precision == VEGAS_FP32, true, prefetch);
 }
 
 namespace {

@@ -21,6 +21,7 @@ constexpr int kHistGlobal = 1;    // per-CTA global histogram, FP64 atomic adds 
 constexpr int kHistTwoPhase = 2;  // FP32: fixed-point tile histogram with shared integer atomics
 constexpr int kMaxCubesPerTile = kTile / 2 + 3;          // n_h >= 2 bounds the cubes a tile meets
 constexpr int kLongSegment = 32;                         // longer cube segments go to a warp
+constexpr int kMaxLongPerTile = kTile / (kLongSegment + 1);  // segments longer than kLongSegment a tile holds
 constexpr int kMaxDerivedParams = 8192;
 constexpr int kAllocThreads = 256;
 constexpr int kAllocItems = 16;  // cubes per thread in the allocation scan
@@ -140,7 +141,9 @@ constexpr int kFloorPeriod = 4;
 int64_t flow_train_rows(int64_t m, float lambda);
 int flow_gather(const float* X, int d, int64_t stride, int64_t m, const float* w, float lambda, uint64_t seed,
                 uint32_t iter, double* wsum, float* xs, float* ws, cudaStream_t s);
-int fill_args_axes(FillArgs& a, const int32_t* nstrat, int precision, int nprm);
+// prefetch: reserve the buffer of the next tile's offsets (the single-integral fill; the batched fill does not
+// prefetch)
+int fill_args_axes(FillArgs& a, const int32_t* nstrat, int precision, int nprm, bool prefetch = true);
 int derived_param_count(int integrand, int d, const double* host_params_or_null, int64_t np);
 
 // status helpers

@@ -25,7 +25,7 @@ int fill_occupancy_f32_exact(int, int, int) { return 0; }
 int fill_occupancy_f32_stream(int, int, int) { return 0; }
 }  // namespace vg
 
-static int check(const FillArgs& a, int d, int G, size_t tsz, int nprm, const char* what) {
+static int check(const FillArgs& a, int d, int G, size_t tsz, int nprm, bool prefetch, const char* what) {
   const size_t dG = (size_t)d * G;
   const bool two = a.hist_mode == kHistTwoPhase;
   const int per_word = 32 >> a.bin_shift;
@@ -35,16 +35,16 @@ static int check(const FillArgs& a, int d, int G, size_t tsz, int nprm, const ch
     size_t size;
   } r[] = {
       {"table", a.sm_table, a.table_smem ? dG * 4 * tsz : 0},
-      {"hist", a.sm_hist, two ? dG * 4 : (a.hist_mode == kHistShared ? dG * tsz : 0)},
+      {"hist", a.sm_hist, two ? dG * 4 : (a.hist_mode == kHistShared ? (dG * tsz) << a.hist_rep_log2 : 0)},
       {"hacc", a.sm_hacc, two ? dG * (a.acc32 ? 4 : 8) : 0},
       {"bins", a.sm_bins, two ? (size_t)kTile * 4 * ((d + per_word - 1) / per_word) : 0},
       {"wv", a.sm_wv, two ? (size_t)kTile * 4 : 0},
       {"params", a.sm_params, (size_t)nprm * tsz},
       {"off", a.sm_off, sizeof(int) * (kMaxCubesPerTile + 1)},
-      {"raw", a.sm_raw, sizeof(int64_t) * (kMaxCubesPerTile + 1)},
+      {"raw", a.sm_raw, prefetch ? sizeof(int64_t) * (kMaxCubesPerTile + 1) : 0},
       {"invn", a.sm_invn, tsz * kMaxCubesPerTile},
       {"vals", a.sm_vals, tsz * kTile},
-      {"long", a.sm_long, sizeof(int) * kMaxCubesPerTile},
+      {"long", a.sm_long, sizeof(int) * kMaxLongPerTile},
       {"start", a.sm_start, sizeof(int) * kFillThreads},
       {"misc", a.sm_misc, 64 + 8 * 32},
   };
@@ -73,19 +73,20 @@ int main() {
   for (int d : dims)
     for (int G : bins)
       for (int prec = 0; prec < 2; ++prec)
-        for (int nprm : nprms) {
+        for (int nprm : nprms)
+          for (int prefetch = 0; prefetch < 2; ++prefetch) {
           FillArgs a{};
           a.d = d;
           a.G = G;
           std::vector<int32_t> ns(d, 2);
-          if (fill_args_axes(a, ns.data(), prec == 0 ? VEGAS_FP64 : VEGAS_FP32, nprm) != VEGAS_OK) continue;
+          if (fill_args_axes(a, ns.data(), prec == 0 ? VEGAS_FP64 : VEGAS_FP32, nprm, prefetch) != VEGAS_OK) continue;
           const size_t tsz = prec == 0 ? sizeof(double) : sizeof(float);
-          if (check(a, d, G, tsz, nprm, "layout")) return 1;
+          if (check(a, d, G, tsz, nprm, prefetch, "layout")) return 1;
           ++cases;
           if (prec == 1 && a.table_smem) {  // the streamed path's alternative without the map table
             FillArgs b = a;
             smem_layout(b, sizeof(float), nprm, true, false);
-            if (b.table_smem || check(b, d, G, tsz, nprm, "no-table layout")) return 1;
+            if (b.table_smem || check(b, d, G, tsz, nprm, true, "no-table layout")) return 1;
             ++cases;
           }
         }
