@@ -1313,7 +1313,11 @@ __global__ void __launch_bounds__(kFillThreads, (sizeof(T) == 4 && (DMAX <= 8 ||
   double* hist_g = a.hist_part + (size_t)blockIdx.x * dG;
   fill_prologue<T>(a, S, d, table_in_smem);
   prep_params<ID, T, DMAX>(a.params_raw, a.np_raw, d, S.prm);
-  if (blockIdx.x < a.ntiles) {  // the first tile's cube offsets; later tiles' come during the tile before
+  // the FP32 form with d <= 8 does without the prefetch buffer, which buys a fourth resident CTA (d = 8 ridge:
+  // 2.09 ms at 3 CTAs with the buffer, 1.99 ms at 4 without); the host leaves the buffer out of exactly these
+  // layouts
+  constexpr bool kPrefetch = !(sizeof(T) == 4 && DMAX <= 8 && !STREAM);
+  if (kPrefetch && blockIdx.x < a.ntiles) {  // the first tile's cube offsets; later tiles' come during the tile before
     const int t = blockIdx.x, fh0 = a.tile_first[t];
     const int nc = min(kMaxCubesPerTile, (t + 1 < a.ntiles ? a.tile_first[t + 1] : a.NH - 1) - fh0 + 1);
     for (int c = tid; c <= nc; c += kFillThreads) cp_async8(S.raw_off + c, a.offsets + (int64_t)fh0 + c);
@@ -1333,7 +1337,7 @@ __global__ void __launch_bounds__(kFillThreads, (sizeof(T) == 4 && (DMAX <= 8 ||
     st.J0 = ldexpf(1.0f, -st.vexp);
   }
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x)
-    fill_tile<ID, T, DMAX, EXACT, STREAM, true>(a, a.rk0, a.rk1, S, st, tile, ps0, ps1, pK, hist_g,
+    fill_tile<ID, T, DMAX, EXACT, STREAM, kPrefetch>(a, a.rk0, a.rk1, S, st, tile, ps0, ps1, pK, hist_g,
                                                  tile + gridDim.x);
   if constexpr (ID == kIntegrandPoints) return;
 

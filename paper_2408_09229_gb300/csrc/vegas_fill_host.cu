@@ -416,7 +416,9 @@ int fill_impl(const vegas_geometry* g, int precision, int integrand, const doubl
     a.train_stride = extra->train_stride > 0 ? extra->train_stride : 1;
     a.train_power = extra->train_power;
   }
-  if (fill_args_axes(a, g->nstrat, precision, nprm) != VEGAS_OK) return VEGAS_EINVAL;
+  // the prefetch buffer: every kernel but the FP32 ones with DMAX <= 8 (the kernel's own rule)
+  if (fill_args_axes(a, g->nstrat, precision, nprm, !(precision == VEGAS_FP32 && dmax <= 8)) != VEGAS_OK)
+    return VEGAS_EINVAL;
 
   const bool exact = d == dmax && (dmax == 4 || dmax == 8) && a.table_smem && !internal && G <= 256;
   // the streamed point path: FP32, 16 or 32 axes, two-phase histogram, at most 256 strata an axis
