@@ -44,12 +44,12 @@ WORKLOAD = ("plain VEGAS+ d=8, ridge of 5 Gaussians (s=0.05) on the diagonal, Ng
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one launch of the dominant kernel on this workload, from one ncu capture of
 # that kernel (dram__bytes_read.sum + dram__bytes_write.sum): the per-cube offsets and weights
-FILL_TRAFFIC_BYTES = (346.28 + 146.85) * 1e6
+FILL_TRAFFIC_BYTES = (345.30 + 144.12) * 1e6
 # the same for the FP64 form's fill kernel (profiles/fill_kernel_ridge8_fp64.md)
-FILL64_TRAFFIC_BYTES = (353.19 + 148.66) * 1e6
-# the same capture: issue slots busy and warp instructions x 32 per evaluation (1.843e9 x 32 / 1e8)
-FILL_ISSUE_ACTIVE = 0.681
-FILL_INSTR_PER_EVAL = 590
+FILL64_TRAFFIC_BYTES = (350.05 + 145.22) * 1e6
+# the same capture: issue slots busy and warp instructions x 32 per evaluation (1.689e9 x 32 / 1e8)
+FILL_ISSUE_ACTIVE = 0.688
+FILL_INSTR_PER_EVAL = 540
 
 
 def measured_hbm_gbs():
