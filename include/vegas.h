@@ -240,11 +240,20 @@ VEGAS_API const char *vegas_strerror(int status);
 /* Level 2: step entry points (one row of Algorithm 1 each)                  */
 /* ======================================================================== */
 
-/* Geometry shared by the step entry points.  Host struct, host pointer. */
+/* Geometry shared by the step entry points.  Host struct, host pointer.
+ * tile_log2 (vegas_fill only): 0 lets the library cut the evaluations into
+ * tiles of 2048, or of 1024 where the larger tile would cost a resident CTA;
+ * 10 or 11 fixes tiles of 2^tile_log2 evaluations (other values: EINVAL).  The
+ * FP32 form folds its fixed-point map weights to FP32 once per tile, so its
+ * map weights depend on the tiles at the level of FP32 rounding; fixing the
+ * tile reproduces them bit for bit, for instance those of a batched run
+ * (VEGAS_BATCH_INFO reports its tile). */
 typedef struct {
   int32_t dim;           /* d                                    */
   int32_t nbins;         /* N_g                                  */
   const int32_t *nstrat; /* host array of d strata s_k           */
+  int32_t tile_log2;     /* 0, 10 or 11 (see above)              */
+  int32_t pad;
 } vegas_geometry;
 
 /* -- updateEvalsPerCube + mapEvalsToCubes (Algorithm 1; Sec. 2.1.2, Eq. (7)) --
@@ -448,7 +457,8 @@ VEGAS_API int vegas_batch_integrate(vegas_batch b, int32_t nitn, double rtol, ve
  *   VEGAS_BATCH_BINS     double [d][N_g]    map weights of the last fill
  *   VEGAS_BATCH_ITER_EST double [nitn_run]  I_t of every recorded iteration
  *   VEGAS_BATCH_ITER_SIG double [nitn_run]  sigma_t
- *   VEGAS_BATCH_INFO     int64  [4]         d, strata per axis, N_h, nitn_run
+ *   VEGAS_BATCH_INFO     int64  [4 or 5]    d, strata per axis, N_h, nitn_run, and with count >= 5
+ *                                           log2 of the fill's tile (evaluations)
  * Errors: EINVAL (unknown what, problem out of range), ENOSPACE (count too
  * small), ECUDA. */
 enum vegas_batch_field {

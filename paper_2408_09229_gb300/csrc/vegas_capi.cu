@@ -582,7 +582,7 @@ extern "C" int vegas_integrate(vegas_handle h, int integrand, const double* para
   DeviceGuard guard(h->device);
   vg::clear_stale_error();
   cudaStream_t s = h->stream();
-  const vegas_geometry geo{d, G, ns.data()};
+  const vegas_geometry geo{d, G, ns.data(), 0, 0};
   int rc;
   if ((rc = ensure_cubes(h, h->arm[0], NH)) != VEGAS_OK) return rc;
   const size_t fill_need = vegas_fill_scratch_bytes(&geo, neval);

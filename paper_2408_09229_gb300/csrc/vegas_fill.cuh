@@ -2,11 +2,11 @@
 // template over integrand, precision and maximum dimension.
 //
 // Work decomposition (Sec. 3.1: every thread does the same number of
-// evaluations).  Evaluations j in [0, neval) are cut into tiles of kTile
-// consecutive indices; a persistent grid walks the tiles round-robin.  A tile
-// meets at most kMaxCubesPerTile hypercubes because n_h >= 2.  It stages their
-// offsets, relative to the tile start, in shared memory.  Each thread takes
-// kSamplesPerThread consecutive evaluations.  Every cube writes its index
+// evaluations).  Evaluations j in [0, neval) are cut into tiles of 2^tile_log2
+// (1024 or 2048) consecutive indices; a persistent grid walks the tiles
+// round-robin.  A tile of n evaluations meets at most n / 2 + 3 hypercubes
+// because n_h >= 2.  It stages their offsets, relative to the tile start, in
+// shared memory.  Each thread takes n / 256 consecutive evaluations.  Every cube writes its index
 // into a start-cube table for the threads whose first evaluation it holds; a
 // thread starts there and steps forward.  No evaluation-to-cube array is ever
 // built.
@@ -524,13 +524,12 @@ constexpr int kStreamMaxPeaks = 8;
 
 // Slot of tile evaluation jl in the per-evaluation arrays written by one
 // thread and read back by the same thread (map weights, packed intervals).
-// Thread t owns evaluations 4t..4t+3, so storing them at jl would put the
-// lanes of a warp 4 (or 4 * words) apart and make them collide on a few
-// shared-memory banks; slot (jl mod 4) * 256 + jl / 4 puts them on
-// consecutive words.  The packed intervals add word w * kTile.
-__device__ __forceinline__ int tix(int jl) {
-  static_assert(kSamplesPerThread == 8 && kFillThreads == 256, "slot layout");
-  return ((jl & 7) << 8) | (jl >> 3);
+// Thread t owns evaluations S t .. S t + S - 1 (S = 2^spt_log2 a thread), so
+// storing them at jl would put the lanes of a warp S (or S * words) apart and
+// make them collide on a few shared-memory banks; slot (jl mod S) * 256 + jl / S
+// puts them on consecutive words.  The packed intervals add word w * tile.
+__device__ __forceinline__ int tix(int jl, int spt_log2) {
+  return ((jl & ((1 << spt_log2) - 1)) << 8) | (jl >> spt_log2);
 }
 
 __host__ __device__ inline bool stream_family(int integrand, int K) {
@@ -571,7 +570,7 @@ __device__ __forceinline__ void decode_packed(const FillArgs& a, uint32_t h, uin
 
 // Point j of the cube with digits cw, its Jacobian J (from J0) and f there.
 // binw_col receives the packed intervals (4 or 2 axes a word, word w at
-// binw_col[w * kTile]); xout, if not NULL,
+// binw_col[w * tile], tile = 2^a.tile_log2); xout, if not NULL,
 // the coordinates.
 template <int ID, int DMAX>
 __device__ __forceinline__ float stream_point_eval(const FillArgs& a, const uint32_t* __restrict__ rk0,
@@ -660,10 +659,10 @@ __device__ __forceinline__ float stream_point_eval(const FillArgs& a, const uint
     }
     if (binw_col) {
       if (a.bin_shift == 3) {
-        binw_col[g * kTile] = word;
+        binw_col[(g << a.tile_log2)] = word;
       } else {
-        binw_col[2 * g * kTile] = w16a;
-        if (4 * g + 2 < d) binw_col[(2 * g + 1) * kTile] = w16b;
+        binw_col[(2 * g) << a.tile_log2] = w16a;
+        if (4 * g + 2 < d) binw_col[(2 * g + 1) << a.tile_log2] = w16b;
       }
     }
     if constexpr (ID == VEGAS_PRODUCT_PEAK) prod = prod / den;  // one division per four axes
@@ -807,11 +806,12 @@ __device__ __forceinline__ void fill_prologue(const FillArgs& a, const FillShare
     }
 }
 
-// One tile of kTile evaluations of integral a (tile index local to a).  rk0 /
+// One tile of 2^a.tile_log2 evaluations of integral a (tile index local to a).  rk0 /
 // rk1: the Philox round keys (kernel parameters, so that they are
 // constant-bank operands).  STREAM: the streamed point path (FP32, DMAX >= 16,
 // two-phase histogram, s_k <= 256).
-template <int ID, typename T, int DMAX, bool EXACT, bool STREAM = false, bool PREFETCH = false>
+// TLC: the tile's log2 at compile time (the exact-d kernels are built for both sizes), 0 to read a.tile_log2.
+template <int ID, typename T, int DMAX, bool EXACT, bool STREAM = false, bool PREFETCH = false, int TLC = 0>
 __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __restrict__ rk0,
                                           const uint32_t* __restrict__ rk1, const FillShared<T>& S,
                                           FillState<T>& st, int tile, T ps0, T ps1, int pK, double* hist_g,
@@ -841,8 +841,10 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
   float& lmax = st.lmax;
   bool& bad = st.bad;
   float& inv_scale = st.inv_scale;
-  const int64_t j0 = (int64_t)tile * kTile;
-  const int len = (int)min((int64_t)kTile, a.neval - j0);
+  const int TL = TLC ? TLC : a.tile_log2, tileN = 1 << TL, spt_log2 = TL - 8, spt = 1 << spt_log2;
+  const int maxc = tile_max_cubes(tileN);
+  const int64_t j0 = (int64_t)tile << TL;
+  const int len = (int)min((int64_t)tileN, a.neval - j0);
   constexpr int kRelCap = 1 << 30;
   // first cube of the tile and the number of cubes it can meet (up to the
   // next tile's first cube); with PREFETCH the previous tile left them, and
@@ -858,7 +860,7 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
     }
   } else {
     h0 = a.tile_first[tile];
-    ncand = min(kMaxCubesPerTile, (tile + 1 < a.ntiles ? a.tile_first[tile + 1] : a.NH - 1) - h0 + 1);
+    ncand = min(maxc, (tile + 1 < a.ntiles ? a.tile_first[tile + 1] : a.NH - 1) - h0 + 1);
   }
 
   // ---- fold the previous tile's fixed-point histogram ----
@@ -891,7 +893,7 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
           const int64_t n = (o0 > -kRelCap && o1 < kRelCap) ? (int64_t)(o1 - o0) : g1 - g0;
           if constexpr (sizeof(T) == 8) inv = 1.0 / (double)n;
           else inv = __fdividef(1.0f, (float)n);
-          for (int t = (r0 + kSamplesPerThread - 1) / kSamplesPerThread; t * kSamplesPerThread < r1; ++t)
+          for (int t = (r0 + spt - 1) >> spt_log2; (t << spt_log2) < r1; ++t)
             startc[VG_IDX(t, kFillThreads, a.flags, 20)] = c;
           if (r1 == len) misc[1] = c + 1;  // cubes met by the tile
         }
@@ -907,7 +909,7 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
     // the offsets of the next tile go to the same buffer, read by now, while
     // this tile computes; they are complete before the barrier after phase A
     if (next_tile < a.ntiles) {
-      const int nc = min(kMaxCubesPerTile, nend - nh0 + 1);
+      const int nc = min(maxc, nend - nh0 + 1);
       for (int c = tid; c <= nc; c += kFillThreads) cp_async8(S.raw_off + c, a.offsets + (int64_t)nh0 + c);
       cp_async_commit();
       if (tid == 0) {
@@ -938,7 +940,7 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
                             : a.offsets[(int64_t)h0 + c + 1] - a.offsets[(int64_t)h0 + c];
       if constexpr (sizeof(T) == 8) inv = 1.0 / (double)n;
       else inv = __fdividef(1.0f, (float)n);
-      for (int t = (r0 + kSamplesPerThread - 1) / kSamplesPerThread; t * kSamplesPerThread < r1; ++t)
+      for (int t = (r0 + spt - 1) >> spt_log2; (t << spt_log2) < r1; ++t)
         startc[VG_IDX(t, kFillThreads, a.flags, 21)] = c;
       if (r1 == len) misc[1] = c + 1;  // cubes met by the tile
     }
@@ -948,7 +950,7 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
   }
 
   // ---- phase A: point, map, integrand, J f; map weights ----
-  const int jl0 = tid * kSamplesPerThread;
+  const int jl0 = tid << spt_log2;
   float my_max = 0.0f;
   if constexpr (STREAM) {
     static_assert(sizeof(T) == 4 && DMAX >= 16, "the streamed path is FP32 and wide");
@@ -957,10 +959,10 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
       int c_decoded = -1;
       uint32_t cw[DMAX / 4];
 #pragma unroll 1
-      for (int s = 0; s < kSamplesPerThread; ++s) {
+      for (int s = 0; s < spt; ++s) {
         const int jl = jl0 + s;
         if (jl < len) {
-          while (off_r[VG_IDX(c + 1, kMaxCubesPerTile + 1, a.flags, 3)] <= jl) ++c;
+          while (off_r[VG_IDX(c + 1, maxc + 1, a.flags, 3)] <= jl) ++c;
           if (c != c_decoded) {
             decode_packed<DMAX>(a, (uint32_t)(h0 + c), cw);
             c_decoded = c;
@@ -968,19 +970,19 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
           float J = st.J0;
           float* xo = (ID == kIntegrandPoints) ? a.points_out + (j0 + jl) * d : nullptr;
           float f = stream_point_eval<ID, DMAX>(a, rk0, rk1, cw, j0 + jl, tab, prm, ps0, ps1, pK, J,
-                                                binw + tix(jl), xo);
+                                                binw + tix(jl, spt_log2), xo);
           if constexpr (ID == kIntegrandPoints) continue;
           if constexpr (ID == kIntegrandTabulated) f = a.values[j0 + jl];
           if (!isfinite(f)) bad = true;
           const float v = J * f;
-          vals[VG_IDX(jl, kTile, a.flags, 4)] = v;
+          vals[VG_IDX(jl, tileN, a.flags, 4)] = v;
           if constexpr (ID == kIntegrandTabulated) {
             const int64_t j = j0 + jl;
             if (a.train_w && j % a.train_stride == 0)
               a.train_w[j / a.train_stride] = powf(fabsf(v) * (float)invn[c], a.train_power);
           }
-          const float wv = v * v * (float)invn[VG_IDX(c, kMaxCubesPerTile, a.flags, 5)];
-          wv_s[tix(jl)] = wv;
+          const float wv = v * v * (float)invn[VG_IDX(c, maxc, a.flags, 5)];
+          wv_s[tix(jl, spt_log2)] = wv;
           my_max = fmaxf(my_max, wv);
         }
       }
@@ -990,10 +992,10 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
     uint32_t cb[DMAX];
     decode_cube<T, DMAX, EXACT>(a, (uint32_t)(h0 + c), cb);
 #pragma unroll 1
-    for (int s = 0; s < kSamplesPerThread; ++s) {
+    for (int s = 0; s < spt; ++s) {
       const int jl = jl0 + s;
       if (jl < len) {
-        while (off_r[VG_IDX(c + 1, kMaxCubesPerTile + 1, a.flags, 6)] <= jl) {
+        while (off_r[VG_IDX(c + 1, maxc + 1, a.flags, 6)] <= jl) {
           ++c;
           next_cube<T, DMAX, EXACT>(a, cb);
         }
@@ -1021,16 +1023,16 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
         else f = integrand<ID, T, DMAX>(x, d, prm, a.np_derived, ps0, ps1, pK);
         if (!isfinite(f)) bad = true;
         const T v = J * f;
-        vals[VG_IDX(jl, kTile, a.flags, 7)] = v;
+        vals[VG_IDX(jl, tileN, a.flags, 7)] = v;
         if constexpr (ID == kIntegrandTabulated) {
           // training weights (|J f| / n_h)^p of every train_stride-th evaluation
           const int64_t j = j0 + jl;
           if (a.train_w && j % a.train_stride == 0)
             a.train_w[j / a.train_stride] = powf(fabsf((float)v) * (float)invn[c], a.train_power);
         }
-        const T wv = v * v * invn[VG_IDX(c, kMaxCubesPerTile, a.flags, 8)];
+        const T wv = v * v * invn[VG_IDX(c, maxc, a.flags, 8)];
         if (two_phase) {
-          wv_s[tix(jl)] = (float)wv;
+          wv_s[tix(jl, spt_log2)] = (float)wv;
           my_max = fmaxf(my_max, (float)wv);
           if (bpw == 4) {
 #pragma unroll
@@ -1042,7 +1044,7 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
                 const uint32_t b2 = 4 * w + 2 < DMAX ? (uint32_t)bin[4 * w + 2] : 0u;
                 const uint32_t b3 = 4 * w + 3 < DMAX ? (uint32_t)bin[4 * w + 3] : 0u;
                 const uint32_t word = __byte_perm(__byte_perm(b0, b1, 0x0040u), __byte_perm(b2, b3, 0x0040u), 0x5410u);
-                binw[w * kTile + tix(jl)] = word;
+                binw[(w << TL) + tix(jl, spt_log2)] = word;
               }
             }
           } else {
@@ -1051,7 +1053,7 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
               if (2 * w < d) {
                 uint32_t word = (uint32_t)bin[2 * w];
                 if (2 * w + 1 < DMAX) word |= (uint32_t)bin[2 * w + 1] << 16;
-                binw[w * kTile + tix(jl)] = word;
+                binw[(w << TL) + tix(jl, spt_log2)] = word;
               }
             }
           }
@@ -1084,24 +1086,24 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
 #pragma unroll
     for (int w = 0; w < kFillThreads / 32; ++w) tmax = fmaxf(tmax, wmax[w]);
     if (tmax > 0.0f && isfinite(tmax)) {
-      // tmax < 2^et and a bin gets at most kTile <= 2^kTileLog2 weights of
-      // the tile, so with scale = 2^(31 - kTileLog2 - et) every bin total
-      // stays below 2^31 (plus the rounding of kTile values)
+      // tmax < 2^et and a bin gets at most 2^TL weights of the tile, so with
+      // scale = 2^(31 - TL - et) every bin total stays below 2^31 (plus the
+      // rounding of 2^TL values)
       int et;
       frexpf(tmax, &et);
-      const int se = min(31 - kTileLog2 - et, 126);
+      const int se = min(31 - TL - et, 126);
       const float scale = ldexpf(1.0f, se);
       inv_scale = ldexpf(1.0f, -se);
       if (jl0 < len) {
 #pragma unroll 1
-        for (int s = 0; s < kSamplesPerThread; ++s) {
+        for (int s = 0; s < spt; ++s) {
           const int jl = jl0 + s;
           if (jl < len) {
-            const uint32_t q = (uint32_t)__float2uint_rn(wv_s[tix(jl)] * scale);
+            const uint32_t q = (uint32_t)__float2uint_rn(wv_s[tix(jl, spt_log2)] * scale);
             if (q) {
               if (bpw == 4) {
                 for (int w = 0; w < nw; ++w) {
-                  const uint32_t word = binw[w * kTile + tix(jl)];
+                  const uint32_t word = binw[(w << TL) + tix(jl, spt_log2)];
                   const int kk = 4 * w;
 #pragma unroll
                   for (int b = 0; b < 4; ++b)
@@ -1110,7 +1112,7 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
                 }
               } else {
                 for (int w = 0; w < nw; ++w) {
-                  const uint32_t word = binw[w * kTile + tix(jl)];
+                  const uint32_t word = binw[(w << TL) + tix(jl, spt_log2)];
                   const int kk = 2 * w;
                   atomicAdd(hist_u + VG_IDX(kk * G + (word & 0xFFFFu), dG, a.flags, 12), q);
                   if (kk + 1 < d) atomicAdd(hist_u + VG_IDX((kk + 1) * G + (word >> 16), dG, a.flags, 13), q);
@@ -1165,17 +1167,17 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
     const int r0 = max(off_r[c], 0), r1 = min(off_r[c + 1], len);
     const int L = r1 - r0;
     if (L > kLongSegment) {
-      longlist[VG_IDX(atomicAdd(&misc[0], 1), kMaxLongPerTile, a.flags, 22)] = c;
+      longlist[VG_IDX(atomicAdd(&misc[0], 1), tile_max_long(tileN), a.flags, 22)] = c;
       had_long = true;
       continue;
     }
     // one pass over the segment, shifted by its first value: mean = v0 + s/L,
     // M2 = q - s^2/L with s, q the sums of (v - v0) and (v - v0)^2; the shift
     // keeps q within (L + 1) M2, so the cancellation costs a few ulps
-    const T v0 = vals[VG_IDX(r0, kTile, a.flags, 18)];
+    const T v0 = vals[VG_IDX(r0, tileN, a.flags, 18)];
     T sd = T(0), qd = T(0);
     for (int r = r0 + 1; r < r1; ++r) {
-      const T dv = vals[VG_IDX(r, kTile, a.flags, 19)] - v0;
+      const T dv = vals[VG_IDX(r, tileN, a.flags, 19)] - v0;
       sd += dv;
       qd = fma(dv, dv, qd);
     }
@@ -1302,7 +1304,7 @@ __device__ __forceinline__ Carry carry_suffix(Carry rec, bool joins) {
 // bounds checks vanish and the table reads are shared-memory loads.  The FP32
 // form with d <= 8 asks for 4 resident CTAs (at most 64 registers): measured
 // 7 % faster than 3 CTAs with more registers.  Wider or FP64 forms would spill.
-template <int ID, typename T, int DMAX, bool EXACT, bool STREAM = false>
+template <int ID, typename T, int DMAX, bool EXACT, bool STREAM = false, int TLC = 0>
 __global__ void __launch_bounds__(kFillThreads, (sizeof(T) == 4 && (DMAX <= 8 || STREAM)) ? 4 : (sizeof(T) == 8 && EXACT) ? 2 : 1)
     fill_kernel(const __grid_constant__ FillArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1319,7 +1321,7 @@ __global__ void __launch_bounds__(kFillThreads, (sizeof(T) == 4 && (DMAX <= 8 ||
   constexpr bool kPrefetch = !(sizeof(T) == 4 && DMAX <= 8 && !STREAM);
   if (kPrefetch && blockIdx.x < a.ntiles) {  // the first tile's cube offsets; later tiles' come during the tile before
     const int t = blockIdx.x, fh0 = a.tile_first[t];
-    const int nc = min(kMaxCubesPerTile, (t + 1 < a.ntiles ? a.tile_first[t + 1] : a.NH - 1) - fh0 + 1);
+    const int nc = min(tile_max_cubes(1 << (TLC ? TLC : a.tile_log2)), (t + 1 < a.ntiles ? a.tile_first[t + 1] : a.NH - 1) - fh0 + 1);
     for (int c = tid; c <= nc; c += kFillThreads) cp_async8(S.raw_off + c, a.offsets + (int64_t)fh0 + c);
     cp_async_commit();
     if (tid == 0) {
@@ -1337,7 +1339,7 @@ __global__ void __launch_bounds__(kFillThreads, (sizeof(T) == 4 && (DMAX <= 8 ||
     st.J0 = ldexpf(1.0f, -st.vexp);
   }
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x)
-    fill_tile<ID, T, DMAX, EXACT, STREAM, kPrefetch>(a, a.rk0, a.rk1, S, st, tile, ps0, ps1, pK, hist_g,
+    fill_tile<ID, T, DMAX, EXACT, STREAM, kPrefetch, TLC>(a, a.rk0, a.rk1, S, st, tile, ps0, ps1, pK, hist_g,
                                                  tile + gridDim.x);
   if constexpr (ID == kIntegrandPoints) return;
 

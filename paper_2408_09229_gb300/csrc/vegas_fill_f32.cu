@@ -15,6 +15,8 @@ int launch_fill_f32(int integrand, int dmax, FillArgs& a, int grid, cudaStream_t
   return Unit::launch(integrand, dmax, a, grid, s);
 }
 
-int fill_occupancy_f32(int integrand, int dmax, int smem) { return Unit::occupancy(integrand, dmax, smem); }
+int fill_occupancy_f32(int integrand, int dmax, int tile_log2, int smem) {
+  return Unit::occupancy(integrand, dmax, tile_log2, smem);
+}
 
 }  // namespace vg

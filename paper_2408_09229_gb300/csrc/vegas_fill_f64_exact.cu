@@ -1,16 +1,18 @@
 // vegas_fill_f64_exact.cu -- FP64 instantiations of the fill kernel for d = DMAX
-// (4 or 8) with the map table in shared memory, and their launcher.
+// (4 or 8) with the map table in shared memory, for both tile sizes, and their launcher.
 #include "vegas_fill_dispatch.cuh"
 
 namespace vg {
 namespace {
-using Unit = FillUnit<double, true, false, AllFamilies, IntList<4, 8>>;
+using Unit = FillUnit<double, true, false, AllFamilies, IntList<4, 8>, true>;
 }  // namespace
 
 int launch_fill_f64_exact(int integrand, int dmax, FillArgs& a, int grid, cudaStream_t s) {
   return Unit::launch(integrand, dmax, a, grid, s);
 }
 
-int fill_occupancy_f64_exact(int integrand, int dmax, int smem) { return Unit::occupancy(integrand, dmax, smem); }
+int fill_occupancy_f64_exact(int integrand, int dmax, int tile_log2, int smem) {
+  return Unit::occupancy(integrand, dmax, tile_log2, smem);
+}
 
 }  // namespace vg

@@ -55,7 +55,8 @@ int num_sms() {
 
 ScratchLayout scratch_layout(int d, int G, int64_t neval, int sms) {
   ScratchLayout L{};
-  L.ntiles = (int)((neval + kTile - 1) / kTile);
+  // sized for the smallest tile (the most tiles), whichever tile a launch takes
+  L.ntiles = (int)((neval + (1 << kTileLog2Min) - 1) >> kTileLog2Min);
   L.grid_max = std::max(1, std::min(L.ntiles, 8 * std::max(sms, 1)));
   L.nfix = (L.ntiles + 255) / 256;
   size_t off = 0;
@@ -87,28 +88,29 @@ void magic_div(uint32_t s, uint32_t& m, uint32_t& shift) {
 // otherwise the kernel reads it from global memory.
 int smem_layout(FillArgs& a, size_t tsz, int nprm, bool fp32, bool table_ok = true, bool prefetch = true) {
   const int dG = a.d * a.G;
+  const int tile = 1 << a.tile_log2, maxc = tile_max_cubes(tile);
   // the buffer of the next tile's global offsets, filled by cp.async during a tile (single-integral fill)
-  const size_t raw = prefetch ? align_up(sizeof(int64_t) * (kMaxCubesPerTile + 1)) : 0;
-  const size_t base = align_up(nprm * tsz) + align_up(sizeof(int) * (kMaxCubesPerTile + 1)) +
+  const size_t raw = prefetch ? align_up(sizeof(int64_t) * (maxc + 1)) : 0;
+  const size_t base = align_up(nprm * tsz) + align_up(sizeof(int) * (maxc + 1)) +
                       raw +
-                      align_up(tsz * kMaxCubesPerTile) + align_up(tsz * kTile) +
-                      align_up(sizeof(int) * kMaxLongPerTile) + align_up(sizeof(int) * kFillThreads) +
+                      align_up(tsz * maxc) + align_up(tsz * tile) +
+                      align_up(sizeof(int) * tile_max_long(tile)) + align_up(sizeof(int) * kFillThreads) +
                       align_up(64 + 8 * 32);
   const size_t budget = 160 * 1024;
   const size_t table = align_up((size_t)dG * 4 * tsz);
   // two-phase: interval indices packed 8 bits (N_g <= 256) or 16 bits wide
   a.bin_shift = a.G <= 256 ? 3 : 4;
   const int per_word = 32 >> a.bin_shift;
-  const size_t bin_words = (size_t)kTile * 4 * ((a.d + per_word - 1) / per_word);
+  const size_t bin_words = (size_t)tile * 4 * ((a.d + per_word - 1) / per_word);
   const size_t two_phase_ff = align_up((size_t)dG * 4) + align_up((size_t)dG * 8) + align_up(bin_words) +
-                              align_up(sizeof(float) * kTile);
+                              align_up(sizeof(float) * tile);
   const size_t two_phase_32 = align_up((size_t)dG * 4) + align_up((size_t)dG * 4) + align_up(bin_words) +
-                              align_up(sizeof(float) * kTile);
+                              align_up(sizeof(float) * tile);
   const size_t shared_hist = align_up((size_t)dG * tsz);
   size_t hist;
   a.acc32 = 0;
   // the two-phase form folds all d N_g intervals of the CTA histogram once per
-  // tile (kTile evaluations): measured faster than shared FP32 atomics for
+  // tile: measured faster than shared FP32 atomics for
   // N_g <= 256 and for d N_g <= 2048, slower beyond (d = 8, N_g = 1024: 2.3x)
   const bool two_phase_ok = fp32 && (a.G <= 256 || dG <= 2048);
   if (two_phase_ok && base + two_phase_ff <= budget) {
@@ -143,17 +145,17 @@ int smem_layout(FillArgs& a, size_t tsz, int nprm, bool fp32, bool table_ok = tr
     off += align_up((size_t)dG * 4);
     a.sm_hacc = (int)off; off += align_up((size_t)dG * (a.acc32 ? 4 : 8));
     a.sm_bins = (int)off; off += align_up(bin_words);
-    a.sm_wv = (int)off;   off += align_up(sizeof(float) * kTile);
+    a.sm_wv = (int)off;   off += align_up(sizeof(float) * tile);
   } else {
     off += a.hist_mode == kHistShared ? hist : 0;
     a.sm_hacc = a.sm_bins = a.sm_wv = (int)off;
   }
   a.sm_params = (int)off; off += align_up(nprm * tsz);
-  a.sm_off = (int)off;    off += align_up(sizeof(int) * (kMaxCubesPerTile + 1));
+  a.sm_off = (int)off;    off += align_up(sizeof(int) * (maxc + 1));
   a.sm_raw = (int)off;    off += raw;
-  a.sm_invn = (int)off;   off += align_up(tsz * kMaxCubesPerTile);
-  a.sm_vals = (int)off;   off += align_up(tsz * kTile);
-  a.sm_long = (int)off;   off += align_up(sizeof(int) * kMaxLongPerTile);
+  a.sm_invn = (int)off;   off += align_up(tsz * maxc);
+  a.sm_vals = (int)off;   off += align_up(tsz * tile);
+  a.sm_long = (int)off;   off += align_up(sizeof(int) * tile_max_long(tile));
   a.sm_start = (int)off;  off += align_up(sizeof(int) * kFillThreads);
   a.sm_misc = (int)off;   off += align_up(64 + 8 * 32);
   a.sm_total = (int)off;
@@ -190,9 +192,9 @@ int fill_args_axes(FillArgs& a, const int32_t* nstrat, int precision, int nprm, 
 
 namespace {
 
-// first cube of every tile: largest h with offsets[h] <= tile * kTile; thread
+// first cube of every tile: largest h with offsets[h] <= tile * 2^tile_log2; thread
 // 0 also resets the max-ell key and writes the FP32 value scale exponent
-__global__ void tile_first_kernel(const int64_t* __restrict__ offsets, int NH, int ntiles, int32_t* tile_first,
+__global__ void tile_first_kernel(const int64_t* __restrict__ offsets, int NH, int ntiles, int tile_log2, int32_t* tile_first,
                                   int* ellmax_key, int* vexp, int fp32, int integrand, int d,
                                   const double* __restrict__ params, int np) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -201,7 +203,7 @@ __global__ void tile_first_kernel(const int64_t* __restrict__ offsets, int NH, i
     *vexp = fp32 ? value_exponent(integrand, d, params, np) : 0;
   }
   if (t >= ntiles) return;
-  const int64_t j0 = (int64_t)t * kTile;
+  const int64_t j0 = (int64_t)t << tile_log2;
   int lo = 0, hi = NH - 1;
   while (lo < hi) {
     const int mid = (int)(((int64_t)lo + hi + 1) >> 1);
@@ -340,6 +342,63 @@ extern "C" size_t vegas_fill_scratch_bytes(const vegas_geometry* g, int64_t neva
 }
 
 namespace vg {
+// One plan per tile size: the shared-memory layout, the kernel it selects and its resident CTAs per SM.  A
+// launch takes the larger tile (fewer tile prologues and barriers) unless that loses the exact-d path or a
+// resident CTA, as the staging grows with the tile (d = 8: 2048 at 4 CTAs an SM; d = 12 to 30, streamed: 1024).
+namespace {
+int plan_one(const FillArgs& base, const int32_t* nstrat, int precision, int integrand, int64_t nparams, int nprm,
+             int tile_log2, FillPlan& p) {
+  const int d = base.d, G = base.G, dmax = dmax_for(d);
+  const bool internal = integrand == kIntegrandTabulated || integrand == kIntegrandPoints;
+  p.a = base;
+  p.a.tile_log2 = tile_log2;
+  p.a.ntiles = (int)((base.neval + (int64_t(1) << tile_log2) - 1) >> tile_log2);
+  // the prefetch buffer: every kernel but the FP32 ones with DMAX <= 8 (the kernel's own rule)
+  if (fill_args_axes(p.a, nstrat, precision, nprm, !(precision == VEGAS_FP32 && dmax <= 8)) != VEGAS_OK)
+    return VEGAS_EINVAL;
+  p.exact = d == dmax && (dmax == 4 || dmax == 8) && p.a.table_smem && !internal && G <= 256;
+  // the streamed point path: FP32, 16 or 32 axes, two-phase histogram, at most 256 strata an axis
+  p.streamed = precision == VEGAS_FP32 && dmax >= 16 && p.a.hist_mode == kHistTwoPhase &&
+               stream_family(integrand, integrand == VEGAS_GAUSS_SUM ? (int)((nparams - 3) / d) : 0);
+  for (int k = 0; k < d && p.streamed; ++k) p.streamed = nstrat[k] <= 256;
+  // the streamed path takes its map table from global memory (read through L1) when that frees enough
+  // shared memory for one more resident CTA: d = 30, 1e8 evaluations, 3 CTAs an SM instead of 2,
+  // 16.5 -> 14.6 ms (its lookups are random either way; the table stays in L1)
+  if (p.streamed && p.a.table_smem) {
+    FillArgs b = p.a;
+    smem_layout(b, sizeof(float), nprm, true, false);
+    if (b.hist_mode == p.a.hist_mode &&
+        fill_occupancy_f32_stream(integrand, dmax, tile_log2, b.sm_total) >
+            fill_occupancy_f32_stream(integrand, dmax, tile_log2, p.a.sm_total))
+      p.a = b;
+  }
+  const int sm = p.a.sm_total;
+  const int tl = tile_log2;
+  p.per_sm = precision == VEGAS_FP64
+                 ? (p.exact ? fill_occupancy_f64_exact(integrand, dmax, tl, sm) : fill_occupancy_f64(integrand, dmax, tl, sm))
+                 : (p.exact      ? fill_occupancy_f32_exact(integrand, dmax, tl, sm)
+                    : p.streamed ? fill_occupancy_f32_stream(integrand, dmax, tl, sm)
+                                 : fill_occupancy_f32(integrand, dmax, tl, sm));
+  return p.per_sm > 0 ? VEGAS_OK : VEGAS_ECUDA;
+}
+}  // namespace
+
+int fill_plan(const FillArgs& base, const int32_t* nstrat, int precision, int integrand, int64_t nparams, int nprm,
+              FillPlan& out, int tile_log2) {
+  if (tile_log2 != 0) {
+    if (tile_log2 < kTileLog2Min || tile_log2 > kTileLog2Max) return VEGAS_EINVAL;
+    return plan_one(base, nstrat, precision, integrand, nparams, nprm, tile_log2, out);
+  }
+  FillPlan big, small;
+  const int rbig = plan_one(base, nstrat, precision, integrand, nparams, nprm, kTileLog2Max, big);
+  const int rsmall = plan_one(base, nstrat, precision, integrand, nparams, nprm, kTileLog2Min, small);
+  if (rbig != VEGAS_OK && rsmall != VEGAS_OK) return rsmall;
+  const bool take_big = rbig == VEGAS_OK && (rsmall != VEGAS_OK || (big.exact && !small.exact) ||
+                                             (big.exact == small.exact && big.per_sm >= small.per_sm));
+  out = take_big ? big : small;
+  return VEGAS_OK;
+}
+
 int fill_impl(const vegas_geometry* g, int precision, int integrand, const double* d_params, int64_t nparams,
               int64_t neval, uint64_t seed, int32_t iteration, uint32_t problem_id, double beta,
               const double* d_edges, const int64_t* d_offsets, float* d_ell, double* d_bins, double* d_result,
@@ -385,7 +444,6 @@ int fill_impl(const vegas_geometry* g, int precision, int integrand, const doubl
   a.d = d;
   a.G = G;
   a.NH = (int)NH;
-  a.ntiles = L.ntiles;
   a.neval = neval;
   a.key0 = (uint32_t)seed;
   a.key1 = (uint32_t)(seed >> 32);
@@ -416,35 +474,17 @@ int fill_impl(const vegas_geometry* g, int precision, int integrand, const doubl
     a.train_stride = extra->train_stride > 0 ? extra->train_stride : 1;
     a.train_power = extra->train_power;
   }
-  // the prefetch buffer: every kernel but the FP32 ones with DMAX <= 8 (the kernel's own rule)
-  if (fill_args_axes(a, g->nstrat, precision, nprm, !(precision == VEGAS_FP32 && dmax <= 8)) != VEGAS_OK)
-    return VEGAS_EINVAL;
+  FillPlan P;
+  const int rp = fill_plan(a, g->nstrat, precision, integrand, nparams, nprm, P, g->tile_log2);
+  if (rp != VEGAS_OK) return rp;
+  a = P.a;
+  const bool exact = P.exact, streamed = P.streamed;
+  const int per_sm = P.per_sm;
+  const int nfix = (a.ntiles + 255) / 256;
+  const int grid = std::max(1, std::min(std::min(L.grid_max, per_sm * sms), a.ntiles));
 
-  const bool exact = d == dmax && (dmax == 4 || dmax == 8) && a.table_smem && !internal && G <= 256;
-  // the streamed point path: FP32, 16 or 32 axes, two-phase histogram, at most 256 strata an axis
-  bool streamed = precision == VEGAS_FP32 && dmax >= 16 && a.hist_mode == kHistTwoPhase &&
-                stream_family(integrand, integrand == VEGAS_GAUSS_SUM ? (int)((nparams - 3) / d) : 0);
-  for (int k = 0; k < d && streamed; ++k) streamed = g->nstrat[k] <= 256;
-  // the streamed path takes its map table from global memory (read through L1) when that frees enough
-  // shared memory for one more resident CTA: d = 30, 1e8 evaluations, 3 CTAs an SM instead of 2,
-  // 16.5 -> 14.6 ms (its lookups are random either way; the table stays in L1)
-  if (streamed && a.table_smem) {
-    FillArgs b = a;
-    smem_layout(b, sizeof(float), nprm, true, false);
-    if (b.hist_mode == a.hist_mode &&
-        fill_occupancy_f32_stream(integrand, dmax, b.sm_total) > fill_occupancy_f32_stream(integrand, dmax, a.sm_total))
-      a = b;
-  }
-  const int per_sm = precision == VEGAS_FP64
-                         ? (exact ? fill_occupancy_f64_exact(integrand, dmax, a.sm_total)
-                                  : fill_occupancy_f64(integrand, dmax, a.sm_total))
-                         : (exact ? fill_occupancy_f32_exact(integrand, dmax, a.sm_total)
-                                  : streamed ? fill_occupancy_f32_stream(integrand, dmax, a.sm_total)
-                                           : fill_occupancy_f32(integrand, dmax, a.sm_total));
-  if (per_sm <= 0) return VEGAS_ECUDA;
-  const int grid = std::max(1, std::min(L.grid_max, per_sm * sms));
-
-  tile_first_kernel<<<(L.ntiles + 255) / 256, 256, 0, s>>>(d_offsets, a.NH, L.ntiles, (int32_t*)(sc + L.tile_first),
+  tile_first_kernel<<<(a.ntiles + 255) / 256, 256, 0, s>>>(d_offsets, a.NH, a.ntiles, a.tile_log2,
+                                                            (int32_t*)(sc + L.tile_first),
                                                             a.ellmax_key, (int*)a.vexp, precision == VEGAS_FP32,
                                                             integrand, d, d_params, (int)nparams);
   VG_CHECK(cudaGetLastError());
@@ -466,11 +506,11 @@ int fill_impl(const vegas_geometry* g, int precision, int integrand, const doubl
   if (ev_after) VG_CHECK(cudaEventRecord(ev_after, s));
   if (integrand == kIntegrandPoints) return VEGAS_OK;  // no sums: the points are the output
   double* fix_part = (double*)(sc + L.fix_part);
-  carry_scan_kernel<<<L.nfix, kCarryBlock, 0, s>>>(a);
+  carry_scan_kernel<<<nfix, kCarryBlock, 0, s>>>(a);
   VG_CHECK(cudaGetLastError());
-  fixup_kernel<<<L.nfix, 256, 0, s>>>(a, fix_part);
+  fixup_kernel<<<nfix, 256, 0, s>>>(a, fix_part);
   VG_CHECK(cudaGetLastError());
-  results_kernel<<<1, 256, 0, s>>>(a.cta_part, grid, fix_part, L.nfix, a.NH, a.vexp, d_result);
+  results_kernel<<<1, 256, 0, s>>>(a.cta_part, grid, fix_part, nfix, a.NH, a.vexp, d_result);
   VG_CHECK(cudaGetLastError());
   bins_kernel<<<(d * G + 31) / 32, 256, 0, s>>>(a.hist_part, grid, d * G, a.vexp, d_bins);
   VG_CHECK(cudaGetLastError());

@@ -11,17 +11,19 @@ namespace vg {
 constexpr int kMaxDim = 32;
 constexpr int kMaxBins = 4096;
 constexpr int kFillThreads = 256;
-constexpr int kSamplesPerThread = 8;
-constexpr int kTile = kFillThreads * kSamplesPerThread;  // evaluations per tile
-constexpr int kTileLog2 = 11;                            // kTile = 2^kTileLog2
-static_assert(kTile == (1 << kTileLog2), "tile size is a power of two");
+// Tiles of the fill: 2^tile_log2 consecutive evaluations, 2^(tile_log2 - 8) a thread.  A launch takes 2048
+// unless that costs a resident CTA (the shared-memory staging grows with the tile), then 1024.
+constexpr int kTileLog2Min = 10, kTileLog2Max = 11;
+constexpr int kTileMax = 1 << kTileLog2Max;
+static_assert(kFillThreads == 256, "tiles of 2^tile_log2 evaluations: 2^(tile_log2 - 8) a thread");
 // how the fill accumulates the map weights
 constexpr int kHistShared = 0;    // shared-memory histogram of the evaluation type, atomic adds
 constexpr int kHistGlobal = 1;    // per-CTA global histogram, FP64 atomic adds (large d * N_g)
 constexpr int kHistTwoPhase = 2;  // FP32: fixed-point tile histogram with shared integer atomics
-constexpr int kMaxCubesPerTile = kTile / 2 + 3;          // n_h >= 2 bounds the cubes a tile meets
-constexpr int kLongSegment = 32;                         // longer cube segments go to a warp
-constexpr int kMaxLongPerTile = kTile / (kLongSegment + 1);  // segments longer than kLongSegment a tile holds
+constexpr int kLongSegment = 32;  // longer cube segments go to a warp
+// the cubes a tile of n evaluations can meet (n_h >= 2), and its segments longer than kLongSegment
+__host__ __device__ constexpr int tile_max_cubes(int n) { return n / 2 + 3; }
+__host__ __device__ constexpr int tile_max_long(int n) { return n / (kLongSegment + 1); }
 constexpr int kMaxDerivedParams = 8192;
 constexpr int kAllocThreads = 256;
 constexpr int kAllocItems = 16;  // cubes per thread in the allocation scan
@@ -57,6 +59,7 @@ struct FillArgs {
   int bin_shift;   // two-phase: log2 of the bits of a packed interval index (3: 8 bits, N_g <= 256; 4: 16 bits)
   int acc32;       // two-phase: 1 when the CTA histogram accumulates in FP32 (large d * N_g), 0 for float-float
   int hist_rep_log2;  // shared FP64 histogram: log2 of its copies; lane l adds into copy l mod 2^hist_rep_log2
+  int tile_log2;      // evaluations per tile: 2^tile_log2 (kTileLog2Min .. kTileLog2Max)
   int np_derived;
   int iid;  // integrand family (the batched fill dispatches on it per tile)
   const double* edges;     // [d][G+1] FP64
@@ -93,16 +96,16 @@ struct FillArgs {
 // launchers (one per precision, defined in vegas_fill_f64.cu / vegas_fill_f32.cu)
 int launch_fill_f64(int integrand, int dmax, FillArgs& a, int grid, cudaStream_t s);
 int launch_fill_f32(int integrand, int dmax, FillArgs& a, int grid, cudaStream_t s);
-int fill_occupancy_f64(int integrand, int dmax, int smem);
-int fill_occupancy_f32(int integrand, int dmax, int smem);
+int fill_occupancy_f64(int integrand, int dmax, int tile_log2, int smem);
+int fill_occupancy_f32(int integrand, int dmax, int tile_log2, int smem);
 // d == dmax (4 or 8) and the map table in shared memory
 int launch_fill_f64_exact(int integrand, int dmax, FillArgs& a, int grid, cudaStream_t s);
 int launch_fill_f32_exact(int integrand, int dmax, FillArgs& a, int grid, cudaStream_t s);
-int fill_occupancy_f64_exact(int integrand, int dmax, int smem);
-int fill_occupancy_f32_exact(int integrand, int dmax, int smem);
+int fill_occupancy_f64_exact(int integrand, int dmax, int tile_log2, int smem);
+int fill_occupancy_f32_exact(int integrand, int dmax, int tile_log2, int smem);
 // DMAX 16 or 32 with the streamed point path (FP32, two-phase histogram, s_k <= 256)
 int launch_fill_f32_stream(int integrand, int dmax, FillArgs& a, int grid, cudaStream_t s);
-int fill_occupancy_f32_stream(int integrand, int dmax, int smem);
+int fill_occupancy_f32_stream(int integrand, int dmax, int tile_log2, int smem);
 
 // buffers of the internal integrands (kIntegrandTabulated, kIntegrandPoints)
 struct FillExtra {
@@ -141,6 +144,16 @@ constexpr int kFloorPeriod = 4;
 int64_t flow_train_rows(int64_t m, float lambda);
 int flow_gather(const float* X, int d, int64_t stride, int64_t m, const float* w, float lambda, uint64_t seed,
                 uint32_t iter, double* wsum, float* xs, float* ws, cudaStream_t s);
+// A single-integral fill launch: its arguments (tile, layout), the kernel it takes and its resident CTAs per SM.
+struct FillPlan {
+  FillArgs a;
+  bool exact, streamed;
+  int per_sm;
+};
+// The launch plan of the single-integral fill for base (d, G, neval and the rest set): with tile_log2 = 0 the
+// tile size that keeps the exact-d path and the most resident CTAs, the larger on a tie; else that tile.
+int fill_plan(const FillArgs& base, const int32_t* nstrat, int precision, int integrand, int64_t nparams, int nprm,
+              FillPlan& out, int tile_log2 = 0);
 // prefetch: reserve the buffer of the next tile's offsets (the single-integral fill; the batched fill does not
 // prefetch)
 int fill_args_axes(FillArgs& a, const int32_t* nstrat, int precision, int nprm, bool prefetch = true);

@@ -59,7 +59,8 @@ class ProblemResult(ctypes.Structure):
 
 
 class Geometry(ctypes.Structure):
-    _fields_ = [("dim", ctypes.c_int32), ("nbins", ctypes.c_int32), ("nstrat", ctypes.POINTER(ctypes.c_int32))]
+    _fields_ = [("dim", ctypes.c_int32), ("nbins", ctypes.c_int32), ("nstrat", ctypes.POINTER(ctypes.c_int32)),
+                ("tile_log2", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 def _load():
@@ -410,9 +411,10 @@ class Batch:
         return out, nrun.value, ms.value
 
     def info(self, p):
-        o = np.zeros(4, dtype=np.int64)
-        _check(lib.vegas_batch_get(self._h, p, BATCH_INFO, o.ctypes.data_as(ctypes.c_void_p), 4), "vegas_batch_get")
-        return {"dim": int(o[0]), "nstrat": int(o[1]), "ncubes": int(o[2]), "nitn_run": int(o[3])}
+        o = np.zeros(5, dtype=np.int64)
+        _check(lib.vegas_batch_get(self._h, p, BATCH_INFO, o.ctypes.data_as(ctypes.c_void_p), 5), "vegas_batch_get")
+        return {"dim": int(o[0]), "nstrat": int(o[1]), "ncubes": int(o[2]), "nitn_run": int(o[3]),
+                "tile_log2": int(o[4])}
 
     def get(self, p, what):
         inf = self.info(p)
@@ -428,9 +430,9 @@ class Batch:
 # ---------------------------------------------------------------------------
 # Level 2: step entry points on torch CUDA tensors
 # ---------------------------------------------------------------------------
-def _geometry(dim, nbins, nstrat):
+def _geometry(dim, nbins, nstrat, tile_log2=0):
     ns = np.ascontiguousarray(nstrat if not isinstance(nstrat, int) else [nstrat] * dim, dtype=np.int32)
-    g = Geometry(dim, nbins, ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    g = Geometry(dim, nbins, ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(tile_log2), 0)
     g._keep = ns
     return g
 
@@ -460,10 +462,10 @@ def fill_scratch_bytes(dim, nbins, nstrat, neval):
 
 
 def fill(dim, nbins, nstrat, precision, integrand, params, neval, seed, iteration, beta, edges, offsets, ell, bins,
-         result, flags, scratch, cube_mean=None, cube_m2=None, problem_id=0, stream=None):
+         result, flags, scratch, cube_mean=None, cube_m2=None, problem_id=0, stream=None, tile_log2=0):
     """vegas_fill on torch CUDA tensors: params/edges/bins/result/cube_* float64, offsets int64,
-    ell float32, flags int32, scratch uint8."""
-    g = _geometry(dim, nbins, nstrat)
+    ell float32, flags int32, scratch uint8; tile_log2 0 (the library's choice), 10 or 11."""
+    g = _geometry(dim, nbins, nstrat, tile_log2)
     _check(lib.vegas_fill(ctypes.byref(g), precision, integrand, _ptr(params) if params is not None and
                           params.numel() else None, 0 if params is None else params.numel(), int(neval), int(seed),
                           int(iteration), int(problem_id), float(beta), _ptr(edges), _ptr(offsets), _ptr(ell),

@@ -18,17 +18,18 @@ int launch_fill_f32(int, int, FillArgs&, int, cudaStream_t) { return VEGAS_ECUDA
 int launch_fill_f64_exact(int, int, FillArgs&, int, cudaStream_t) { return VEGAS_ECUDA; }
 int launch_fill_f32_exact(int, int, FillArgs&, int, cudaStream_t) { return VEGAS_ECUDA; }
 int launch_fill_f32_stream(int, int, FillArgs&, int, cudaStream_t) { return VEGAS_ECUDA; }
-int fill_occupancy_f64(int, int, int) { return 0; }
-int fill_occupancy_f32(int, int, int) { return 0; }
-int fill_occupancy_f64_exact(int, int, int) { return 0; }
-int fill_occupancy_f32_exact(int, int, int) { return 0; }
-int fill_occupancy_f32_stream(int, int, int) { return 0; }
+int fill_occupancy_f64(int, int, int, int) { return 0; }
+int fill_occupancy_f32(int, int, int, int) { return 0; }
+int fill_occupancy_f64_exact(int, int, int, int) { return 0; }
+int fill_occupancy_f32_exact(int, int, int, int) { return 0; }
+int fill_occupancy_f32_stream(int, int, int, int) { return 0; }
 }  // namespace vg
 
 static int check(const FillArgs& a, int d, int G, size_t tsz, int nprm, bool prefetch, const char* what) {
   const size_t dG = (size_t)d * G;
   const bool two = a.hist_mode == kHistTwoPhase;
   const int per_word = 32 >> a.bin_shift;
+  const size_t tile = (size_t)1 << a.tile_log2, maxc = tile_max_cubes((int)tile);
   struct R {
     const char* name;
     int off;
@@ -37,14 +38,14 @@ static int check(const FillArgs& a, int d, int G, size_t tsz, int nprm, bool pre
       {"table", a.sm_table, a.table_smem ? dG * 4 * tsz : 0},
       {"hist", a.sm_hist, two ? dG * 4 : (a.hist_mode == kHistShared ? (dG * tsz) << a.hist_rep_log2 : 0)},
       {"hacc", a.sm_hacc, two ? dG * (a.acc32 ? 4 : 8) : 0},
-      {"bins", a.sm_bins, two ? (size_t)kTile * 4 * ((d + per_word - 1) / per_word) : 0},
-      {"wv", a.sm_wv, two ? (size_t)kTile * 4 : 0},
+      {"bins", a.sm_bins, two ? tile * 4 * ((d + per_word - 1) / per_word) : 0},
+      {"wv", a.sm_wv, two ? tile * 4 : 0},
       {"params", a.sm_params, (size_t)nprm * tsz},
-      {"off", a.sm_off, sizeof(int) * (kMaxCubesPerTile + 1)},
-      {"raw", a.sm_raw, prefetch ? sizeof(int64_t) * (kMaxCubesPerTile + 1) : 0},
-      {"invn", a.sm_invn, tsz * kMaxCubesPerTile},
-      {"vals", a.sm_vals, tsz * kTile},
-      {"long", a.sm_long, sizeof(int) * kMaxLongPerTile},
+      {"off", a.sm_off, sizeof(int) * (maxc + 1)},
+      {"raw", a.sm_raw, prefetch ? sizeof(int64_t) * (maxc + 1) : 0},
+      {"invn", a.sm_invn, tsz * maxc},
+      {"vals", a.sm_vals, tsz * tile},
+      {"long", a.sm_long, sizeof(int) * tile_max_long((int)tile)},
       {"start", a.sm_start, sizeof(int) * kFillThreads},
       {"misc", a.sm_misc, 64 + 8 * 32},
   };
@@ -74,10 +75,12 @@ int main() {
     for (int G : bins)
       for (int prec = 0; prec < 2; ++prec)
         for (int nprm : nprms)
-          for (int prefetch = 0; prefetch < 2; ++prefetch) {
+          for (int prefetch = 0; prefetch < 2; ++prefetch)
+          for (int tl = kTileLog2Min; tl <= kTileLog2Max; ++tl) {
           FillArgs a{};
           a.d = d;
           a.G = G;
+          a.tile_log2 = tl;
           std::vector<int32_t> ns(d, 2);
           if (fill_args_axes(a, ns.data(), prec == 0 ? VEGAS_FP64 : VEGAS_FP32, nprm, prefetch) != VEGAS_OK) continue;
           const size_t tsz = prec == 0 ? sizeof(double) : sizeof(float);

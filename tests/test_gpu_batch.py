@@ -69,8 +69,8 @@ def dev(a, dtype):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype).cuda()
 
 
-def single_fill(V, d, nstrat, iid, params, neval, t, edges, offsets, pid):
-    """the single-integral FP32 fill on the same inputs, problem_id = pid"""
+def single_fill(V, d, nstrat, iid, params, neval, t, edges, offsets, pid, tile_log2=0):
+    """the single-integral FP32 fill on the same inputs and tiles, problem_id = pid"""
     sb = V.fill_scratch_bytes(d, G, [nstrat] * d, neval)
     nh = nstrat ** d
     scratch = torch.empty(sb, dtype=torch.uint8, device="cuda")
@@ -79,7 +79,8 @@ def single_fill(V, d, nstrat, iid, params, neval, t, edges, offsets, pid):
     res = torch.zeros(2, dtype=torch.float64, device="cuda")
     flags = torch.zeros(1, dtype=torch.int32, device="cuda")
     V.fill(d, G, [nstrat] * d, V.FP32, iid, dev(params, torch.float64), neval, SEED, t, BETA,
-           dev(edges, torch.float64), dev(offsets, torch.int64), ell, bins, res, flags, scratch, problem_id=pid)
+           dev(edges, torch.float64), dev(offsets, torch.int64), ell, bins, res, flags, scratch, problem_id=pid,
+           tile_log2=tile_log2)
     torch.cuda.synchronize()
     return float(res[0]), float(res[1]), bins.cpu().numpy().reshape(d, G), int(flags[0])
 
@@ -100,7 +101,7 @@ def test_iteration0_matches_single_fill_and_oracle(V, orc):
         bins = b.get(p, V.BATCH_BINS)
         cfg = orc.Config(d, G, ns, ALPHA, BETA, points_f32=True, problem_id=p)
         edges = cfg.uniform_edges()
-        s_est, s_var, s_bins, s_flags = single_fill(V, d, ns, iid, params, neval, 0, edges, off, p)
+        s_est, s_var, s_bins, s_flags = single_fill(V, d, ns, iid, params, neval, 0, edges, off, p, inf["tile_log2"])
         assert s_flags == 0
         assert est == pytest.approx(s_est, rel=1e-12, abs=1e-13)  # oscillatory sums cancel; |f| <= 1
         assert var == pytest.approx(s_var, rel=1e-12)

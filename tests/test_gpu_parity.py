@@ -42,7 +42,7 @@ def dev(a, dtype=None):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype).cuda()
 
 
-def gpu_fill(V, cfg, precision, iid, params, neval, t, seed, edges, offsets, beta=0.75, want_cubes=True):
+def gpu_fill(V, cfg, precision, iid, params, neval, t, seed, edges, offsets, beta=0.75, want_cubes=True, tile_log2=0):
     nh = cfg.ncubes
     sb = V.fill_scratch_bytes(cfg.dim, cfg.nbins, list(cfg.nstrat), neval)
     scratch = torch.empty(sb, dtype=torch.uint8, device="cuda")
@@ -54,7 +54,8 @@ def gpu_fill(V, cfg, precision, iid, params, neval, t, seed, edges, offsets, bet
     c2 = torch.full((nh,), float("nan"), dtype=torch.float64, device="cuda") if want_cubes else None
     p = dev(params, torch.float64) if len(params) else None
     V.fill(cfg.dim, cfg.nbins, list(cfg.nstrat), precision, iid, p, neval, seed, t, beta,
-           dev(edges, torch.float64), dev(offsets, torch.int64), ell, bins, result, flags, scratch, cm, c2)
+           dev(edges, torch.float64), dev(offsets, torch.int64), ell, bins, result, flags, scratch, cm, c2,
+           tile_log2=tile_log2)
     torch.cuda.synchronize()
     out = {"ell": ell.cpu().numpy(), "bins": bins.cpu().numpy().reshape(cfg.dim, cfg.nbins),
            "est": float(result[0]), "var": float(result[1]), "flags": int(flags[0])}
@@ -62,6 +63,16 @@ def gpu_fill(V, cfg, precision, iid, params, neval, t, seed, edges, offsets, bet
         out["mean"] = cm.cpu().numpy()
         out["m2"] = c2.cpu().numpy()
     return out
+
+
+def test_fill_rejects_unknown_tile(V, orc):
+    """tile_log2 other than 0, 10 or 11 is EINVAL, before anything runs"""
+    cfg = orc.Config(2, 8, 4, 0.5, 0.75)
+    off = orc.allocate(None, cfg.ncubes, 100, 0.75)
+    for bad in (9, 12, -1):
+        with pytest.raises(V.VegasError) as e:
+            gpu_fill(V, cfg, V.FP64, W.LINEAR, [], 100, 0, 0, cfg.uniform_edges(), off, tile_log2=bad)
+        assert e.value.status == V.EINVAL
 
 
 def gpu_allocate(V, ell, nh, neval, uniform):
@@ -148,15 +159,17 @@ FILL_CASES = [
 ]
 
 
+@pytest.mark.parametrize("tile_log2", [10, 11], ids=["tile1024", "tile2048"])
 @pytest.mark.parametrize("name,d,G,ns,iid,params,neval", FILL_CASES, ids=[c[0] for c in FILL_CASES])
-def test_fill_fp64_matches_oracle(V, orc, name, d, G, ns, iid, params, neval):
+def test_fill_fp64_matches_oracle(V, orc, name, d, G, ns, iid, params, neval, tile_log2):
+    """both tile sizes the library chooses between, against the oracle"""
     cfg = orc.Config(d, G, ns, 0.5, 0.75)
     rng = np.random.default_rng(len(name))
     edges = random_edges(rng, d, G) if "one cube" not in name else cfg.uniform_edges()
     ell = rng.normal(0, 5, cfg.ncubes).astype(np.float32)
     off = orc.allocate(ell, cfg.ncubes, neval, 0.75)
     t, seed = 3, 12345
-    g = gpu_fill(V, cfg, V.FP64, iid, params, neval, t, seed, edges, off)
+    g = gpu_fill(V, cfg, V.FP64, iid, params, neval, t, seed, edges, off, tile_log2=tile_log2)
     r = orc.iteration(cfg, iid, params, neval, t, seed, edges, off)
     assert g["flags"] == 0
     big = np.abs(r["mean"]).max()
@@ -193,15 +206,16 @@ def test_fill_nonfinite_flag(V, orc):
 # ---------------------------------------------------------------------------
 # fill: FP32 evaluation path against the oracle on the same FP32 points
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("tile_log2", [10, 11], ids=["tile1024", "tile2048"])
 @pytest.mark.parametrize("name,d,G,ns,iid,params,neval", FILL_CASES[:4] + FILL_CASES[10:12],
                          ids=[c[0] for c in FILL_CASES[:4] + FILL_CASES[10:12]])
-def test_fill_fp32_matches_oracle(V, orc, name, d, G, ns, iid, params, neval):
+def test_fill_fp32_matches_oracle(V, orc, name, d, G, ns, iid, params, neval, tile_log2):
     cfg = orc.Config(d, G, ns, 0.5, 0.75, points_f32=True)
     rng = np.random.default_rng(len(name) + 1)
     edges = random_edges(rng, d, G)
     ell = rng.normal(0, 5, cfg.ncubes).astype(np.float32)
     off = orc.allocate(ell, cfg.ncubes, neval, 0.75)
-    g = gpu_fill(V, cfg, V.FP32, iid, params, neval, 1, 77, edges, off)
+    g = gpu_fill(V, cfg, V.FP32, iid, params, neval, 1, 77, edges, off, tile_log2=tile_log2)
     r = orc.iteration(cfg, iid, params, neval, 1, 77, edges, off)
     assert g["flags"] == 0
     assert g["est"] == pytest.approx(r["est"], rel=2e-5)
