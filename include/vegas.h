@@ -427,15 +427,24 @@ VEGAS_API int vegas_batch_set_chi2_bound(vegas_batch b, double bound);
 VEGAS_API int vegas_batch_set_stream(vegas_batch b, void *stream);
 /* Iterations with index < skip stay out of the combination (default 0). */
 VEGAS_API int vegas_batch_set_skip(vegas_batch b, int32_t skip);
-/* Launch shape of the fill: variant 0 (64 registers a thread, up to 4 CTAs
- * per SM) or 1 (128 registers, up to 2), ctas_per_sm (<= 0: as many as fit)
- * and chunk_tiles, the consecutive 1024-evaluation tiles a CTA takes from the
- * work counter at a time.  Errors: EINVAL. */
+/* Launch shape of the fill: variant 0 (the larger resident-CTA count per
+ * width: 4, 3 or 2 CTAs of 256 threads for 4, 8 or 16 axes) or 1 (half of
+ * that, twice the registers), ctas_per_sm (<= 0: as many as fit) and
+ * chunk_tiles, the consecutive tiles a CTA takes from the work counter at a
+ * time.  Errors: EINVAL. */
 VEGAS_API int vegas_batch_set_launch(vegas_batch b, int32_t variant, int32_t ctas_per_sm, int32_t chunk_tiles);
-/* Time one iteration of the batch under each candidate launch shape (both
- * variants, every resident-CTA count, chunk_tiles in {1, 4, 16}), keep the
- * fastest, and reset the batch (vegas_batch_reset).  The chosen shape and its
- * iteration time go to the non-NULL outputs.  Errors: ECUDA. */
+/* Tiles of 2^tile_log2 evaluations (10 or 11) for every integral of the
+ * batch: the shared-memory layout of the fill changes with the tile.  A batch
+ * starts at 11 where its layout fits, else 10; VEGAS_BATCH_INFO reports it.
+ * The FP32 map weights depend on the tiles at the level of FP32 rounding (see
+ * vegas_geometry).  Errors: EINVAL (another value, or a layout that does not
+ * fit), ECUDA. */
+VEGAS_API int vegas_batch_set_tile(vegas_batch b, int32_t tile_log2);
+/* Time one iteration of the batch under each candidate launch shape (each tile
+ * size whose layout fits, both variants, every resident-CTA count, chunk_tiles
+ * in {1, 4, 16}), keep the fastest, and reset the batch (vegas_batch_reset).
+ * The chosen shape and its iteration time go to the non-NULL outputs (the tile
+ * through VEGAS_BATCH_INFO).  Errors: ECUDA. */
 VEGAS_API int vegas_batch_tune(vegas_batch b, int32_t *variant, int32_t *ctas_per_sm, int32_t *chunk_tiles,
                                float *ms);
 /* Uniform maps, uniform counts, no recorded iterations, iteration counter 0. */

@@ -405,6 +405,7 @@ using namespace vg;
 struct HostProblem {
   int d, iid, nstrat, dmax, nprm, tile_log2;
   int64_t neval, NH, ntiles, nblocks;
+  int64_t ntiles_cap;  // tiles at the smallest usable tile: the size of its tile arrays
   std::vector<double> params;
 };
 
@@ -418,6 +419,10 @@ struct vegas_batch_s {
   std::vector<HostProblem> hp;
   int64_t tiles_total = 0, blocks_total = 0;
   int maxd = 1, smem = 0;
+  // the shared-memory layouts for tiles of 1024 and 2048 evaluations (layout_ok: it fits) and the tile in use
+  FillArgs layout[2] = {};
+  bool layout_ok[2] = {false, false};
+  int tile_log2 = kTileLog2Max;
   double* d_bins = nullptr;  // all integrals' map weights, contiguous
   size_t bins_total = 0;
   // device memory: one arena, plus the iteration records
@@ -686,28 +691,34 @@ extern "C" int vegas_batch_create_ex(const vegas_problem* problems, int32_t npro
     maxd = std::max(maxd, h.d);
     nprm_max = std::max(nprm_max, h.nprm);
   }
-  // one shared-memory layout for every integral: the widest map and parameter set, and one tile size, 2048
-  // evaluations where that layout fits (measured 112 ms an iteration on the 256-integral workload against 123
-  // with tiles of 1024), else 1024
-  FillArgs layout{};
+  // one shared-memory layout for every integral: the widest map and parameter set, for each tile size whose
+  // layout fits; the batch starts at 2048 evaluations where that fits (the 256-integral workload: 112 ms an
+  // iteration against 123 with tiles of 1024), and vegas_batch_tune / vegas_batch_set_tile may change it
+  FillArgs layouts[2] = {};
+  bool ok[2] = {false, false};
   {
     std::vector<int32_t> ones(maxd, 1);
-    layout.d = maxd;
-    layout.G = G;
-    int rc = VEGAS_EINVAL;
-    for (int tl = kTileLog2Max; tl >= kTileLog2Min && rc != VEGAS_OK; --tl) {
-      layout.tile_log2 = tl;
-      rc = fill_args_axes(layout, ones.data(), VEGAS_FP32, nprm_max, false);
-      if (rc == VEGAS_OK && (!layout.table_smem || layout.hist_mode != kHistTwoPhase)) rc = VEGAS_EINVAL;
+    for (int i = 0; i < 2; ++i) {
+      FillArgs& l = layouts[i];
+      l.d = maxd;
+      l.G = G;
+      l.tile_log2 = kTileLog2Min + i;
+      ok[i] = fill_args_axes(l, ones.data(), VEGAS_FP32, nprm_max, false) == VEGAS_OK && l.table_smem &&
+              l.hist_mode == kHistTwoPhase;
     }
-    if (rc != VEGAS_OK) return VEGAS_EINVAL;
+    if (!ok[0] && !ok[1]) return VEGAS_EINVAL;
   }
+  const int tile0 = ok[1] ? kTileLog2Max : kTileLog2Min, tile_min = ok[0] ? kTileLog2Min : kTileLog2Max;
+  int64_t tiles_cap = 0;
   for (HostProblem& h : hp) {
-    h.tile_log2 = layout.tile_log2;
-    h.ntiles = (h.neval + (int64_t(1) << h.tile_log2) - 1) >> h.tile_log2;
+    h.tile_log2 = tile0;
+    h.ntiles = (h.neval + (int64_t(1) << tile0) - 1) >> tile0;
+    h.ntiles_cap = (h.neval + (int64_t(1) << tile_min) - 1) >> tile_min;
     tiles += h.ntiles;
+    tiles_cap += h.ntiles_cap;
   }
-  if (tiles >= (int64_t(1) << 31) || blocks >= (int64_t(1) << 31)) return VEGAS_EINVAL;
+  if (tiles_cap >= (int64_t(1) << 31) || blocks >= (int64_t(1) << 31)) return VEGAS_EINVAL;
+  const FillArgs& layout = layouts[tile0 - kTileLog2Min];
 
   vegas_batch_s* b = new (std::nothrow) vegas_batch_s;
   if (!b) return VEGAS_ENOMEM;
@@ -724,6 +735,11 @@ extern "C" int vegas_batch_create_ex(const vegas_problem* problems, int32_t npro
   b->blocks_total = blocks;
   b->maxd = maxd;
   b->smem = layout.sm_total;
+  b->tile_log2 = tile0;
+  for (int i = 0; i < 2; ++i) {
+    b->layout[i] = layouts[i];
+    b->layout_ok[i] = ok[i];
+  }
   auto fail = [&](int rc) {
     release(b);
     delete b;
@@ -759,8 +775,8 @@ extern "C" int vegas_batch_create_ex(const vegas_problem* problems, int32_t npro
   for (int p = 0; p < P; ++p) o_params[p] = take(sizeof(double) * std::max<size_t>(1, b->hp[p].params.size()));
   for (int p = 0; p < P; ++p) o_offsets[p] = take(sizeof(int64_t) * (size_t)(b->hp[p].NH + 1));
   for (int p = 0; p < P; ++p) o_ell[p] = take(sizeof(float) * (size_t)b->hp[p].NH);
-  for (int p = 0; p < P; ++p) o_tf[p] = take(sizeof(int32_t) * (size_t)b->hp[p].ntiles);
-  for (int p = 0; p < P; ++p) o_car[p] = take(sizeof(Carry) * 2 * (size_t)b->hp[p].ntiles);
+  for (int p = 0; p < P; ++p) o_tf[p] = take(sizeof(int32_t) * (size_t)b->hp[p].ntiles_cap);
+  for (int p = 0; p < P; ++p) o_car[p] = take(sizeof(Carry) * 2 * (size_t)b->hp[p].ntiles_cap);
   for (int p = 0; p < P; ++p) o_bsum[p] = take(sizeof(uint64_t) * (size_t)(b->hp[p].nblocks + 1));
   b->arena = (unsigned char*)batch_alloc(b, off);
   if (!b->arena) return fail(VEGAS_ENOMEM);
@@ -828,6 +844,7 @@ extern "C" int vegas_batch_create_ex(const vegas_problem* problems, int32_t npro
     if (fill_args_axes(a, ns.data(), VEGAS_FP32, nprm_max, false) != VEGAS_OK) return fail(VEGAS_EINVAL);
     a.table_smem = layout.table_smem;
     a.hist_mode = layout.hist_mode;
+    a.acc32 = layout.acc32;  // the accumulator regions are the layout's
     a.sm_table = layout.sm_table;
     a.sm_hist = layout.sm_hist;
     a.sm_hacc = layout.sm_hacc;
@@ -897,6 +914,66 @@ extern "C" int vegas_batch_set_skip(vegas_batch b, int32_t skip) {
   return VEGAS_OK;
 }
 
+namespace {
+
+// every integral to tiles of 2^tile_log2 evaluations: the arguments' tile, tile count and shared-memory layout,
+// the group tile counts, uploaded; the next iteration recaptures its graph
+int apply_tile(vegas_batch_s* b, int tile_log2) {
+  const int i = tile_log2 - kTileLog2Min;
+  if (i < 0 || i > 1 || !b->layout_ok[i]) return VEGAS_EINVAL;
+  const FillArgs& l = b->layout[i];
+  cudaStream_t s = b->stream();
+  VG_CHECK(cudaStreamSynchronize(s));
+  // read back, change the tile fields only, write back: the device copy also holds what the device sets (the
+  // Philox iteration of each integral, the pointers to its iteration records)
+  std::vector<BatchProblem> prob(b->P);
+  VG_CHECK(cudaMemcpy(prob.data(), b->L.prob, sizeof(BatchProblem) * b->P, cudaMemcpyDeviceToHost));
+  int64_t tiles = 0;
+  for (int g = 0; g < kBatchGroups; ++g) b->group_tiles[g] = 0;
+  for (int p = 0; p < b->P; ++p) {
+    HostProblem& h = b->hp[p];
+    BatchProblem& q = prob[p];
+    FillArgs& a = q.a;
+    h.tile_log2 = tile_log2;
+    h.ntiles = (h.neval + (int64_t(1) << tile_log2) - 1) >> tile_log2;
+    a.tile_log2 = tile_log2;
+    a.ntiles = (int)h.ntiles;
+    a.table_smem = l.table_smem;
+    a.hist_mode = l.hist_mode;
+    a.acc32 = l.acc32;
+    a.sm_table = l.sm_table;
+    a.sm_hist = l.sm_hist;
+    a.sm_hacc = l.sm_hacc;
+    a.sm_bins = l.sm_bins;
+    a.sm_wv = l.sm_wv;
+    a.sm_params = l.sm_params;
+    a.sm_off = l.sm_off;
+    a.sm_raw = l.sm_raw;
+    a.sm_invn = l.sm_invn;
+    a.sm_vals = l.sm_vals;
+    a.sm_long = l.sm_long;
+    a.sm_start = l.sm_start;
+    a.sm_misc = l.sm_misc;
+    a.sm_total = l.sm_total;
+    b->group_tiles[q.group] += h.ntiles;
+    tiles += h.ntiles;
+  }
+  VG_CHECK(cudaMemcpy(b->L.prob, prob.data(), sizeof(BatchProblem) * b->P, cudaMemcpyHostToDevice));
+  b->tiles_total = tiles;
+  b->smem = l.sm_total;
+  b->tile_log2 = tile_log2;
+  b->graph_dirty = true;
+  return VEGAS_OK;
+}
+
+}  // namespace
+
+extern "C" int vegas_batch_set_tile(vegas_batch b, int32_t tile_log2) {
+  if (!b) return VEGAS_EINVAL;
+  DevGuard g(b->device);
+  return apply_tile(b, tile_log2);
+}
+
 extern "C" int vegas_batch_set_launch(vegas_batch b, int32_t variant, int32_t ctas_per_sm, int32_t chunk_tiles) {
   if (!b || variant < 0 || variant >= kBatchVariants || chunk_tiles < 1 || chunk_tiles > 4096) return VEGAS_EINVAL;
   b->variant = variant;
@@ -955,34 +1032,40 @@ extern "C" int vegas_batch_tune(vegas_batch b, int32_t* variant, int32_t* ctas_p
   DevGuard g(b->device);
   const int chunks[3] = {1, 4, 16};
   float best = INFINITY;
-  int bv = b->variant, bc = b->ctas_per_sm, bk = b->chunk;
-  for (int v = 0; v < kBatchVariants; ++v) {
-    int occ = 0;  // the most resident CTAs of any present group's kernel (capture clamps each group to its own)
-    for (int g = 0; g < kBatchGroups; ++g)
-      if (b->group_tiles[g] > 0) occ = std::max(occ, batch_fill_occupancy(v, g, b->smem));
-    for (int c = 1; c <= occ; ++c) {
-      for (int k : chunks) {
-        int rc = vegas_batch_set_launch(b, v, c, k);
-        if (rc != VEGAS_OK) return rc;
-        float t = INFINITY;
-        for (int rep = 0; rep < 2; ++rep) {  // the first run captures the graph and warms up
-          if ((rc = reset_batch(b)) != VEGAS_OK) return rc;
-          float m = 0.0f;
-          int n = 0;
-          if ((rc = run_iterations(b, 1, 0.0, &n, &m)) != VEGAS_OK) return rc;
-          if (rep > 0) t = m;
-        }
-        if (t < best) {
-          best = t;
-          bv = v;
-          bc = c;
-          bk = k;
+  int bv = b->variant, bc = b->ctas_per_sm, bk = b->chunk, bt = b->tile_log2;
+  for (int tl = kTileLog2Min; tl <= kTileLog2Max; ++tl) {
+    if (!b->layout_ok[tl - kTileLog2Min]) continue;
+    int rc = apply_tile(b, tl);
+    if (rc != VEGAS_OK) return rc;
+    for (int v = 0; v < kBatchVariants; ++v) {
+      int occ = 0;  // the most resident CTAs of any present group's kernel (capture clamps each group to its own)
+      for (int gr = 0; gr < kBatchGroups; ++gr)
+        if (b->group_tiles[gr] > 0) occ = std::max(occ, batch_fill_occupancy(v, gr, b->smem));
+      for (int c = 1; c <= occ; ++c) {
+        for (int k : chunks) {
+          if ((rc = vegas_batch_set_launch(b, v, c, k)) != VEGAS_OK) return rc;
+          float t = INFINITY;
+          for (int rep = 0; rep < 2; ++rep) {  // the first run captures the graph and warms up
+            if ((rc = reset_batch(b)) != VEGAS_OK) return rc;
+            float m = 0.0f;
+            int n = 0;
+            if ((rc = run_iterations(b, 1, 0.0, &n, &m)) != VEGAS_OK) return rc;
+            if (rep > 0) t = m;
+          }
+          if (t < best) {
+            best = t;
+            bv = v;
+            bc = c;
+            bk = k;
+            bt = tl;
+          }
         }
       }
     }
   }
-  int rc = vegas_batch_set_launch(b, bv, bc, bk);
+  int rc = apply_tile(b, bt);
   if (rc != VEGAS_OK) return rc;
+  if ((rc = vegas_batch_set_launch(b, bv, bc, bk)) != VEGAS_OK) return rc;
   if ((rc = reset_batch(b)) != VEGAS_OK) return rc;
   if (variant) *variant = bv;
   if (ctas_per_sm) *ctas_per_sm = bc;

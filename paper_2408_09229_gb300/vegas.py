@@ -111,6 +111,7 @@ def _load():
         "vegas_batch_set_stream": ([P, P], i32),
         "vegas_batch_set_skip": ([P, i32], i32),
         "vegas_batch_set_launch": ([P, i32, i32, i32], i32),
+        "vegas_batch_set_tile": ([P, i32], i32),
         "vegas_batch_tune": ([P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                               ctypes.POINTER(ctypes.c_float)], i32),
         "vegas_batch_reset": ([P], i32),
@@ -389,12 +390,17 @@ class Batch:
     def set_launch(self, variant, ctas_per_sm=0, chunk_tiles=4):
         _check(lib.vegas_batch_set_launch(self._h, variant, ctas_per_sm, chunk_tiles), "vegas_batch_set_launch")
 
+    def set_tile(self, tile_log2):
+        """tiles of 2^tile_log2 evaluations (10 or 11) for every integral"""
+        _check(lib.vegas_batch_set_tile(self._h, int(tile_log2)), "vegas_batch_set_tile")
+
     def tune(self):
         v, c, k = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         ms = ctypes.c_float()
         _check(lib.vegas_batch_tune(self._h, ctypes.byref(v), ctypes.byref(c), ctypes.byref(k), ctypes.byref(ms)),
                "vegas_batch_tune")
-        return {"variant": v.value, "ctas_per_sm": c.value, "chunk_tiles": k.value, "ms": ms.value}
+        return {"variant": v.value, "ctas_per_sm": c.value, "chunk_tiles": k.value, "ms": ms.value,
+                "tile_log2": self.info(0)["tile_log2"]}
 
     def reset(self):
         _check(lib.vegas_batch_reset(self._h), "vegas_batch_reset")

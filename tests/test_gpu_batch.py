@@ -220,12 +220,44 @@ def test_launch_shapes_agree_and_tune(V):
             ref = est
         else:
             assert np.allclose(est, ref, rtol=1e-9, atol=0)
+    tile0 = b.info(0)["tile_log2"]
     t = b.tune()
     assert t["variant"] in (0, 1) and t["ctas_per_sm"] >= 1 and t["chunk_tiles"] in (1, 4, 16) and t["ms"] > 0
-    # tune resets the batch
+    assert t["tile_log2"] in (10, 11) and all(b.info(p)["tile_log2"] == t["tile_log2"] for p in range(len(PROBLEMS)))
+    # tune resets the batch; on the starting tile the tuned shape gives the same iterations
     assert b.info(0)["nitn_run"] == 0
+    b.set_tile(tile0)
     out, _, _ = b.integrate(2)
     assert np.allclose([r["estimate"] for r in out], ref, rtol=1e-9, atol=0)
+
+
+def test_tile_sizes(V, orc):
+    """both tile sizes: each integral's first iteration equals the single fill on the same tiles, and the two
+    tile sizes agree to the FP32 form's rounding; an unknown tile is EINVAL"""
+    b = V.Batch(as_dicts(PROBLEMS), nbins=G, alpha=ALPHA, beta=BETA, seed=SEED)
+    est = {}
+    for tl in (10, 11):
+        b.reset()
+        b.set_tile(tl)
+        out, _, _ = b.integrate(1)
+        est[tl] = np.array([r["estimate"] for r in out])
+        for p, (d, iid, params, neval) in enumerate(PROBLEMS):
+            inf = b.info(p)
+            assert inf["tile_log2"] == tl
+            off = b.get(p, V.BATCH_OFFSETS)
+            cfg = orc.Config(d, G, inf["nstrat"], ALPHA, BETA, points_f32=True, problem_id=p)
+            s_est, _, s_bins, _ = single_fill(V, d, inf["nstrat"], iid, params, neval, 0, cfg.uniform_edges(), off,
+                                              p, tl)
+            assert est[tl][p] == pytest.approx(s_est, rel=1e-12, abs=1e-13)
+            bins = b.get(p, V.BATCH_BINS)
+            assert np.allclose(bins, s_bins, rtol=0, atol=1e-12 * s_bins.max())
+    # cubes that cross a tile edge are merged from other parts: the estimates differ at FP32 rounding
+    assert np.allclose(est[10], est[11], rtol=1e-6, atol=1e-9)
+    for bad in (9, 12):
+        with pytest.raises(V.VegasError) as e:
+            b.set_tile(bad)
+        assert e.value.status == V.EINVAL
+    b.close()
 
 
 def test_argument_errors(V):
