@@ -353,10 +353,16 @@ int plan_one(const FillArgs& base, const int32_t* nstrat, int precision, int int
   p.a = base;
   p.a.tile_log2 = tile_log2;
   p.a.ntiles = (int)((base.neval + (int64_t(1) << tile_log2) - 1) >> tile_log2);
-  // the prefetch buffer: every kernel but the FP32 ones with DMAX <= 8 (the kernel's own rule)
+  // the prefetch buffer: every kernel but the exact-d FP32 ones (the kernel's own rule); first laid out without it
+  // for FP32 with DMAX <= 8, where the exact-d path may apply
   if (fill_args_axes(p.a, nstrat, precision, nprm, !(precision == VEGAS_FP32 && dmax <= 8)) != VEGAS_OK)
     return VEGAS_EINVAL;
   p.exact = d == dmax && (dmax == 4 || dmax == 8) && p.a.table_smem && !internal && G <= 256;
+  // the general FP32 kernels with DMAX <= 8 take the prefetch buffer (only the exact-d ones go without): lay out
+  // again with it; the larger layout cannot make the exact-d path possible
+  if (!p.exact && precision == VEGAS_FP32 && dmax <= 8 &&
+      fill_args_axes(p.a, nstrat, precision, nprm, true) != VEGAS_OK)
+    return VEGAS_EINVAL;
   // the streamed point path: FP32, 16 or 32 axes, two-phase histogram, at most 256 strata an axis
   p.streamed = precision == VEGAS_FP32 && dmax >= 16 && p.a.hist_mode == kHistTwoPhase &&
                stream_family(integrand, integrand == VEGAS_GAUSS_SUM ? (int)((nparams - 3) / d) : 0);
