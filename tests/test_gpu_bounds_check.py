@@ -5,10 +5,10 @@ the histogram) is checked on the device, and a failed check sets bit 3 of the
 caller's flag word and is replaced by a safe index.  The workloads below cover
 the fill's paths (FP64 and FP32, the exact-width and general array paths, the
 streamed 16- and 32-axis paths with the map table in shared and in global
-memory, the learned proposal's points and tabulated passes, the batched fill,
-cubes longer than a tile, ragged last tiles) and must run with no check failing.
-They run in a child process that loads libvegas_gb300_check.so through
-VEGAS_GB300_LIB.
+memory, the step entry point at both tile sizes, the learned proposal's points
+and tabulated passes, the batched fill, cubes longer than a tile, ragged last
+tiles) and must run with no check failing.  They run in a child process that
+loads libvegas_gb300_check.so through VEGAS_GB300_LIB.
 """
 import json
 import os
@@ -56,6 +56,10 @@ CHILD = textwrap.dedent("""
     b = V.Batch(W.batch_problems(24, seed=3, neval_range=(1e5, 3e6)), 50, 0.5, 0.75, seed=0)
     res, _, _ = b.integrate(3)
     out.append({"name": "batched", "status": max((r["status"] for r in res), key=abs)})
+    b.reset()
+    b.set_tile(10)
+    res, _, _ = b.integrate(3)
+    out.append({"name": "batched, tiles of 1024", "status": max((r["status"] for r in res), key=abs)})
     # the step entry point: the caller's flag word itself
     cfg_d, G, neval = 4, 50, 100_000
     nh = 14 ** 4
@@ -71,8 +75,9 @@ CHILD = textwrap.dedent("""
     flags = torch.zeros(1, dtype=torch.int32, device="cuda")
     p = torch.tensor(W.ridge4_params(), dtype=torch.float64, device="cuda")
     for prec in (V.FP64, V.FP32):
-        V.fill(cfg_d, G, [14] * 4, prec, W.GAUSS_SUM, p, neval, 0, 0, 0.75, edges, off, ell, bins, result, flags,
-               scratch)
+        for tl in (0, 10, 11):  # the library's tile, then each tile size forced (both exact-d instances)
+            V.fill(cfg_d, G, [14] * 4, prec, W.GAUSS_SUM, p, neval, 0, 0, 0.75, edges, off, ell, bins, result, flags,
+                   scratch, tile_log2=tl)
     torch.cuda.synchronize()
     out.append({"name": "step fill flags", "status": int(flags[0])})
     print("RESULT " + json.dumps(out))
@@ -87,6 +92,6 @@ def test_bounds_checking_build_runs_every_path_clean():
     assert r.returncode == 0, r.stderr[-3000:]
     line = [ln for ln in r.stdout.splitlines() if ln.startswith("RESULT ")][-1]
     rows = json.loads(line[len("RESULT "):])
-    assert len(rows) == 12
+    assert len(rows) == 13
     bad = [row for row in rows if row["status"] != 0]
     assert not bad, bad
