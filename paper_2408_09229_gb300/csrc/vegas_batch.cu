@@ -845,6 +845,7 @@ extern "C" int vegas_batch_create_ex(const vegas_problem* problems, int32_t npro
     a.table_smem = layout.table_smem;
     a.hist_mode = layout.hist_mode;
     a.acc32 = layout.acc32;  // the accumulator regions are the layout's
+    a.wv_recompute = layout.wv_recompute;
     a.sm_table = layout.sm_table;
     a.sm_hist = layout.sm_hist;
     a.sm_hacc = layout.sm_hacc;
@@ -941,6 +942,7 @@ int apply_tile(vegas_batch_s* b, int tile_log2) {
     a.table_smem = l.table_smem;
     a.hist_mode = l.hist_mode;
     a.acc32 = l.acc32;
+    a.wv_recompute = l.wv_recompute;
     a.sm_table = l.sm_table;
     a.sm_hist = l.sm_hist;
     a.sm_hacc = l.sm_hacc;

@@ -982,7 +982,7 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
               a.train_w[j / a.train_stride] = powf(fabsf(v) * (float)invn[c], a.train_power);
           }
           const float wv = v * v * (float)invn[VG_IDX(c, maxc, a.flags, 5)];
-          wv_s[tix(jl, spt_log2)] = wv;
+          if (!(STREAM && a.wv_recompute)) wv_s[tix(jl, spt_log2)] = wv;  // else phase B recomputes it
           my_max = fmaxf(my_max, wv);
         }
       }
@@ -1095,11 +1095,20 @@ __device__ __forceinline__ void fill_tile(const FillArgs& a, const uint32_t* __r
       const float scale = ldexpf(1.0f, se);
       inv_scale = ldexpf(1.0f, -se);
       if (jl0 < len) {
+        int c = startc[tid];  // the evaluation's cube, for a weight recomputed from its value
 #pragma unroll 1
         for (int s = 0; s < spt; ++s) {
           const int jl = jl0 + s;
           if (jl < len) {
-            const uint32_t q = (uint32_t)__float2uint_rn(wv_s[tix(jl, spt_log2)] * scale);
+            float wv;
+            if (STREAM && a.wv_recompute) {  // the single fill's streamed layout has no weight slots
+              while (off_r[VG_IDX(c + 1, maxc + 1, a.flags, 23)] <= jl) ++c;
+              const float v = vals[VG_IDX(jl, tileN, a.flags, 24)];
+              wv = (float)(v * v * (float)invn[VG_IDX(c, maxc, a.flags, 25)]);
+            } else {
+              wv = wv_s[tix(jl, spt_log2)];
+            }
+            const uint32_t q = (uint32_t)__float2uint_rn(wv * scale);
             if (q) {
               if (bpw == 4) {
                 for (int w = 0; w < nw; ++w) {
@@ -1315,10 +1324,11 @@ __global__ void __launch_bounds__(kFillThreads, (sizeof(T) == 4 && (DMAX <= 8 ||
   double* hist_g = a.hist_part + (size_t)blockIdx.x * dG;
   fill_prologue<T>(a, S, d, table_in_smem);
   prep_params<ID, T, DMAX>(a.params_raw, a.np_raw, d, S.prm);
-  // the exact-d FP32 kernels (d = 4 or 8) do without the prefetch buffer, which buys a fourth resident CTA (d = 8
-  // ridge: 2.09 ms at 3 CTAs with the buffer, 1.99 ms at 4 without); the host leaves the buffer out of exactly
-  // these layouts.  The general FP32 kernels keep it (d = 8, N_g = 1024: 4-26 % faster with it)
-  constexpr bool kPrefetch = !(sizeof(T) == 4 && DMAX <= 8 && !STREAM && EXACT);
+  // the exact-d FP32 kernels (d = 4 or 8) and the streamed ones do without the prefetch buffer, which buys a
+  // fourth resident CTA (d = 8 ridge: 2.09 ms at 3 CTAs with the buffer, 1.99 ms at 4 without; d = 30 streamed,
+  // with no weight slots either: 61.4 -> 55 ms an iteration); the host leaves the buffer out of exactly these
+  // layouts.  The general FP32 kernels keep it (d = 8, N_g = 1024: 4-26 % faster with it)
+  constexpr bool kPrefetch = !(sizeof(T) == 4 && ((DMAX <= 8 && EXACT) || STREAM));
   if (kPrefetch && blockIdx.x < a.ntiles) {  // the first tile's cube offsets; later tiles' come during the tile before
     const int t = blockIdx.x, fh0 = a.tile_first[t];
     const int nc = min(tile_max_cubes(1 << (TLC ? TLC : a.tile_log2)), (t + 1 < a.ntiles ? a.tile_first[t + 1] : a.NH - 1) - fh0 + 1);

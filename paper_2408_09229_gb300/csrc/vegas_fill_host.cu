@@ -86,34 +86,39 @@ void magic_div(uint32_t s, uint32_t& m, uint32_t& shift) {
 // type.  When the histogram does not fit, a per-CTA global histogram takes
 // FP64 atomic adds.  The map table goes to shared memory when it also fits;
 // otherwise the kernel reads it from global memory.
-int smem_layout(FillArgs& a, size_t tsz, int nprm, bool fp32, bool table_ok = true, bool prefetch = true) {
+int smem_layout(FillArgs& a, size_t tsz, int nprm, bool fp32, bool table_ok = true, bool prefetch = true,
+                bool streamed = false) {
   const int dG = a.d * a.G;
+  // shared-memory regions start on 128-byte boundaries (the widest access is a 32-byte FP64 table entry)
+  auto al = [](size_t x) { return (x + 127) / 128 * 128; };
   const int tile = 1 << a.tile_log2, maxc = tile_max_cubes(tile);
   // the buffer of the next tile's global offsets, filled by cp.async during a tile (single-integral fill)
-  const size_t raw = prefetch ? align_up(sizeof(int64_t) * (maxc + 1)) : 0;
-  const size_t base = align_up(nprm * tsz) + align_up(sizeof(int) * (maxc + 1)) +
+  const size_t raw = prefetch ? al(sizeof(int64_t) * (maxc + 1)) : 0;
+  const size_t base = al(nprm * tsz) + al(sizeof(int) * (maxc + 1)) +
                       raw +
-                      align_up(tsz * maxc) + align_up(tsz * tile) +
-                      align_up(sizeof(int) * tile_max_long(tile)) + align_up(sizeof(int) * kFillThreads) +
-                      align_up(64 + 8 * 32);
+                      al(tsz * maxc) + al(tsz * tile) +
+                      al(sizeof(int) * tile_max_long(tile)) + al(sizeof(int) * kFillThreads) +
+                      al(64 + 8 * 32);
   const size_t budget = 160 * 1024;
-  const size_t table = align_up((size_t)dG * 4 * tsz);
+  const size_t table = al((size_t)dG * 4 * tsz);
   // two-phase: interval indices packed 8 bits (N_g <= 256) or 16 bits wide
   a.bin_shift = a.G <= 256 ? 3 : 4;
   const int per_word = 32 >> a.bin_shift;
   const size_t bin_words = (size_t)tile * 4 * ((a.d + per_word - 1) / per_word);
-  const size_t two_phase_ff = align_up((size_t)dG * 4) + align_up((size_t)dG * 8) + align_up(bin_words) +
-                              align_up(sizeof(float) * tile);
-  const size_t two_phase_32 = align_up((size_t)dG * 4) + align_up((size_t)dG * 4) + align_up(bin_words) +
-                              align_up(sizeof(float) * tile);
-  const size_t shared_hist = align_up((size_t)dG * tsz);
+  // the streamed path recomputes each evaluation's weight in phase B (no weight slots) and accumulates the CTA
+  // histogram in FP32: the smaller layout holds a fourth resident CTA at d = 30
+  const size_t wv_bytes = streamed ? 0 : al(sizeof(float) * tile);
+  a.wv_recompute = streamed ? 1 : 0;
+  const size_t two_phase_ff = al((size_t)dG * 4) + al((size_t)dG * 8) + al(bin_words) + wv_bytes;
+  const size_t two_phase_32 = al((size_t)dG * 4) + al((size_t)dG * 4) + al(bin_words) + wv_bytes;
+  const size_t shared_hist = al((size_t)dG * tsz);
   size_t hist;
   a.acc32 = 0;
   // the two-phase form folds all d N_g intervals of the CTA histogram once per
   // tile: measured faster than shared FP32 atomics for
   // N_g <= 256 and for d N_g <= 2048, slower beyond (d = 8, N_g = 1024: 2.3x)
   const bool two_phase_ok = fp32 && (a.G <= 256 || dG <= 2048);
-  if (two_phase_ok && base + two_phase_ff <= budget) {
+  if (two_phase_ok && !streamed && base + two_phase_ff <= budget) {
     a.hist_mode = kHistTwoPhase;
     hist = two_phase_ff;
   } else if (two_phase_ok && base + two_phase_32 <= budget) {
@@ -130,9 +135,9 @@ int smem_layout(FillArgs& a, size_t tsz, int nprm, bool fp32, bool table_ok = tr
     a.hist_rep_log2 = 0;
     if (!fp32)
       while (a.hist_rep_log2 < 4 && ((size_t)dG * tsz << (a.hist_rep_log2 + 1)) <= 64 * 1024 &&
-             base + align_up((size_t)dG * tsz << (a.hist_rep_log2 + 1)) <= budget)
+             base + al((size_t)dG * tsz << (a.hist_rep_log2 + 1)) <= budget)
         ++a.hist_rep_log2;
-    hist = align_up((size_t)dG * tsz << a.hist_rep_log2);
+    hist = al((size_t)dG * tsz << a.hist_rep_log2);
   } else {
     a.hist_mode = kHistGlobal;
     hist = 0;
@@ -142,22 +147,22 @@ int smem_layout(FillArgs& a, size_t tsz, int nprm, bool fp32, bool table_ok = tr
   a.sm_table = (int)off;  off += a.table_smem ? table : 0;
   a.sm_hist = (int)off;
   if (a.hist_mode == kHistTwoPhase) {
-    off += align_up((size_t)dG * 4);
-    a.sm_hacc = (int)off; off += align_up((size_t)dG * (a.acc32 ? 4 : 8));
-    a.sm_bins = (int)off; off += align_up(bin_words);
-    a.sm_wv = (int)off;   off += align_up(sizeof(float) * tile);
+    off += al((size_t)dG * 4);
+    a.sm_hacc = (int)off; off += al((size_t)dG * (a.acc32 ? 4 : 8));
+    a.sm_bins = (int)off; off += al(bin_words);
+    a.sm_wv = (int)off;   off += wv_bytes;
   } else {
     off += a.hist_mode == kHistShared ? hist : 0;
     a.sm_hacc = a.sm_bins = a.sm_wv = (int)off;
   }
-  a.sm_params = (int)off; off += align_up(nprm * tsz);
-  a.sm_off = (int)off;    off += align_up(sizeof(int) * (maxc + 1));
+  a.sm_params = (int)off; off += al(nprm * tsz);
+  a.sm_off = (int)off;    off += al(sizeof(int) * (maxc + 1));
   a.sm_raw = (int)off;    off += raw;
-  a.sm_invn = (int)off;   off += align_up(tsz * maxc);
-  a.sm_vals = (int)off;   off += align_up(tsz * tile);
-  a.sm_long = (int)off;   off += align_up(sizeof(int) * tile_max_long(tile));
-  a.sm_start = (int)off;  off += align_up(sizeof(int) * kFillThreads);
-  a.sm_misc = (int)off;   off += align_up(64 + 8 * 32);
+  a.sm_invn = (int)off;   off += al(tsz * maxc);
+  a.sm_vals = (int)off;   off += al(tsz * tile);
+  a.sm_long = (int)off;   off += al(sizeof(int) * tile_max_long(tile));
+  a.sm_start = (int)off;  off += al(sizeof(int) * kFillThreads);
+  a.sm_misc = (int)off;   off += al(64 + 8 * 32);
   a.sm_total = (int)off;
   return off <= 227 * 1024 ? VEGAS_OK : VEGAS_EINVAL;
 }
@@ -167,7 +172,7 @@ int smem_layout(FillArgs& a, size_t tsz, int nprm, bool fp32, bool table_ok = tr
 // Per-axis constants (magic reciprocals, z scales, FP32 fraction bits), the
 // Philox round keys and the shared-memory layout of a.  a.d, a.G, a.key0 and
 // a.key1 must be set.
-int fill_args_axes(FillArgs& a, const int32_t* nstrat, int precision, int nprm, bool prefetch) {
+int fill_args_axes(FillArgs& a, const int32_t* nstrat, int precision, int nprm, bool prefetch, bool streamed) {
   const int G = a.G;
   for (int k = 0; k < a.d; ++k) {
     a.nstrat[k] = (uint32_t)nstrat[k];
@@ -187,7 +192,7 @@ int fill_args_axes(FillArgs& a, const int32_t* nstrat, int precision, int nprm, 
     a.rk1[r] = a.key1 + (uint32_t)r * 0xBB67AE85u;
   }
   const size_t tsz = precision == VEGAS_FP64 ? sizeof(double) : sizeof(float);
-  return smem_layout(a, tsz, nprm, precision == VEGAS_FP32, true, prefetch);
+  return smem_layout(a, tsz, nprm, precision == VEGAS_FP32, true, prefetch, streamed);
 }
 
 namespace {
@@ -353,8 +358,8 @@ int plan_one(const FillArgs& base, const int32_t* nstrat, int precision, int int
   p.a = base;
   p.a.tile_log2 = tile_log2;
   p.a.ntiles = (int)((base.neval + (int64_t(1) << tile_log2) - 1) >> tile_log2);
-  // the prefetch buffer: every kernel but the exact-d FP32 ones (the kernel's own rule); first laid out without it
-  // for FP32 with DMAX <= 8, where the exact-d path may apply
+  // the prefetch buffer: every kernel but the exact-d FP32 ones and the streamed ones (the kernel's own rule); first
+  // laid out without it for FP32 with DMAX <= 8, where the exact-d path may apply
   if (fill_args_axes(p.a, nstrat, precision, nprm, !(precision == VEGAS_FP32 && dmax <= 8)) != VEGAS_OK)
     return VEGAS_EINVAL;
   p.exact = d == dmax && (dmax == 4 || dmax == 8) && p.a.table_smem && !internal && G <= 256;
@@ -367,12 +372,15 @@ int plan_one(const FillArgs& base, const int32_t* nstrat, int precision, int int
   p.streamed = precision == VEGAS_FP32 && dmax >= 16 && p.a.hist_mode == kHistTwoPhase &&
                stream_family(integrand, integrand == VEGAS_GAUSS_SUM ? (int)((nparams - 3) / d) : 0);
   for (int k = 0; k < d && p.streamed; ++k) p.streamed = nstrat[k] <= 256;
+  // the streamed kernels' own layout: no prefetch buffer, no weight slots, an FP32 CTA histogram (their rule)
+  if (p.streamed && fill_args_axes(p.a, nstrat, precision, nprm, false, true) != VEGAS_OK) return VEGAS_EINVAL;
+  if (p.streamed && p.a.hist_mode != kHistTwoPhase) return VEGAS_EINVAL;
   // the streamed path takes its map table from global memory (read through L1) when that frees enough
   // shared memory for one more resident CTA: d = 30, 1e8 evaluations, 3 CTAs an SM instead of 2,
   // 16.5 -> 14.6 ms (its lookups are random either way; the table stays in L1)
   if (p.streamed && p.a.table_smem) {
     FillArgs b = p.a;
-    smem_layout(b, sizeof(float), nprm, true, false);
+    smem_layout(b, sizeof(float), nprm, true, false, false, true);
     if (b.hist_mode == p.a.hist_mode &&
         fill_occupancy_f32_stream(integrand, dmax, tile_log2, b.sm_total) >
             fill_occupancy_f32_stream(integrand, dmax, tile_log2, p.a.sm_total))

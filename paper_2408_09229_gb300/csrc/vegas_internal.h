@@ -60,6 +60,7 @@ struct FillArgs {
   int acc32;       // two-phase: 1 when the CTA histogram accumulates in FP32 (large d * N_g), 0 for float-float
   int hist_rep_log2;  // shared FP64 histogram: log2 of its copies; lane l adds into copy l mod 2^hist_rep_log2
   int tile_log2;      // evaluations per tile: 2^tile_log2 (kTileLog2Min .. kTileLog2Max)
+  int wv_recompute;   // streamed path: phase B recomputes each evaluation's weight (the layout has no weight slots)
   int np_derived;
   int iid;  // integrand family (the batched fill dispatches on it per tile)
   const double* edges;     // [d][G+1] FP64
@@ -156,7 +157,8 @@ int fill_plan(const FillArgs& base, const int32_t* nstrat, int precision, int in
               FillPlan& out, int tile_log2 = 0);
 // prefetch: reserve the buffer of the next tile's offsets (the single-integral fill; the batched fill does not
 // prefetch)
-int fill_args_axes(FillArgs& a, const int32_t* nstrat, int precision, int nprm, bool prefetch = true);
+int fill_args_axes(FillArgs& a, const int32_t* nstrat, int precision, int nprm, bool prefetch = true,
+                   bool streamed = false);
 int derived_param_count(int integrand, int d, const double* host_params_or_null, int64_t np);
 
 // status helpers

@@ -1,8 +1,9 @@
 // Host-only check of the fill's shared-memory layout (no CUDA call is made):
 // for many (d, N_g, precision, parameter count) the regions that the fill
-// kernels index lie in order, 16-byte aligned, without overlap and inside the
-// dynamic shared memory total; the streamed path's layout without the map
-// table is checked the same way.  Prints "ok <cases>" or the first failure.
+// kernels index lie in order, 128-byte aligned, without overlap and inside the
+// dynamic shared memory total; the streamed path's layouts (no prefetch buffer,
+// no weight slots, an FP32 CTA histogram) with and without the map table are
+// checked the same way.  Prints "ok <cases>" or the first failure.
 #include "../../paper_2408_09229_gb300/csrc/vegas_fill_host.cu"
 
 #include <cstdio>
@@ -39,7 +40,7 @@ static int check(const FillArgs& a, int d, int G, size_t tsz, int nprm, bool pre
       {"hist", a.sm_hist, two ? dG * 4 : (a.hist_mode == kHistShared ? (dG * tsz) << a.hist_rep_log2 : 0)},
       {"hacc", a.sm_hacc, two ? dG * (a.acc32 ? 4 : 8) : 0},
       {"bins", a.sm_bins, two ? tile * 4 * ((d + per_word - 1) / per_word) : 0},
-      {"wv", a.sm_wv, two ? tile * 4 : 0},
+      {"wv", a.sm_wv, two && !a.wv_recompute ? tile * 4 : 0},
       {"params", a.sm_params, (size_t)nprm * tsz},
       {"off", a.sm_off, sizeof(int) * (maxc + 1)},
       {"raw", a.sm_raw, prefetch ? sizeof(int64_t) * (maxc + 1) : 0},
@@ -53,11 +54,15 @@ static int check(const FillArgs& a, int d, int G, size_t tsz, int nprm, bool pre
   for (int i = 0; i < n; ++i) {
     const size_t end = (size_t)r[i].off + r[i].size;
     const size_t next = i + 1 < n ? (size_t)r[i + 1].off : (size_t)a.sm_total;
-    if (r[i].off % 16 != 0 || end > next) {
+    if (r[i].off % 128 != 0 || end > next) {
       std::printf("FAIL %s d=%d G=%d tsz=%zu nprm=%d: %s at %d size %zu, next at %zu\n", what, d, G, tsz, nprm,
                   r[i].name, r[i].off, r[i].size, next);
       return 1;
     }
+  }
+  if (a.wv_recompute && a.hist_mode == kHistTwoPhase && !a.acc32) {
+    std::printf("FAIL %s d=%d G=%d: the streamed layout's CTA histogram is not FP32\n", what, d, G);
+    return 1;
   }
   if (a.sm_total > 227 * 1024) {
     std::printf("FAIL %s d=%d G=%d: total %d above 227 KB\n", what, d, G, a.sm_total);
@@ -76,20 +81,27 @@ int main() {
       for (int prec = 0; prec < 2; ++prec)
         for (int nprm : nprms)
           for (int prefetch = 0; prefetch < 2; ++prefetch)
+          for (int streamed = 0; streamed < 2; ++streamed)
           for (int tl = kTileLog2Min; tl <= kTileLog2Max; ++tl) {
+          if (streamed && (prec == 0 || prefetch)) continue;  // the streamed layout is FP32 and never prefetches
           FillArgs a{};
           a.d = d;
           a.G = G;
           a.tile_log2 = tl;
           std::vector<int32_t> ns(d, 2);
-          if (fill_args_axes(a, ns.data(), prec == 0 ? VEGAS_FP64 : VEGAS_FP32, nprm, prefetch) != VEGAS_OK) continue;
+          if (fill_args_axes(a, ns.data(), prec == 0 ? VEGAS_FP64 : VEGAS_FP32, nprm, prefetch, streamed) != VEGAS_OK)
+            continue;
+          if (a.wv_recompute != streamed) {
+            std::printf("FAIL d=%d G=%d: wv_recompute %d for streamed %d\n", d, G, a.wv_recompute, streamed);
+            return 1;
+          }
           const size_t tsz = prec == 0 ? sizeof(double) : sizeof(float);
           if (check(a, d, G, tsz, nprm, prefetch, "layout")) return 1;
           ++cases;
-          if (prec == 1 && a.table_smem) {  // the streamed path's alternative without the map table
+          if (prec == 1 && a.table_smem) {  // the alternative without the map table
             FillArgs b = a;
-            smem_layout(b, sizeof(float), nprm, true, false);
-            if (b.table_smem || check(b, d, G, tsz, nprm, true, "no-table layout")) return 1;
+            smem_layout(b, sizeof(float), nprm, true, false, prefetch, streamed);
+            if (b.table_smem || check(b, d, G, tsz, nprm, prefetch, "no-table layout")) return 1;
             ++cases;
           }
         }
