@@ -106,8 +106,10 @@ __host__ __device__ inline int derived_smem_count(int integrand, int d, int dmax
 // Turn the caller's parameters into the derived form read by vg::integrand:
 //   GAUSS_SUM         [A, c, K, 0, mu rows of DMAX]  c = -1/(2 s^2) (FP64, exp),
 //                                                    c = -log2(e)/(2 s^2) (FP32, exp2);
-//                     FP32 with DMAX = 4: the peaks in pairs, [K/2][axis][2], so that one
-//                     16-byte load holds two axes of both peaks, and an odd last peak as a row;
+//                     FP32 with DMAX = 4: slot 3 holds sigma = sqrt(log2(e)/(2 s^2)), the
+//                     centres are scaled by sigma and stored in pairs of peaks, [K/2][axis][2],
+//                     so that one 16-byte load holds two axes of both peaks, an odd last peak
+//                     as a row;
 //                     for DMAX >= 16 followed by the centres by axis,
 //                     [DMAX][K padded to 4], for the streamed point path
 //   PRODUCT_PEAK      [c_i^-2 (DMAX), w (DMAX)]   padded axes: c^-2 = 1, w = 0
@@ -126,11 +128,16 @@ __device__ void prep_params(const double* __restrict__ raw, int np, int d, T* ou
         out[4 + K * DMAX + i] = (T)((k < d && q < K) ? raw[3 + q * d + k] : 0.0);
       }
     }
+    // FP32 with four axes: the scale sigma = sqrt(log2(e) / (2 s^2)) in slot 3 and the centres times sigma, so
+    // that a peak's term is 2^-(sum of squared scaled distances)
+    constexpr bool kScaled = sizeof(T) == 4 && DMAX == 4;
+    const double sigma = kScaled ? sqrt(0.5 * 1.4426950408889634) / fabs(raw[1]) : 1.0;
     for (int i = tid; i < 4 + K * DMAX; i += nt) {
       double v = 0.0;
       if (i == 0) v = raw[0];
       else if (i == 1) v = (sizeof(T) == 8 ? -1.0 : -1.4426950408889634) / (2.0 * raw[1] * raw[1]);
       else if (i == 2) v = (double)K;
+      else if (i == 3) v = kScaled ? sigma : 0.0;
       else if (i >= 4) {
         const int e = i - 4;
         int k = e / DMAX, j = e - k * DMAX;
@@ -139,7 +146,7 @@ __device__ void prep_params(const double* __restrict__ raw, int np, int d, T* ou
           k = 2 * (e / (2 * DMAX)) + (r & 1);
           j = 2 * (r >> 2) + ((r >> 1) & 1);
         }
-        v = j < d ? raw[3 + k * d + j] : 0.0;
+        v = j < d ? raw[3 + k * d + j] * sigma : 0.0;
       }
       out[i] = (T)v;
     }
@@ -245,10 +252,12 @@ template <int ID, typename T, int DMAX>
 __device__ __forceinline__ T integrand(const T (&x)[DMAX], int d, const T* __restrict__ p, int np, T s0, T s1,
                                        int K) {
   if constexpr (ID == VEGAS_GAUSS_SUM && sizeof(T) == 4 && DMAX == 4) {
-    // FP32, four axes: two peaks a step, each packed operation doing one axis of both, one packed scale and
-    // accumulate a pair (the 1000-Gaussian ridge, 5e6 evaluations: fill 2.33 -> 2.21 ms against pairs of axes)
-    const uint64_t x0 = pk2(x[0], x[0]), x1 = pk2(x[1], x[1]), x2 = pk2(x[2], x[2]), x3 = pk2(x[3], x[3]);
-    const uint64_t sc = pk2(s1, s1);
+    // FP32, four axes: two peaks a step, each packed operation doing one axis of both, one packed accumulate a
+    // pair (the 1000-Gaussian ridge, 5e6 evaluations: fill 2.33 -> 2.21 ms against pairs of axes).  Point and
+    // centres are scaled by sigma (slot 3), so a peak's term is 2^-r with r its squared scaled distance
+    const float sg = p[3];
+    const float y0 = x[0] * sg, y1 = x[1] * sg, y2 = x[2] * sg, y3 = x[3] * sg;
+    const uint64_t x0 = pk2(y0, y0), x1 = pk2(y1, y1), x2 = pk2(y2, y2), x3 = pk2(y3, y3);
     const float4* mu = reinterpret_cast<const float4*>(p + 4);
     uint64_t acc2 = 0ull;  // (+0, +0)
     int k = 0;
@@ -261,14 +270,13 @@ __device__ __forceinline__ T integrand(const T (&x)[DMAX], int d, const T* __res
       r2 = fma2(d1, d1, r2);
       r2 = fma2(d2, d2, r2);
       r2 = fma2(d3, d3, r2);
-      const uint64_t e = mul2(r2, sc);
-      acc2 = add2(acc2, pk2(ex2_approx(lo2(e)), ex2_approx(hi2(e))));
+      acc2 = add2(acc2, pk2(ex2_approx(-lo2(r2)), ex2_approx(-hi2(r2))));
     }
     float acc = lo2(acc2) + hi2(acc2);
     if (k < K) {  // an odd last peak, stored as a row
       const float4 m = *reinterpret_cast<const float4*>(p + 4 + 4 * k);
-      const float e0 = x[0] - m.x, e1 = x[1] - m.y, e2 = x[2] - m.z, e3 = x[3] - m.w;
-      acc += ex2_approx(fmaf(e3, e3, fmaf(e2, e2, fmaf(e1, e1, e0 * e0))) * s1);
+      const float e0 = y0 - m.x, e1 = y1 - m.y, e2 = y2 - m.z, e3 = y3 - m.w;
+      acc += ex2_approx(-fmaf(e3, e3, fmaf(e2, e2, fmaf(e1, e1, e0 * e0))));
     }
     return s0 * acc;
   } else if constexpr (ID == VEGAS_GAUSS_SUM && sizeof(T) == 4 && DMAX % 4 == 0) {
