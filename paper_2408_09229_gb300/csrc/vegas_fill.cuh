@@ -1374,7 +1374,7 @@ __global__ void __launch_bounds__(kFillThreads, (sizeof(T) == 4 && (DMAX <= 8 ||
   prep_params<ID, T, DMAX>(a.params_raw, a.np_raw, d, S.prm);
   // the exact-d FP32 kernels (d = 4 or 8) and the streamed ones do without the prefetch buffer, which buys a
   // fourth resident CTA (d = 8 ridge: 2.09 ms at 3 CTAs with the buffer, 1.99 ms at 4 without; d = 30 streamed,
-  // with no weight slots either: 61.4 -> 55 ms an iteration); the host leaves the buffer out of exactly these
+  // with no weight slots either: 61.6 -> 56.8 ms an iteration); the host leaves the buffer out of exactly these
   // layouts.  The general FP32 kernels keep it (d = 8, N_g = 1024: 4-26 % faster with it)
   constexpr bool kPrefetch = !(sizeof(T) == 4 && ((DMAX <= 8 && EXACT) || STREAM));
   if (kPrefetch && blockIdx.x < a.ntiles) {  // the first tile's cube offsets; later tiles' come during the tile before
