@@ -448,6 +448,19 @@ def run_ours(args, rank, world):
             print(json.dumps({"profile": "d30 stress", "evals_per_s": neval * args.steps / (float(np.sum(it_ms)) / 1e3),
                               "iteration_ms": [float(x) for x in it_ms], "fill_ms": [float(x) for x in fill_ms]}))
         return
+    if args.profile_ridge:
+        # the paper's Ridge with 1000 Gaussians in d = 4 under the "def" configuration (N_g = 1024), FP32 form
+        d, neval = 4, int(args.profile_ridge)
+        v = V.Vegas(d, 1024, 0, 0.5, 0.75, precision=V.FP32, stream=stream)
+        prm = W.paper_ridge(d, 1000)
+        v.integrate(W.GAUSS_SUM, prm, neval, args.warmup, seed=5)
+        r = v.integrate(W.GAUSS_SUM, prm, neval, args.steps, seed=SEED)
+        it_ms, fill_ms = v.timings()
+        if rank == 0:
+            print(json.dumps({"profile": "ridge d4 N1000", "evals_per_s": neval * args.steps / (float(np.sum(it_ms)) / 1e3),
+                              "iteration_ms": [float(x) for x in it_ms], "fill_ms": [float(x) for x in fill_ms],
+                              "estimate": r["estimate"], "sigma": r["sigma"]}))
+        return
     if args.profile_flow:
         d, neval = 12, 10_000_000
         v = V.Vegas(d, NBINS, 0, ALPHA, BETA, precision=V.FP32, stream=stream)
@@ -826,6 +839,8 @@ def main():
                     help="fill scaling sweep of the paper's Table 4 parameters on the linear integrand")
     ap.add_argument("--profile-stress", type=float, default=0.0, metavar="NEVAL",
                     help="profiling run of the d = 30 workload (FP32 form) at NEVAL evaluations per iteration")
+    ap.add_argument("--profile-ridge", type=float, default=0.0, metavar="NEVAL",
+                    help="profiling run of the paper's Ridge, 1000 Gaussians in d = 4 (FP32 form), NEVAL per iteration")
     ap.add_argument("--profile-flow", action="store_true",
                     help="profiling run of the learned proposal: d = 12 ridge, 1e7 evaluations, a fixed flow")
     ap.add_argument("--profile-grad", type=int, default=0, metavar="D",
