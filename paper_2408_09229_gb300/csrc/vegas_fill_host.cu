@@ -386,6 +386,16 @@ int plan_one(const FillArgs& base, const int32_t* nstrat, int precision, int int
             fill_occupancy_f32_stream(integrand, dmax, tile_log2, p.a.sm_total))
       p.a = b;
   }
+  // the general FP32 kernels, too, read the map table from global memory (through L1) when that gives more
+  // resident CTAs: the 1000-Gaussian ridge in d = 4 with N_g = 1024 held 2 CTAs an SM with its 64 KB table in
+  // shared memory
+  if (!p.exact && !p.streamed && precision == VEGAS_FP32 && p.a.table_smem) {
+    FillArgs b = p.a;
+    smem_layout(b, sizeof(float), nprm, true, false, true, false);
+    if (fill_occupancy_f32(integrand, dmax, tile_log2, b.sm_total) >
+        fill_occupancy_f32(integrand, dmax, tile_log2, p.a.sm_total))
+      p.a = b;
+  }
   const int sm = p.a.sm_total;
   const int tl = tile_log2;
   p.per_sm = precision == VEGAS_FP64
