@@ -254,6 +254,20 @@ def test_fill_fp32_wide_map_matches_oracle(V, orc, name, d, G, ns, iid, params, 
     test_fill_fp32_streamed_matches_oracle(V, orc, name, d, G, ns, iid, params, neval)
 
 
+GAUSS4_CASES = [  # FP32 Gaussian sums in four axes: peaks in pairs, point and centres scaled
+    ("ridge d4 K2 one pair", 4, 50, 8, W.GAUSS_SUM, W.ridge(4, 2, 0.1), 30_000),
+    ("ridge d4 K8 pairs only", 4, 50, 8, W.GAUSS_SUM, W.ridge(4, 8, 0.05), 30_001),
+    ("ridge d3 K5 padded axis, odd peak", 3, 40, 10, W.GAUSS_SUM, W.ridge(3, 5, 0.05), 20_011),
+    ("gaussian d2 K1 single peak", 2, 64, 20, W.GAUSS_SUM, W.gaussian(2, 0.4, 0.05), 10_000),
+    ("paper ridge d4 K1000 G1024", 4, 1024, 4, W.GAUSS_SUM, W.paper_ridge(4, 1000), 8_000),
+]
+
+
+@pytest.mark.parametrize("name,d,G,ns,iid,params,neval", GAUSS4_CASES, ids=[c[0] for c in GAUSS4_CASES])
+def test_fill_fp32_gauss4_matches_oracle(V, orc, name, d, G, ns, iid, params, neval):
+    test_fill_fp32_streamed_matches_oracle(V, orc, name, d, G, ns, iid, params, neval)
+
+
 @pytest.mark.parametrize("name,d,G,ns,iid,params,neval", STREAM_CASES, ids=[c[0] for c in STREAM_CASES])
 def test_fill_fp32_streamed_matches_oracle(V, orc, name, d, G, ns, iid, params, neval):
     cfg = orc.Config(d, G, ns, 0.5, 0.75, points_f32=True)
