@@ -613,16 +613,18 @@ VEGAS_API int vegas_probe_pipes(double rates[4]);
  * Errors: EINVAL, ENOMEM, ECUDA. */
 VEGAS_API int vegas_probe_shared_atomics(double *rate);
 /* Measured throughput of the FP64 exponential that the FP64 form's Gaussian
- * integrand evaluates once per peak and evaluation (a table-driven method with
- * 64 entries, Tang 1989) (Table 3's Gaussian and Ridge;
- * the ridge workloads): exp calls per SM per clock on the current device, same
+ * integrand evaluates once per peak and evaluation (2^(y/64) from a table of
+ * 64 entries, after Tang 1989, on an argument already scaled to units of
+ * ln2/64) (Table 3's Gaussian and Ridge;
+ * the ridge workloads): calls per SM per clock on the current device, same
  * method as vegas_probe_pipes.  With the FP64 FMA rate it states the FP64 fill's
  * roofline: the time the FP64 pipe needs for the evaluation's FP64 operations
  * and exponentials against the kernel's measured time.  Errors: ENOMEM, ECUDA. */
 VEGAS_API int vegas_probe_exp64(double *rate);
-/* e^x on n arguments d_x (device, FP64) into d_y: which = 0 the FP64 form's
- * table-driven exponential, which = 1 the CUDA library's exp(), for tests of
- * the first against the second and against correctly rounded values.
+/* n arguments d_x (device, FP64) into d_y: which = 0 e^x by the table-driven
+ * exponential, which = 1 e^x by the CUDA library's exp(), which = 2 2^(x/64) by
+ * the table-driven exponential that the FP64 Gaussian sum evaluates; for tests
+ * against the library and against correctly rounded values.
  * Asynchronous on stream.  Errors: EINVAL, ECUDA. */
 VEGAS_API int vegas_exp64_eval(const double *d_x, double *d_y, int64_t n, int32_t which, void *stream);
 

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kFillThreads, MINB) batch_fill_kernel(const __
         __syncthreads();
         {
           const FillShared<float> S = fill_shared<float>(smem, sa, true);
-          fill_prologue<float>(sa, S, sa.d, true);
+          fill_prologue<float>(sa, S, sa.d, true, 1.0);
           prep_params<ID, float, DMAX>(sa.params_raw, sa.np_raw, sa.d, S.prm);
         }
         st = FillState<float>{};

@@ -304,6 +304,42 @@ __device__ __forceinline__ double exp_table64(double x) {
   return __hiloint2double(__double2hiint(y) + (m << 20), __double2loint(y));
 }
 
+// 2^(y/64) by the same 64-entry table, for arguments already in units of ln2/64 (the FP64 Gaussian sum scales its
+// point and centres so that the squared distance is this argument: no multiply before the reduction).  n = the
+// integer nearest y (from adding 1.5 2^52, its low word), f = y - n in [-1/2, 1/2] (exact), and
+// 2^(f/64) - 1 = e^(f c) - 1 with c = ln2/64 as a degree-5 polynomial in f whose coefficients are c^k/k!
+// (|f c| <= ln2/128: truncation below 4e-17).  The result 2^(n>>6) 2^((n&63)/64) (1 + p) is within about one ulp
+// of 2^(y/64).  Nine FP64 operations (three adds, five FMAs, one multiply) against the ten of exp_table64 and the
+// multiply that would form its argument.  Below y = -68800 the result is 0 (2^(y/64) is below half the smallest
+// subnormal); from -68800 to -65344 one more multiply rounds to the subnormal result; from 65344 up and for NaN
+// the library exp2() runs.
+__device__ __forceinline__ double exp2_64ths(double y) {
+  constexpr double kShift = 0x1.8p52;
+  constexpr double kC1 = 0x1.62e42fefa39efp-7;   // c = ln2 / 64
+  constexpr double kC2 = 0x1.ebfbdff82c58fp-15;  // c^2 / 2
+  constexpr double kC3 = 0x1.c6b08d704a0c0p-23;  // c^3 / 6
+  constexpr double kC4 = 0x1.3b2ab6fba4e77p-31;  // c^4 / 24
+  constexpr double kC5 = 0x1.5d87fe78a6731p-40;  // c^5 / 120
+  const double t = y + kShift;
+  const int n = __double2loint(t);
+  const double f = y - (t - kShift);
+  double q = fma(f, kC5, kC4);
+  q = fma(q, f, kC3);
+  q = fma(q, f, kC2);
+  q = fma(q, f, kC1);
+  const double p = q * f;  // 2^(f/64) - 1
+  const double T = __ldg(&kExp2Table64[n & 63]);
+  const double r = fma(T, p, T);
+  const int m = n >> 6;
+  if ((__double2hiint(y) & 0x7FFFFFFF) >= 0x40EFE800) {  // |y| >= 65344, or NaN
+    if (y < -68800.0) return 0.0;
+    if (!(y < 0.0)) return exp2(y * 0x1p-6);  // NaN, or above the normal range
+    // m in [-1075, -1021]: r 2^(m + 64) is normal; the exact scale 2^-64 then rounds once, to the subnormal result
+    return __hiloint2double(__double2hiint(r) + ((m + 64) << 20), __double2loint(r)) * 0x1p-64;
+  }
+  return __hiloint2double(__double2hiint(r) + (m << 20), __double2loint(r));
+}
+
 // ---------------------------------------------------------------------------
 // Bounds-checking builds (nvcc -DVEGAS_BOUNDS_CHECK; build_lib.build(check=True)), the substitute for a memory
 // sanitizer: every index that the fill derives from data (an interval from a point, a cube from the offsets, a

@@ -104,8 +104,9 @@ __host__ __device__ inline int derived_smem_count(int integrand, int d, int dmax
 }
 
 // Turn the caller's parameters into the derived form read by vg::integrand:
-//   GAUSS_SUM         [A, c, K, 0, mu rows of DMAX]  c = -1/(2 s^2) (FP64, exp),
-//                                                    c = -log2(e)/(2 s^2) (FP32, exp2);
+//   GAUSS_SUM         [A, c, K, sigma, mu rows of DMAX]  c = -log2(e)/(2 s^2) (FP32, exp2);
+//                     FP64: sigma = sqrt(32/ln2)/s in slot 3 and the centres times sigma
+//                     (the point comes scaled from the map table);
 //                     FP32 with DMAX = 4: slot 3 holds sigma = sqrt(log2(e)/(2 s^2)), the
 //                     centres are scaled by sigma and stored in pairs of peaks, [K/2][axis][2],
 //                     so that one 16-byte load holds two axes of both peaks, an odd last peak
@@ -116,6 +117,10 @@ __host__ __device__ inline int derived_smem_count(int integrand, int d, int dmax
 //   OSCILLATORY       [2 pi u, 0, 0, 0, a (DMAX)]
 //   MOROKOFF_CAFLISCH [(1+1/d)^d, 1/d, 0, 0]
 //   MAP_DENSITY       [edges (d*(G'+1))]
+// FP64 Gaussian sum: the point and the centres are scaled by sqrt(32 / ln2) / s, so that a peak's squared scaled
+// distance y gives its term e^(-r^2 / 2s^2) = 2^(-y/64) (exp2_64ths); the map table carries the scale
+__host__ __device__ inline double gauss_scale64(double s) { return 0x1.b2da4e9808a53p+2 / fabs(s); }
+
 template <int ID, typename T, int DMAX>
 __device__ void prep_params(const double* __restrict__ raw, int np, int d, T* out) {
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -129,9 +134,12 @@ __device__ void prep_params(const double* __restrict__ raw, int np, int d, T* ou
       }
     }
     // FP32 with four axes: the scale sigma = sqrt(log2(e) / (2 s^2)) in slot 3 and the centres times sigma, so
-    // that a peak's term is 2^-(sum of squared scaled distances)
-    constexpr bool kScaled = sizeof(T) == 4 && DMAX == 4;
-    const double sigma = kScaled ? sqrt(0.5 * 1.4426950408889634) / fabs(raw[1]) : 1.0;
+    // that a peak's term is 2^-(sum of squared scaled distances); FP64: sigma = gauss_scale64(s), the term
+    // 2^(-y/64)
+    constexpr bool kScaled = (sizeof(T) == 4 && DMAX == 4) || sizeof(T) == 8;
+    const double sigma = sizeof(T) == 8 ? gauss_scale64(raw[1])
+                         : kScaled      ? sqrt(0.5 * 1.4426950408889634) / fabs(raw[1])
+                                        : 1.0;
     for (int i = tid; i < 4 + K * DMAX; i += nt) {
       double v = 0.0;
       if (i == 0) v = raw[0];
@@ -313,7 +321,7 @@ __device__ __forceinline__ T integrand(const T (&x)[DMAX], int d, const T* __res
         const T dx = x[j] - m[j];  // padded axes hold x = mu = 0
         r2 = fma(dx, dx, r2);
       }
-      if constexpr (sizeof(T) == 8) acc += exp_table64(r2 * s1);
+      if constexpr (sizeof(T) == 8) acc += exp2_64ths(-r2);  // point and centres scaled: r2 = 64 log2(e) r^2/2s^2
       else acc += ex2_approx(r2 * s1);
     }
     return s0 * acc;
@@ -833,16 +841,18 @@ __host__ __device__ inline int value_exponent(int integrand, int d, const double
   return e < 0 ? 0 : (e > 120 ? 120 : e);
 }
 
-// map table {e, dx, N_g dx} from the FP64 edges, and zeroed histograms
+// map table {xs e, xs dx, N_g dx} from the FP64 edges (xs: the point's scale, 1 but for the FP64 Gaussian sum),
+// and zeroed histograms
 template <typename T>
-__device__ __forceinline__ void fill_prologue(const FillArgs& a, const FillShared<T>& S, int d, bool table_in_smem) {
+__device__ __forceinline__ void fill_prologue(const FillArgs& a, const FillShared<T>& S, int d, bool table_in_smem,
+                                              double xs) {
   const int G = a.G, dG = d * G, tid = threadIdx.x;
   if (table_in_smem) {
     for (int b = tid; b < dG; b += kFillThreads) {
       const int k = b / G, i = b - k * G;
       const double e0 = a.edges[k * (G + 1) + i], e1 = a.edges[k * (G + 1) + i + 1];
       const double dx = __dsub_rn(e1, e0), jk = __dmul_rn((double)G, dx);
-      S.tab[b] = TabEntry<T>{(T)e0, (T)dx, (T)jk, T(0)};
+      S.tab[b] = TabEntry<T>{(T)(e0 * xs), (T)(dx * xs), (T)jk, T(0)};
     }
   }
   if (a.hist_mode == kHistShared)
@@ -1371,7 +1381,9 @@ __global__ void __launch_bounds__(kFillThreads, (sizeof(T) == 4 && (DMAX <= 8 ||
   const bool table_in_smem = EXACT || a.table_smem;
   const FillShared<T> S = fill_shared<T>(smem, a, table_in_smem);
   double* hist_g = a.hist_part + (size_t)blockIdx.x * dG;
-  fill_prologue<T>(a, S, d, table_in_smem);
+  double xs = 1.0;  // the FP64 Gaussian sum takes its point scaled (gauss_scale64)
+  if constexpr (ID == VEGAS_GAUSS_SUM && sizeof(T) == 8) xs = gauss_scale64(a.params_raw[1]);
+  fill_prologue<T>(a, S, d, table_in_smem, xs);
   prep_params<ID, T, DMAX>(a.params_raw, a.np_raw, d, S.prm);
   // the exact-d FP32 kernels (d = 4 or 8) and the streamed ones do without the prefetch buffer, which buys a
   // fourth resident CTA (d = 8 ridge: 2.09 ms at 3 CTAs with the buffer, 1.99 ms at 4 without; d = 30 streamed,

@@ -219,13 +219,17 @@ __global__ void tile_first_kernel(const int64_t* __restrict__ offsets, int NH, i
 }
 
 template <typename T>
-__global__ void table_kernel(const double* __restrict__ edges, int d, int G, TabEntry<T>* tab) {
+// gauss_params: the FP64 Gaussian sum's parameters [A, s, ...], whose point scale gauss_scale64(s) the table
+// carries (the fill kernel's prologue does the same), else null
+__global__ void table_kernel(const double* __restrict__ edges, int d, int G, TabEntry<T>* tab,
+                             const double* __restrict__ gauss_params) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= d * G) return;
+  const double xs = gauss_params ? gauss_scale64(gauss_params[1]) : 1.0;
   const int k = b / G, i = b - k * G;
   const double e0 = edges[k * (G + 1) + i], e1 = edges[k * (G + 1) + i + 1];
   const double dx = __dsub_rn(e1, e0), jk = __dmul_rn((double)G, dx);
-  tab[b] = TabEntry<T>{(T)e0, (T)dx, (T)jk, T(0)};
+  tab[b] = TabEntry<T>{(T)(e0 * xs), (T)(dx * xs), (T)jk, T(0)};
 }
 
 // Runs of "before" records reduced from the right within blocks of
@@ -516,8 +520,11 @@ int fill_impl(const vegas_geometry* g, int precision, int integrand, const doubl
     VG_CHECK(cudaMemsetAsync(a.hist_part, 0, sizeof(double) * (size_t)grid * d * G, s));
   if (!a.table_smem) {
     const int n = d * G;
-    if (precision == VEGAS_FP64) table_kernel<double><<<(n + 255) / 256, 256, 0, s>>>(d_edges, d, G, (TabEntry<double>*)a.gtable);
-    else table_kernel<float><<<(n + 255) / 256, 256, 0, s>>>(d_edges, d, G, (TabEntry<float>*)a.gtable);
+    if (precision == VEGAS_FP64)
+      table_kernel<double><<<(n + 255) / 256, 256, 0, s>>>(d_edges, d, G, (TabEntry<double>*)a.gtable,
+                                                          integrand == VEGAS_GAUSS_SUM ? d_params : nullptr);
+    else
+      table_kernel<float><<<(n + 255) / 256, 256, 0, s>>>(d_edges, d, G, (TabEntry<float>*)a.gtable, nullptr);
     VG_CHECK(cudaGetLastError());
   }
   if (ev_before) VG_CHECK(cudaEventRecord(ev_before, s));

@@ -1,6 +1,6 @@
 // vegas_probe.cu -- issue-rate probes of the arithmetic pipes the fill kernel
-// uses (FP32 FMA, FP64 FMA, MUFU ex2, 32-bit multiply-high, the FP64 exp of
-// the FP64 form's Gaussian integrand) and of the shared
+// uses (FP32 FMA, FP64 FMA, MUFU ex2, 32-bit multiply-high, the FP64
+// exponential of the FP64 form's Gaussian integrand, exp2_64ths) and of the shared
 // memory integer atomics its map-weight histogram accumulates with.  Each thread runs
 // eight independent dependent chains; every block times itself with the SM
 // cycle counter.  The rate is operations per SM per clock, taken from the
@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(kProbeThreads) probe_kernel(float seedf, doubl
       if constexpr (KIND == 0) f[c] = fmaf(f[c], 0.999999f, 1e-7f);
       else if constexpr (KIND == 1) g[c] = fma(g[c], 0.999999, 1e-7);
       else if constexpr (KIND == 2) asm volatile("ex2.approx.ftz.f32 %0, %0;" : "+f"(f[c]));
-      else if constexpr (KIND == 5) g[c] = exp_table64(-g[c]);  // converges to 0.567..., stays in range
+      else if constexpr (KIND == 5) g[c] = exp2_64ths(-g[c]);  // converges to 0.989..., stays in range
       else u[c] = __umulhi(u[c], 0x9E3779B9u) + c;
     }
   }
@@ -120,12 +120,12 @@ int probe_one(double& rate) {
 namespace {
 __global__ void exp64_eval_kernel(const double* __restrict__ x, double* __restrict__ y, int64_t n, int which) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = which == 0 ? vg::exp_table64(x[i]) : exp(x[i]);
+    y[i] = which == 0 ? vg::exp_table64(x[i]) : which == 2 ? vg::exp2_64ths(x[i]) : exp(x[i]);
 }
 }  // namespace
 
 extern "C" int vegas_exp64_eval(const double* d_x, double* d_y, int64_t n, int32_t which, void* stream) {
-  if (n < 0 || (n > 0 && (!d_x || !d_y)) || (which != 0 && which != 1)) return VEGAS_EINVAL;
+  if (n < 0 || (n > 0 && (!d_x || !d_y)) || which < 0 || which > 2) return VEGAS_EINVAL;
   if (n == 0) return VEGAS_OK;
   const int grid = (int)std::min<int64_t>((n + 255) / 256, 4096);
   exp64_eval_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(d_x, d_y, n, which);

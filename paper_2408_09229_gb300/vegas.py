@@ -563,7 +563,8 @@ def probe_exp64():
 
 
 def exp64_eval(x, y, which=0, stream=None):
-    """vegas_exp64_eval on float64 CUDA tensors: which 0 the FP64 form's exponential, 1 the library exp()"""
+    """vegas_exp64_eval on float64 CUDA tensors: which 0 the table-driven e^x, 1 the library exp(), 2 the
+    table-driven 2^(x/64) of the FP64 Gaussian sum"""
     _check(lib.vegas_exp64_eval(_ptr(x), _ptr(y), x.numel(), int(which), _stream_ptr(stream)), "vegas_exp64_eval")
 
 

@@ -602,6 +602,35 @@ def test_exp64_against_library_and_correct_rounding(V):
     assert np.all(np.abs(yt[sub] - host[sub]) <= 5e-324)
 
 
+def test_exp2_64ths_against_host(V):
+    """the FP64 Gaussian sum's 2^(y/64) (64-entry table, degree-5 polynomial in y - round(y)) against Python's
+    exp2 on random arguments over its whole range and at the edges of its branches: within 1 ulp for normal
+    results, within the smallest subnormal below them, exact 0 below y = -68800, the library above 65344"""
+    rng = np.random.default_rng(13)
+    ys = np.concatenate([rng.uniform(-64 * 1021.0, 64 * 1021.0, 200_000), rng.uniform(-64.0, 64.0, 200_000),
+                         -rng.exponential(2000.0, 100_000), rng.uniform(-68800.0, -65344.0, 20_000),
+                         np.arange(-300.0, 300.0, 0.5),
+                         [0.0, -0.0, 1e-300, -1e-300, -65343.9, -65344.0, -65344.1, -68799.9, -68800.0, -68800.1,
+                          -1e6, -1e300, 65343.9, 65344.0, 65500.0, np.nextafter(-68800.0, 0.0)]])
+    x = dev(ys, torch.float64)
+    y = torch.empty_like(x)
+    V.exp64_eval(x, y, 2)
+    torch.cuda.synchronize()
+    y = y.cpu().numpy()
+    host = np.array([math.exp2(v / 64.0) if v < 65600.0 else math.inf for v in ys])
+
+    def ulps(a, b):
+        return np.abs(np.asarray(a).view(np.int64) - np.asarray(b).view(np.int64))
+
+    normal = (host > 2.2250738585072014e-308) & np.isfinite(host)
+    table = normal & (ys < 65344.0)
+    assert ulps(y[table], host[table]).max() <= 1
+    assert ulps(y[normal & ~table], host[normal & ~table]).max() <= 2  # the library's exp2
+    assert np.all(y[ys < -68800.0] == 0.0)
+    sub = (~normal) & (ys >= -68800.0)
+    assert np.all(np.abs(y[sub] - host[sub]) <= 5e-324)
+
+
 def test_probe_shared_atomics(V):
     r = V.probe_shared_atomics()
     assert 2.0 < r < 1024.0, r  # 32-bit shared atomic adds per SM per clock
