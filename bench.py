@@ -46,7 +46,7 @@ FP32_LANES_PER_SM = 128
 # that kernel (dram__bytes_read.sum + dram__bytes_write.sum): the per-cube offsets and weights
 FILL_TRAFFIC_BYTES = (345.26 + 144.44) * 1e6
 # the same for the FP64 form's fill kernel (profiles/fill_kernel_ridge8_fp64.md)
-FILL64_TRAFFIC_BYTES = (348.45 + 145.14) * 1e6
+FILL64_TRAFFIC_BYTES = (350.64 + 145.65) * 1e6
 # the same capture: issue slots busy and warp instructions x 32 per evaluation (1.685e9 x 32 / 1e8)
 FILL_ISSUE_ACTIVE = 0.679
 FILL_INSTR_PER_EVAL = 539
