@@ -376,9 +376,15 @@ int plan_one(const FillArgs& base, const int32_t* nstrat, int precision, int int
   p.streamed = precision == VEGAS_FP32 && dmax >= 16 && p.a.hist_mode == kHistTwoPhase &&
                stream_family(integrand, integrand == VEGAS_GAUSS_SUM ? (int)((nparams - 3) / d) : 0);
   for (int k = 0; k < d && p.streamed; ++k) p.streamed = nstrat[k] <= 256;
-  // the streamed kernels' own layout: no prefetch buffer, no weight slots, an FP32 CTA histogram (their rule)
-  if (p.streamed && fill_args_axes(p.a, nstrat, precision, nprm, false, true) != VEGAS_OK) return VEGAS_EINVAL;
-  if (p.streamed && p.a.hist_mode != kHistTwoPhase) return VEGAS_EINVAL;
+  // the streamed kernels' own layout: no prefetch buffer, no weight slots, an FP32 CTA histogram (their rule).
+  // It is smaller than the layout above, so the two-phase histogram still fits; were it not, the general kernel runs
+  if (p.streamed) {
+    FillArgs b = p.a;
+    if (fill_args_axes(b, nstrat, precision, nprm, false, true) == VEGAS_OK && b.hist_mode == kHistTwoPhase)
+      p.a = b;
+    else
+      p.streamed = false;
+  }
   // the streamed path takes its map table from global memory (read through L1) when that frees enough
   // shared memory for one more resident CTA: d = 30, 1e8 evaluations, 3 CTAs an SM instead of 2,
   // 16.5 -> 14.6 ms (its lookups are random either way; the table stays in L1)
