@@ -212,6 +212,10 @@ FLOW_TRAIN = dict(iterations=10, steps_per_iteration=200, samples=65536, batch=4
 # never samples
 FLOW_TRAIN_TEMPERED = dict(iterations=20, steps_per_iteration=500, samples=65536, batch=4096, lr=2e-3, temper=0.03,
                            floor=0.03)
+# exploration before the run (vegas_flow_explore): 16 VEGAS+ maps adapted from uniform with their own seeds, 10
+# iterations each at the run's budget, 32768 samples of each pooled by the balance heuristic, 2000 Adam steps
+FLOW_EXPLORE = dict(iterations=10, maps=16, samples_per_map=32768, steps=2000, batch=4096, lr=1e-3, floor=0.03)
+FLOW_EXPLORE_CAP = 400
 # iterations after training over which the judge compares the learned proposal with plain VEGAS+
 JUDGE_WINDOW = 3
 
@@ -230,7 +234,7 @@ def learned_proposal(V, W, stream, rank):
     Gaussians along the diagonal of the 8-cube) at 1e6 and 1e7 evaluations per iteration."""
     import torch
     out = {"training": dict(FLOW_TRAIN, adam_steps=FLOW_TRAIN["iterations"] * FLOW_TRAIN["steps_per_iteration"]),
-           "training_tempered": FLOW_TRAIN_TEMPERED}
+           "training_tempered": FLOW_TRAIN_TEMPERED, "exploration": FLOW_EXPLORE}
     tube = W.paper_ridge(8, 100)
     cases = [("d12_4peaks_s0.03", 12, W.ridge(12, 4, 0.03), 1.0, 10_000_000, 40, 40),
              ("d12_3peaks_s0.1", 12, W.ridge(12, 3, 0.1), 1.0, 1_000_000, 1200, 1200),
@@ -241,25 +245,31 @@ def learned_proposal(V, W, stream, rank):
              ("d8_paper_ridge_N100_1e7", 8, tube, W.exact(W.GAUSS_SUM, 8, tube), 10_000_000, 300, 300)]
     for name, d, params, exact, neval, cap_plain, cap_flow in cases:
         row = {}
-        forms = ("plain", "flow", "flow_judged") + (("flow_tempered",) if name.startswith("d12_4peaks") else ())
+        forms = ("plain", "flow", "flow_judged") + (("flow_tempered", "flow_explored") if name.startswith("d12_4peaks")
+                                                    else ())
         for form in forms:
             cap = cap_plain if form == "plain" else cap_flow
             train = FLOW_TRAIN_TEMPERED if form == "flow_tempered" else FLOW_TRAIN
             if form == "flow_tempered":
                 cap = train["iterations"] + 30
+            if form == "flow_explored":
+                cap = FLOW_EXPLORE_CAP
             v = V.Vegas(d, NBINS, 0, ALPHA, BETA, precision=V.FP32, rtol=1e-4, stream=stream)
             if form != "plain":
                 v.set_flow(W.flow_params(d, seed=0))
+            if form not in ("plain", "flow_explored"):
                 v.set_flow_training(**train)
                 v.set_skip(train["iterations"])
                 if form == "flow_judged":
                     v.set_flow_judge(JUDGE_WINDOW)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
+            if form == "flow_explored":  # exploration and training inside the timed region
+                v.flow_explore(W.GAUSS_SUM, params, neval, seed=SEED + 100 + rank, **FLOW_EXPLORE)
             r = v.integrate(W.GAUSS_SUM, params, neval, cap, seed=SEED + rank)
             dt = time.perf_counter() - t0
             it_ms, _ = v.timings()
-            k = train["iterations"] if form != "plain" else min(10, r["nitn_run"] - 1)
+            k = train["iterations"] if form not in ("plain", "flow_explored") else min(10, r["nitn_run"] - 1)
             late = r["it_sig"][k:] / np.abs(r["it_est"][k:])
             pull = (r["estimate"] - exact) / r["sigma"]
             row[form] = {"seconds": dt, "iterations": r["nitn_run"], "estimate": r["estimate"], "sigma": r["sigma"],

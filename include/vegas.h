@@ -571,6 +571,41 @@ VEGAS_API int vegas_set_flow(vegas_handle h, const float *params, int64_t nparam
 VEGAS_API int vegas_set_flow_training(vegas_handle h, int32_t iterations, int32_t steps_per_iteration,
                                       int32_t samples, int32_t batch, float lr, float temper, float floor);
 VEGAS_API int vegas_get_flow(vegas_handle h, float *params, int64_t nparams, float *last_loss);
+/* Exploration for the learned proposal (not in the paper).  A VEGAS+ map
+ * (Sec. 2.1.1) adapted from the uniform map follows the peaks its first
+ * samples favour; maps adapted with other seeds favour others.
+ * vegas_flow_explore adapts nmaps maps (1..64) on the handle, map k by
+ * `iterations` plain VEGAS+ iterations of `neval` evaluations from the
+ * uniform map with seed + k (the handle's strata and FP32 form; the flow is
+ * set aside meanwhile), pools samples_per_map samples of each into one
+ * training set and trains the handle's flow on it: `steps` Adam steps
+ * (learning rate lr) on windows of `batch` consecutive rows, with the floor's
+ * uniform rows as in vegas_set_flow_training.  Sample r comes from map
+ * r mod nmaps; its weight is |f(x)| / q(x) with q = (1/nmaps) sum_k q_k the
+ * mixture of the maps' densities q_k = prod_a 1 / (N_g dx_a) (the balance
+ * heuristic, Veach and Guibas 1995), so every peak that some map reaches
+ * carries its own mass however many maps reach it.  The handle's map is the
+ * uniform map again on return, its flow trained, its in-loop training
+ * schedule unchanged.  Requires a flow (vegas_set_flow) and the FP32 form;
+ * integrand and params as for vegas_integrate (not MAP_DENSITY).  Returns
+ * after the device work is done.  Errors: EINVAL (no flow, FP64, arguments),
+ * ENOMEM, ECUDA, and those of vegas_integrate.
+ *
+ * vegas_explore_points is its sampling step: nmaps maps d_maps (device, FP64,
+ * [nmaps][dim][nbins + 1], each axis's edges increasing from 0 to 1), and
+ * m = nmaps * samples_per_map samples: sample r from map r mod nmaps, with
+ * uniform numbers from Philox4x32-10, counter (r low, r high, 4 g, "EXPR"
+ * = 0x45585052) for axes 4g..4g+3, key (seed low, seed high), y = (u + 1/2)
+ * 2^-32, z = y nbins, i = min(floor z, nbins - 1), x = e_i + (z - i)(e_{i+1}
+ * - e_i) in FP64.  Writes d_x [m][dim] (x rounded to FP32) and d_q [m] (FP64,
+ * the mixture density at the FP64 x; the interval of x_a in a map is the j
+ * with e_j <= x_a < e_{j+1}, clamped to [0, nbins - 1]).  Caller-owned device
+ * buffers; asynchronous on stream.  Errors: EINVAL, ECUDA. */
+VEGAS_API int vegas_flow_explore(vegas_handle h, int32_t integrand, const double *params, int64_t nparams,
+                                 int64_t neval, int32_t iterations, int32_t nmaps, int64_t samples_per_map,
+                                 int32_t steps, int32_t batch, float lr, float floor, uint64_t seed);
+VEGAS_API int vegas_explore_points(int32_t dim, int32_t nbins, int32_t nmaps, const double *d_maps,
+                                   int64_t samples_per_map, uint64_t seed, float *d_x, double *d_q, void *stream);
 /* Plain VEGAS+ as the fallback and the judge of the learned proposal (not in
  * the paper, which has no learned component; the yardstick is its estimator,
  * Eq. (6) of Sec. 2.1.2).  window > 0 turns the judge on; it applies from the

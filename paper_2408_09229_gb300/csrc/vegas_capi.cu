@@ -81,6 +81,9 @@ struct vegas_s {
   int64_t tx_cap = 0, tw_cap = 0;
   void* d_grad_scratch = nullptr;
   size_t grad_scratch_cap = 0;
+  // exploration: the adapted maps [S][d][G+1] and the samples' mixture density
+  double* d_explore = nullptr;
+  int64_t explore_cap = 0;
   // the judge of the learned proposal: window (0: off), state, paired iterations since the flow was
   // set, and sigma_t^2 x iteration time of each form over the paired iterations after training
   int judge_window = 0, judge_state = kJudgeOpen;
@@ -194,6 +197,7 @@ std::vector<void**> device_fields(vegas_s* h) {
                     &h->d_values, &h->d_train_x, &h->d_train_w})
     f.push_back((void**)p);
   f.push_back(&h->d_grad_scratch);
+  f.push_back((void**)&h->d_explore);
   return f;
 }
 
@@ -920,6 +924,73 @@ extern "C" int vegas_set_flow_training(vegas_handle h, int32_t iterations, int32
   h->flow_lr = lr;
   h->flow_trained = 0;
   return VEGAS_OK;
+}
+
+extern "C" int vegas_flow_explore(vegas_handle h, int32_t integrand, const double* params, int64_t nparams,
+                                  int64_t neval, int32_t iterations, int32_t nmaps, int64_t samples_per_map,
+                                  int32_t steps, int32_t batch, float lr, float floor, uint64_t seed) {
+  if (!h || !h->d_flow || h->precision != VEGAS_FP32 || iterations < 1 || nmaps < 1 ||
+      nmaps > vg::kMaxExploreMaps || samples_per_map < 1 || samples_per_map > vg::kMaxEval / nmaps || steps < 0 ||
+      batch < 1 || !(lr > 0.0f) || !(floor >= 0.0f) || integrand == VEGAS_MAP_DENSITY)
+    return VEGAS_EINVAL;
+  const int d = h->dim, G = h->nbins;
+  const int64_t m = (int64_t)nmaps * samples_per_map;
+  if (m * d > vg::kMaxEval || vg::derived_param_count(integrand, d, params, nparams) < 0) return VEGAS_EINVAL;
+  DeviceGuard guard(h->device);
+  cudaStream_t s = h->stream();
+  const int64_t ne = (int64_t)d * (G + 1);
+  int rc;
+  if ((rc = grow(h, h->d_explore, h->explore_cap, nmaps * ne + m)) != VEGAS_OK) return rc;
+  double* maps = h->d_explore;
+  double* q = h->d_explore + nmaps * ne;
+  // 1. nmaps maps, each adapted from the uniform map by plain VEGAS+ with seed + k (the flow set aside meanwhile)
+  float* flow = h->d_flow;
+  h->d_flow = nullptr;
+  vegas_result r{};
+  for (int k = 0; k < nmaps && rc == VEGAS_OK; ++k) {
+    if ((rc = vegas_reset_map(h)) != VEGAS_OK) break;
+    if ((rc = vegas_integrate(h, integrand, params, nparams, neval, iterations, seed + (uint64_t)k, &r)) != VEGAS_OK)
+      break;
+    const Arm& A = h->arm[0];
+    if (cudaMemcpyAsync(maps + k * ne, A.d_edges[A.cur], sizeof(double) * (size_t)ne, cudaMemcpyDeviceToDevice, s) !=
+        cudaSuccess)
+      rc = VEGAS_ECUDA;
+  }
+  h->d_flow = flow;
+  if (rc != VEGAS_OK) return rc;
+  // 2. their pooled samples, the integrand there (the parameters are on the device since the last iteration) and
+  // the balance-heuristic weights; the training set with the floor's uniform rows
+  const int64_t rows = vg::flow_train_rows(m, floor);
+  const int64_t nb = std::min<int64_t>(rows, batch);
+  const size_t gs = vegas_flow_grad_scratch_bytes(d, nb);
+  if (gs == 0) return VEGAS_EINVAL;
+  if ((rc = grow(h, h->d_X, h->x_cap, m * d)) != VEGAS_OK || (rc = grow(h, h->d_logdet, h->ld_cap, m)) != VEGAS_OK ||
+      (rc = grow(h, h->d_values, h->val_cap, m)) != VEGAS_OK ||
+      (rc = grow(h, h->d_train_x, h->tx_cap, rows * d)) != VEGAS_OK ||
+      (rc = grow(h, h->d_train_w, h->tw_cap, rows + m + 4)) != VEGAS_OK ||
+      (rc = grow_bytes(h, h->d_grad_scratch, h->grad_scratch_cap, gs)) != VEGAS_OK)
+    return rc;
+  VG_CHECK(cudaMemsetAsync(h->d_logdet, 0, sizeof(float) * (size_t)m, s));
+  if ((rc = vg::explore_points(d, G, nmaps, maps, m, seed, h->d_X, q, s)) != VEGAS_OK) return rc;
+  if ((rc = vg::flow_eval(integrand, d, h->d_params, nparams, h->d_X, h->d_logdet, h->d_values, m, s)) != VEGAS_OK)
+    return rc;
+  float* wraw = h->d_train_w + rows;
+  if ((rc = vg::explore_weights(h->d_values, q, m, wraw, s)) != VEGAS_OK) return rc;
+  double* wsum = (double*)(h->d_train_w + ((rows + m + 1) & ~(int64_t)1));
+  if ((rc = vg::flow_gather(h->d_X, d, 1, m, wraw, floor, seed, 0x45585052u, wsum, h->d_train_x, h->d_train_w, s)) !=
+      VEGAS_OK)
+    return rc;
+  // 3. Adam steps on consecutive windows of the training set, cycling (the samples of all maps interleave)
+  for (int k = 0; k < steps; ++k) {
+    const int64_t off = ((int64_t)k * nb) % (rows - nb + 1);
+    if ((rc = vegas_flow_grad(d, h->d_flow, h->d_train_x + off * d, h->d_train_w + off, nb, h->d_flow_g,
+                              h->d_flow_loss, h->d_grad_scratch, h->grad_scratch_cap, s)) != VEGAS_OK ||
+        (rc = vegas_flow_adam(h->flow_np, h->d_flow, h->d_flow_g, h->d_flow_m, h->d_flow_v, ++h->flow_step, lr, 0.9f,
+                              0.999f, 1e-8f, s)) != VEGAS_OK)
+      return rc;
+  }
+  // 4. a uniform map again, for the run under the trained flow
+  return vegas_reset_map(h);
 }
 
 extern "C" int vegas_get_flow(vegas_handle h, float* params, int64_t nparams, float* last_loss) {

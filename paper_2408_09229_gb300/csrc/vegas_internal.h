@@ -145,6 +145,12 @@ constexpr int kFloorPeriod = 4;
 int64_t flow_train_rows(int64_t m, float lambda);
 int flow_gather(const float* X, int d, int64_t stride, int64_t m, const float* w, float lambda, uint64_t seed,
                 uint32_t iter, double* wsum, float* xs, float* ws, cudaStream_t s);
+// exploration (vegas_explore.cu): m samples of S maps [S][d][G+1], sample r from map r mod S, as FP32 points X [m][d]
+// and the mixture density q [m]; the weights |f| / q (0 where not finite)
+constexpr int kMaxExploreMaps = 64;
+int explore_points(int d, int G, int S, const double* maps, int64_t m, uint64_t seed, float* X, double* q,
+                   cudaStream_t s);
+int explore_weights(const float* f, const double* q, int64_t m, float* w, cudaStream_t s);
 // A single-integral fill launch: its arguments (tile, layout), the kernel it takes and its resident CTAs per SM.
 struct FillPlan {
   FillArgs a;

@@ -122,6 +122,9 @@ def _load():
         "vegas_set_flow": ([P, P, i64], i32),
         "vegas_set_flow_training": ([P, i32, i32, i32, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float], i32),
         "vegas_get_flow": ([P, P, i64, P], i32),
+        "vegas_flow_explore": ([P, i32, P, i64, i64, i32, i32, i64, i32, i32, ctypes.c_float, ctypes.c_float, u64],
+                               i32),
+        "vegas_explore_points": ([i32, i32, i32, P, i64, u64, P, P, P], i32),
         "vegas_flow_apply": ([i32, i32, P, P, P, P, i64, P], i32),
         "vegas_flow_check": ([P], i32),
         "vegas_flow_wait_selftest": ([i32, i32, P], i32),
@@ -326,6 +329,16 @@ class Vegas:
         _check(lib.vegas_set_flow_training(self._h, iterations, steps_per_iteration, samples, batch, lr, temper,
                                            floor), "vegas_set_flow_training")
 
+    def flow_explore(self, integrand, params, neval, iterations=10, maps=8, samples_per_map=32768, steps=2000,
+                     batch=4096, lr=1e-3, floor=0.03, seed=0):
+        """vegas_flow_explore: adapt `maps` VEGAS+ maps with seeds seed, seed + 1, ..., pool their samples by the
+        balance heuristic and train the flow on them; the map is uniform again afterwards"""
+        p = np.ascontiguousarray(params, dtype=np.float64) if len(params) else np.zeros(0)
+        _check(lib.vegas_flow_explore(self._h, integrand, p.ctypes.data_as(ctypes.c_void_p) if p.size else None,
+                                      p.size, int(neval), int(iterations), int(maps), int(samples_per_map),
+                                      int(steps), int(batch), float(lr), float(floor), int(seed)),
+               "vegas_flow_explore")
+
     def get_flow(self):
         n = lib.vegas_flow_param_count(self.dim)
         p = np.zeros(n, dtype=np.float32)
@@ -498,6 +511,16 @@ def combine_weighted(it_est, it_sig, skip, weighting, out, stream=None):
 # Level 4: the learned proposal's coupling flow, on torch CUDA tensors (FP32)
 # ---------------------------------------------------------------------------
 FLOW_NORMALISE, FLOW_SAMPLE = 0, 1
+
+
+def explore_points(dim, nbins, maps, samples_per_map, seed, x, q, stream=None):
+    """vegas_explore_points: maps a float64 CUDA tensor [nmaps][dim][nbins + 1]; x float32 [nmaps * samples][dim]
+    and q float64 [nmaps * samples] receive the points and the mixture density"""
+    import torch
+    if not (maps.is_cuda and maps.dtype == torch.float64 and q.dtype == torch.float64 and x.dtype == torch.float32):
+        raise TypeError("explore_points: maps and q float64, x float32, all CUDA tensors")
+    _check(lib.vegas_explore_points(int(dim), int(nbins), int(maps.shape[0]), _ptr(maps), int(samples_per_map),
+                                    int(seed), _ptr(x), _ptr(q), _stream_ptr(stream)), "vegas_explore_points")
 
 
 def flow_param_count(dim):
