@@ -216,6 +216,8 @@ FLOW_TRAIN_TEMPERED = dict(iterations=20, steps_per_iteration=500, samples=65536
 # iterations each at the run's budget, 32768 samples of each pooled by the balance heuristic, 2000 Adam steps
 FLOW_EXPLORE = dict(iterations=10, maps=16, samples_per_map=32768, steps=2000, batch=4096, lr=1e-3, floor=0.03)
 FLOW_EXPLORE_CAP = 400
+# the exploration's seeds (+ rank): the first is the arm `flow_explored`, the others `flow_explored_seed<s>`
+FLOW_EXPLORE_SEEDS = (100, 200, 300, 400)
 # iterations after training over which the judge compares the learned proposal with plain VEGAS+
 JUDGE_WINDOW = 3
 
@@ -231,10 +233,13 @@ def learned_proposal(V, W, stream, rank):
     for the flow to reach 1e-4 where plain VEGAS+ stops at a wrong value.  variance_time_ratio compares the steady state:
     (sigma_t^2 x iteration time) of plain VEGAS+ over that of the flow, above 1 where the flow reaches
     a given error sooner once trained.  The last two rows are the paper's Ridge integrand (Table 3 (8), 100
-    Gaussians along the diagonal of the 8-cube) at 1e6 and 1e7 evaluations per iteration."""
+    Gaussians along the diagonal of the 8-cube) at 1e6 and 1e7 evaluations per iteration.  On the 4-peak ridge
+    the flow is also trained by exploration alone (vegas_flow_explore: 16 maps with their own seeds, pooled by the
+    balance heuristic, then the run under the fixed flow), once per exploration seed, exploration inside the
+    timed region."""
     import torch
     out = {"training": dict(FLOW_TRAIN, adam_steps=FLOW_TRAIN["iterations"] * FLOW_TRAIN["steps_per_iteration"]),
-           "training_tempered": FLOW_TRAIN_TEMPERED, "exploration": FLOW_EXPLORE}
+           "training_tempered": FLOW_TRAIN_TEMPERED, "exploration": dict(FLOW_EXPLORE, seeds=FLOW_EXPLORE_SEEDS)}
     tube = W.paper_ridge(8, 100)
     cases = [("d12_4peaks_s0.03", 12, W.ridge(12, 4, 0.03), 1.0, 10_000_000, 40, 40),
              ("d12_3peaks_s0.1", 12, W.ridge(12, 3, 0.1), 1.0, 1_000_000, 1200, 1200),
@@ -245,31 +250,35 @@ def learned_proposal(V, W, stream, rank):
              ("d8_paper_ridge_N100_1e7", 8, tube, W.exact(W.GAUSS_SUM, 8, tube), 10_000_000, 300, 300)]
     for name, d, params, exact, neval, cap_plain, cap_flow in cases:
         row = {}
-        forms = ("plain", "flow", "flow_judged") + (("flow_tempered", "flow_explored") if name.startswith("d12_4peaks")
-                                                    else ())
+        forms = ("plain", "flow", "flow_judged") + (
+            ("flow_tempered",) + tuple("flow_explored" + ("" if i == 0 else f"_seed{sd}")
+                                       for i, sd in enumerate(FLOW_EXPLORE_SEEDS))
+            if name.startswith("d12_4peaks") else ())
         for form in forms:
             cap = cap_plain if form == "plain" else cap_flow
             train = FLOW_TRAIN_TEMPERED if form == "flow_tempered" else FLOW_TRAIN
             if form == "flow_tempered":
                 cap = train["iterations"] + 30
-            if form == "flow_explored":
+            explored = form.startswith("flow_explored")
+            if explored:
                 cap = FLOW_EXPLORE_CAP
+                ex_seed = FLOW_EXPLORE_SEEDS[0] if form == "flow_explored" else int(form.rsplit("seed", 1)[1])
             v = V.Vegas(d, NBINS, 0, ALPHA, BETA, precision=V.FP32, rtol=1e-4, stream=stream)
             if form != "plain":
                 v.set_flow(W.flow_params(d, seed=0))
-            if form not in ("plain", "flow_explored"):
+            if form != "plain" and not explored:
                 v.set_flow_training(**train)
                 v.set_skip(train["iterations"])
                 if form == "flow_judged":
                     v.set_flow_judge(JUDGE_WINDOW)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            if form == "flow_explored":  # exploration and training inside the timed region
-                v.flow_explore(W.GAUSS_SUM, params, neval, seed=SEED + 100 + rank, **FLOW_EXPLORE)
+            if explored:  # exploration and training inside the timed region
+                v.flow_explore(W.GAUSS_SUM, params, neval, seed=ex_seed + rank, **FLOW_EXPLORE)
             r = v.integrate(W.GAUSS_SUM, params, neval, cap, seed=SEED + rank)
             dt = time.perf_counter() - t0
             it_ms, _ = v.timings()
-            k = train["iterations"] if form not in ("plain", "flow_explored") else min(10, r["nitn_run"] - 1)
+            k = train["iterations"] if form != "plain" and not explored else min(10, r["nitn_run"] - 1)
             late = r["it_sig"][k:] / np.abs(r["it_est"][k:])
             pull = (r["estimate"] - exact) / r["sigma"]
             row[form] = {"seconds": dt, "iterations": r["nitn_run"], "estimate": r["estimate"], "sigma": r["sigma"],
@@ -295,6 +304,11 @@ def learned_proposal(V, W, stream, rank):
         t_flow = [row[k]["time_to_rtol_correct"] for k in row if isinstance(row[k], dict) and k != "plain" and
                   "time_to_rtol_correct" in row[k] and row[k]["time_to_rtol_correct"] is not None]
         row["objective_met"] = bool(t_flow and (t_plain is None or min(t_flow) < t_plain))
+        ex = [row[k] for k in row if k.startswith("flow_explored")]
+        if ex:  # how many of the exploration seeds reach a correct 1e-4 sooner than plain VEGAS+
+            row["objective_met_explored_seeds"] = "%d of %d" % (
+                sum(1 for e in ex if e["time_to_rtol_correct"] is not None and
+                    (t_plain is None or e["time_to_rtol_correct"] < t_plain)), len(ex))
         out[name] = row
     return out
 
