@@ -213,8 +213,10 @@ FLOW_TRAIN = dict(iterations=10, steps_per_iteration=200, samples=65536, batch=4
 FLOW_TRAIN_TEMPERED = dict(iterations=20, steps_per_iteration=500, samples=65536, batch=4096, lr=2e-3, temper=0.03,
                            floor=0.03)
 # exploration before the run (vegas_flow_explore): 16 VEGAS+ maps adapted from uniform with their own seeds, 10
-# iterations each at the run's budget, 32768 samples of each pooled by the balance heuristic, 2000 Adam steps
-FLOW_EXPLORE = dict(iterations=10, maps=16, samples_per_map=32768, steps=2000, batch=4096, lr=1e-3, floor=0.03)
+# iterations each at the run's budget, 32768 samples of each pooled by the balance heuristic, 2000 Adam steps; then
+# two rounds of 2000 steps on as many samples of the flow itself
+FLOW_EXPLORE = dict(iterations=10, maps=16, samples_per_map=32768, steps=2000, batch=4096, lr=1e-3, floor=0.03,
+                    rounds=3)
 FLOW_EXPLORE_CAP = 400
 # the exploration's seeds (+ rank): the first is the arm `flow_explored`, the others `flow_explored_seed<s>`
 FLOW_EXPLORE_SEEDS = (100, 200, 300, 400)
@@ -235,8 +237,8 @@ def learned_proposal(V, W, stream, rank):
     a given error sooner once trained.  The last two rows are the paper's Ridge integrand (Table 3 (8), 100
     Gaussians along the diagonal of the 8-cube) at 1e6 and 1e7 evaluations per iteration.  On the 4-peak ridge
     the flow is also trained by exploration alone (vegas_flow_explore: 16 maps with their own seeds, pooled by the
-    balance heuristic, then the run under the fixed flow), once per exploration seed, exploration inside the
-    timed region."""
+    balance heuristic, two more rounds on the flow's own samples, then the run under the fixed flow), once per
+    exploration seed, exploration inside the timed region."""
     import torch
     out = {"training": dict(FLOW_TRAIN, adam_steps=FLOW_TRAIN["iterations"] * FLOW_TRAIN["steps_per_iteration"]),
            "training_tempered": FLOW_TRAIN_TEMPERED, "exploration": dict(FLOW_EXPLORE, seeds=FLOW_EXPLORE_SEEDS)}

@@ -584,12 +584,18 @@ VEGAS_API int vegas_get_flow(vegas_handle h, float *params, int64_t nparams, flo
  * r mod nmaps; its weight is |f(x)| / q(x) with q = (1/nmaps) sum_k q_k the
  * mixture of the maps' densities q_k = prod_a 1 / (N_g dx_a) (the balance
  * heuristic, Veach and Guibas 1995), so every peak that some map reaches
- * carries its own mass however many maps reach it.  The handle's map is the
+ * carries its own mass however many maps reach it.  Each of rounds - 1
+ * further rounds (rounds 1..16) replaces the pool by nmaps * samples_per_map
+ * samples of the flow itself, x = F(u) with u uniform, weighted
+ * |f(x)| |det dF/du|, and runs `steps` more Adam steps from fresh moments:
+ * the flow then covers every peak, so its own samples weigh them more evenly
+ * than the maps' did.  The handle's map is the
  * uniform map again on return, its flow trained, its in-loop training
  * schedule unchanged.  Requires a flow (vegas_set_flow) and the FP32 form;
  * integrand and params as for vegas_integrate (not MAP_DENSITY).  Returns
  * after the device work is done.  Errors: EINVAL (no flow, FP64, arguments),
- * ENOMEM, ECUDA, and those of vegas_integrate.
+ * ENOMEM, ECUDA, ETIMEOUT (a bounded wait of the flow's kernels), and those of
+ * vegas_integrate.
  *
  * vegas_explore_points is its sampling step: nmaps maps d_maps (device, FP64,
  * [nmaps][dim][nbins + 1], each axis's edges increasing from 0 to 1), and
@@ -603,7 +609,8 @@ VEGAS_API int vegas_get_flow(vegas_handle h, float *params, int64_t nparams, flo
  * buffers; asynchronous on stream.  Errors: EINVAL, ECUDA. */
 VEGAS_API int vegas_flow_explore(vegas_handle h, int32_t integrand, const double *params, int64_t nparams,
                                  int64_t neval, int32_t iterations, int32_t nmaps, int64_t samples_per_map,
-                                 int32_t steps, int32_t batch, float lr, float floor, uint64_t seed);
+                                 int32_t steps, int32_t batch, float lr, float floor, int32_t rounds,
+                                 uint64_t seed);
 VEGAS_API int vegas_explore_points(int32_t dim, int32_t nbins, int32_t nmaps, const double *d_maps,
                                    int64_t samples_per_map, uint64_t seed, float *d_x, double *d_q, void *stream);
 /* Plain VEGAS+ as the fallback and the judge of the learned proposal (not in

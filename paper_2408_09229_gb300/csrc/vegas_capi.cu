@@ -928,8 +928,9 @@ extern "C" int vegas_set_flow_training(vegas_handle h, int32_t iterations, int32
 
 extern "C" int vegas_flow_explore(vegas_handle h, int32_t integrand, const double* params, int64_t nparams,
                                   int64_t neval, int32_t iterations, int32_t nmaps, int64_t samples_per_map,
-                                  int32_t steps, int32_t batch, float lr, float floor, uint64_t seed) {
-  if (!h || !h->d_flow || h->precision != VEGAS_FP32 || iterations < 1 || nmaps < 1 ||
+                                  int32_t steps, int32_t batch, float lr, float floor, int32_t rounds,
+                                  uint64_t seed) {
+  if (!h || !h->d_flow || h->precision != VEGAS_FP32 || iterations < 1 || nmaps < 1 || rounds < 1 || rounds > 16 ||
       nmaps > vg::kMaxExploreMaps || samples_per_map < 1 || samples_per_map > vg::kMaxEval / nmaps || steps < 0 ||
       batch < 1 || !(lr > 0.0f) || !(floor >= 0.0f) || integrand == VEGAS_MAP_DENSITY)
     return VEGAS_EINVAL;
@@ -980,17 +981,39 @@ extern "C" int vegas_flow_explore(vegas_handle h, int32_t integrand, const doubl
   if ((rc = vg::flow_gather(h->d_X, d, 1, m, wraw, floor, seed, 0x45585052u, wsum, h->d_train_x, h->d_train_w, s)) !=
       VEGAS_OK)
     return rc;
-  // 3. Adam steps on consecutive windows of the training set, cycling (the samples of all maps interleave)
-  for (int k = 0; k < steps; ++k) {
-    const int64_t off = ((int64_t)k * nb) % (rows - nb + 1);
-    if ((rc = vegas_flow_grad(d, h->d_flow, h->d_train_x + off * d, h->d_train_w + off, nb, h->d_flow_g,
-                              h->d_flow_loss, h->d_grad_scratch, h->grad_scratch_cap, s)) != VEGAS_OK ||
-        (rc = vegas_flow_adam(h->flow_np, h->d_flow, h->d_flow_g, h->d_flow_m, h->d_flow_v, ++h->flow_step, lr, 0.9f,
-                              0.999f, 1e-8f, s)) != VEGAS_OK)
-      return rc;
+  for (int round = 0; round < rounds; ++round) {
+    if (round > 0) {
+      // a later round's pool: m samples of the flow itself, x = F(u) with u uniform (the uniform map's points, whose
+      // density is 1), weighted |f(x)| |det dF/du|; fresh Adam moments
+      if ((rc = vegas_reset_map(h)) != VEGAS_OK) return rc;
+      const Arm& A = h->arm[0];
+      if ((rc = vg::explore_points(d, G, 1, A.d_edges[A.cur], m, seed + 0x9E3779B97F4A7C15ull * (uint64_t)round,
+                                   h->d_X, q, s)) != VEGAS_OK ||
+          (rc = vg::flow_apply(d, VEGAS_FLOW_SAMPLE, h->d_flow, h->d_X, h->d_X, h->d_logdet, m, s)) != VEGAS_OK ||
+          (rc = vg::flow_eval(integrand, d, h->d_params, nparams, h->d_X, h->d_logdet, h->d_values, m, s)) !=
+              VEGAS_OK ||
+          (rc = vg::explore_weights(h->d_values, q, m, wraw, s)) != VEGAS_OK ||
+          (rc = vg::flow_gather(h->d_X, d, 1, m, wraw, floor, seed, 0x45585052u + (uint32_t)round, wsum,
+                                h->d_train_x, h->d_train_w, s)) != VEGAS_OK)
+        return rc;
+      VG_CHECK(cudaMemsetAsync(h->d_flow_m, 0, sizeof(float) * (size_t)h->flow_np, s));
+      VG_CHECK(cudaMemsetAsync(h->d_flow_v, 0, sizeof(float) * (size_t)h->flow_np, s));
+      h->flow_step = 0;
+    }
+    // 3. Adam steps on consecutive windows of the training set, cycling (the samples of all maps interleave)
+    for (int k = 0; k < steps; ++k) {
+      const int64_t off = ((int64_t)k * nb) % (rows - nb + 1);
+      if ((rc = vegas_flow_grad(d, h->d_flow, h->d_train_x + off * d, h->d_train_w + off, nb, h->d_flow_g,
+                                h->d_flow_loss, h->d_grad_scratch, h->grad_scratch_cap, s)) != VEGAS_OK ||
+          (rc = vegas_flow_adam(h->flow_np, h->d_flow, h->d_flow_g, h->d_flow_m, h->d_flow_v, ++h->flow_step, lr,
+                                0.9f, 0.999f, 1e-8f, s)) != VEGAS_OK)
+        return rc;
+    }
   }
-  // 4. a uniform map again, for the run under the trained flow
-  return vegas_reset_map(h);
+  // 4. a uniform map again, for the run under the trained flow; the bounded waits of the flow's kernels
+  if ((rc = vegas_reset_map(h)) != VEGAS_OK) return rc;
+  if ((rc = vg::flow_tc_status(true)) != VEGAS_OK) return rc;
+  return vg::flow_grad_tc_status(true);
 }
 
 extern "C" int vegas_get_flow(vegas_handle h, float* params, int64_t nparams, float* last_loss) {

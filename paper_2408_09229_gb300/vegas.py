@@ -122,8 +122,8 @@ def _load():
         "vegas_set_flow": ([P, P, i64], i32),
         "vegas_set_flow_training": ([P, i32, i32, i32, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float], i32),
         "vegas_get_flow": ([P, P, i64, P], i32),
-        "vegas_flow_explore": ([P, i32, P, i64, i64, i32, i32, i64, i32, i32, ctypes.c_float, ctypes.c_float, u64],
-                               i32),
+        "vegas_flow_explore": ([P, i32, P, i64, i64, i32, i32, i64, i32, i32, ctypes.c_float, ctypes.c_float, i32,
+                                u64], i32),
         "vegas_explore_points": ([i32, i32, i32, P, i64, u64, P, P, P], i32),
         "vegas_flow_apply": ([i32, i32, P, P, P, P, i64, P], i32),
         "vegas_flow_check": ([P], i32),
@@ -330,13 +330,14 @@ class Vegas:
                                            floor), "vegas_set_flow_training")
 
     def flow_explore(self, integrand, params, neval, iterations=10, maps=8, samples_per_map=32768, steps=2000,
-                     batch=4096, lr=1e-3, floor=0.03, seed=0):
+                     batch=4096, lr=1e-3, floor=0.03, rounds=1, seed=0):
         """vegas_flow_explore: adapt `maps` VEGAS+ maps with seeds seed, seed + 1, ..., pool their samples by the
-        balance heuristic and train the flow on them; the map is uniform again afterwards"""
+        balance heuristic and train the flow on them, then rounds - 1 times on samples of the flow itself; the map
+        is uniform again afterwards"""
         p = np.ascontiguousarray(params, dtype=np.float64) if len(params) else np.zeros(0)
         _check(lib.vegas_flow_explore(self._h, integrand, p.ctypes.data_as(ctypes.c_void_p) if p.size else None,
                                       p.size, int(neval), int(iterations), int(maps), int(samples_per_map),
-                                      int(steps), int(batch), float(lr), float(floor), int(seed)),
+                                      int(steps), int(batch), float(lr), float(floor), int(rounds), int(seed)),
                "vegas_flow_explore")
 
     def get_flow(self):

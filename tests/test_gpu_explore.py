@@ -67,6 +67,12 @@ def test_flow_explore_needs_a_flow_and_the_fp32_form(V):
     with pytest.raises(V.VegasError) as e:
         v.flow_explore(W.GAUSS_SUM, prm, 100_000, iterations=2, maps=2, samples_per_map=1000, steps=10)
     assert e.value.status == V.EINVAL
+    v.set_flow(W.flow_params(4, seed=0))
+    for bad in (dict(rounds=0), dict(maps=0), dict(maps=65), dict(steps=-1)):
+        with pytest.raises(V.VegasError) as e:
+            v.flow_explore(W.GAUSS_SUM, prm, 100_000, **dict(dict(iterations=2, maps=2, samples_per_map=1000,
+                                                                  steps=10), **bad))
+        assert e.value.status == V.EINVAL
     v.close()
 
 
@@ -74,15 +80,15 @@ def test_flow_explore_needs_a_flow_and_the_fp32_form(V):
 def test_flow_explore_finds_all_four_peaks(V, seed):
     """d = 12, 4 Gaussians of width 0.03 on the diagonal, 1e7 evaluations an iteration: one adapted map finds one
     peak (plain VEGAS+ ends near 1/4); sixteen maps pooled by the balance heuristic train a flow under which
-    VEGAS+ finds all four: the estimate within 3 sigma + 2 % of 1.  How much variance the flow then removes
-    varies with the exploration's samples (per-iteration sigma 5e-4 to 2e-2 of I over four seeds)"""
+    VEGAS+ finds all four: the estimate within 3 sigma + 2 % of 1 (two more rounds on the flow's own samples)"""
     d, neval = 12, 10_000_000
     prm = W.ridge(d, 4, 0.03)
     v = V.Vegas(d, 50, 0, 0.5, 0.75, precision=V.FP32)
     r = v.integrate(W.GAUSS_SUM, prm, neval, 20, seed=3)
     assert r["estimate"] < 0.5  # a single map: at most two of the four peaks
     v.set_flow(W.flow_params(d, seed=0))
-    v.flow_explore(W.GAUSS_SUM, prm, neval, iterations=10, maps=16, samples_per_map=32768, steps=2000, seed=seed)
+    v.flow_explore(W.GAUSS_SUM, prm, neval, iterations=10, maps=16, samples_per_map=32768, steps=2000, rounds=3,
+                   seed=seed)
     r = v.integrate(W.GAUSS_SUM, prm, neval, 40, seed=7)
     assert abs(r["estimate"] - 1.0) <= 3 * r["sigma"] + 0.02, (r["estimate"], r["sigma"])
     v.close()
