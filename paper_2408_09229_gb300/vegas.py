@@ -330,7 +330,7 @@ class Vegas:
                                            floor), "vegas_set_flow_training")
 
     def flow_explore(self, integrand, params, neval, iterations=10, maps=8, samples_per_map=32768, steps=2000,
-                     batch=4096, lr=1e-3, floor=0.03, rounds=1, seed=0):
+                     batch=4096, lr=1e-3, floor=0.03, rounds=3, seed=0):
         """vegas_flow_explore: adapt `maps` VEGAS+ maps with seeds seed, seed + 1, ..., pool their samples by the
         balance heuristic and train the flow on them, then rounds - 1 times on samples of the flow itself; the map
         is uniform again afterwards"""
